@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit grey FLD radiation step on GB300.
+
+Default workload: a 512^3 zero-gradient grid, log-normal density
+(sigma_ln = 1.5, mean n_H = 1e-3 cm^-3, clamped to [1e-3, 1e3] x mean, i.e.
+opacity contrast up to 1e6), fully neutral, 65536 sources of 5e48 photons/s
+at the densest peaks; one step = assembly + MG-preconditioned CG to
+||r||/||b|| <= 1e-8 + finalise, in mixed precision (FP32 V-cycles and inner
+CG inside FP64 iterative refinement).  The plain FP64 GPU multigrid runs on
+the same input beside it.  Inputs are synthetic (seeded generators), every
+field is 1 GiB (larger than L2), and successive steps advance E in time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank steps its own
+replica of the workload (no collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-solves/s to 1e-8 rel. residual, mixed vs FP64 MG on 1 GB300; p50/p99 latency"
+UNIT = "cell-solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=512, help="grid cells per axis")
+    ap.add_argument("--sources", type=int, default=65536)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-n", type=int, default=256, help="grid of the CPU-baseline sample")
+    ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference-arm sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(n, sources, device):
+    from paper_1306_0645_gb300 import synth
+    sources = max(1, min(sources, (sources * n ** 3) // 512 ** 3 if n != 512 else sources))
+    return synth.config4(n=n, sources=sources, device=device)
+
+
+def workload_desc(n, sources):
+    return (f"{n}^3 zero-gradient, log-normal density sigma_ln 1.5 mean n_H 1e-3 clamped to "
+            f"[1e-3,1e3]x mean (opacity contrast 1e6), neutral, {sources} sources of 5e48 /s at the "
+            f"densest peaks, dt 1e5 yr, box 6.6 kpc, paper limiter; MG-PCG to 1e-8")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def time_steps(fld, torch, ctx, E, nHI, eta, steps):
+    """K steps on the context's stream; returns (total_ms, per-step ms, infos)."""
+    s = ctx.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    infos = []
+    torch.cuda.synchronize()
+    ev[0].record(s)
+    for k in range(steps):
+        infos.append(fld.fld_step(ctx, E, nHI, eta))
+        ev[k + 1].record(s)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return ev[0].elapsed_time(ev[steps]), per, infos
+
+
+def cpu_baseline(n, sources, steps=1):
+    import oracle
+    from paper_1306_0645_gb300 import synth
+    case = synth.config4(n=n, sources=sources)
+    oracle.build()
+    E = case.E.copy()
+    t0 = time.perf_counter()
+    iters = []
+    for _ in range(steps):
+        E, info = oracle.step(case.grid, case.params, {}, E, case.nHI, case.eta)
+        iters.append(info["iters"])
+    dt = time.perf_counter() - t0
+    return {"value": case.grid.cells * steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle step(s) (MG-PCG to 1e-8, plain C + OpenMP) on the same "
+                      f"recipe at {n}^3 with {sources} sources ({dt:.1f} s, iters {iters})"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1306_0645_gb300 import synth
+    oracle.build()
+    n = args.ref_n
+    src = max(1, args.sources * n ** 3 // 512 ** 3)
+    case = synth.config4(n=n, sources=src)
+    E = case.E.copy()
+    for _ in range(args.warmup):
+        E, _ = oracle.step(case.grid, case.params, {}, E, case.nHI, case.eta)
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        E, info = oracle.step(case.grid, case.params, {}, E, case.nHI, case.eta)
+        per.append((time.perf_counter() - t1) * 1e3)
+    total = time.perf_counter() - t0
+    value = case.grid.cells * args.steps / total
+    cores = oracle.num_threads()
+    sample = (f"FP64 oracle (plain C + OpenMP, {cores} threads) on the benchmark recipe at {n}^3 with "
+              f"{src} sources, one oracle step per step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+           "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_desc(n, src), "n": n, "sources": src},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1306_0645_gb300 import fld, synth
+
+    n = args.n
+    sources = args.sources if n == 512 else max(1, args.sources * n ** 3 // 512 ** 3)
+    case = synth.config4(n=n, sources=sources, device="cuda")
+    cells = case.grid.cells
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    E0, nHI, eta = dev(case.E), dev(case.nHI), dev(case.eta)
+    stream = torch.cuda.current_stream()
+
+    # ---- mixed precision (the measured path)
+    pm = case.params
+    pm.precision = synth.PREC_MIXED
+    ctx = fld.fld_create(case.grid, pm, stream)
+    E = E0.clone()
+    for _ in range(args.warmup):
+        fld.fld_step(ctx, E, nHI, eta)
+    # one untimed step with every kernel class timed picks the dominant kernel
+    fld.fld_profile(ctx, (1 << 62) - 1)
+    Ecal = E.clone()
+    fld.fld_step(ctx, Ecal, nHI, eta)
+    stats = fld.fld_profile_read(ctx)
+    dom = max(stats, key=lambda k: k["ms"])
+    del Ecal
+    fld.fld_profile(ctx, 1 << dom["cls"])
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    clocks.start()
+    total_ms, per, infos = time_steps(fld, torch, ctx, E, nHI, eta, args.steps)
+    clk = clocks.stop()
+    stats = fld.fld_profile_read(ctx)
+    launches = int(sum(k["launches"] for k in stats))
+    d = next(k for k in stats if k["cls"] == dom["cls"])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = cells * args.steps * world / (total_ms * 1e-3)
+
+    peak, peak_kind = measured_hbm_peak()
+    avg_ms = d["ms"] / max(d["timed"], 1)
+    bytes_per = d["timed_bytes"] / max(d["timed"], 1)
+    achieved = bytes_per / (avg_ms * 1e-3) / 1e9
+    roofline = {"kernel": d["name"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "launches_timed": d["timed"], "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per,
+                "share_of_step": d["ms"] / total_ms}
+    # whole-step algorithmic bytes over step time (all kernels)
+    step_bytes = sum(k["bytes"] for k in stats) / args.steps
+    step_frac = step_bytes / (total_ms / args.steps * 1e-3) / (peak * 1e9)
+
+    # ---- plain FP64 multigrid on the same input
+    fp64 = None
+    if args.fp64_steps > 0:
+        p64 = synth.config4(n=2).params
+        p64.precision = synth.PREC_FP64
+        ctx64 = fld.fld_create(case.grid, p64, stream)
+        E64 = E0.clone()
+        for _ in range(min(args.warmup, 1)):
+            fld.fld_step(ctx64, E64, nHI, eta)
+        ms64, per64, inf64 = time_steps(fld, torch, ctx64, E64, nHI, eta, args.fp64_steps)
+        fp64 = {"value": cells * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "iters": [i["iters"] for i in inf64],
+                "rel_res": [i["rel_res"] for i in inf64]}
+        ctx64.close()
+        del E64
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        Eh = torch.empty(cells, dtype=torch.float64, pin_memory=True)
+        Eh.copy_(E0.cpu())
+        nh = torch.empty(cells, dtype=torch.float64, pin_memory=True)
+        nh.copy_(nHI.cpu())
+        eh = torch.empty(cells, dtype=torch.float64, pin_memory=True)
+        eh.copy_(eta.cpu())
+        Ehn, nhn, ehn = Eh.numpy(), nh.numpy(), eh.numpy()
+        fld.fld_step_host(ctx, Ehn, nhn, ehn)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fld.fld_step_host(ctx, Ehn, nhn, ehn)
+        el = time.perf_counter() - t0
+        e2e = {"value": cells * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": 3 * cells * 8,
+               "d2h_bytes_per_step": cells * 8}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and args.cpu_n > 0:
+        src = max(1, args.sources * args.cpu_n ** 3 // 512 ** 3)
+        cpu = cpu_baseline(args.cpu_n, src)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 outer (mixed)", "data": "synthetic (seeded generators, no dataset)",
+            "config": {"workload": workload_desc(n, sources), "n": n, "sources": sources,
+                       "precision": "mixed", "l2": "inputs larger than L2 (each field 1 GiB at 512^3)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "iters": [i["iters"] for i in infos], "outer_iters": [i["outer_iters"] for i in infos],
+            "rel_res": [i["rel_res"] for i in infos],
+            "fp64_mg": fp64,
+            "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
+            "roofline": roofline, "step_roofline_frac": step_frac,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * fld.h -- C ABI of libfld.so: one implicit grey flux-limited-diffusion (FLD)
+ * radiation step on one GB300 GPU.
+ *
+ * The operation (Norman et al., arXiv:1306.0645):
+ *   The radiation component of the operator split (Sec. 3.2, Eq. "fld"),
+ *       dE/dt = div(D grad E) - (adot/a) E - c kappa E + eta,
+ *   is advanced by backward Euler with the flux limiter D evaluated at E^n,
+ *   which makes the step one linear system, posed for the correction
+ *   dE = E^{n+1} - E^n (Sec. 3.2).  D is the limiter of Sec. 2,
+ *       D = min{ c (9 kappa_f^2 + R^2)^(-1/2), D_max },
+ *       R = max{ |E_2 - E_1| / (h E_f), R_min },
+ *   with face energy E_f the arithmetic mean and face opacity kappa_f the
+ *   harmonic mean of the two cells, D_max = 0.006 c L_unit and
+ *   R_min = 1e-20 / L_unit; or (FLD_LIMITER_LP) the Levermore-Pomraning
+ *   form the paper cites (Sec. 1).  The opacity is kappa = n_HI sigma
+ *   (Eq. "opacity", one species, monochromatic).  The system is solved by
+ *   conjugate gradients preconditioned with a geometric multigrid V-cycle
+ *   using red/black Gauss-Seidel, 1 pre- and 1 post-sweep, at most 50
+ *   iterations to a relative residual of 1e-8 (Table 1).
+ *
+ * Discretisation (the library's reading where the paper is silent):
+ *   cell-centred uniform grid, CGS units; face weight w_f = dt D_f / h_d^2;
+ *   A dE = b with (A u)_i = m_i u_i + sum_f w_f (u_i - u_nbr),
+ *   m_i = 1 + dt (c kappa_i + adot/a),
+ *   b_i = dt eta_i - dt (c kappa_i + adot/a) E_i + sum_f w_f (E_nbr - E_i).
+ *   Zero-gradient boundaries carry no flux; periodic axes wrap.
+ *   Multigrid: full 2x coarsening while all dimensions are even and the
+ *   smallest exceeds 4; trilinear prolongation P, restriction P^T/8; coarse
+ *   operators by rediscretisation; dense direct solve on the coarsest grid
+ *   (at most fld_params.coarse_cap cells, else FLD_EINVAL).
+ *
+ * Conventions for every call:
+ *   - Fields are contiguous FP64 arrays of nx*ny*nz cells, x fastest:
+ *     idx = i + nx * (j + ny * k).  Field pointers are DEVICE pointers
+ *     unless the function name ends in _host.  The caller owns them; the
+ *     library never frees or retains them past the call.
+ *   - The context owns its multigrid hierarchy and work buffers; they are
+ *     allocated once in fld_create and reused by every step.
+ *   - Work is enqueued on the stream given to fld_create.  Calls that
+ *     return an fld_info synchronise that stream before returning.
+ *   - No call throws across the ABI or traps on the device.  Every call
+ *     returns an fld_status; fld_last_error() gives a message for the
+ *     calling thread's most recent failure.
+ */
+#ifndef FLD_H
+#define FLD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLD_OK = 0,
+    FLD_EINVAL = 1,      /* invalid argument; nothing was launched */
+    FLD_ENOMEM = 2,      /* device or host allocation failed */
+    FLD_ENOCONV = 3,     /* max_iter reached with ||r||/||b|| > rtol; E unchanged */
+    FLD_ENONFINITE = 4,  /* NaN/Inf met in a reduction; E unchanged */
+    FLD_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    FLD_ECUDA = 6        /* a CUDA runtime call failed */
+} fld_status;
+
+typedef enum { FLD_LIMITER_PAPER = 0, FLD_LIMITER_LP = 1 } fld_limiter;
+typedef enum { FLD_BC_ZERO_GRADIENT = 0, FLD_BC_PERIODIC = 1 } fld_bc;
+typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 } fld_precision;
+typedef enum { FLD_SMOOTH_RBGS = 0, FLD_SMOOTH_JACOBI = 1 } fld_smoother;
+
+/* Grid: cells per axis (>= 1), cell widths in cm (> 0), boundary per axis. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int bc[3];                 /* fld_bc for x, y, z */
+} fld_grid;
+
+/* Physical and solver parameters.  fld_params_default fills the values of
+ * the paper's solver (Table 1) and limiter constants (Sec. 2). */
+typedef struct {
+    double dt;                 /* time step, s (> 0) */
+    double c;                  /* speed of light, cm/s */
+    double L_unit;             /* length unit of D_max and R_min, cm */
+    double dmax_coef;          /* D_max = dmax_coef * c * L_unit (0.006) */
+    double rmin_coef;          /* R_min = rmin_coef / L_unit (1e-20) */
+    double sigma;              /* grey cross-section, cm^2 (>= 0) */
+    double adot_over_a;        /* cosmological sink adot/a, 1/s (>= 0) */
+    double hnu;                /* erg per photon, for the photon balance */
+    int limiter;               /* fld_limiter */
+    int precision;             /* fld_precision */
+    int smoother;              /* fld_smoother */
+    double jacobi_omega;       /* weight of the Jacobi smoother (0.8) */
+    double rtol;               /* ||b - A dE||_2 / ||b||_2 target (1e-8) */
+    int max_iter;              /* CG iterations (50); in mixed mode the
+                                  total of inner iterations */
+    int pre, post;             /* smoothing sweeps per level (1, 1) */
+    double inner_rtol;         /* mixed mode: inner FP32 solve target (1e-4) */
+    int coarse_cap;            /* largest coarsest grid, cells (1024) */
+} fld_params;
+
+/* Result of one solve or step (host memory, filled on return). */
+typedef struct {
+    int status;                /* fld_status of the call */
+    int iters;                 /* CG iterations (mixed: inner, summed) */
+    int outer_iters;           /* mixed mode: refinement steps; else 0 */
+    double rel_res;            /* ||b - A dE||_2 / ||b||_2 of the result,
+                                  recomputed in FP64 */
+    double balance_abs;        /* photons: sum_i V [dE_i - dt (eta_i -
+                                  (c kappa_i + adot/a) E^{n+1}_i)] / h nu */
+    double balance_rel;        /* |balance_abs| / max(emitted, absorbed) */
+    double emitted;            /* photons emitted in the step, V dt sum eta / h nu */
+    double absorbed;           /* photons absorbed in the step */
+    double ms;                 /* device time of the call, ms */
+} fld_info;
+
+typedef struct fld_ctx fld_ctx;
+
+/* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
+ * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
+ * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024.
+ * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
+fld_status fld_params_default(fld_params* p);
+
+/* Device bytes a context for (g, p) allocates; 0 if (g, p) is invalid.
+ * Used for admission against an HBM budget. */
+size_t fld_footprint_bytes(const fld_grid* g, const fld_params* p);
+
+/* Create a context: validates g and p, builds the level shapes and
+ * allocates every device buffer.  cuda_stream is a cudaStream_t (NULL for
+ * the legacy default stream) on which all later work of the context is
+ * enqueued.  *ctx is NULL on failure. */
+fld_status fld_create(fld_ctx** ctx, const fld_grid* g, const fld_params* p,
+                      void* cuda_stream);
+
+/* Per-cell opacity, per-face limiter and coefficients, and the right-hand
+ * side b of the correction system (Sec. 2 limiter; Sec. 3.2 system), then
+ * the coarse operators and the coarsest-grid factorisation.  E, n_HI, eta:
+ * device, FP64, finite and >= 0 (checked on the device; FLD_EINVAL if not).
+ * Asynchronous except for that check. */
+fld_status fld_assemble(fld_ctx* ctx, const double* E, const double* n_HI,
+                        const double* eta);
+
+/* Solve A dE = b for the last assembled system by MG-preconditioned CG
+ * (Table 1), in FP64 or mixed precision per fld_params.precision.  dE:
+ * device, FP64, written on success (and on FLD_ENOCONV, with the last
+ * iterate).  info (may be NULL) receives iteration counts and the true
+ * relative residual. */
+fld_status fld_solve(fld_ctx* ctx, double* dE, fld_info* info);
+
+/* One full step: assemble, solve, and E <- E + dE in place (device,
+ * FP64).  On any failure E is left unchanged.  info (may be NULL) also
+ * receives the photon balance of the step. */
+fld_status fld_step(fld_ctx* ctx, double* E, const double* n_HI,
+                    const double* eta, fld_info* info);
+
+/* fld_step with HOST arrays: copies E, n_HI, eta to the context's device
+ * staging buffers, steps, and copies E back.  Host arrays may be pageable
+ * or pinned; pinned memory gives full copy bandwidth. */
+fld_status fld_step_host(fld_ctx* ctx, double* E, const double* n_HI,
+                         const double* eta, fld_info* info);
+
+/* Step n independent contexts whose work may overlap on the device.  Each
+ * context runs on its own stream; infos[i] receives context i's result.
+ * Returns FLD_OK if every step succeeded, else the first failing status
+ * (the other steps still complete). */
+fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E,
+                            const double** n_HI, const double** eta,
+                            fld_info* infos);
+
+/* Apply the assembled operator: y = A x (device, FP64).  For tests. */
+fld_status fld_apply(fld_ctx* ctx, const double* x, double* y);
+
+/* One multigrid V-cycle with zero initial guess, z = B r, on the
+ * assembled FP64 hierarchy (device, FP64).  For tests. */
+fld_status fld_vcycle(fld_ctx* ctx, const double* r, double* z);
+
+/* Copy the assembled fine-level operator and right-hand side to caller
+ * device buffers (any pointer may be NULL).  For tests. */
+fld_status fld_get_system(fld_ctx* ctx, double* m, double* wx, double* wy,
+                          double* wz, double* b);
+
+/* Hydrogen-only photoionisation/recombination update of the neutral
+ * density between steps, one linearly implicit backward-Euler iteration
+ * per cell in the manner of the loosely coupled chemistry solver
+ * (Sec. 3.2): Gamma = c sigma E / h nu,
+ * x' = (x + dt alpha_B n_H (1 - x)^2) / (1 + dt Gamma), x = n_HI / n_H,
+ * clamped to [1e-12, 1]; n_HI_out = x' n_H.  All arrays device FP64 of
+ * n cells; n_HI_out may alias n_HI.  Enqueued on cuda_stream. */
+fld_status fld_opacity_update(size_t n, const double* E, const double* n_H,
+                              const double* n_HI, double* n_HI_out,
+                              double dt, double c, double sigma, double hnu,
+                              double alpha_B, void* cuda_stream);
+
+/* Number of levels and their shapes (dims[3*l .. 3*l+2]) for grid g. */
+int fld_levels(const fld_grid* g, int* dims, int max_levels);
+
+/* Per-kernel-class launch statistics of one context.  bytes is the
+ * algorithmic traffic of the launches (every array a kernel streams counted
+ * once per cell of its level, in the array's word size); ms and timed_bytes
+ * cover only the launches timed with CUDA events (see fld_profile). */
+typedef struct {
+    const char* name;          /* kernel class, static storage */
+    long long launches;        /* launches since the last fld_profile */
+    long long timed;           /* launches bracketed by events */
+    double ms;                 /* summed event time of the timed launches */
+    double bytes;              /* algorithmic bytes of all launches */
+    double timed_bytes;        /* algorithmic bytes of the timed launches */
+} fld_kernel_stat;
+
+/* Reset the context's launch statistics and select the kernel classes
+ * (bit i = class i of fld_profile_read's order) whose launches are
+ * bracketed by CUDA events on the context's stream; 0 times nothing.
+ * Synchronises the context's stream. */
+fld_status fld_profile(fld_ctx* ctx, unsigned long long class_mask);
+
+/* Copy up to max per-class statistics to out; returns the number of
+ * classes (call with max = 0 to size out). */
+int fld_profile_read(fld_ctx* ctx, fld_kernel_stat* out, int max);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* fld_last_error(void);
+
+/* Release every buffer of the context (NULL is ignored). */
+void fld_destroy(fld_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLD_H */

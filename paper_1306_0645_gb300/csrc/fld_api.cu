@@ -1,0 +1,808 @@
+// fld_api.cu -- the C ABI of libfld.so (declared in include/fld.h): context
+// and hierarchy management, the MG-preconditioned CG driver (Table 1), the
+// mixed-precision iterative-refinement driver, and the step wrapper.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fld.h"
+#include "kernels.h"
+
+using namespace fld;
+
+namespace {
+
+constexpr int MAX_LEVELS = 32;
+constexpr int COARSE_CAP_MAX = 4096;
+
+thread_local std::string g_err;
+
+fld_status set_err(fld_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err(FLD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+struct Level {
+    Dims d;
+    Op<double> A64;
+    Op<float> A32;
+    void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
+};
+
+// Kernel classes for launch counting and optional CUDA-event timing.
+enum KClass {
+    K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_TO_F32, K_COARSE_SETUP, K_SMOOTH_ZERO,
+    K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
+    K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
+    K_OPACITY, K_NUM
+};
+const char* const KNAMES[K_NUM] = {
+    "assemble_faces", "assemble_rhs", "coarsen", "invd", "to_f32", "coarse_setup", "smooth_zero",
+    "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
+    "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
+    "opacity_update"};
+
+struct KStat {
+    long long launches, timed;
+    double ms, bytes, timed_bytes;
+};
+
+bool coarsenable(const int n[3]) {
+    int mn = n[0] < n[1] ? n[0] : n[1];
+    if (n[2] < mn) mn = n[2];
+    return mn > 4 && n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0;
+}
+
+int level_shapes(const fld_grid* g, int dims[][3]) {
+    int n[3] = {g->nx, g->ny, g->nz};
+    int nl = 0;
+    for (;;) {
+        dims[nl][0] = n[0];
+        dims[nl][1] = n[1];
+        dims[nl][2] = n[2];
+        nl++;
+        if (!coarsenable(n) || nl >= MAX_LEVELS) break;
+        n[0] /= 2;
+        n[1] /= 2;
+        n[2] /= 2;
+    }
+    return nl;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+fld_status validate(const fld_grid* g, const fld_params* p) {
+    if (!g || !p) return set_err(FLD_EINVAL, "null grid or params");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+        return set_err(FLD_EINVAL, "grid dimensions must be >= 1 (got %d %d %d)", g->nx, g->ny, g->nz);
+    if ((long long)g->nx * g->ny * g->nz > (1LL << 33))
+        return set_err(FLD_EINVAL, "grid too large");
+    if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
+        return set_err(FLD_EINVAL, "cell widths must be finite and > 0");
+    for (int a = 0; a < 3; a++)
+        if (g->bc[a] != FLD_BC_ZERO_GRADIENT && g->bc[a] != FLD_BC_PERIODIC)
+            return set_err(FLD_EINVAL, "unknown boundary condition %d on axis %d", g->bc[a], a);
+    if (!finite_pos(p->dt)) return set_err(FLD_EINVAL, "dt must be finite and > 0");
+    if (!finite_pos(p->c)) return set_err(FLD_EINVAL, "c must be finite and > 0");
+    if (!finite_pos(p->L_unit)) return set_err(FLD_EINVAL, "L_unit must be finite and > 0");
+    if (!finite_pos(p->dmax_coef)) return set_err(FLD_EINVAL, "dmax_coef must be finite and > 0");
+    if (!(std::isfinite(p->rmin_coef) && p->rmin_coef >= 0.0))
+        return set_err(FLD_EINVAL, "rmin_coef must be finite and >= 0");
+    if (!(std::isfinite(p->sigma) && p->sigma >= 0.0))
+        return set_err(FLD_EINVAL, "sigma must be finite and >= 0");
+    if (!(std::isfinite(p->adot_over_a) && p->adot_over_a >= 0.0))
+        return set_err(FLD_EINVAL, "adot_over_a must be finite and >= 0");
+    if (!finite_pos(p->hnu)) return set_err(FLD_EINVAL, "hnu must be finite and > 0");
+    if (p->limiter != FLD_LIMITER_PAPER && p->limiter != FLD_LIMITER_LP)
+        return set_err(FLD_EINVAL, "unknown limiter %d", p->limiter);
+    if (p->precision != FLD_PREC_FP64 && p->precision != FLD_PREC_MIXED)
+        return set_err(FLD_EINVAL, "unknown precision %d", p->precision);
+    if (p->smoother != FLD_SMOOTH_RBGS && p->smoother != FLD_SMOOTH_JACOBI)
+        return set_err(FLD_EINVAL, "unknown smoother %d", p->smoother);
+    if (p->smoother == FLD_SMOOTH_JACOBI && !(p->jacobi_omega > 0.0 && p->jacobi_omega < 2.0))
+        return set_err(FLD_EINVAL, "jacobi_omega must lie in (0, 2)");
+    if (!(p->rtol > 0.0 && p->rtol < 1.0)) return set_err(FLD_EINVAL, "rtol must lie in (0, 1)");
+    if (p->max_iter < 1 || p->max_iter > 100000) return set_err(FLD_EINVAL, "max_iter out of range");
+    if (p->pre < 0 || p->post < 0 || p->pre > 16 || p->post > 16 || p->pre + p->post < 1)
+        return set_err(FLD_EINVAL, "pre/post sweeps must be in [0, 16] with at least one sweep");
+    if (p->precision == FLD_PREC_MIXED && !(p->inner_rtol > 0.0 && p->inner_rtol < 1.0))
+        return set_err(FLD_EINVAL, "inner_rtol must lie in (0, 1)");
+    if (p->coarse_cap < 1 || p->coarse_cap > COARSE_CAP_MAX)
+        return set_err(FLD_EINVAL, "coarse_cap must lie in [1, %d]", COARSE_CAP_MAX);
+    int dims[MAX_LEVELS][3];
+    int nl = level_shapes(g, dims);
+    long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
+    if (nc > p->coarse_cap)
+        return set_err(FLD_EINVAL,
+                       "coarsest grid %dx%dx%d has %lld cells > coarse_cap %d (coarsening stops at "
+                       "the first odd dimension or a dimension <= 4)",
+                       dims[nl - 1][0], dims[nl - 1][1], dims[nl - 1][2], nc, p->coarse_cap);
+    return FLD_OK;
+}
+
+// Enumerates every device buffer a context needs, in a fixed order; the
+// same walk sizes the footprint and performs the allocation.
+template <class F>
+void plan(const fld_grid* g, const fld_params* p, F&& buf) {
+    int dims[MAX_LEVELS][3];
+    const int nl = level_shapes(g, dims);
+    const bool mixed = p->precision == FLD_PREC_MIXED;
+    const size_t ts = mixed ? sizeof(float) : sizeof(double);
+    for (int l = 0; l < nl; l++) {
+        const size_t n = (size_t)dims[l][0] * dims[l][1] * dims[l][2];
+        for (int q = 0; q < 4; q++) buf(l, "A64", q, n * sizeof(double));
+        if (!(mixed && l == 0)) buf(l, "A64", 4, n * sizeof(double));
+        if (mixed)
+            for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
+        if (l > 0) {
+            buf(l, "vec", 0, n * ts);
+            buf(l, "vec", 1, n * ts);
+        }
+        buf(l, "vec", 2, n * ts);
+    }
+    const size_t n0 = (size_t)g->nx * g->ny * g->nz;
+    buf(0, "b", 0, n0 * sizeof(double));
+    buf(0, "dE", 0, n0 * sizeof(double));
+    if (mixed) buf(0, "r64", 0, n0 * sizeof(double));
+    for (int q = 0; q < 6; q++) buf(0, "cg", q, n0 * ts);
+    const size_t nc = (size_t)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
+    buf(0, "dense", 0, nc * nc * sizeof(double));
+    buf(0, "dense", 1, nc * nc * sizeof(double));
+    buf(0, "red", 0, 3 * RED_MAX_BLOCKS * sizeof(double));
+    buf(0, "red", 1, 256);
+    buf(0, "red", 2, NUM_SLOTS * sizeof(double));
+}
+
+}  // namespace
+
+struct fld_ctx {
+    fld_grid g;
+    fld_params p;
+    cudaStream_t s;
+    bool mixed;
+    int nl;
+    Level L[MAX_LEVELS];
+    double *b, *dE, *r64;
+    void* cg[6];   // r, z, p0, p1, q, x
+    int nc;
+    double *dense, *ainv;
+    double* partials;
+    unsigned* counter;
+    double* sc;
+    double* h_sc;  // pinned mirror of sc
+    double *stage[3];
+    cudaEvent_t e0, e1;
+    PhysDev pd;
+    bool assembled;
+    std::vector<void*> allocs;
+    // launch accounting and optional per-class event timing
+    unsigned long long tmask;
+    KStat kstat[K_NUM];
+    struct Pend { int cls; double bytes; cudaEvent_t a, b; };
+    std::vector<Pend> pend;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used;
+};
+
+namespace {
+
+RedArgs red(fld_ctx* c, int op, int slot0 = 0, int slot1 = 0, int first = 0) {
+    RedArgs r;
+    r.partials = c->partials;
+    r.counter = c->counter;
+    r.sc = c->sc;
+    r.op = op;
+    r.slot0 = slot0;
+    r.slot1 = slot1;
+    r.first = first;
+    return r;
+}
+
+cudaEvent_t pool_event(fld_ctx* c) {
+    if (c->pool_used == c->pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        c->pool.push_back(e);
+    }
+    return c->pool[c->pool_used++];
+}
+
+// Counts one kernel launch of class cls moving `bytes` of algorithmic
+// traffic; when the class is selected for timing, brackets it with events.
+struct KScope {
+    fld_ctx* c;
+    int cls;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KScope(fld_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+        c->kstat[cls].launches++;
+        c->kstat[cls].bytes += bytes;
+        if ((c->tmask >> cls) & 1ULL) {
+            a = pool_event(c);
+            b = pool_event(c);
+            if (a && b) cudaEventRecord(a, c->s); else a = b = nullptr;
+        }
+    }
+    ~KScope() {
+        if (a) {
+            cudaEventRecord(b, c->s);
+            c->pend.push_back({cls, bytes, a, b});
+        }
+    }
+};
+
+// Called once the stream has drained: turn pending event pairs into times.
+void harvest(fld_ctx* c) {
+    for (auto& p : c->pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            c->kstat[p.cls].ms += ms;
+            c->kstat[p.cls].timed++;
+            c->kstat[p.cls].timed_bytes += p.bytes;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    c->pend.clear();
+    c->pool_used = 0;
+}
+
+fld_status read_scalars(fld_ctx* c) {
+    CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    harvest(c);
+    return FLD_OK;
+}
+
+template <class T>
+Op<T> op_of(Level& L);
+template <>
+Op<double> op_of<double>(Level& L) { return L.A64; }
+template <>
+Op<float> op_of<float>(Level& L) { return L.A32; }
+
+// z = B r on level l (zero initial guess).
+template <class T>
+void vcycle(fld_ctx* c, int l, const T* r, T* z) {
+    Level& L = c->L[l];
+    cudaStream_t s = c->s;
+    const double n = (double)L.d.n, ts = sizeof(T);
+    if (l == c->nl - 1) {
+        KScope k(c, K_COARSE_APPLY, n * n * 8.0 + 2.0 * n * ts);
+        launch_coarse_apply<T>((int)L.d.n, c->ainv, r, z, s);
+        return;
+    }
+    Op<T> A = op_of<T>(L);
+    T* t = (T*)L.t;
+    const fld_params& p = c->p;
+    if (p.smoother == FLD_SMOOTH_RBGS) {
+        if (p.pre >= 1) {
+            { KScope k(c, K_SMOOTH_ZERO, 6.0 * n * ts); launch_smooth_zero<T>(L.d, A, r, z, s); }
+            for (int it = 1; it < p.pre; it++)
+                for (int colour = 0; colour < 2; colour++) {
+                    KScope k(c, K_RB_COLOUR, 6.5 * n * ts);
+                    launch_rb_colour<T>(L.d, A, r, z, colour, s);
+                }
+        } else {
+            cudaMemsetAsync(z, 0, L.d.n * sizeof(T), s);
+        }
+    } else {
+        if (p.pre >= 1) {
+            { KScope k(c, K_JACOBI, 3.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, z, p.jacobi_omega, true, s); }
+            for (int it = 1; it < p.pre; it++) {
+                { KScope k(c, K_JACOBI, 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
+                cudaMemcpyAsync(z, t, L.d.n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            }
+        } else {
+            cudaMemsetAsync(z, 0, L.d.n * sizeof(T), s);
+        }
+    }
+    Level& C = c->L[l + 1];
+    const double nc = (double)C.d.n;
+    { KScope k(c, K_RESIDUAL, 7.0 * n * ts); launch_residual<T>(L.d, A, r, z, t, s); }
+    { KScope k(c, K_RESTRICT, (n + nc) * ts); launch_restrict<T>(L.d, C.d, t, (T*)C.r, s); }
+    vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
+    { KScope k(c, K_PROLONG, (2.0 * n + nc) * ts); launch_prolong_add<T>(L.d, C.d, (const T*)C.z, z, s); }
+    for (int it = 0; it < p.post; it++) {
+        if (p.smoother == FLD_SMOOTH_RBGS) {
+            for (int colour = 1; colour >= 0; colour--) {
+                KScope k(c, K_RB_COLOUR, 6.5 * n * ts);
+                launch_rb_colour<T>(L.d, A, r, z, colour, s);
+            }
+        } else {
+            { KScope k(c, K_JACOBI, 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
+            cudaMemcpyAsync(z, t, L.d.n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        }
+    }
+}
+
+// Preconditioned CG on the fine level in precision T: r holds the initial
+// residual (x = 0), r0sq = ||r||^2; stops when ||r||^2 <= rtol^2 r0sq.
+template <class T>
+fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
+    T* r = (T*)c->cg[0];
+    T* z = (T*)c->cg[1];
+    T* p[2] = {(T*)c->cg[2], (T*)c->cg[3]};
+    T* q = (T*)c->cg[4];
+    T* x = (T*)c->cg[5];
+    Level& L0 = c->L[0];
+    Op<T> A = op_of<T>(L0);
+    const long long n = L0.d.n;
+    const double thresh = rtol * rtol * r0sq;
+    *converged = false;
+    *iters = 0;
+    CUDA_TRY(cudaMemsetAsync(p[0], 0, n * sizeof(T), c->s));
+    int cur = 0;
+    for (int k = 1; k <= max_iter; k++) {
+        vcycle<T>(c, 0, r, z);
+        const double ts = sizeof(T);
+        { KScope ks(c, K_DOT, 2.0 * n * ts); launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s); }
+        { KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
+          launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s); }
+        { KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
+          launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s); }
+        cur ^= 1;
+        fld_status st = read_scalars(c);
+        if (st) return st;
+        *iters = k;
+        if (c->h_sc[S_NONFINITE] != 0.0)
+            return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
+        if (c->h_sc[S_RR] <= thresh) {
+            *converged = true;
+            break;
+        }
+    }
+    return FLD_OK;
+}
+
+fld_status alloc_ctx(fld_ctx* c) {
+    int li = -1;
+    fld_status st = FLD_OK;
+    plan(&c->g, &c->p, [&](int l, const char* kind, int q, size_t bytes) {
+        if (st != FLD_OK) return;
+        void* ptr = nullptr;
+        cudaError_t e = cudaMalloc(&ptr, bytes < 256 ? 256 : bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = set_err(FLD_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            return;
+        }
+        c->allocs.push_back(ptr);
+        Level& L = c->L[l];
+        (void)li;
+        if (!strcmp(kind, "A64")) {
+            double* d = (double*)ptr;
+            if (q == 0) L.A64.m = d; else if (q == 1) L.A64.wx = d; else if (q == 2) L.A64.wy = d;
+            else if (q == 3) L.A64.wz = d; else L.A64.invd = d;
+        } else if (!strcmp(kind, "A32")) {
+            float* f = (float*)ptr;
+            if (q == 0) L.A32.m = f; else if (q == 1) L.A32.wx = f; else if (q == 2) L.A32.wy = f;
+            else if (q == 3) L.A32.wz = f; else L.A32.invd = f;
+        } else if (!strcmp(kind, "vec")) {
+            if (q == 0) L.r = ptr; else if (q == 1) L.z = ptr; else L.t = ptr;
+        } else if (!strcmp(kind, "b")) c->b = (double*)ptr;
+        else if (!strcmp(kind, "dE")) c->dE = (double*)ptr;
+        else if (!strcmp(kind, "r64")) c->r64 = (double*)ptr;
+        else if (!strcmp(kind, "cg")) c->cg[q] = ptr;
+        else if (!strcmp(kind, "dense")) { if (q == 0) c->dense = (double*)ptr; else c->ainv = (double*)ptr; }
+        else if (!strcmp(kind, "red")) {
+            if (q == 0) c->partials = (double*)ptr;
+            else if (q == 1) c->counter = (unsigned*)ptr;
+            else c->sc = (double*)ptr;
+        }
+    });
+    return st;
+}
+
+void free_ctx(fld_ctx* c) {
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    for (void* p : c->allocs) cudaFree(p);
+    for (int q = 0; q < 3; q++)
+        if (c->stage[q]) cudaFree(c->stage[q]);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->e0) cudaEventDestroy(c->e0);
+    if (c->e1) cudaEventDestroy(c->e1);
+    delete c;
+}
+
+fld_status solve_impl(fld_ctx* c, fld_info* info) {
+    const long long n = c->L[0].d.n;
+    const double bb = c->h_sc[S_BB];
+    fld_info inf{};
+    if (bb == 0.0) {
+        CUDA_TRY(cudaMemsetAsync(c->dE, 0, n * sizeof(double), c->s));
+        if (info) *info = inf;
+        return FLD_OK;
+    }
+    const double rtol = c->p.rtol;
+    fld_status st = FLD_OK;
+    bool conv = false;
+    if (!c->mixed) {
+        CUDA_TRY(cudaMemcpyAsync(c->cg[0], c->b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        CUDA_TRY(cudaMemsetAsync(c->cg[5], 0, n * sizeof(double), c->s));
+        int it = 0;
+        st = pcg<double>(c, bb, rtol, c->p.max_iter, &it, &conv);
+        inf.iters = it;
+        if (st) return st;
+        CUDA_TRY(cudaMemcpyAsync(c->dE, c->cg[5], n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        { KScope k(c, K_RESIDUAL64, 48.0 * n);
+          launch_residual64(c->L[0].d, c->L[0].A64, c->b, c->dE, nullptr,
+                            red(c, R_STORE_SUM_MAX, S_TRUE_RR, S_RMAX), c->s); }
+        if ((st = read_scalars(c))) return st;
+        inf.rel_res = std::sqrt(c->h_sc[S_TRUE_RR] / bb);
+    } else {
+        CUDA_TRY(cudaMemsetAsync(c->dE, 0, n * sizeof(double), c->s));
+        int inner_total = 0, outer = 0;
+        for (;;) {
+            { KScope k(c, K_RESIDUAL64, 56.0 * n);
+              launch_residual64(c->L[0].d, c->L[0].A64, c->b, c->dE, c->r64,
+                                red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
+            if ((st = read_scalars(c))) return st;
+            if (c->h_sc[S_NONFINITE] != 0.0)
+                return set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", outer);
+            inf.rel_res = std::sqrt(c->h_sc[S_R64] / bb);
+            if (inf.rel_res <= rtol) { conv = true; break; }
+            if (inner_total >= c->p.max_iter) break;
+            { KScope k(c, K_IR_SCALE, 16.0 * n);
+              launch_ir_scale(n, c->r64, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
+            if ((st = read_scalars(c))) return st;
+            int it = 0;
+            bool iconv = false;
+            st = pcg<float>(c, c->h_sc[S_R0], c->p.inner_rtol, c->p.max_iter - inner_total, &it, &iconv);
+            if (st) return st;
+            inner_total += it;
+            { KScope k(c, K_IR_UPDATE, 20.0 * n); launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, c->s); }
+            outer++;
+        }
+        inf.iters = inner_total;
+        inf.outer_iters = outer;
+    }
+    inf.status = conv ? FLD_OK : FLD_ENOCONV;
+    if (info) *info = inf;
+    if (!conv)
+        return set_err(FLD_ENOCONV, "no convergence: relative residual %.3e > rtol %.3e after %d iterations",
+                       inf.rel_res, rtol, inf.iters);
+    return FLD_OK;
+}
+
+fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
+    cudaStream_t s = c->s;
+    c->assembled = false;
+    CUDA_TRY(cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), s));
+    Level& L0 = c->L[0];
+    Op<float> op32{};
+    if (c->mixed) op32 = L0.A32;
+    const double n0 = (double)L0.d.n;
+    { KScope k(c, K_ASM_FACES, n0 * (56.0 + (c->mixed ? 16.0 : 0.0)));
+      launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, s); }
+    { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 4.0 : 8.0)));
+      launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, red(c, R_STORE1, S_BB), s); }
+    for (int l = 1; l < c->nl; l++) {
+        Level& F = c->L[l - 1];
+        Level& C = c->L[l];
+        const double nf = (double)F.d.n, nc = (double)C.d.n;
+        { KScope k(c, K_COARSEN, 32.0 * (nf + nc)); launch_coarsen(F.d, C.d, F.A64, C.A64, s); }
+        { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
+        if (c->mixed) {
+            { KScope k(c, K_TO_F32, 48.0 * nc); launch_to_f32(C.d, C.A64, C.A32, s); }
+            { KScope k(c, K_INVD, 36.0 * nc); launch_invd<float>(C.d, C.A32, C.A64, s); }
+        }
+    }
+    Level& Lc = c->L[c->nl - 1];
+    { const double nc = (double)Lc.d.n;
+      KScope k(c, K_COARSE_SETUP, 16.0 * nc * nc);
+      launch_coarse_setup(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, s); }
+    CUDA_TRY(cudaGetLastError());
+    fld_status st = read_scalars(c);
+    if (st) return st;
+    if (c->h_sc[S_BAD] == 1.0)
+        return set_err(FLD_EINVAL, "E, n_HI and eta must be finite and >= 0");
+    if (c->h_sc[S_BAD] == 2.0)
+        return set_err(FLD_ENONFINITE, "coarsest-grid operator is not positive definite");
+    if (c->h_sc[S_NONFINITE] != 0.0 || !std::isfinite(c->h_sc[S_BB]))
+        return set_err(FLD_ENONFINITE, "non-finite right-hand side");
+    c->assembled = true;
+    return FLD_OK;
+}
+
+fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
+    fld_info inf{};
+    CUDA_TRY(cudaEventRecord(c->e0, c->s));
+    fld_status st = assemble_impl(c, E, nHI, eta);
+    if (st) {
+        inf.status = st;
+        if (info) *info = inf;
+        return st;
+    }
+    st = solve_impl(c, &inf);
+    if (st) {
+        inf.status = st;
+        if (info) *info = inf;
+        return st;
+    }
+    const long long n = c->L[0].d.n;
+    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE3, S_BAL), c->s); }
+    CUDA_TRY(cudaEventRecord(c->e1, c->s));
+    if ((st = read_scalars(c))) return st;
+    const double V = c->g.dx * c->g.dy * c->g.dz;
+    const double scale = V / c->p.hnu;
+    inf.balance_abs = c->h_sc[S_BAL] * scale;
+    inf.emitted = c->h_sc[S_EMIT] * scale;
+    inf.absorbed = c->h_sc[S_ABSORB] * scale;
+    const double budget = inf.emitted > inf.absorbed ? inf.emitted : inf.absorbed;
+    inf.balance_rel = budget > 0.0 ? std::fabs(inf.balance_abs) / budget : std::fabs(inf.balance_abs);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->e0, c->e1);
+    inf.ms = ms;
+    inf.status = FLD_OK;
+    if (info) *info = inf;
+    return FLD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fld_status fld_params_default(fld_params* p) {
+    if (!p) return set_err(FLD_EINVAL, "null params");
+    memset(p, 0, sizeof(*p));
+    p->dt = 1e5 * 3.15576e7;
+    p->c = 2.99792458e10;
+    p->L_unit = 6.6 * 3.0856776e21;
+    p->dmax_coef = 0.006;
+    p->rmin_coef = 1e-20;
+    p->sigma = 1.6e-18;
+    p->adot_over_a = 0.0;
+    p->hnu = 13.6 * 1.602176634e-12;
+    p->limiter = FLD_LIMITER_PAPER;
+    p->precision = FLD_PREC_FP64;
+    p->smoother = FLD_SMOOTH_RBGS;
+    p->jacobi_omega = 0.8;
+    p->rtol = 1e-8;
+    p->max_iter = 50;
+    p->pre = 1;
+    p->post = 1;
+    p->inner_rtol = 1e-4;
+    p->coarse_cap = 1024;
+    return FLD_OK;
+}
+
+size_t fld_footprint_bytes(const fld_grid* g, const fld_params* p) {
+    if (validate(g, p) != FLD_OK) return 0;
+    size_t total = 0;
+    plan(g, p, [&](int, const char*, int, size_t bytes) { total += (bytes + 511) / 512 * 512; });
+    return total;
+}
+
+int fld_levels(const fld_grid* g, int* dims, int max_levels) {
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1) return 0;
+    int d[MAX_LEVELS][3];
+    int nl = level_shapes(g, d);
+    for (int l = 0; l < nl && l < max_levels; l++)
+        for (int a = 0; a < 3; a++) dims[3 * l + a] = d[l][a];
+    return nl;
+}
+
+fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, void* stream) {
+    if (!out) return set_err(FLD_EINVAL, "null output pointer");
+    *out = nullptr;
+    fld_status st = validate(g, p);
+    if (st) return st;
+    fld_ctx* c = new (std::nothrow) fld_ctx();
+    if (!c) return set_err(FLD_ENOMEM, "host allocation failed");
+    c->g = *g;
+    c->p = *p;
+    c->s = (cudaStream_t)stream;
+    c->mixed = p->precision == FLD_PREC_MIXED;
+    int dims[MAX_LEVELS][3];
+    c->nl = level_shapes(g, dims);
+    for (int l = 0; l < c->nl; l++) {
+        Dims& d = c->L[l].d;
+        d.nx = dims[l][0];
+        d.ny = dims[l][1];
+        d.nz = dims[l][2];
+        d.px = g->bc[0] == FLD_BC_PERIODIC;
+        d.py = g->bc[1] == FLD_BC_PERIODIC;
+        d.pz = g->bc[2] == FLD_BC_PERIODIC;
+        d.n = (long long)d.nx * d.ny * d.nz;
+    }
+    c->nc = (int)c->L[c->nl - 1].d.n;
+    st = alloc_ctx(c);
+    if (st) { free_ctx(c); return st; }
+    if (cudaMallocHost(&c->h_sc, NUM_SLOTS * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return set_err(FLD_ENOMEM, "pinned scalar buffer or event creation failed");
+    }
+    memset(c->h_sc, 0, NUM_SLOTS * sizeof(double));
+    if (cudaMemsetAsync(c->counter, 0, 256, c->s) != cudaSuccess ||
+        cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), c->s) != cudaSuccess) {
+        free_ctx(c);
+        return set_err(FLD_ECUDA, "initial memset failed");
+    }
+    PhysDev& pd = c->pd;
+    pd.dt = p->dt;
+    pd.c = p->c;
+    pd.Dmax = p->dmax_coef * p->c * p->L_unit;
+    pd.Rmin = p->rmin_coef / p->L_unit;
+    pd.sigma = p->sigma;
+    pd.adot = p->adot_over_a;
+    pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
+    for (int a = 0; a < 3; a++) pd.dt_h2[a] = p->dt / (pd.h[a] * pd.h[a]);
+    pd.limiter = p->limiter;
+    *out = c;
+    return FLD_OK;
+}
+
+void fld_destroy(fld_ctx* c) { free_ctx(c); }
+
+fld_status fld_assemble(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+    return assemble_impl(c, E, nHI, eta);
+}
+
+fld_status fld_solve(fld_ctx* c, double* dE, fld_info* info) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!dE) return set_err(FLD_EINVAL, "null dE");
+    if (!c->assembled) return set_err(FLD_EINVAL, "fld_solve before a successful fld_assemble");
+    if (cudaEventRecord(c->e0, c->s) != cudaSuccess) return set_err(FLD_ECUDA, "event record failed");
+    fld_info inf{};
+    fld_status st = solve_impl(c, &inf);
+    if (st == FLD_OK || st == FLD_ENOCONV) {
+        CUDA_TRY(cudaMemcpyAsync(dE, c->dE, c->L[0].d.n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        CUDA_TRY(cudaEventRecord(c->e1, c->s));
+        CUDA_TRY(cudaStreamSynchronize(c->s));
+        harvest(c);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->e0, c->e1);
+        inf.ms = ms;
+    }
+    inf.status = st;
+    if (info) *info = inf;
+    return st;
+}
+
+fld_status fld_step(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    return step_impl(c, E, nHI, eta, info);
+}
+
+fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
+    const size_t bytes = c->L[0].d.n * sizeof(double);
+    for (int q = 0; q < 3; q++)
+        if (!c->stage[q]) {
+            if (cudaMalloc(&c->stage[q], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                c->stage[q] = nullptr;
+                return set_err(FLD_ENOMEM, "staging allocation failed");
+            }
+        }
+    CUDA_TRY(cudaMemcpyAsync(c->stage[0], E, bytes, cudaMemcpyHostToDevice, c->s));
+    CUDA_TRY(cudaMemcpyAsync(c->stage[1], nHI, bytes, cudaMemcpyHostToDevice, c->s));
+    CUDA_TRY(cudaMemcpyAsync(c->stage[2], eta, bytes, cudaMemcpyHostToDevice, c->s));
+    fld_status st = step_impl(c, c->stage[0], c->stage[1], c->stage[2], info);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(E, c->stage[0], bytes, cudaMemcpyDeviceToHost, c->s));
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    return FLD_OK;
+}
+
+fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E, const double** nHI,
+                            const double** eta, fld_info* infos) {
+    if (n < 0 || (n > 0 && (!ctxs || !E || !nHI || !eta || !infos)))
+        return set_err(FLD_EINVAL, "invalid batch arguments");
+    for (int i = 0; i < n; i++)
+        if (!ctxs[i]) return set_err(FLD_EINVAL, "null context %d in batch", i);
+    std::vector<fld_status> st(n, FLD_OK);
+    std::vector<std::string> msg(n);
+    std::vector<std::thread> th;
+    th.reserve(n);
+    // Each context drives its own stream from its own host thread, so the
+    // steps' kernels overlap on the device.
+    for (int i = 0; i < n; i++)
+        th.emplace_back([&, i] {
+            st[i] = step_impl(ctxs[i], E[i], nHI[i], eta[i], &infos[i]);
+            if (st[i]) msg[i] = g_err;
+        });
+    for (auto& t : th) t.join();
+    for (int i = 0; i < n; i++)
+        if (st[i]) {
+            g_err = "batch item " + std::to_string(i) + ": " + msg[i];
+            return st[i];
+        }
+    return FLD_OK;
+}
+
+fld_status fld_apply(fld_ctx* c, const double* x, double* y) {
+    if (!c || !x || !y) return set_err(FLD_EINVAL, "null argument");
+    if (!c->assembled) return set_err(FLD_EINVAL, "fld_apply before fld_assemble");
+    { KScope k(c, K_APPLY, 48.0 * c->L[0].d.n); launch_apply<double>(c->L[0].d, c->L[0].A64, x, y, c->s); }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    harvest(c);
+    return FLD_OK;
+}
+
+fld_status fld_vcycle(fld_ctx* c, const double* r, double* z) {
+    if (!c || !r || !z) return set_err(FLD_EINVAL, "null argument");
+    if (!c->assembled) return set_err(FLD_EINVAL, "fld_vcycle before fld_assemble");
+    if (c->mixed) return set_err(FLD_EINVAL, "fld_vcycle needs an FP64 context");
+    vcycle<double>(c, 0, r, z);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    harvest(c);
+    return FLD_OK;
+}
+
+fld_status fld_get_system(fld_ctx* c, double* m, double* wx, double* wy, double* wz, double* b) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!c->assembled) return set_err(FLD_EINVAL, "fld_get_system before fld_assemble");
+    const size_t bytes = c->L[0].d.n * sizeof(double);
+    const double* src[5] = {c->L[0].A64.m, c->L[0].A64.wx, c->L[0].A64.wy, c->L[0].A64.wz, c->b};
+    double* dst[5] = {m, wx, wy, wz, b};
+    for (int q = 0; q < 5; q++)
+        if (dst[q]) CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, c->s));
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    return FLD_OK;
+}
+
+fld_status fld_opacity_update(size_t n, const double* E, const double* nH, const double* nHI,
+                              double* out, double dt, double c, double sigma, double hnu,
+                              double alpha_B, void* stream) {
+    if (!E || !nH || !nHI || !out) return set_err(FLD_EINVAL, "null argument");
+    if (!(dt > 0.0) || !(c > 0.0) || !(sigma >= 0.0) || !(hnu > 0.0) || !(alpha_B >= 0.0))
+        return set_err(FLD_EINVAL, "invalid opacity-update constants");
+    if (n == 0) return FLD_OK;
+    launch_opacity_update((long long)n, E, nH, nHI, out, dt, c, sigma, hnu, alpha_B,
+                          (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return FLD_OK;
+}
+
+fld_status fld_profile(fld_ctx* c, unsigned long long class_mask) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (c->s) cudaStreamSynchronize(c->s);
+    harvest(c);
+    c->tmask = class_mask;
+    for (int k = 0; k < K_NUM; k++) c->kstat[k] = KStat{};
+    return FLD_OK;
+}
+
+int fld_profile_read(fld_ctx* c, fld_kernel_stat* out, int max) {
+    if (!c) return 0;
+    for (int k = 0; k < K_NUM && k < max; k++) {
+        out[k].name = KNAMES[k];
+        out[k].launches = c->kstat[k].launches;
+        out[k].timed = c->kstat[k].timed;
+        out[k].ms = c->kstat[k].ms;
+        out[k].bytes = c->kstat[k].bytes;
+        out[k].timed_bytes = c->kstat[k].timed_bytes;
+    }
+    return K_NUM;
+}
+
+const char* fld_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

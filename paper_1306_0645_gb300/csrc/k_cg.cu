@@ -1,0 +1,215 @@
+// k_cg.cu -- conjugate-gradient vector kernels (Table 1 outer solver),
+// FP64 iterative-refinement kernels of the mixed-precision solve, and the
+// step finaliser with the photon balance.
+//
+// Every dot product and norm goes through the deterministic two-level FP64
+// reduction of common.cuh, so a given launch shape always adds in the same
+// order.
+#include "kernels.h"
+
+namespace fld {
+
+#define GRID_LOOP(c, n) \
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
+
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) k_dot(long long n, const T* __restrict__ a,
+                                                     const T* __restrict__ b, RedArgs ra) {
+    double acc[1] = {0.0};
+    GRID_LOOP(c, n) acc[0] = fma((double)a[c], (double)b[c], acc[0]);
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+// p_out = z + beta p_in;  q = A p_out;  <p_out, q>  ->  alpha = rho / <p, q>.
+// p is double-buffered because neighbours of p_out are formed from p_in.
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) k_cg_p_matvec(Dims d, Op<T> A, const T* __restrict__ z,
+                                                             const T* __restrict__ p_in,
+                                                             T* __restrict__ p_out, T* __restrict__ q,
+                                                             RedArgs ra) {
+    const T beta = (T)ra.sc[S_BETA];
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    double acc[1] = {0.0};
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        const T pc = z[c] + beta * p_in[c];
+        T a = T(0), s = T(0);
+#define NB(widx, nb)                                      \
+    {                                                     \
+        const T w_ = A.widx;                              \
+        a += w_ * (z[nb] + beta * p_in[nb]);              \
+        s += w_;                                          \
+    }
+        if (i > 0) NB(wx[c], c - 1) else if (d.px) NB(wx[c], c + d.nx - 1)
+        if (i < d.nx - 1) NB(wx[c + 1], c + 1) else if (d.px) NB(wx[c - (d.nx - 1)], c - (d.nx - 1))
+        if (j > 0) NB(wy[c], c - sy) else if (d.py) NB(wy[c], c + (long long)(d.ny - 1) * sy)
+        if (j < d.ny - 1) NB(wy[c + sy], c + sy) else if (d.py) NB(wy[c - (long long)(d.ny - 1) * sy], c - (long long)(d.ny - 1) * sy)
+        if (k > 0) NB(wz[c], c - sz) else if (d.pz) NB(wz[c], c + (long long)(d.nz - 1) * sz)
+        if (k < d.nz - 1) NB(wz[c + sz], c + sz) else if (d.pz) NB(wz[c - (long long)(d.nz - 1) * sz], c - (long long)(d.nz - 1) * sz)
+#undef NB
+        const T qc = A.m[c] * pc + s * pc - a;
+        p_out[c] = pc;
+        q[c] = qc;
+        acc[0] = fma((double)pc, (double)qc, acc[0]);
+    }
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+// x += alpha p;  r -= alpha q;  ||r||^2.
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) k_cg_update(long long n, T* __restrict__ x, T* __restrict__ r,
+                                                           const T* __restrict__ p, const T* __restrict__ q,
+                                                           RedArgs ra) {
+    const T alpha = (T)ra.sc[S_ALPHA];
+    double acc[1] = {0.0};
+    GRID_LOOP(c, n) {
+        x[c] += alpha * p[c];
+        const T rc = r[c] - alpha * q[c];
+        r[c] = rc;
+        acc[0] = fma((double)rc, (double)rc, acc[0]);
+    }
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+template <class T>
+__global__ void k_apply(Dims d, Op<T> A, const T* __restrict__ x, T* __restrict__ y) {
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        const T xc = x[c];
+        T acc = A.m[c] * xc;
+        if (i > 0) acc += A.wx[c] * (xc - x[c - 1]); else if (d.px) acc += A.wx[c] * (xc - x[c + d.nx - 1]);
+        if (i < d.nx - 1) acc += A.wx[c + 1] * (xc - x[c + 1]); else if (d.px) acc += A.wx[c - (d.nx - 1)] * (xc - x[c - (d.nx - 1)]);
+        if (j > 0) acc += A.wy[c] * (xc - x[c - sy]); else if (d.py) acc += A.wy[c] * (xc - x[c + (long long)(d.ny - 1) * sy]);
+        if (j < d.ny - 1) acc += A.wy[c + sy] * (xc - x[c + sy]); else if (d.py) acc += A.wy[c - (long long)(d.ny - 1) * sy] * (xc - x[c - (long long)(d.ny - 1) * sy]);
+        if (k > 0) acc += A.wz[c] * (xc - x[c - sz]); else if (d.pz) acc += A.wz[c] * (xc - x[c + (long long)(d.nz - 1) * sz]);
+        if (k < d.nz - 1) acc += A.wz[c + sz] * (xc - x[c + sz]); else if (d.pz) acc += A.wz[c - (long long)(d.nz - 1) * sz] * (xc - x[c - (long long)(d.nz - 1) * sz]);
+        y[c] = acc;
+    }
+}
+
+// FP64 residual r = b - A x with ||r||^2 and max |r|.
+__global__ void __launch_bounds__(RED_THREADS) k_residual64(Dims d, Op<double> A, const double* __restrict__ b,
+                                                            const double* __restrict__ x, double* __restrict__ r,
+                                                            RedArgs ra) {
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        const double xc = x[c];
+        double Ax = A.m[c] * xc;
+        if (i > 0) Ax += A.wx[c] * (xc - x[c - 1]); else if (d.px) Ax += A.wx[c] * (xc - x[c + d.nx - 1]);
+        if (i < d.nx - 1) Ax += A.wx[c + 1] * (xc - x[c + 1]); else if (d.px) Ax += A.wx[c - (d.nx - 1)] * (xc - x[c - (d.nx - 1)]);
+        if (j > 0) Ax += A.wy[c] * (xc - x[c - sy]); else if (d.py) Ax += A.wy[c] * (xc - x[c + (long long)(d.ny - 1) * sy]);
+        if (j < d.ny - 1) Ax += A.wy[c + sy] * (xc - x[c + sy]); else if (d.py) Ax += A.wy[c - (long long)(d.ny - 1) * sy] * (xc - x[c - (long long)(d.ny - 1) * sy]);
+        if (k > 0) Ax += A.wz[c] * (xc - x[c - sz]); else if (d.pz) Ax += A.wz[c] * (xc - x[c + (long long)(d.nz - 1) * sz]);
+        if (k < d.nz - 1) Ax += A.wz[c + sz] * (xc - x[c + sz]); else if (d.pz) Ax += A.wz[c - (long long)(d.nz - 1) * sz] * (xc - x[c - (long long)(d.nz - 1) * sz]);
+        const double rc = b[c] - Ax;
+        if (r) r[c] = rc;
+        acc[0] = fma(rc, rc, acc[0]);
+        acc[1] = fmax(acc[1], fabs(rc));
+    }
+    const bool mx[2] = {false, true};
+    grid_reduce<2>(acc, mx, ra);
+}
+
+// r32 = r64 / s with s = max |r64|; x32 = 0; ||r32||^2 -> S_R0 and S_RR.
+__global__ void __launch_bounds__(RED_THREADS) k_ir_scale(long long n, const double* __restrict__ r64,
+                                                          float* __restrict__ r32, float* __restrict__ x32,
+                                                          RedArgs ra) {
+    const double s = ra.sc[S_RMAX];
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(c, n) {
+        const float v = (float)(r64[c] * inv);
+        r32[c] = v;
+        x32[c] = 0.0f;
+        acc[0] = fma((double)v, (double)v, acc[0]);
+    }
+    acc[1] = acc[0];
+    const bool mx[2] = {false, false};
+    grid_reduce<2>(acc, mx, ra);
+}
+
+__global__ void k_ir_update(long long n, double* __restrict__ x64, const float* __restrict__ x32,
+                            const double* __restrict__ sc) {
+    const double s = sc[S_RMAX];
+    GRID_LOOP(c, n) x64[c] = fma(s, (double)x32[c], x64[c]);
+}
+
+// E_out = E + dE; photon balance sums (energy density units; the host
+// scales by V / h nu).
+__global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p, const double* __restrict__ E,
+                                                          const double* __restrict__ dE,
+                                                          const double* __restrict__ nHI,
+                                                          const double* __restrict__ eta, double* E_out,
+                                                          RedArgs ra) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    GRID_LOOP(c, n) {
+        const double d = dE[c];
+        const double En = E[c] + d;
+        const double sink = p.dt * (p.c * nHI[c] * p.sigma + p.adot) * En;
+        const double emit = p.dt * eta[c];
+        acc[0] += d - (emit - sink);
+        acc[1] += emit;
+        acc[2] += sink;
+        E_out[c] = En;
+    }
+    const bool mx[3] = {false, false, false};
+    grid_reduce<3>(acc, mx, ra);
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <class T>
+void launch_dot(long long n, const T* a, const T* b, const RedArgs& ra, cudaStream_t s) {
+    k_dot<T><<<red_blocks(n), RED_THREADS, 0, s>>>(n, a, b, ra);
+}
+template <class T>
+void launch_cg_p_matvec(const Dims& d, Op<T> A, const T* z, const T* p_in, T* p_out, T* q,
+                        const RedArgs& ra, cudaStream_t s) {
+    k_cg_p_matvec<T><<<red_blocks(d.n), RED_THREADS, 0, s>>>(d, A, z, p_in, p_out, q, ra);
+}
+template <class T>
+void launch_cg_update(long long n, T* x, T* r, const T* p, const T* q, const RedArgs& ra,
+                      cudaStream_t s) {
+    k_cg_update<T><<<red_blocks(n), RED_THREADS, 0, s>>>(n, x, r, p, q, ra);
+}
+template <class T>
+void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s) {
+    k_apply<T><<<grid_blocks(d.n, 256), 256, 0, s>>>(d, A, x, y);
+}
+void launch_residual64(const Dims& d, Op<double> A, const double* b, const double* x, double* r,
+                       const RedArgs& ra, cudaStream_t s) {
+    k_residual64<<<red_blocks(d.n), RED_THREADS, 0, s>>>(d, A, b, x, r, ra);
+}
+void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
+                     cudaStream_t s) {
+    k_ir_scale<<<red_blocks(n), RED_THREADS, 0, s>>>(n, r64, r32, x32, ra);
+}
+void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, cudaStream_t s) {
+    k_ir_update<<<grid_blocks(n, 256), 256, 0, s>>>(n, x64, x32, sc);
+}
+void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
+                     const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
+                     cudaStream_t s) {
+    k_finalize<<<red_blocks(n), RED_THREADS, 0, s>>>(n, p, E, dE, nHI, eta, E_out, ra);
+}
+
+#define INST(T)                                                                                     \
+    template void launch_dot<T>(long long, const T*, const T*, const RedArgs&, cudaStream_t);        \
+    template void launch_cg_p_matvec<T>(const Dims&, Op<T>, const T*, const T*, T*, T*,              \
+                                        const RedArgs&, cudaStream_t);                              \
+    template void launch_cg_update<T>(long long, T*, T*, const T*, const T*, const RedArgs&,         \
+                                      cudaStream_t);                                                \
+    template void launch_apply<T>(const Dims&, Op<T>, const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace fld

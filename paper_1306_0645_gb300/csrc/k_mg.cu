@@ -1,0 +1,410 @@
+// k_mg.cu -- geometric multigrid V-cycle pieces for the 7-point FLD system
+// (the preconditioner of Table 1): coarse operators, red/black Gauss-Seidel
+// and weighted Jacobi smoothing, residual, full-weighting restriction,
+// trilinear prolongation, and the dense coarsest-grid solve.
+//
+// Cell-centred full coarsening; operators by rediscretisation (coarse face
+// weight = sum of the 4 fine face weights across the coarse face / 16,
+// coarse mass term = mean of the 8 children); prolongation trilinear with
+// 1-D weights 3/4 (nearer coarse cell) and 1/4 (farther one), ghost cells
+// equal to the boundary cell on zero-gradient axes and wrapped on periodic
+// ones; restriction is the transpose of prolongation divided by 8.
+#include "kernels.h"
+
+namespace fld {
+
+// Sum over the faces of cell c of w_f * u_nbr, and of w_f.
+template <class T>
+__device__ __forceinline__ void nbr_sums(const Dims& d, const Op<T>& A, long long c, int i, int j,
+                                         int k, const T* __restrict__ u, T& swu, T& sw) {
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    T a = T(0), s = T(0);
+    {
+        const T wl = A.wx[c];
+        if (i > 0) { a += wl * u[c - 1]; s += wl; }
+        else if (d.px) { a += wl * u[c + d.nx - 1]; s += wl; }
+        if (i < d.nx - 1) { const T wu = A.wx[c + 1]; a += wu * u[c + 1]; s += wu; }
+        else if (d.px) { const long long up = c - (d.nx - 1); const T wu = A.wx[up]; a += wu * u[up]; s += wu; }
+    }
+    {
+        const T wl = A.wy[c];
+        if (j > 0) { a += wl * u[c - sy]; s += wl; }
+        else if (d.py) { a += wl * u[c + (long long)(d.ny - 1) * sy]; s += wl; }
+        if (j < d.ny - 1) { const T wu = A.wy[c + sy]; a += wu * u[c + sy]; s += wu; }
+        else if (d.py) { const long long up = c - (long long)(d.ny - 1) * sy; const T wu = A.wy[up]; a += wu * u[up]; s += wu; }
+    }
+    {
+        const T wl = A.wz[c];
+        if (k > 0) { a += wl * u[c - sz]; s += wl; }
+        else if (d.pz) { a += wl * u[c + (long long)(d.nz - 1) * sz]; s += wl; }
+        if (k < d.nz - 1) { const T wu = A.wz[c + sz]; a += wu * u[c + sz]; s += wu; }
+        else if (d.pz) { const long long up = c - (long long)(d.nz - 1) * sz; const T wu = A.wz[up]; a += wu * u[up]; s += wu; }
+    }
+    swu = a;
+    sw = s;
+}
+
+// Sum over the faces of cell c of w_f * u_nbr * v_nbr (smoothing from a
+// zero guess needs the red neighbours' values r * invd on the fly).
+template <class T>
+__device__ __forceinline__ T nbr_sum_prod(const Dims& d, const Op<T>& A, long long c, int i, int j,
+                                          int k, const T* __restrict__ u, const T* __restrict__ v) {
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    T a = T(0);
+    if (i > 0) a += A.wx[c] * u[c - 1] * v[c - 1];
+    else if (d.px) a += A.wx[c] * u[c + d.nx - 1] * v[c + d.nx - 1];
+    if (i < d.nx - 1) a += A.wx[c + 1] * u[c + 1] * v[c + 1];
+    else if (d.px) { const long long up = c - (d.nx - 1); a += A.wx[up] * u[up] * v[up]; }
+    if (j > 0) a += A.wy[c] * u[c - sy] * v[c - sy];
+    else if (d.py) { const long long lo = c + (long long)(d.ny - 1) * sy; a += A.wy[c] * u[lo] * v[lo]; }
+    if (j < d.ny - 1) a += A.wy[c + sy] * u[c + sy] * v[c + sy];
+    else if (d.py) { const long long up = c - (long long)(d.ny - 1) * sy; a += A.wy[up] * u[up] * v[up]; }
+    if (k > 0) a += A.wz[c] * u[c - sz] * v[c - sz];
+    else if (d.pz) { const long long lo = c + (long long)(d.nz - 1) * sz; a += A.wz[c] * u[lo] * v[lo]; }
+    if (k < d.nz - 1) a += A.wz[c + sz] * u[c + sz] * v[c + sz];
+    else if (d.pz) { const long long up = c - (long long)(d.nz - 1) * sz; a += A.wz[up] * u[up] * v[up]; }
+    return a;
+}
+
+#define GRID_LOOP(c, n) \
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------ operators
+
+__global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
+    GRID_LOOP(c, cd.n) {
+        int I, J, K;
+        cell_ijk(c, cd, I, J, K);
+        const long long fx = f.nx, fxy = (long long)f.nx * f.ny;
+        const long long base = 2LL * I + fx * 2LL * J + fxy * 2LL * K;
+        double ms = 0.0;
+#pragma unroll
+        for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+            for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+                for (int di = 0; di < 2; di++) ms += F.m[base + di + fx * dj + fxy * dk];
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                sx += F.wx[base + fx * a + fxy * b];
+                sy += F.wy[base + a + fxy * b];
+                sz += F.wz[base + a + fx * b];
+            }
+        C.m[c] = ms * 0.125;
+        C.wx[c] = sx * 0.0625;
+        C.wy[c] = sy * 0.0625;
+        C.wz[c] = sz * 0.0625;
+    }
+}
+
+template <class T>
+__global__ void k_invd(Dims d, Op<T> A, Op<double> A64) {
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        double swu, sw;
+        // u unused: pass m as a harmless array for the weight sum only
+        nbr_sums<double>(d, A64, c, i, j, k, A64.m, swu, sw);
+        const double diag = A64.m[c] + sw;
+        A.invd[c] = (T)(1.0 / diag);
+    }
+}
+
+__global__ void k_to_f32(Dims d, Op<double> A, Op<float> B) {
+    GRID_LOOP(c, d.n) {
+        B.m[c] = (float)A.m[c];
+        B.wx[c] = (float)A.wx[c];
+        B.wy[c] = (float)A.wy[c];
+        B.wz[c] = (float)A.wz[c];
+    }
+}
+
+// ------------------------------------------------------------- smoothers
+
+// First red/black Gauss-Seidel sweep from z = 0: red cells get r / diag,
+// black cells (r + sum_f w_f z_red_nbr) / diag with the red values formed
+// on the fly.
+template <class T>
+__global__ void k_smooth_zero(Dims d, Op<T> A, const T* __restrict__ r, T* __restrict__ z) {
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        if (((i + j + k) & 1) == 0) {
+            z[c] = r[c] * A.invd[c];
+        } else {
+            z[c] = A.invd[c] * (r[c] + nbr_sum_prod<T>(d, A, c, i, j, k, r, A.invd));
+        }
+    }
+}
+
+// One colour of a red/black Gauss-Seidel sweep; every dimension is even on
+// a smoothed level, so cell (2s + ((j + k + colour) & 1), j, k) enumerates
+// the colour.
+template <class T>
+__global__ void k_rb_colour(Dims d, Op<T> A, const T* __restrict__ r, T* z, int colour) {
+    const int hx = d.nx >> 1;
+    const long long nh = d.n >> 1;
+    GRID_LOOP(t, nh) {
+        const long long row = t / hx;
+        const int s = (int)(t - row * hx);
+        const int k = (int)(row / d.ny);
+        const int j = (int)(row - (long long)k * d.ny);
+        const int i = 2 * s + ((j + k + colour) & 1);
+        const long long c = i + (long long)d.nx * row;
+        T swu, sw;
+        nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
+        z[c] = A.invd[c] * (r[c] + swu);
+    }
+}
+
+// Weighted Jacobi: out = z + omega (r - A z) / diag, or omega r / diag from
+// a zero guess.
+template <class T>
+__global__ void k_jacobi(Dims d, Op<T> A, const T* __restrict__ r, const T* __restrict__ z,
+                         T* __restrict__ out, T omega, int zero_guess) {
+    GRID_LOOP(c, d.n) {
+        if (zero_guess) {
+            out[c] = omega * A.invd[c] * r[c];
+        } else {
+            int i, j, k;
+            cell_ijk(c, d, i, j, k);
+            T swu, sw;
+            nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
+            const T Az = A.m[c] * z[c] + sw * z[c] - swu;
+            out[c] = z[c] + omega * A.invd[c] * (r[c] - Az);
+        }
+    }
+}
+
+template <class T>
+__global__ void k_residual(Dims d, Op<T> A, const T* __restrict__ r, const T* __restrict__ z,
+                           T* __restrict__ res) {
+    GRID_LOOP(c, d.n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        T swu, sw;
+        nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
+        res[c] = r[c] - (A.m[c] * z[c] + sw * z[c] - swu);
+    }
+}
+
+// ------------------------------------------------------------- transfers
+
+// Fine index of tap t (0..3 = offsets -1, 0, +1, +2 from 2I) along an axis,
+// with the ghost rule; weights 1/4, 3/4, 3/4, 1/4.
+__device__ __forceinline__ int fine_tap(int I, int t, int nf, int periodic) {
+    int f = 2 * I - 1 + t;
+    if (f < 0) f = periodic ? f + nf : 0;
+    if (f >= nf) f = periodic ? f - nf : nf - 1;
+    return f;
+}
+
+template <class T>
+__global__ void k_restrict(Dims f, Dims cd, const T* __restrict__ rf, T* __restrict__ rc) {
+    const T wt[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
+    GRID_LOOP(c, cd.n) {
+        int I, J, K;
+        cell_ijk(c, cd, I, J, K);
+        int fi[4], fj[4], fk[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            fi[t] = fine_tap(I, t, f.nx, f.px);
+            fj[t] = fine_tap(J, t, f.ny, f.py);
+            fk[t] = fine_tap(K, t, f.nz, f.pz);
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int tk = 0; tk < 4; tk++) {
+            T acc_j = T(0);
+#pragma unroll
+            for (int tj = 0; tj < 4; tj++) {
+                const long long row = (long long)f.nx * (fj[tj] + (long long)f.ny * fk[tk]);
+                T acc_i = T(0);
+#pragma unroll
+                for (int ti = 0; ti < 4; ti++) acc_i += wt[ti] * rf[row + fi[ti]];
+                acc_j += wt[tj] * acc_i;
+            }
+            acc += wt[tk] * acc_j;
+        }
+        rc[c] = acc * T(0.125);
+    }
+}
+
+// Coarse neighbours of fine index i: nearer (weight 3/4) and farther (1/4).
+__device__ __forceinline__ void coarse_pair(int i, int nc, int periodic, int& I0, int& I1) {
+    I0 = i >> 1;
+    int J = (i & 1) ? I0 + 1 : I0 - 1;
+    if (J < 0) J = periodic ? nc - 1 : I0;
+    if (J >= nc) J = periodic ? 0 : I0;
+    I1 = J;
+}
+
+template <class T>
+__global__ void k_prolong_add(Dims f, Dims cd, const T* __restrict__ ec, T* __restrict__ zf) {
+    GRID_LOOP(c, f.n) {
+        int i, j, k;
+        cell_ijk(c, f, i, j, k);
+        int Ix[2], Iy[2], Iz[2];
+        coarse_pair(i, cd.nx, cd.px, Ix[0], Ix[1]);
+        coarse_pair(j, cd.ny, cd.py, Iy[0], Iy[1]);
+        coarse_pair(k, cd.nz, cd.pz, Iz[0], Iz[1]);
+        const T w[2] = {T(0.75), T(0.25)};
+        T acc = T(0);
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            T acc_j = T(0);
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const long long row = (long long)cd.nx * (Iy[a] + (long long)cd.ny * Iz[b]);
+                acc_j += w[a] * (w[0] * ec[row + Ix[0]] + w[1] * ec[row + Ix[1]]);
+            }
+            acc += w[b] * acc_j;
+        }
+        zf[c] += acc;
+    }
+}
+
+// ---------------------------------------------------------- coarsest grid
+
+__global__ void k_dense_build(Dims d, Op<double> A, double* __restrict__ M) {
+    const long long n = d.n;
+    GRID_LOOP(c, n) {
+        double* row = M + c * n;
+        for (long long q = 0; q < n; q++) row[q] = 0.0;
+    }
+    // rows are owned by one thread each, so the adds below do not race
+    GRID_LOOP(c, n) {
+        int i, j, k;
+        cell_ijk(c, d, i, j, k);
+        double* row = M + c * n;
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+        double diag = A.m[c];
+        auto add = [&](double w, long long nb) { diag += w; row[nb] -= w; };
+        if (i > 0) add(A.wx[c], c - 1); else if (d.px) add(A.wx[c], c + d.nx - 1);
+        if (i < d.nx - 1) add(A.wx[c + 1], c + 1); else if (d.px) add(A.wx[c - (d.nx - 1)], c - (d.nx - 1));
+        if (j > 0) add(A.wy[c], c - sy); else if (d.py) add(A.wy[c], c + (long long)(d.ny - 1) * sy);
+        if (j < d.ny - 1) add(A.wy[c + sy], c + sy); else if (d.py) add(A.wy[c - (long long)(d.ny - 1) * sy], c - (long long)(d.ny - 1) * sy);
+        if (k > 0) add(A.wz[c], c - sz); else if (d.pz) add(A.wz[c], c + (long long)(d.nz - 1) * sz);
+        if (k < d.nz - 1) add(A.wz[c + sz], c + sz); else if (d.pz) add(A.wz[c - (long long)(d.nz - 1) * sz], c - (long long)(d.nz - 1) * sz);
+        row[c] += diag;
+    }
+}
+
+// One CTA: in-place Cholesky of the dense SPD matrix M (row-major, lower
+// triangle becomes L), then the explicit inverse Ainv = L^-T L^-1, one
+// column per thread.  A non-positive pivot sets sc[S_BAD] = 2.
+__global__ void k_chol_inverse(int n, double* M, double* Ainv, double* sc) {
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        if (threadIdx.x == 0) {
+            const double piv = M[(long long)j * n + j];
+            if (!(piv > 0.0)) { fail = 1; M[(long long)j * n + j] = 1.0; }
+            else M[(long long)j * n + j] = sqrt(piv);
+        }
+        __syncthreads();
+        const double ljj = M[(long long)j * n + j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(long long)i * n + j] /= ljj;
+        __syncthreads();
+        // trailing update of the lower triangle: M[i][k] -= L[i][j] L[k][j], j < k <= i
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const double lij = M[(long long)i * n + j];
+            for (int k = j + 1; k <= i; k++) M[(long long)i * n + k] -= lij * M[(long long)k * n + j];
+        }
+        __syncthreads();
+    }
+    if (fail && threadIdx.x == 0) sc[S_BAD] = 2.0;
+    // inverse, column t: L y = e_t, then L^T x = y, written in Ainv[:, t]
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        for (int i = 0; i < t; i++) Ainv[(long long)i * n + t] = 0.0;
+        for (int i = t; i < n; i++) {
+            double s = (i == t) ? 1.0 : 0.0;
+            for (int k = t; k < i; k++) s -= M[(long long)i * n + k] * Ainv[(long long)k * n + t];
+            Ainv[(long long)i * n + t] = s / M[(long long)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = Ainv[(long long)i * n + t];
+            for (int k = i + 1; k < n; k++) s -= M[(long long)k * n + i] * Ainv[(long long)k * n + t];
+            Ainv[(long long)i * n + t] = s / M[(long long)i * n + i];
+        }
+    }
+}
+
+template <class T>
+__global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* __restrict__ r,
+                               T* __restrict__ z) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < n; j++) s += Ainv[(long long)j * n + i] * (double)r[j];
+        z[i] = (T)s;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static const int TPB = 256;
+
+void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s) {
+    k_coarsen<<<grid_blocks(c.n, TPB), TPB, 0, s>>>(f, c, F, C);
+}
+template <class T>
+void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s) {
+    k_invd<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, A64);
+}
+void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s) {
+    k_to_f32<<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, B);
+}
+template <class T>
+void launch_smooth_zero(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s) {
+    k_smooth_zero<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z);
+}
+template <class T>
+void launch_rb_colour(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s) {
+    k_rb_colour<T><<<grid_blocks(d.n / 2, TPB), TPB, 0, s>>>(d, A, r, z, colour);
+}
+template <class T>
+void launch_jacobi(const Dims& d, Op<T> A, const T* r, const T* z, T* out, double omega,
+                   bool zero_guess, cudaStream_t s) {
+    k_jacobi<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z, out, (T)omega, zero_guess ? 1 : 0);
+}
+template <class T>
+void launch_residual(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s) {
+    k_residual<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z, res);
+}
+template <class T>
+void launch_restrict(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s) {
+    k_restrict<T><<<grid_blocks(c.n, TPB), TPB, 0, s>>>(f, c, rf, rc);
+}
+template <class T>
+void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s) {
+    k_prolong_add<T><<<grid_blocks(f.n, TPB), TPB, 0, s>>>(f, c, ec, zf);
+}
+void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc,
+                         cudaStream_t s) {
+    k_dense_build<<<1, TPB, 0, s>>>(d, A, dense);
+    const int threads = d.n < 1024 ? (int)((d.n + 31) / 32 * 32) : 1024;
+    k_chol_inverse<<<1, threads, 0, s>>>((int)d.n, dense, ainv, sc);
+}
+template <class T>
+void launch_coarse_apply(int n, const double* ainv, const T* r, T* z, cudaStream_t s) {
+    k_coarse_apply<T><<<(n + 127) / 128, 128, 0, s>>>(n, ainv, r, z);
+}
+
+#define INST(T)                                                                                    \
+    template void launch_invd<T>(const Dims&, Op<T>, const Op<double>&, cudaStream_t);              \
+    template void launch_smooth_zero<T>(const Dims&, Op<T>, const T*, T*, cudaStream_t);            \
+    template void launch_rb_colour<T>(const Dims&, Op<T>, const T*, T*, int, cudaStream_t);         \
+    template void launch_jacobi<T>(const Dims&, Op<T>, const T*, const T*, T*, double, bool,        \
+                                   cudaStream_t);                                                  \
+    template void launch_residual<T>(const Dims&, Op<T>, const T*, const T*, T*, cudaStream_t);     \
+    template void launch_restrict<T>(const Dims&, const Dims&, const T*, T*, cudaStream_t);         \
+    template void launch_prolong_add<T>(const Dims&, const Dims&, const T*, T*, cudaStream_t);      \
+    template void launch_coarse_apply<T>(int, const double*, const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace fld

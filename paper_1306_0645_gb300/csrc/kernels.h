@@ -1,0 +1,85 @@
+// kernels.h -- host-side launchers of the libfld CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace fld {
+
+// Physical constants of one step, precomputed on the host.
+struct PhysDev {
+    double dt, c, Dmax, Rmin, sigma, adot;
+    double h[3];        // cell widths
+    double dt_h2[3];    // dt / h^2
+    int limiter;        // 0 paper, 1 Levermore-Pomraning
+};
+
+// Operator of one level: mass term m, lower-face weights, inverse diagonal.
+template <class T>
+struct Op {
+    T *m, *wx, *wy, *wz, *invd;
+};
+
+// ---- assembly (k_assemble.cu)
+// Pass 1: opacity, face limiter and weights (FP64, plus FP32 copies of the
+// weights and mass term when op32.m != nullptr); flags invalid inputs.
+void launch_assemble_faces(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
+                           const double* eta, Op<double> op, Op<float> op32, double* sc,
+                           cudaStream_t s);
+// Pass 2: right-hand side b, inverse diagonals (FP64 if op.invd, FP32 if
+// op32.invd) and ||b||^2 into sc[S_BB].
+void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
+                         const double* eta, Op<double> op, Op<float> op32, double* b,
+                         const RedArgs& ra, cudaStream_t s);
+
+// ---- multigrid (k_mg.cu), T = float or double
+void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s);
+template <class T>
+void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s);
+void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s);
+template <class T>
+void launch_smooth_zero(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s);
+template <class T>
+void launch_rb_colour(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s);
+template <class T>
+void launch_jacobi(const Dims& d, Op<T> A, const T* r, const T* z, T* out, double omega,
+                   bool zero_guess, cudaStream_t s);
+template <class T>
+void launch_residual(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s);
+template <class T>
+void launch_restrict(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s);
+template <class T>
+void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s);
+// Coarsest grid: dense matrix, Cholesky, explicit inverse (one CTA).
+void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc,
+                         cudaStream_t s);
+template <class T>
+void launch_coarse_apply(int n, const double* ainv, const T* r, T* z, cudaStream_t s);
+
+// ---- Krylov and refinement (k_cg.cu)
+template <class T>
+void launch_dot(long long n, const T* a, const T* b, const RedArgs& ra, cudaStream_t s);
+template <class T>
+void launch_cg_p_matvec(const Dims& d, Op<T> A, const T* z, const T* p_in, T* p_out, T* q,
+                        const RedArgs& ra, cudaStream_t s);
+template <class T>
+void launch_cg_update(long long n, T* x, T* r, const T* p, const T* q, const RedArgs& ra,
+                      cudaStream_t s);
+template <class T>
+void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s);
+// r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.
+void launch_residual64(const Dims& d, Op<double> A, const double* b, const double* x, double* r,
+                       const RedArgs& ra, cudaStream_t s);
+// r32 = r64 / sc[S_RMAX]; x32 = 0; ||r32||^2 -> S_R0 (and S_RR).
+void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
+                     cudaStream_t s);
+// x64 += sc[S_RMAX] * x32
+void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, cudaStream_t s);
+// E_out = E + dE and the photon balance sums into S_BAL, S_EMIT, S_ABSORB.
+void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
+                     const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
+                     cudaStream_t s);
+void launch_opacity_update(long long n, const double* E, const double* nH, const double* nHI,
+                           double* out, double dt, double c, double sigma, double hnu,
+                           double alpha_B, cudaStream_t s);
+
+}  // namespace fld

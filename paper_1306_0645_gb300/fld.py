@@ -1,0 +1,311 @@
+"""Python binding of libfld.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see
+include/fld.h) and forwards plain pointers and sizes: device tensors are
+passed as ``torch.Tensor`` (CUDA, float64, contiguous), host arrays for
+``fld_step_host`` as numpy float64 arrays.  All arithmetic of the step runs
+in the library's CUDA kernels; if the library cannot be built or loaded the
+import of the first call raises -- there is no other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+FLD_OK, FLD_EINVAL, FLD_ENOMEM, FLD_ENOCONV, FLD_ENONFINITE, FLD_ETIMEOUT, FLD_ECUDA = range(7)
+STATUS_NAMES = {0: "FLD_OK", 1: "FLD_EINVAL", 2: "FLD_ENOMEM", 3: "FLD_ENOCONV",
+                4: "FLD_ENONFINITE", 5: "FLD_ETIMEOUT", 6: "FLD_ECUDA"}
+
+
+class FldError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class fld_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("bc", ctypes.c_int * 3)]
+
+
+class fld_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("c", ctypes.c_double), ("L_unit", ctypes.c_double),
+                ("dmax_coef", ctypes.c_double), ("rmin_coef", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("adot_over_a", ctypes.c_double),
+                ("hnu", ctypes.c_double), ("limiter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("pre", ctypes.c_int),
+                ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("coarse_cap", ctypes.c_int)]
+
+
+class fld_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("balance_abs", ctypes.c_double),
+                ("balance_rel", ctypes.c_double), ("emitted", ctypes.c_double),
+                ("absorbed", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fld_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
+                ("timed", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("timed_bytes", ctypes.c_double)]
+
+
+_P = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "fld_params_default": ([ctypes.POINTER(fld_params)], ctypes.c_int),
+    "fld_footprint_bytes": ([ctypes.POINTER(fld_grid), ctypes.POINTER(fld_params)], ctypes.c_size_t),
+    "fld_create": ([ctypes.POINTER(_VP), ctypes.POINTER(fld_grid), ctypes.POINTER(fld_params), _VP],
+                   ctypes.c_int),
+    "fld_assemble": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "fld_solve": ([_VP, _VP, ctypes.POINTER(fld_info)], ctypes.c_int),
+    "fld_step": ([_VP, _VP, _VP, _VP, ctypes.POINTER(fld_info)], ctypes.c_int),
+    "fld_step_host": ([_VP, _VP, _VP, _VP, ctypes.POINTER(fld_info)], ctypes.c_int),
+    "fld_step_batched": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                          ctypes.POINTER(_VP), ctypes.POINTER(fld_info)], ctypes.c_int),
+    "fld_apply": ([_VP, _VP, _VP], ctypes.c_int),
+    "fld_vcycle": ([_VP, _VP, _VP], ctypes.c_int),
+    "fld_get_system": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "fld_opacity_update": ([ctypes.c_size_t, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
+    "fld_levels": ([ctypes.POINTER(fld_grid), ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
+    "fld_profile": ([_VP, ctypes.c_ulonglong], ctypes.c_int),
+    "fld_profile_read": ([_VP, ctypes.POINTER(fld_kernel_stat), ctypes.c_int], ctypes.c_int),
+    "fld_last_error": ([], ctypes.c_char_p),
+    "fld_destroy": ([_VP], None),
+}
+
+EXPORTS = tuple(_SIGS)
+
+
+def lib():
+    """Load (building first if needed) the in-tree libfld.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            h = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(h, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = h
+    return _lib
+
+
+def fld_last_error() -> str:
+    return lib().fld_last_error().decode()
+
+
+def _check(st: int, what: str):
+    if st != FLD_OK:
+        raise FldError(st, f"{what}: {fld_last_error()}")
+
+
+def _get(o, k, default=None):
+    return o.get(k, default) if isinstance(o, dict) else getattr(o, k, default)
+
+
+def make_grid(g) -> fld_grid:
+    n, h, per = _get(g, "n"), _get(g, "h"), _get(g, "periodic")
+    return fld_grid(int(n[0]), int(n[1]), int(n[2]), float(h[0]), float(h[1]), float(h[2]),
+                    (ctypes.c_int * 3)(*[1 if v else 0 for v in per]))
+
+
+def make_params(p=None, **overrides) -> fld_params:
+    out = fld_params()
+    _check(lib().fld_params_default(ctypes.byref(out)), "fld_params_default")
+    if p is not None:
+        for name, _ in fld_params._fields_:
+            v = _get(p, name)
+            if v is not None:
+                setattr(out, name, type(getattr(out, name))(v))
+    for k, v in overrides.items():
+        setattr(out, k, type(getattr(out, k))(v))
+    return out
+
+
+def _dptr(t, n=None, what="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{what} must be contiguous float64")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, n, what="array"):
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError(f"{what} must be a C-contiguous float64 numpy array")
+    if a.size != n:
+        raise ValueError(f"{what} has {a.size} elements, expected {n}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def fld_footprint_bytes(grid, params) -> int:
+    g, p = make_grid(grid), make_params(params)
+    return int(lib().fld_footprint_bytes(ctypes.byref(g), ctypes.byref(p)))
+
+
+def fld_levels(grid) -> List[tuple]:
+    g = make_grid(grid)
+    dims = (ctypes.c_int * 96)()
+    nl = lib().fld_levels(ctypes.byref(g), dims, 32)
+    return [tuple(dims[3 * l: 3 * l + 3]) for l in range(nl)]
+
+
+class Context:
+    """Owns one fld_ctx: a grid, parameters, a stream and device buffers."""
+
+    def __init__(self, grid, params=None, stream=None, **overrides):
+        import torch
+        self.grid = grid
+        self._g = make_grid(grid)
+        self._p = make_params(params, **overrides)
+        self.n = self._g.nx * self._g.ny * self._g.nz
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = _VP()
+        _check(lib().fld_create(ctypes.byref(handle), ctypes.byref(self._g), ctypes.byref(self._p),
+                                _VP(stream.cuda_stream)), "fld_create")
+        self.handle = handle
+
+    @property
+    def params(self) -> fld_params:
+        return self._p
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().fld_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fld_create(grid, params=None, stream=None, **overrides) -> Context:
+    return Context(grid, params, stream, **overrides)
+
+
+def fld_destroy(ctx: Context):
+    ctx.close()
+
+
+def fld_assemble(ctx: Context, E, nHI, eta):
+    _check(lib().fld_assemble(ctx.handle, _dptr(E, ctx.n, "E"), _dptr(nHI, ctx.n, "n_HI"),
+                              _dptr(eta, ctx.n, "eta")), "fld_assemble")
+
+
+def fld_solve(ctx: Context, dE, check: bool = True) -> dict:
+    info = fld_info()
+    st = lib().fld_solve(ctx.handle, _dptr(dE, ctx.n, "dE"), ctypes.byref(info))
+    if check:
+        _check(st, "fld_solve")
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def fld_step(ctx: Context, E, nHI, eta, check: bool = True) -> dict:
+    info = fld_info()
+    st = lib().fld_step(ctx.handle, _dptr(E, ctx.n, "E"), _dptr(nHI, ctx.n, "n_HI"),
+                        _dptr(eta, ctx.n, "eta"), ctypes.byref(info))
+    if check:
+        _check(st, "fld_step")
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def fld_step_host(ctx: Context, E: np.ndarray, nHI: np.ndarray, eta: np.ndarray,
+                  check: bool = True) -> dict:
+    info = fld_info()
+    st = lib().fld_step_host(ctx.handle, _hptr(E, ctx.n, "E"), _hptr(nHI, ctx.n, "n_HI"),
+                             _hptr(eta, ctx.n, "eta"), ctypes.byref(info))
+    if check:
+        _check(st, "fld_step_host")
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def fld_step_batched(ctxs: Sequence[Context], Es, nHIs, etas, check: bool = True):
+    n = len(ctxs)
+    arr = lambda xs: (_VP * n)(*xs)
+    infos = (fld_info * n)()
+    st = lib().fld_step_batched(n, arr([c.handle for c in ctxs]),
+                                arr([_dptr(e, c.n, "E") for e, c in zip(Es, ctxs)]),
+                                arr([_dptr(e, c.n, "n_HI") for e, c in zip(nHIs, ctxs)]),
+                                arr([_dptr(e, c.n, "eta") for e, c in zip(etas, ctxs)]), infos)
+    if check:
+        _check(st, "fld_step_batched")
+    return st, [i.as_dict() for i in infos]
+
+
+def fld_apply(ctx: Context, x, y):
+    _check(lib().fld_apply(ctx.handle, _dptr(x, ctx.n, "x"), _dptr(y, ctx.n, "y")), "fld_apply")
+
+
+def fld_vcycle(ctx: Context, r, z):
+    _check(lib().fld_vcycle(ctx.handle, _dptr(r, ctx.n, "r"), _dptr(z, ctx.n, "z")), "fld_vcycle")
+
+
+def fld_get_system(ctx: Context, m=None, wx=None, wy=None, wz=None, b=None):
+    ptrs = [None if t is None else _dptr(t, ctx.n) for t in (m, wx, wy, wz, b)]
+    _check(lib().fld_get_system(ctx.handle, *ptrs), "fld_get_system")
+
+
+def fld_opacity_update(E, nH, nHI, out, dt, c, sigma, hnu, alpha_B, stream=None):
+    import torch
+    n = E.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().fld_opacity_update(n, _dptr(E, n, "E"), _dptr(nH, n, "n_H"), _dptr(nHI, n, "n_HI"),
+                                    _dptr(out, n, "out"), float(dt), float(c), float(sigma),
+                                    float(hnu), float(alpha_B), _VP(stream.cuda_stream)),
+           "fld_opacity_update")
+
+
+def fld_params_default() -> fld_params:
+    p = fld_params()
+    _check(lib().fld_params_default(ctypes.byref(p)), "fld_params_default")
+    return p
+
+
+def fld_profile(ctx: Context, class_mask: int = 0):
+    """Reset launch statistics; time the kernel classes in class_mask."""
+    _check(lib().fld_profile(ctx.handle, ctypes.c_ulonglong(class_mask)), "fld_profile")
+
+
+def fld_profile_read(ctx: Context) -> List[dict]:
+    n = lib().fld_profile_read(ctx.handle, None, 0)
+    arr = (fld_kernel_stat * n)()
+    lib().fld_profile_read(ctx.handle, arr, n)
+    out = []
+    for i, k in enumerate(arr):
+        out.append({"cls": i, "name": k.name.decode(), "launches": k.launches, "timed": k.timed,
+                    "ms": k.ms, "bytes": k.bytes, "timed_bytes": k.timed_bytes})
+    return out
