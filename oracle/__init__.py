@@ -254,7 +254,7 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
     sh = _shape(grid)
     E, nHI, eta = _arr(E, sh), _arr(nHI, sh), _arr(eta, sh)
     E_new = E.copy()
-    info = np.zeros(6)
+    info = np.zeros(7)
     g, p, s = _grid(grid), _phys(phys), _solver(solver or {})
     st = _lib_handle().or_step(ctypes.byref(g), ctypes.byref(p), ctypes.byref(s), _ptr(E),
                                _ptr(nHI), _ptr(eta), _ptr(E_new), _ptr(info))
@@ -262,7 +262,7 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
         raise OracleError(st, "step")
     return E_new, {"status": st, "iters": int(info[0]), "rel_res": info[1],
                    "balance_abs": info[2], "balance_rel": info[3],
-                   "emitted": info[4], "absorbed": info[5]}
+                   "emitted": info[4], "absorbed": info[5], "floor_added": info[6]}
 
 
 def num_levels(n):

@@ -45,7 +45,11 @@
  *     pre-sweeps red then black, post-sweeps black then red (symmetric);
  *     weighted Jacobi as the alternative smoother;
  *   - PCG from x0 = 0, stop when ||r||_2 / ||b||_2 <= rtol on the
- *     recursively updated residual; b = 0 gives dE = 0 in 0 iterations.
+ *     recursively updated residual; b = 0 gives dE = 0 in 0 iterations;
+ *   - E^{n+1} = max(E^n + dE, 0): the exact solution is non-negative (A is
+ *     an M-matrix and A E^{n+1} = E^n + dt eta >= 0), so negative values are
+ *     solver-tolerance artefacts; the photon balance is taken on E^n + dE
+ *     before the floor, and the floor's addition is reported.
  *
  * Layout: every field is a contiguous FP64 array, x fastest,
  * idx = i + nx (j + ny k).  The operator of a level is stored as the mass
@@ -687,7 +691,8 @@ int or_pcg(const or_grid* g, const double* m, const double* wx,
 
 /* info[0] iters, [1] true ||b - A dE|| / ||b||, [2] photon imbalance
  * (photons), [3] imbalance relative to the step's photon budget,
- * [4] photons emitted in the step, [5] photons absorbed in the step. */
+ * [4] photons emitted in the step, [5] photons absorbed in the step,
+ * [6] photons added by the E >= 0 floor. */
 int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
             const double* E, const double* nHI, const double* eta,
             double* E_new, double* info) {
@@ -703,16 +708,20 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
     st = or_pcg(g, m, wx, wy, wz, b, dE, s, &iters, &rel, NULL);
     if (st != OR_OK && st != OR_ENOCONV) { free(buf); return st; }
     double V = g->h[0] * g->h[1] * g->h[2];
-    double bal = 0.0, emit = 0.0, absorb = 0.0;
+    double bal = 0.0, emit = 0.0, absorb = 0.0, floor_add = 0.0;
     for (size_t i = 0; i < n; i++) {
         double En = E[i] + dE[i];
         double sink = p->dt * (p->c * nHI[i] * p->sigma + p->adot) * En;
         bal += dE[i] - (p->dt * eta[i] - sink);
         emit += p->dt * eta[i];
         absorb += sink;
+        if (En < 0.0) floor_add -= En;
     }
-    if (st == OR_OK) memcpy(E_new, E, n * sizeof(double));
-    if (st == OR_OK) for (size_t i = 0; i < n; i++) E_new[i] += dE[i];
+    if (st == OR_OK)
+        for (size_t i = 0; i < n; i++) {
+            double En = E[i] + dE[i];
+            E_new[i] = En < 0.0 ? 0.0 : En;
+        }
     double scale = V / p->hnu;
     double budget = emit > absorb ? emit : absorb;
     info[0] = iters;
@@ -721,6 +730,7 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
     info[3] = budget > 0.0 ? fabs(bal) / budget : fabs(bal);
     info[4] = emit * scale;
     info[5] = absorb * scale;
+    info[6] = floor_add * scale;
     free(buf);
     return st;
 }

@@ -270,6 +270,9 @@ def test_photon_balance_and_positivity(oracle, per):
     p = case.params
     s = {"rtol": 1e-8}
     E1, info = oracle.step(case.grid, p, s, case.E, case.nHI, case.eta)
+    # the floor keeps E^{n+1} >= 0 and adds no more than the tolerance allows
+    assert E1.min() >= 0.0
+    assert info["floor_added"] <= 1e-6 * info["emitted"]
     # |imbalance| <= V sqrt(N) ||r|| / h nu, with ||r|| = rel_res ||b||
     op = oracle.assemble(case.grid, p, case.E, case.nHI, case.eta)
     bnorm = np.linalg.norm(op["b"])
