@@ -231,6 +231,9 @@ def main():
     fld.fld_step(ctx, Ecal, nHI, eta)
     stats = fld.fld_profile_read(ctx)
     dom = max(stats, key=lambda k: k["ms"])
+    breakdown = {k["name"]: {"ms": round(k["ms"], 3), "launches": k["launches"],
+                             "GBps": round(k["timed_bytes"] / (k["ms"] * 1e-3) / 1e9, 1) if k["ms"] > 0 else None}
+                 for k in stats if k["launches"] > 0}
     del Ecal
     fld.fld_profile(ctx, 1 << dom["cls"])
 
@@ -272,8 +275,8 @@ def main():
     # ---- plain FP64 multigrid on the same input
     fp64 = None
     if args.fp64_steps > 0:
-        p64 = synth.config4(n=2).params
-        p64.precision = synth.PREC_FP64
+        import dataclasses
+        p64 = dataclasses.replace(pm, precision=synth.PREC_FP64)
         ctx64 = fld.fld_create(case.grid, p64, stream)
         E64 = E0.clone()
         for _ in range(min(args.warmup, 1)):
@@ -322,7 +325,7 @@ def main():
             "rel_res": [i["rel_res"] for i in infos],
             "fp64_mg": fp64,
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
-            "roofline": roofline, "step_roofline_frac": step_frac,
+            "roofline": roofline, "step_roofline_frac": step_frac, "kernel_breakdown_one_step": breakdown,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(out), flush=True)

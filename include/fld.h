@@ -109,6 +109,7 @@ typedef struct {
     double balance_rel;        /* |balance_abs| / max(emitted, absorbed) */
     double emitted;            /* photons emitted in the step, V dt sum eta / h nu */
     double absorbed;           /* photons absorbed in the step */
+    double floor_added;        /* photons added by flooring E^{n+1} at 0 */
     double ms;                 /* device time of the call, ms */
 } fld_info;
 
@@ -146,9 +147,12 @@ fld_status fld_assemble(fld_ctx* ctx, const double* E, const double* n_HI,
  * relative residual. */
 fld_status fld_solve(fld_ctx* ctx, double* dE, fld_info* info);
 
-/* One full step: assemble, solve, and E <- E + dE in place (device,
- * FP64).  On any failure E is left unchanged.  info (may be NULL) also
- * receives the photon balance of the step. */
+/* One full step: assemble, solve, and E <- max(E + dE, 0) in place
+ * (device, FP64).  The floor removes negative values of the size the
+ * solver tolerance allows, so the result is a valid input of the next step;
+ * info->floor_added reports what it added.  On any failure E is left
+ * unchanged.  info (may be NULL) also receives the photon balance of the
+ * step, evaluated on E + dE before the floor. */
 fld_status fld_step(fld_ctx* ctx, double* E, const double* n_HI,
                     const double* eta, fld_info* info);
 

@@ -32,6 +32,7 @@ enum Slot {
     S_BAD,        // > 0: invalid input seen by the assembly
     S_NONFINITE,  // > 0: a reduction produced NaN/Inf
     S_TRUE_RR,    // ||b - A x||^2 recomputed
+    S_FLOOR,      // energy density added by the E >= 0 floor (after S_ABSORB)
     NUM_SLOTS = 32
 };
 
@@ -42,11 +43,12 @@ enum RedOp {
     R_ALPHA,        // alpha = rho / v0
     R_STORE2,       // sc[slot0] = v0, sc[slot1] = v1
     R_STORE3,       // sc[slot0..2] = v0..v2 (slots consecutive from slot0)
+    R_STORE4_FIN,   // sc[S_BAL], sc[S_EMIT], sc[S_ABSORB], sc[S_FLOOR] = v0..v3
     R_STORE_SUM_MAX // sc[slot0] = v0 (sum), sc[slot1] = v1 (max)
 };
 
 struct RedArgs {
-    double* partials;     // >= 3 * max_blocks doubles
+    double* partials;     // >= 4 * RED_MAX_BLOCKS doubles
     unsigned* counter;    // one counter, 0 between reductions
     double* sc;           // scalar slots
     int op;
@@ -55,7 +57,7 @@ struct RedArgs {
 };
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_MAX_BLOCKS = 152 * 8;
+constexpr int RED_MAX_BLOCKS = 16384;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -73,8 +75,10 @@ __device__ __forceinline__ double warp_max(double v) {
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], const bool (&ismax)[NV]) {
     __shared__ double sh[NV][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (nthr + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         v[k] = ismax[k] ? warp_max(v[k]) : warp_sum(v[k]);
@@ -118,6 +122,13 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
         sc[ra.slot1] = v[1];
         bad = !isfinite(v[0]) || !isfinite(v[1]);
         break;
+    case R_STORE4_FIN:
+        sc[S_BAL] = v[0];
+        sc[S_EMIT] = v[1];
+        sc[S_ABSORB] = v[2];
+        sc[S_FLOOR] = v[3];
+        bad = !isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(v[3]);
+        break;
     case R_STORE3:
         sc[ra.slot0] = v[0];
         sc[ra.slot0 + 1] = v[1];
@@ -137,10 +148,13 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], const bool (&ismax)
                                             const RedArgs& ra) {
     block_reduce<NV>(v, ismax);
     __shared__ bool last;
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
+    const int G = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; k++) ra.partials[k * RED_MAX_BLOCKS + blockIdx.x] = v[k];
+        for (int k = 0; k < NV; k++) ra.partials[k * RED_MAX_BLOCKS + bid] = v[k];
         __threadfence();
         unsigned t = atomicAdd(ra.counter, 1u);
         last = (t == (unsigned)(G - 1));
@@ -152,22 +166,54 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], const bool (&ismax)
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         double acc = ismax[k] ? -INFINITY : 0.0;
-        for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        for (int b = tid; b < G; b += nthr) {
             double p = __ldcg(&ra.partials[k * RED_MAX_BLOCKS + b]);
             acc = ismax[k] ? fmax(acc, p) : acc + p;
         }
         w[k] = acc;
     }
     block_reduce<NV>(w, ismax);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         red_finalize(ra, w);
         *ra.counter = 0u;
     }
 }
 
+// Per-thread accumulator of a dot product.  FP64 data accumulate with FMA.
+// FP32 data keep FP64-level accuracy without FP64 arithmetic per element
+// (the FP64 pipe of this GPU is 1/64 of the FP32 one): each product is split
+// exactly into p + e (p = fl(a b), e = fma(a, b, -p)), and the products are
+// summed in a compensated pair (Knuth's two-sum).  Only the per-thread
+// result goes to FP64.  The _rn intrinsics keep the compiler from fusing
+// the error-free steps.
+template <class T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+constexpr int FLAT_MAX_BLOCKS = 152 * 16;
+
 inline int red_blocks(long long n, int threads = RED_THREADS) {
     long long b = (n + threads - 1) / threads;
-    if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+    if (b > FLAT_MAX_BLOCKS) b = FLAT_MAX_BLOCKS;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -179,6 +225,48 @@ inline int grid_blocks(long long n, int threads) {
     if (b < 1) b = 1;
     return (int)b;
 }
+
+// Launch shape of a stencil sweep over one level: a 2-D thread block tiles
+// (x, y), the grid covers the (x, y) tiles times z chunks, and every thread
+// walks k through its chunk (no integer division per cell).
+struct ColShape {
+    dim3 grid, block;
+};
+
+inline int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+inline ColShape col_shape(const Dims& d, int threads = 256, int target_blocks = 152 * 8) {
+    int bx = pow2ceil(d.nx) < 32 ? pow2ceil(d.nx) : 32;
+    int by = threads / bx;
+    if (by > pow2ceil(d.ny)) by = pow2ceil(d.ny);
+    const int gx = (d.nx + bx - 1) / bx, gy = (d.ny + by - 1) / by;
+    long long xy = (long long)gx * gy;
+    long long gz = (target_blocks + xy - 1) / xy;
+    if (gz > d.nz) gz = d.nz;
+    if (xy * gz > RED_MAX_BLOCKS) gz = RED_MAX_BLOCKS / xy;
+    if (gz < 1) gz = 1;
+    ColShape s;
+    s.block = dim3(bx, by, 1);
+    s.grid = dim3(gx, gy, (unsigned)gz);
+    return s;
+}
+
+// Per-thread column walk: defines i, j and loops k over the thread's chunk.
+#define COL_BEGIN(d)                                                                    \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;                                \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;                                \
+    const int kch_ = ((d).nz + (int)gridDim.z - 1) / (int)gridDim.z;                   \
+    const int k0_ = (int)blockIdx.z * kch_;                                             \
+    const int k1_ = min((d).nz, k0_ + kch_);                                            \
+    const bool inb_ = i < (d).nx && j < (d).ny;                                         \
+    const long long nxy_ = (long long)(d).nx * (d).ny;                                  \
+    for (int k = inb_ ? k0_ : k1_; k < k1_; k++) {                                      \
+        const long long c = (long long)k * nxy_ + (long long)j * (d).nx + i;
+#define COL_END }
 
 // Decompose a flat cell index.
 __device__ __forceinline__ void cell_ijk(long long c, const Dims& d, int& i, int& j, int& k) {

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "fld.h"
@@ -50,13 +51,13 @@ enum KClass {
     K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_TO_F32, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
-    K_OPACITY, K_NUM
+    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
     "assemble_faces", "assemble_rhs", "coarsen", "invd", "to_f32", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
-    "opacity_update"};
+    "opacity_update", "coarse_levels", "assemble_fix"};
 
 struct KStat {
     long long launches, timed;
@@ -93,6 +94,8 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
         return set_err(FLD_EINVAL, "grid dimensions must be >= 1 (got %d %d %d)", g->nx, g->ny, g->nz);
     if ((long long)g->nx * g->ny * g->nz > (1LL << 33))
         return set_err(FLD_EINVAL, "grid too large");
+    if ((long long)g->nx * g->ny > (1LL << 22))
+        return set_err(FLD_EINVAL, "an x-y plane may hold at most 4194304 cells");
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
         return set_err(FLD_EINVAL, "cell widths must be finite and > 0");
     for (int a = 0; a < 3; a++)
@@ -160,11 +163,25 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     buf(0, "b", 0, n0 * sizeof(double));
     buf(0, "dE", 0, n0 * sizeof(double));
     if (mixed) buf(0, "r64", 0, n0 * sizeof(double));
+    if (mixed) buf(0, "diag64", 0, n0 * sizeof(double));
+    {
+        Dims d0;
+        d0.nx = g->nx; d0.ny = g->ny; d0.nz = g->nz;
+        d0.px = d0.py = d0.pz = 0;
+        d0.n = (long long)n0;
+        long long blocks = 0;
+        int cap = 0;
+        face_list_shape(d0, p->limiter, &blocks, &cap);
+        if (cap > 0) {
+            buf(0, "flist", 0, (size_t)blocks * cap * sizeof(unsigned));
+            buf(0, "flist", 1, (size_t)blocks * sizeof(unsigned));
+        }
+    }
     for (int q = 0; q < 6; q++) buf(0, "cg", q, n0 * ts);
     const size_t nc = (size_t)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
     buf(0, "dense", 0, nc * nc * sizeof(double));
     buf(0, "dense", 1, nc * nc * sizeof(double));
-    buf(0, "red", 0, 3 * RED_MAX_BLOCKS * sizeof(double));
+    buf(0, "red", 0, 4 * RED_MAX_BLOCKS * sizeof(double));
     buf(0, "red", 1, 256);
     buf(0, "red", 2, NUM_SLOTS * sizeof(double));
 }
@@ -179,6 +196,8 @@ struct fld_ctx {
     int nl;
     Level L[MAX_LEVELS];
     double *b, *dE, *r64;
+    double* diag64;   // mixed mode: FP64 diagonal of the fine operator
+    FaceList flist;   // faces left by the FP32 limiter screen
     void* cg[6];   // r, z, p0, p1, q, x
     int nc;
     double *dense, *ainv;
@@ -277,14 +296,59 @@ Op<double> op_of<double>(Level& L) { return L.A64; }
 template <>
 Op<float> op_of<float>(Level& L) { return L.A32; }
 
+// FP32 sweeps on levels with nx % 4 == 0 use the four-cells-per-thread
+// kernels; everything else the scalar ones.
+template <class T>
+bool use4(const Dims& d) {
+    return std::is_same<T, float>::value && fine4_ok(d);
+}
+template <class T>
+void smooth_zero_any(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (fine4_ok(d)) return launch_smooth_zero4(d, A, r, z, s);
+    }
+    launch_smooth_zero<T>(d, A, r, z, s);
+}
+template <class T>
+void rb_colour_any(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (fine4_ok(d)) return launch_rb_colour4(d, A, r, z, colour, s);
+    }
+    launch_rb_colour<T>(d, A, r, z, colour, s);
+}
+template <class T>
+void residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (fine4_ok(d)) return launch_residual4(d, A, r, z, res, s);
+    }
+    launch_residual<T>(d, A, r, z, res, s);
+}
+
+template <class T>
+void restrict_any(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (fine4_ok(f)) return launch_restrict4(f, c, rf, rc, s);
+    }
+    launch_restrict<T>(f, c, rf, rc, s);
+}
+template <class T>
+void prolong_any(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (fine4_ok(f)) return launch_prolong_add4(f, c, ec, zf, s);
+    }
+    launch_prolong_add<T>(f, c, ec, zf, s);
+}
+
 // z = B r on level l (zero initial guess).
 template <class T>
 void vcycle(fld_ctx* c, int l, const T* r, T* z) {
     Level& L = c->L[l];
     cudaStream_t s = c->s;
     const double n = (double)L.d.n, ts = sizeof(T);
+    // launches on levels below the finest are accounted as one class
+    auto kc = [&](int cls) { return l == 0 ? cls : (int)K_COARSE_LEVELS; };
     if (l == c->nl - 1) {
-        KScope k(c, K_COARSE_APPLY, n * n * 8.0 + 2.0 * n * ts);
+        KScope k(c, kc(K_COARSE_APPLY), n * n * 8.0 + 2.0 * n * ts);
         launch_coarse_apply<T>((int)L.d.n, c->ainv, r, z, s);
         return;
     }
@@ -293,20 +357,20 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z) {
     const fld_params& p = c->p;
     if (p.smoother == FLD_SMOOTH_RBGS) {
         if (p.pre >= 1) {
-            { KScope k(c, K_SMOOTH_ZERO, 6.0 * n * ts); launch_smooth_zero<T>(L.d, A, r, z, s); }
+            { KScope k(c, kc(K_SMOOTH_ZERO), 6.0 * n * ts); smooth_zero_any<T>(L.d, A, r, z, s); }
             for (int it = 1; it < p.pre; it++)
                 for (int colour = 0; colour < 2; colour++) {
-                    KScope k(c, K_RB_COLOUR, 6.5 * n * ts);
-                    launch_rb_colour<T>(L.d, A, r, z, colour, s);
+                    KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
+                    rb_colour_any<T>(L.d, A, r, z, colour, s);
                 }
         } else {
             cudaMemsetAsync(z, 0, L.d.n * sizeof(T), s);
         }
     } else {
         if (p.pre >= 1) {
-            { KScope k(c, K_JACOBI, 3.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, z, p.jacobi_omega, true, s); }
+            { KScope k(c, kc(K_JACOBI), 3.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, z, p.jacobi_omega, true, s); }
             for (int it = 1; it < p.pre; it++) {
-                { KScope k(c, K_JACOBI, 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
+                { KScope k(c, kc(K_JACOBI), 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
                 cudaMemcpyAsync(z, t, L.d.n * sizeof(T), cudaMemcpyDeviceToDevice, s);
             }
         } else {
@@ -315,18 +379,18 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z) {
     }
     Level& C = c->L[l + 1];
     const double nc = (double)C.d.n;
-    { KScope k(c, K_RESIDUAL, 7.0 * n * ts); launch_residual<T>(L.d, A, r, z, t, s); }
-    { KScope k(c, K_RESTRICT, (n + nc) * ts); launch_restrict<T>(L.d, C.d, t, (T*)C.r, s); }
+    { KScope k(c, kc(K_RESIDUAL), 7.0 * n * ts); residual_any<T>(L.d, A, r, z, t, s); }
+    { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
-    { KScope k(c, K_PROLONG, (2.0 * n + nc) * ts); launch_prolong_add<T>(L.d, C.d, (const T*)C.z, z, s); }
+    { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts); prolong_any<T>(L.d, C.d, (const T*)C.z, z, s); }
     for (int it = 0; it < p.post; it++) {
         if (p.smoother == FLD_SMOOTH_RBGS) {
             for (int colour = 1; colour >= 0; colour--) {
-                KScope k(c, K_RB_COLOUR, 6.5 * n * ts);
-                launch_rb_colour<T>(L.d, A, r, z, colour, s);
+                KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
+                rb_colour_any<T>(L.d, A, r, z, colour, s);
             }
         } else {
-            { KScope k(c, K_JACOBI, 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
+            { KScope k(c, kc(K_JACOBI), 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
             cudaMemcpyAsync(z, t, L.d.n * sizeof(T), cudaMemcpyDeviceToDevice, s);
         }
     }
@@ -352,11 +416,33 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
     for (int k = 1; k <= max_iter; k++) {
         vcycle<T>(c, 0, r, z);
         const double ts = sizeof(T);
-        { KScope ks(c, K_DOT, 2.0 * n * ts); launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s); }
-        { KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
-          launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s); }
-        { KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
-          launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s); }
+        {
+            KScope ks(c, K_DOT, 2.0 * n * ts);
+            if constexpr (std::is_same<T, float>::value) {
+                if (use4<T>(L0.d)) launch_dot4(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
+                else launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
+            } else {
+                launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
+            }
+        }
+        {
+            KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
+            if constexpr (std::is_same<T, float>::value) {
+                if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+                else launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+            } else {
+                launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+            }
+        }
+        {
+            KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
+            if constexpr (std::is_same<T, float>::value) {
+                if (use4<T>(L0.d)) launch_cg_update4(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+                else launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+            } else {
+                launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+            }
+        }
         cur ^= 1;
         fld_status st = read_scalars(c);
         if (st) return st;
@@ -399,6 +485,11 @@ fld_status alloc_ctx(fld_ctx* c) {
         } else if (!strcmp(kind, "b")) c->b = (double*)ptr;
         else if (!strcmp(kind, "dE")) c->dE = (double*)ptr;
         else if (!strcmp(kind, "r64")) c->r64 = (double*)ptr;
+        else if (!strcmp(kind, "diag64")) c->diag64 = (double*)ptr;
+        else if (!strcmp(kind, "flist")) {
+            if (q == 0) c->flist.entries = (unsigned*)ptr;
+            else c->flist.counts = (unsigned*)ptr;
+        }
         else if (!strcmp(kind, "cg")) c->cg[q] = ptr;
         else if (!strcmp(kind, "dense")) { if (q == 0) c->dense = (double*)ptr; else c->ainv = (double*)ptr; }
         else if (!strcmp(kind, "red")) {
@@ -444,32 +535,41 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
         if (st) return st;
         CUDA_TRY(cudaMemcpyAsync(c->dE, c->cg[5], n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
         { KScope k(c, K_RESIDUAL64, 48.0 * n);
-          launch_residual64(c->L[0].d, c->L[0].A64, c->b, c->dE, nullptr,
+          launch_residual64(c->L[0].d, c->L[0].A64, nullptr, c->b, c->dE, nullptr,
                             red(c, R_STORE_SUM_MAX, S_TRUE_RR, S_RMAX), c->s); }
         if ((st = read_scalars(c))) return st;
         inf.rel_res = std::sqrt(c->h_sc[S_TRUE_RR] / bb);
     } else {
-        CUDA_TRY(cudaMemsetAsync(c->dE, 0, n * sizeof(double), c->s));
+        // Iterative refinement: FP64 residual, FP32 inner MG-PCG on the
+        // scaled residual, FP64 update.  The first residual is b itself
+        // (x = 0), whose norm and max |b| the assembly already reduced.
         int inner_total = 0, outer = 0;
+        double r64sq = bb;
+        const double* rsrc = c->b;
         for (;;) {
-            { KScope k(c, K_RESIDUAL64, 56.0 * n);
-              launch_residual64(c->L[0].d, c->L[0].A64, c->b, c->dE, c->r64,
-                                red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
-            if ((st = read_scalars(c))) return st;
-            if (c->h_sc[S_NONFINITE] != 0.0)
-                return set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", outer);
-            inf.rel_res = std::sqrt(c->h_sc[S_R64] / bb);
+            if (outer > 0) {
+                { KScope k(c, K_RESIDUAL64, 56.0 * n);
+                  launch_residual64(c->L[0].d, c->L[0].A64, c->diag64, c->b, c->dE, c->r64,
+                                    red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
+                if ((st = read_scalars(c))) return st;
+                if (c->h_sc[S_NONFINITE] != 0.0)
+                    return set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", outer);
+                r64sq = c->h_sc[S_R64];
+                rsrc = c->r64;
+            }
+            inf.rel_res = std::sqrt(r64sq / bb);
             if (inf.rel_res <= rtol) { conv = true; break; }
             if (inner_total >= c->p.max_iter) break;
             { KScope k(c, K_IR_SCALE, 16.0 * n);
-              launch_ir_scale(n, c->r64, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
+              launch_ir_scale(n, rsrc, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
             if ((st = read_scalars(c))) return st;
             int it = 0;
             bool iconv = false;
             st = pcg<float>(c, c->h_sc[S_R0], c->p.inner_rtol, c->p.max_iter - inner_total, &it, &iconv);
             if (st) return st;
             inner_total += it;
-            { KScope k(c, K_IR_UPDATE, 20.0 * n); launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, c->s); }
+            { KScope k(c, K_IR_UPDATE, (outer == 0 ? 12.0 : 20.0) * n);
+              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, outer == 0, c->s); }
             outer++;
         }
         inf.iters = inner_total;
@@ -494,9 +594,14 @@ fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const d
     if (c->mixed) op32 = L0.A32;
     const double n0 = (double)L0.d.n;
     { KScope k(c, K_ASM_FACES, n0 * (56.0 + (c->mixed ? 16.0 : 0.0)));
-      launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, s); }
+      launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, c->flist, s); }
+    if (c->flist.entries) {
+        KScope k(c, K_ASM_FIX, 0.0);
+        launch_assemble_fix(L0.d, c->pd, E, nHI, L0.A64, op32, c->flist, s);
+    }
     { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 4.0 : 8.0)));
-      launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, red(c, R_STORE1, S_BB), s); }
+      launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr,
+                          red(c, R_STORE_SUM_MAX, S_BB, S_RMAX), s); }
     for (int l = 1; l < c->nl; l++) {
         Level& F = c->L[l - 1];
         Level& C = c->L[l];
@@ -541,7 +646,7 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
         return st;
     }
     const long long n = c->L[0].d.n;
-    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE3, S_BAL), c->s); }
+    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE4_FIN), c->s); }
     CUDA_TRY(cudaEventRecord(c->e1, c->s));
     if ((st = read_scalars(c))) return st;
     const double V = c->g.dx * c->g.dy * c->g.dz;
@@ -549,6 +654,7 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
     inf.balance_abs = c->h_sc[S_BAL] * scale;
     inf.emitted = c->h_sc[S_EMIT] * scale;
     inf.absorbed = c->h_sc[S_ABSORB] * scale;
+    inf.floor_added = c->h_sc[S_FLOOR] * scale;
     const double budget = inf.emitted > inf.absorbed ? inf.emitted : inf.absorbed;
     inf.balance_rel = budget > 0.0 ? std::fabs(inf.balance_abs) / budget : std::fabs(inf.balance_abs);
     float ms = 0.f;
@@ -629,6 +735,13 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     c->nc = (int)c->L[c->nl - 1].d.n;
     st = alloc_ctx(c);
     if (st) { free_ctx(c); return st; }
+    {
+        long long blocks = 0;
+        int cap = 0;
+        face_list_shape(c->L[0].d, p->limiter, &blocks, &cap);
+        c->flist.cap = cap;
+        if (cap == 0) c->flist.entries = c->flist.counts = nullptr;
+    }
     if (cudaMallocHost(&c->h_sc, NUM_SLOTS * sizeof(double)) != cudaSuccess ||
         cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) {
         cudaGetLastError();
@@ -649,7 +762,22 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     pd.sigma = p->sigma;
     pd.adot = p->adot_over_a;
     pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
-    for (int a = 0; a < 3; a++) pd.dt_h2[a] = p->dt / (pd.h[a] * pd.h[a]);
+    for (int a = 0; a < 3; a++) {
+        pd.dt_h2[a] = p->dt / (pd.h[a] * pd.h[a]);
+        pd.wmax[a] = pd.dt_h2[a] * pd.Dmax;
+        pd.wmax32[a] = (float)pd.wmax[a];
+        pd.twoL_h32[a] = (float)(2.0 * p->L_unit / pd.h[a]);
+    }
+    pd.dtcs = p->dt * p->c * p->sigma;
+    pd.dta = p->dt * p->adot_over_a;
+    pd.one_dta = 1.0 + pd.dta;
+    pd.sigmaL32 = (float)(p->sigma * p->L_unit);
+    // D = D_max exactly when 9 (kappa_f L)^2 + (R L)^2 <= (c L / D_max)^2;
+    // the FP32 screen accepts a face only 1e-3 inside that bound
+    pd.thr32 = (float)((1.0 / (p->dmax_coef * p->dmax_coef)) * (1.0 - 1e-3));
+    // the FP32 error of (R L)^2 grows with L / h; beyond 1e5 the screen is off
+    for (int a = 0; a < 3; a++)
+        if (!(pd.twoL_h32[a] < 2e5f)) pd.thr32 = -1.0f;
     pd.limiter = p->limiter;
     *out = c;
     return FLD_OK;

@@ -84,35 +84,116 @@ __device__ __forceinline__ double face_D(double E1, double E2, double k1, double
     return p.limiter == 1 ? limiter_lp(E1, E2, k1, k2, h, p) : limiter_paper(E1, E2, k1, k2, h, p);
 }
 
-__device__ __forceinline__ bool bad_value(double v) { return !(v >= 0.0) || !isfinite(v); }
+// Finite and >= 0 (or -0), tested on the bits with integer instructions.
+__device__ __forceinline__ bool valid_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 52) < 0x7FFull || b == 0x8000000000000000ull;
+}
+
+// FP32 value of a finite non-negative double by exponent rebias and
+// mantissa truncation, with integer instructions only (no FP64 pipe);
+// ok becomes false outside the FP32 normal range.
+__device__ __forceinline__ float f32_trunc(double x, bool& ok) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if ((b << 1) == 0ull) return 0.0f;
+    ok = ok && e >= 1023 - 126 && e <= 1023 + 127;
+    const unsigned int fb = ((unsigned int)(b >> 32) & 0x80000000u) |
+                            ((unsigned int)(e - 896) << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
+    return __int_as_float((int)fb);
+}
+
+// The two face energies as FP32 numbers sharing one power-of-two scale (the
+// larger one's FP64 exponent maps to 2^0), by integer instructions only.
+// The screen needs only their ratio, so E far below the FP32 range (a
+// radiation field decaying over many steps) is screened all the same; a
+// value 2^-126 or more below the other flushes to 0, which leaves the
+// ratio |E2 - E1| / (E1 + E2) within FP32 rounding.  ok is false for
+// negative or non-finite input.
+__device__ __forceinline__ void pair32(double a, double b, float& fa, float& fb, bool& ok) {
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+    ok = ok && (ba >> 52) < 0x7FFull && (bb >> 52) < 0x7FFull;   // >= +0 and finite
+    const int ea = (int)(ba >> 52), eb = (int)(bb >> 52);
+    const int emax = ea > eb ? ea : eb;
+    auto conv = [&](unsigned long long bits, int e) {
+        const int ne = e - emax + 127;
+        if (e == 0 || ne <= 0) return 0.0f;
+        return __int_as_float((int)(((unsigned int)ne << 23) | (unsigned int)((bits >> 29) & 0x7FFFFFu)));
+    };
+    fa = conv(ba, ea);
+    fb = conv(bb, eb);
+}
+
+// FP32 screen of the square-root-sum limiter: true only if the face is
+// certainly capped, D = D_max, i.e. 9 (kappa_f L)^2 + (R L)^2 lies below
+// the threshold with a margin far above the FP32 error of the estimate.
+__device__ __forceinline__ bool capped32(float e1, float e2, float kL1, float kL2, float twoL_h,
+                                         float thr) {
+    const float esum = e1 + e2;
+    if (!(esum > 0.0f)) return false;
+    const float kf = (kL1 > 0.0f && kL2 > 0.0f) ? __fdividef(2.0f * kL1 * kL2, kL1 + kL2) : 0.0f;
+    const float RL = __fdividef(fabsf(e2 - e1) * twoL_h, esum);
+    const float X = 9.0f * kf * kf + RL * RL;
+    return X < thr;
+}
 
 __global__ void __launch_bounds__(256) k_assemble_faces(Dims d, PhysDev p, const double* __restrict__ E,
                                                        const double* __restrict__ nHI,
                                                        const double* __restrict__ eta, Op<double> op,
-                                                       Op<float> op32, double* sc) {
-    const long long sx = 1, sy = d.nx, sz = (long long)d.nx * d.ny;
+                                                       Op<float> op32, double* sc, FaceList fl) {
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     bool bad = false;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n;
-         c += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, d, i, j, k);
+    const bool screen = p.limiter == 0;
+    __shared__ unsigned s_cnt;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    if (tid == 0) s_cnt = 0u;
+    __syncthreads();
+    unsigned* seg = fl.entries ? fl.entries + bid * fl.cap : nullptr;
+    COL_BEGIN(d)
         const double Ec = E[c], nc = nHI[c];
-        bad |= bad_value(Ec) || bad_value(nc) || bad_value(eta[c]);
+        bad |= !valid_bits(Ec) || !valid_bits(nc) || !valid_bits(eta[c]);
         const double kc = nc * p.sigma;
-        const double m = 1.0 + p.dt * (p.c * kc + p.adot);
+        const double m = fma(p.dtcs, nc, p.one_dta);
+        bool okc = true;
+        const float kL32 = f32_trunc(nc, okc) * p.sigmaL32;
         double w[3];
+        float w32[3];
         const int ijk[3] = {i, j, k};
         const int nn[3] = {d.nx, d.ny, d.nz};
         const int per[3] = {d.px, d.py, d.pz};
-        const long long st[3] = {sx, sy, sz};
+        const long long st[3] = {1, sy, sz};
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             long long lo;
             if (ijk[a] > 0) lo = c - st[a];
             else if (per[a]) lo = c + (long long)(nn[a] - 1) * st[a];
-            else { w[a] = 0.0; continue; }
-            const double D = face_D(E[lo], Ec, nHI[lo] * p.sigma, kc, p.h[a], p);
+            else { w[a] = 0.0; w32[a] = 0.0f; continue; }
+            const double El = E[lo], nl = nHI[lo];
+            bool ok = okc;
+            float el32, e32;
+            pair32(El, Ec, el32, e32, ok);
+            const float kLl = f32_trunc(nl, ok) * p.sigmaL32;
+            if (screen && ok && capped32(el32, e32, kLl, kL32, p.twoL_h32[a], p.thr32)) {
+                w[a] = p.wmax[a];
+                w32[a] = p.wmax32[a];
+                continue;
+            }
+            // queue the face for the compacted FP64 pass; compute it here
+            // only if this block's list is full
+            if (seg) {
+                const unsigned pos = atomicAdd(&s_cnt, 1u);
+                if (pos < (unsigned)fl.cap) {
+                    seg[pos] = ((unsigned)c << 2) | (unsigned)a;
+                    w[a] = 0.0;
+                    w32[a] = 0.0f;
+                    continue;
+                }
+            }
+            const double D = face_D(El, Ec, nl * p.sigma, kc, p.h[a], p);
             w[a] = p.dt_h2[a] * D;
+            w32[a] = (float)w[a];
         }
         op.m[c] = m;
         op.wx[c] = w[0];
@@ -120,77 +201,117 @@ __global__ void __launch_bounds__(256) k_assemble_faces(Dims d, PhysDev p, const
         op.wz[c] = w[2];
         if (op32.m) {
             op32.m[c] = (float)m;
-            op32.wx[c] = (float)w[0];
-            op32.wy[c] = (float)w[1];
-            op32.wz[c] = (float)w[2];
+            op32.wx[c] = w32[0];
+            op32.wy[c] = w32[1];
+            op32.wz[c] = w32[2];
         }
     }
     if (bad) sc[S_BAD] = 1.0;
+    __syncthreads();
+    if (tid == 0 && seg) fl.counts[bid] = s_cnt < (unsigned)fl.cap ? s_cnt : (unsigned)fl.cap;
 }
 
+// The faces the screen left: FP64 limiter with whole warps busy.  Entry
+// = (cell << 2) | axis; the face couples the cell with its lower
+// neighbour along the axis (wrapping on a periodic axis; zero-gradient
+// boundary faces are never listed).
+__global__ void __launch_bounds__(256) k_assemble_fix(Dims d, PhysDev p, const double* __restrict__ E,
+                                                     const double* __restrict__ nHI, Op<double> op,
+                                                     Op<float> op32, FaceList fl) {
+    const unsigned cnt = fl.counts[blockIdx.x];
+    const unsigned* seg = fl.entries + (long long)blockIdx.x * fl.cap;
+    const unsigned nx = (unsigned)d.nx, ny = (unsigned)d.ny, nz = (unsigned)d.nz;
+    const unsigned nxy = nx * ny;
+    for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const unsigned e = seg[t];
+        const unsigned cu = e >> 2;
+        const int a = (int)(e & 3u);
+        const long long c = cu;
+        long long lo;
+        if (a == 0) lo = (cu % nx) > 0 ? c - 1 : c + (nx - 1);
+        else if (a == 1) lo = ((cu / nx) % ny) > 0 ? c - nx : c + (long long)(ny - 1) * nx;
+        else lo = (cu / nxy) > 0 ? c - nxy : c + (long long)(nz - 1) * nxy;
+        const double D = face_D(E[lo], E[c], nHI[lo] * p.sigma, nHI[c] * p.sigma, p.h[a], p);
+        const double w = p.dt_h2[a] * D;
+        double* W = a == 0 ? op.wx : (a == 1 ? op.wy : op.wz);
+        W[c] = w;
+        if (op32.m) {
+            float* W32 = a == 0 ? op32.wx : (a == 1 ? op32.wy : op32.wz);
+            W32[c] = (float)w;
+        }
+    }
+}
+
+// Right-hand side and inverse diagonal.  In mixed mode the FP32 diagonal
+// comes from the FP32 weights, so no FP64 division is needed.
 __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p, const double* __restrict__ E,
                                                              const double* __restrict__ nHI,
                                                              const double* __restrict__ eta, Op<double> op,
                                                              Op<float> op32, double* __restrict__ b,
-                                                             RedArgs ra) {
+                                                             double* __restrict__ diag64, RedArgs ra) {
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    double acc[1] = {0.0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n;
-         c += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, d, i, j, k);
+    double acc[2] = {0.0, 0.0};
+    COL_BEGIN(d)
         const double Ec = E[c];
         double flux = 0.0, wsum = 0.0;
-        // x faces
-        {
-            const double wl = op.wx[c];
-            if (i > 0) flux += wl * (E[c - 1] - Ec);
-            else if (d.px) flux += wl * (E[c + d.nx - 1] - Ec);
-            const long long up = (i < d.nx - 1) ? c + 1 : (d.px ? c - (d.nx - 1) : -1);
-            const double wu = up >= 0 ? op.wx[up] : 0.0;
-            if (up >= 0) flux += wu * (E[up] - Ec);
-            wsum += wl + wu;
+        float wsum32 = 0.0f;
+        const bool f64diag = op.invd != nullptr || diag64 != nullptr;
+#define FACE(WARR, W32ARR, wi, nb)                                 \
+        {                                                          \
+            const double w_ = op.WARR[wi];                         \
+            flux = fma(w_, E[nb] - Ec, flux);                      \
+            if (f64diag) wsum += w_;                               \
+            if (op32.invd) wsum32 += op32.W32ARR[wi];              \
         }
-        {
-            const double wl = op.wy[c];
-            if (j > 0) flux += wl * (E[c - sy] - Ec);
-            else if (d.py) flux += wl * (E[c + (long long)(d.ny - 1) * sy] - Ec);
-            const long long up = (j < d.ny - 1) ? c + sy : (d.py ? c - (long long)(d.ny - 1) * sy : -1);
-            const double wu = up >= 0 ? op.wy[up] : 0.0;
-            if (up >= 0) flux += wu * (E[up] - Ec);
-            wsum += wl + wu;
-        }
-        {
-            const double wl = op.wz[c];
-            if (k > 0) flux += wl * (E[c - sz] - Ec);
-            else if (d.pz) flux += wl * (E[c + (long long)(d.nz - 1) * sz] - Ec);
-            const long long up = (k < d.nz - 1) ? c + sz : (d.pz ? c - (long long)(d.nz - 1) * sz : -1);
-            const double wu = up >= 0 ? op.wz[up] : 0.0;
-            if (up >= 0) flux += wu * (E[up] - Ec);
-            wsum += wl + wu;
-        }
-        const double sink = p.dt * (p.c * nHI[c] * p.sigma + p.adot);
-        const double bc = p.dt * eta[c] - sink * Ec + flux;
+        if (i > 0) FACE(wx, wx, c, c - 1) else if (d.px) FACE(wx, wx, c, c + d.nx - 1)
+        if (i < d.nx - 1) FACE(wx, wx, c + 1, c + 1) else if (d.px) FACE(wx, wx, c - (d.nx - 1), c - (d.nx - 1))
+        if (j > 0) FACE(wy, wy, c, c - sy) else if (d.py) FACE(wy, wy, c, c + (long long)(d.ny - 1) * sy)
+        if (j < d.ny - 1) FACE(wy, wy, c + sy, c + sy) else if (d.py) FACE(wy, wy, c - (long long)(d.ny - 1) * sy, c - (long long)(d.ny - 1) * sy)
+        if (k > 0) FACE(wz, wz, c, c - sz) else if (d.pz) FACE(wz, wz, c, c + (long long)(d.nz - 1) * sz)
+        if (k < d.nz - 1) FACE(wz, wz, c + sz, c + sz) else if (d.pz) FACE(wz, wz, c - (long long)(d.nz - 1) * sz, c - (long long)(d.nz - 1) * sz)
+#undef FACE
+        const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
+        const double bc = fma(p.dt, eta[c], -sink) + flux;
         b[c] = bc;
-        acc[0] += bc * bc;
-        const double diag = op.m[c] + wsum;
-        if (op.invd) op.invd[c] = 1.0 / diag;
-        if (op32.invd) op32.invd[c] = 1.0f / (float)diag;
+        acc[0] = fma(bc, bc, acc[0]);
+        acc[1] = fmax(acc[1], fabs(bc));
+        if (op.invd) op.invd[c] = 1.0 / (op.m[c] + wsum);
+        if (diag64) diag64[c] = op.m[c] + wsum;
+        if (op32.invd) op32.invd[c] = 1.0f / (op32.m[c] + wsum32);
     }
-    const bool ismax[1] = {false};
-    grid_reduce<1>(acc, ismax, ra);
+    const bool ismax[2] = {false, true};
+    grid_reduce<2>(acc, ismax, ra);
 }
 
 void launch_assemble_faces(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                            const double* eta, Op<double> op, Op<float> op32, double* sc,
-                           cudaStream_t s) {
-    k_assemble_faces<<<grid_blocks(d.n, 256), 256, 0, s>>>(d, p, E, nHI, eta, op, op32, sc);
+                           FaceList fl, cudaStream_t s) {
+    ColShape sh = col_shape(d);
+    k_assemble_faces<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, sc, fl);
+}
+
+void launch_assemble_fix(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
+                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s) {
+    if (!fl.entries) return;
+    ColShape sh = col_shape(d);
+    const unsigned blocks = sh.grid.x * sh.grid.y * sh.grid.z;
+    k_assemble_fix<<<blocks, 256, 0, s>>>(d, p, E, nHI, op, op32, fl);
+}
+
+void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap) {
+    ColShape sh = col_shape(d);
+    *blocks = (long long)sh.grid.x * sh.grid.y * sh.grid.z;
+    const long long kch = (d.nz + sh.grid.z - 1) / sh.grid.z;
+    const long long cells = (long long)sh.block.x * sh.block.y * kch;
+    // 40% of the block's faces; a fuller block computes the rest in place
+    *cap = (limiter == 0 && d.n <= (1LL << 30)) ? (int)((3 * cells * 2 + 4) / 5) : 0;
 }
 
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
-                         const double* eta, Op<double> op, Op<float> op32, double* b,
+                         const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
                          const RedArgs& ra, cudaStream_t s) {
-    k_assemble_rhs<<<red_blocks(d.n), RED_THREADS, 0, s>>>(d, p, E, nHI, eta, op, op32, b, ra);
+    ColShape sh = col_shape(d);
+    k_assemble_rhs<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, ra);
 }
 
 __global__ void k_opacity_update(long long n, const double* __restrict__ E, const double* __restrict__ nH,

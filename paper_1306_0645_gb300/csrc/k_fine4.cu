@@ -1,0 +1,527 @@
+// k_fine4.cu -- FP32 stencil sweeps of the mixed-precision solve, each
+// thread owning four consecutive cells along x (float4 loads and stores).
+//
+// Every sweep streams its arrays once: a thread walks k through its chunk
+// of planes and keeps the z-neighbour values in registers (one new float4
+// per array and plane), takes the x-neighbours of its four cells from the
+// adjacent lanes with warp shuffles, and reads the y-neighbour rows (which
+// the neighbouring threads of the block stream) through L1.  These are the
+// same operations as the scalar kernels of k_mg.cu / k_cg.cu, restricted to
+// levels whose x extent is a multiple of 4.
+#include "kernels.h"
+
+namespace fld {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p, long long i) {
+    return *reinterpret_cast<const float4*>(p + i);
+}
+__device__ __forceinline__ void st4(float* p, long long i, float4 v) {
+    *reinterpret_cast<float4*>(p + i) = v;
+}
+
+// Geometry of one 4-cell vector on one plane.  Indices of missing
+// neighbours (zero-gradient boundary) point at the cell itself; the matching
+// face weights are zero, so those values never contribute.
+struct Geo {
+    long long c;            // first cell of the vector
+    long long ym, yp;       // first cell of the y-neighbour vectors
+    long long xl, xr;       // left neighbour of element 0, right of element 3
+    long long xr_w;         // weight index of the upper x face of element 3
+    bool has_xr, has_yp;    // upper faces exist
+    bool load_l, load_r;    // x neighbour not held by the adjacent lane
+};
+
+struct Walk {
+    int i4, j, k0, k1, nx4;
+    bool valid;             // owns real cells (else computes on clamped ones)
+    long long nxy;
+};
+
+__device__ __forceinline__ Walk walk_of(const Dims& d) {
+    Walk w;
+    w.nx4 = d.nx >> 2;
+    const int i4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    w.valid = i4 < w.nx4 && j < d.ny;
+    w.i4 = min(i4, w.nx4 - 1);
+    w.j = min(j, d.ny - 1);
+    const int kch = (d.nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    w.k0 = (int)blockIdx.z * kch;
+    w.k1 = min(d.nz, w.k0 + kch);
+    w.nxy = (long long)d.nx * d.ny;
+    return w;
+}
+
+__device__ __forceinline__ Geo geo_of(const Dims& d, const Walk& w, int k) {
+    Geo g;
+    const int i0 = 4 * w.i4;
+    const long long row = (long long)k * w.nxy + (long long)w.j * d.nx;
+    g.c = row + i0;
+    // y
+    if (w.j > 0) g.ym = g.c - d.nx;
+    else g.ym = d.py ? g.c + (long long)(d.ny - 1) * d.nx : g.c;
+    g.has_yp = w.j < d.ny - 1 || d.py;
+    g.yp = (w.j < d.ny - 1) ? g.c + d.nx : (d.py ? g.c - (long long)(d.ny - 1) * d.nx : g.c);
+    // x: left of element 0, right of element 3
+    g.xl = (i0 > 0) ? g.c - 1 : (d.px ? row + d.nx - 1 : g.c);
+    g.has_xr = (i0 + 4 < d.nx) || d.px;
+    g.xr = (i0 + 4 < d.nx) ? g.c + 4 : (d.px ? row : g.c + 3);
+    g.xr_w = (i0 + 4 < d.nx) ? g.c + 4 : row;   // weight of that face (periodic: cell 0's lower face)
+    // the adjacent lane holds the neighbouring vector unless this lane is
+    // the first / last of its block row or the row ends
+    g.load_l = threadIdx.x == 0 || i0 == 0;
+    g.load_r = threadIdx.x == blockDim.x - 1 || i0 + 4 >= d.nx;
+    return g;
+}
+
+// z-neighbour plane offsets (missing: own plane, weight 0)
+__device__ __forceinline__ long long zdn(const Dims& d, int k, long long nxy) {
+    return k > 0 ? -nxy : (d.pz ? (long long)(d.nz - 1) * nxy : 0);
+}
+__device__ __forceinline__ long long zup(const Dims& d, int k, long long nxy) {
+    return k < d.nz - 1 ? nxy : (d.pz ? -(long long)(d.nz - 1) * nxy : 0);
+}
+
+// x-neighbour values of the 4-vector v of array u.
+__device__ __forceinline__ void xnb(const float* __restrict__ u, const Geo& g, float4 v, float& L,
+                                    float& R) {
+    const float l = __shfl_up_sync(FULL, v.w, 1);
+    const float r = __shfl_down_sync(FULL, v.x, 1);
+    L = g.load_l ? u[g.xl] : l;
+    R = g.load_r ? u[g.xr] : r;
+}
+
+// Weight of the upper x face of element 3 (0 on a zero-gradient boundary).
+__device__ __forceinline__ float wx_up(const float* __restrict__ wx, const Geo& g, float4 wv) {
+    const float r = __shfl_down_sync(FULL, wv.x, 1);
+    if (!g.has_xr) return 0.0f;
+    return g.load_r ? wx[g.xr_w] : r;
+}
+
+struct Faces4 {      // the six face weights of each of the four cells
+    float4 xl, xu, yl, yu, zl, zu;
+};
+
+__device__ __forceinline__ Faces4 faces_of(const Op<float>& A, const Geo& g, float4 wxc, float4 wzc,
+                                           float4 wzu, bool has_zu) {
+    Faces4 f;
+    f.xl = wxc;
+    const float xu3 = wx_up(A.wx, g, wxc);
+    f.xu = make_float4(wxc.y, wxc.z, wxc.w, xu3);
+    f.yl = ld4(A.wy, g.c);
+    f.yu = g.has_yp ? ld4(A.wy, g.yp) : make_float4(0.f, 0.f, 0.f, 0.f);
+    f.zl = wzc;
+    f.zu = has_zu ? wzu : make_float4(0.f, 0.f, 0.f, 0.f);
+    return f;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ p, q
+
+// p_out = z + beta p_in;  q = A p_out;  <p_out, q>.
+__global__ void __launch_bounds__(256) k_cg_p_matvec4(Dims d, Op<float> A, const float* __restrict__ z,
+                                                      const float* __restrict__ p_in,
+                                                      float* __restrict__ p_out, float* __restrict__ q,
+                                                      RedArgs ra) {
+    const float beta = (float)ra.sc[S_BETA];
+    const Walk w = walk_of(d);
+    DotAcc<float> da;
+    auto P = [&](long long i) {
+        const float4 a = ld4(z, i), b = ld4(p_in, i);
+        return make_float4(fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y), fmaf(beta, b.z, a.z),
+                           fmaf(beta, b.w, a.w));
+    };
+    auto Ps = [&](long long i) { return fmaf(beta, p_in[i], z[i]); };
+    if (w.k0 < w.k1) {
+        Geo g = geo_of(d, w, w.k0);
+        float4 pc = P(g.c);
+        float4 pd = P(g.c + zdn(d, w.k0, w.nxy));
+        float4 wzc = ld4(A.wz, g.c);
+        for (int k = w.k0; k < w.k1; k++) {
+            if (k > w.k0) g = geo_of(d, w, k);
+            const long long up = zup(d, k, w.nxy);
+            const bool has_zu = k < d.nz - 1 || d.pz;
+            const float4 pu = P(g.c + up);
+            const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : -(long long)(d.nz - 1) * w.nxy * (d.pz ? 1 : 0)));
+            const float4 wxc = ld4(A.wx, g.c);
+            const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
+            // x neighbours of p
+            const float lsh = __shfl_up_sync(FULL, pc.w, 1);
+            const float rsh = __shfl_down_sync(FULL, pc.x, 1);
+            const float L = g.load_l ? Ps(g.xl) : lsh;
+            const float R = g.load_r ? Ps(g.xr) : rsh;
+            const float4 pym = P(g.ym), pyp = P(g.yp);
+            const float4 m = ld4(A.m, g.c);
+            float4 qv;
+#define Q1(X, LX, RX)                                                                   \
+            qv.X = m.X * pc.X + f.xl.X * (pc.X - (LX)) + f.xu.X * (pc.X - (RX)) +       \
+                   f.yl.X * (pc.X - pym.X) + f.yu.X * (pc.X - pyp.X) +                 \
+                   f.zl.X * (pc.X - pd.X) + f.zu.X * (pc.X - pu.X);
+            Q1(x, L, pc.y)
+            Q1(y, pc.x, pc.z)
+            Q1(z, pc.y, pc.w)
+            Q1(w, pc.z, R)
+#undef Q1
+            if (w.valid) {
+                st4(p_out, g.c, pc);
+                st4(q, g.c, qv);
+                da.add(pc.x, qv.x);
+                da.add(pc.y, qv.y);
+                da.add(pc.z, qv.z);
+                da.add(pc.w, qv.w);
+            }
+            pd = pc;
+            pc = pu;
+            wzc = wzu;
+        }
+    }
+    double acc[1] = {da.value()};
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+// ---------------------------------------------------------------- residual
+
+// res = r - A z
+__global__ void __launch_bounds__(256) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
+                                                   const float* __restrict__ z, float* __restrict__ res) {
+    const Walk w = walk_of(d);
+    if (w.k0 >= w.k1) return;
+    Geo g = geo_of(d, w, w.k0);
+    float4 zc = ld4(z, g.c);
+    float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
+    float4 wzc = ld4(A.wz, g.c);
+    for (int k = w.k0; k < w.k1; k++) {
+        if (k > w.k0) g = geo_of(d, w, k);
+        const bool has_zu = k < d.nz - 1 || d.pz;
+        const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
+        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+        const float4 wxc = ld4(A.wx, g.c);
+        const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
+        float L, R;
+        xnb(z, g, zc, L, R);
+        const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
+        const float4 m = ld4(A.m, g.c), rc = ld4(r, g.c);
+        float4 o;
+#define R1(X, LX, RX)                                                                   \
+        o.X = rc.X - (m.X * zc.X + f.xl.X * (zc.X - (LX)) + f.xu.X * (zc.X - (RX)) +    \
+                      f.yl.X * (zc.X - zym.X) + f.yu.X * (zc.X - zyp.X) +               \
+                      f.zl.X * (zc.X - zd.X) + f.zu.X * (zc.X - zu.X));
+        R1(x, L, zc.y)
+        R1(y, zc.x, zc.z)
+        R1(z, zc.y, zc.w)
+        R1(w, zc.z, R)
+#undef R1
+        if (w.valid) st4(res, g.c, o);
+        zd = zc;
+        zc = zu;
+        wzc = wzu;
+    }
+}
+
+// ------------------------------------------------------------- smoothers
+
+// First red/black Gauss-Seidel sweep from z = 0 (see k_smooth_zero): red
+// cells r / diag; black cells (r + sum_f w_f r_nbr / diag_nbr) / diag.
+__global__ void __launch_bounds__(256) k_smooth_zero4(Dims d, Op<float> A, const float* __restrict__ r,
+                                                      float* __restrict__ z) {
+    const Walk w = walk_of(d);
+    if (w.k0 >= w.k1) return;
+    auto U = [&](long long i) {
+        const float4 a = ld4(r, i), b = ld4(A.invd, i);
+        return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+    };
+    auto Us = [&](long long i) { return r[i] * A.invd[i]; };
+    Geo g = geo_of(d, w, w.k0);
+    float4 uc = U(g.c);
+    float4 ud = U(g.c + zdn(d, w.k0, w.nxy));
+    float4 wzc = ld4(A.wz, g.c);
+    for (int k = w.k0; k < w.k1; k++) {
+        if (k > w.k0) g = geo_of(d, w, k);
+        const bool has_zu = k < d.nz - 1 || d.pz;
+        const float4 uu = U(g.c + zup(d, k, w.nxy));
+        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+        const float4 wxc = ld4(A.wx, g.c);
+        const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
+        const float lsh = __shfl_up_sync(FULL, uc.w, 1);
+        const float rsh = __shfl_down_sync(FULL, uc.x, 1);
+        const float L = g.load_l ? Us(g.xl) : lsh;
+        const float R = g.load_r ? Us(g.xr) : rsh;
+        const float4 uym = U(g.ym), uyp = U(g.yp);
+        const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
+        // parity of element 0: red = (i + j + k) even, i0 = 4 i4 is even
+        const bool e0_red = ((w.j + k) & 1) == 0;
+        float4 o;
+#define B1(X, LX, RX)                                                                       \
+        (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * uym.X + f.yu.X * uyp.X +  \
+                 f.zl.X * ud.X + f.zu.X * uu.X))
+        if (e0_red) {
+            o.x = uc.x;
+            o.y = B1(y, uc.x, uc.z);
+            o.z = uc.z;
+            o.w = B1(w, uc.z, R);
+        } else {
+            o.x = B1(x, L, uc.y);
+            o.y = uc.y;
+            o.z = B1(z, uc.y, uc.w);
+            o.w = uc.w;
+        }
+#undef B1
+        if (w.valid) st4(z, g.c, o);
+        ud = uc;
+        uc = uu;
+        wzc = wzu;
+    }
+}
+
+// One colour of a red/black Gauss-Seidel sweep, in place: the cells of the
+// other colour are read, never written, so the in-place update is exact.
+__global__ void __launch_bounds__(256) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
+                                                    float* z, int colour) {
+    const Walk w = walk_of(d);
+    if (w.k0 >= w.k1) return;
+    Geo g = geo_of(d, w, w.k0);
+    float4 zc = ld4(z, g.c);
+    float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
+    float4 wzc = ld4(A.wz, g.c);
+    for (int k = w.k0; k < w.k1; k++) {
+        if (k > w.k0) g = geo_of(d, w, k);
+        const bool has_zu = k < d.nz - 1 || d.pz;
+        const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
+        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+        const float4 wxc = ld4(A.wx, g.c);
+        const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
+        float L, R;
+        xnb(z, g, zc, L, R);
+        const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
+        const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
+        const bool e0_mine = ((w.j + k + colour) & 1) == 0;
+        float4 o = zc;
+#define U1(X, LX, RX)                                                                       \
+        (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * zym.X + f.yu.X * zyp.X +  \
+                 f.zl.X * zd.X + f.zu.X * zu.X))
+        if (e0_mine) {
+            o.x = U1(x, L, zc.y);
+            o.z = U1(z, zc.y, zc.w);
+        } else {
+            o.y = U1(y, zc.x, zc.z);
+            o.w = U1(w, zc.z, R);
+        }
+#undef U1
+        // z-neighbour values are of the other colour in the planes k +- 1
+        // and are not modified by this sweep, so rotating the loaded values
+        // is exact
+        if (w.valid) st4(z, g.c, o);
+        zd = o;
+        zc = zu;
+        wzc = wzu;
+    }
+}
+
+// ---------------------------------------------------------------- transfers
+
+// Full-weighting restriction rc = P^T rf / 8 (see k_restrict): per axis the
+// fine taps 2I-1, 2I, 2I+1, 2I+2 with weights 1/4, 3/4, 3/4, 1/4, a tap
+// outside a zero-gradient boundary folding onto the boundary cell and one
+// outside a periodic boundary wrapping.  A thread owns coarse cells 2t and
+// 2t+1 of a row and walks coarse planes, keeping the x-y sums of the two
+// fine planes it shares with the next coarse plane.
+__device__ __forceinline__ int fold(int f, int n, int periodic) {
+    if (f < 0) return periodic ? f + n : 0;
+    if (f >= n) return periodic ? f - n : n - 1;
+    return f;
+}
+
+// x-y weighted sums of fine plane fz for coarse cells (2t, J) and (2t+1, J)
+__device__ __forceinline__ float2 xy_sum(const Dims& f, const float* __restrict__ rf, int t, int J,
+                                         int fz, bool load_l, bool load_r) {
+    const float wv[4] = {0.25f, 0.75f, 0.75f, 0.25f};
+    float2 acc = make_float2(0.f, 0.f);
+    const long long plane = (long long)fz * f.nx * f.ny;
+    const int x0 = 4 * t;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int fy = fold(2 * J - 1 + q, f.ny, f.py);
+        const long long row = plane + (long long)fy * f.nx;
+        const float4 v = ld4(rf, row + x0);
+        const float lsh = __shfl_up_sync(FULL, v.w, 1);
+        const float rsh = __shfl_down_sync(FULL, v.x, 1);
+        const float L = load_l ? rf[row + fold(x0 - 1, f.nx, f.px)] : lsh;
+        const float R = load_r ? rf[row + fold(x0 + 4, f.nx, f.px)] : rsh;
+        const float a = 0.25f * L + 0.75f * v.x + 0.75f * v.y + 0.25f * v.z;
+        const float b = 0.25f * v.y + 0.75f * v.z + 0.75f * v.w + 0.25f * R;
+        acc.x = fmaf(wv[q], a, acc.x);
+        acc.y = fmaf(wv[q], b, acc.y);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float* __restrict__ rf,
+                                                   float* __restrict__ rc) {
+    const int ht = cd.nx >> 1;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J0 = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = t0 < ht && J0 < cd.ny;
+    const int t = min(t0, ht - 1), J = min(J0, cd.ny - 1);
+    const int kch = (cd.nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int K0 = (int)blockIdx.z * kch, K1 = min(cd.nz, K0 + kch);
+    if (K0 >= K1) return;
+    // the adjacent lane holds the neighbouring fine float4 of the same row
+    // unless it is the first / last lane of the block row or the row ends
+    const bool load_l = threadIdx.x == 0 || t == 0;
+    const bool load_r = threadIdx.x == blockDim.x - 1 || t == ht - 1;
+    float2 s0 = xy_sum(f, rf, t, J, fold(2 * K0 - 1, f.nz, f.pz), load_l, load_r);
+    float2 s1 = xy_sum(f, rf, t, J, 2 * K0, load_l, load_r);
+    for (int K = K0; K < K1; K++) {
+        const float2 s2 = xy_sum(f, rf, t, J, 2 * K + 1, load_l, load_r);
+        const float2 s3 = xy_sum(f, rf, t, J, fold(2 * K + 2, f.nz, f.pz), load_l, load_r);
+        float2 o;
+        o.x = 0.125f * (0.25f * s0.x + 0.75f * s1.x + 0.75f * s2.x + 0.25f * s3.x);
+        o.y = 0.125f * (0.25f * s0.y + 0.75f * s1.y + 0.75f * s2.y + 0.25f * s3.y);
+        if (valid)
+            *reinterpret_cast<float2*>(rc + (long long)K * cd.nx * cd.ny + (long long)J * cd.nx + 2 * t) = o;
+        s0 = s2;
+        s1 = s3;
+    }
+}
+
+// Trilinear prolongation and correction zf += P ec (see k_prolong_add): a
+// thread owns four fine cells along x, which interpolate from coarse cells
+// 2 i4 - 1 .. 2 i4 + 2 of two coarse rows in two coarse planes.
+__global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const float* __restrict__ ec,
+                                                      float* __restrict__ zf) {
+    const Walk w = walk_of(f);
+    if (w.k0 >= w.k1) return;
+    const int I = 2 * w.i4;
+    const int xi[4] = {fold(I - 1, cd.nx, cd.px), I, I + 1, fold(I + 2, cd.nx, cd.px)};
+    const int J0 = w.j >> 1;
+    const int J1 = fold((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
+    const long long cxy = (long long)cd.nx * cd.ny;
+    for (int k = w.k0; k < w.k1; k++) {
+        const int K0 = k >> 1;
+        const int K1 = fold((k & 1) ? K0 + 1 : K0 - 1, cd.nz, cd.pz);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int Jq = (q & 1) ? J1 : J0;
+            const int Kq = (q & 2) ? K1 : K0;
+            const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
+            const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
+            const float cm = ec[row + xi[0]], c0 = ec[row + xi[1]], c1 = ec[row + xi[2]],
+                        cp = ec[row + xi[3]];
+            acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
+            acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
+            acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
+            acc.w = fmaf(wq, 0.75f * c1 + 0.25f * cp, acc.w);
+        }
+        const long long c = (long long)k * w.nxy + (long long)w.j * f.nx + 4 * w.i4;
+        if (w.valid) {
+            float4 z = ld4(zf, c);
+            z.x += acc.x;
+            z.y += acc.y;
+            z.z += acc.z;
+            z.w += acc.w;
+            st4(zf, c, z);
+        }
+    }
+}
+
+// ------------------------------------------------------------ flat vectors
+
+__global__ void __launch_bounds__(RED_THREADS) k_dot4(long long n4, const float* __restrict__ a,
+                                                      const float* __restrict__ b, RedArgs ra) {
+    DotAcc<float> da;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n4;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float4 x = ld4(a, 4 * c), y = ld4(b, 4 * c);
+        da.add(x.x, y.x);
+        da.add(x.y, y.y);
+        da.add(x.z, y.z);
+        da.add(x.w, y.w);
+    }
+    double acc[1] = {da.value()};
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+// x += alpha p;  r -= alpha q;  ||r||^2
+__global__ void __launch_bounds__(RED_THREADS) k_cg_update4(long long n4, float* __restrict__ x,
+                                                            float* __restrict__ r, const float* __restrict__ p,
+                                                            const float* __restrict__ q, RedArgs ra) {
+    const float alpha = (float)ra.sc[S_ALPHA];
+    DotAcc<float> da;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n4;
+         c += (long long)gridDim.x * blockDim.x) {
+        float4 xv = ld4(x, 4 * c), rv = ld4(r, 4 * c);
+        const float4 pv = ld4(p, 4 * c), qv = ld4(q, 4 * c);
+        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+        rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
+        rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
+        st4(x, 4 * c, xv);
+        st4(r, 4 * c, rv);
+        da.add(rv.x, rv.x);
+        da.add(rv.y, rv.y);
+        da.add(rv.z, rv.z);
+        da.add(rv.w, rv.w);
+    }
+    double acc[1] = {da.value()};
+    const bool mx[1] = {false};
+    grid_reduce<1>(acc, mx, ra);
+}
+
+// ---------------------------------------------------------------- launchers
+
+void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s) {
+    k_dot4<<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, a, b, ra);
+}
+void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
+                       const RedArgs& ra, cudaStream_t s) {
+    k_cg_update4<<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, x, r, p, q, ra);
+}
+
+static ColShape shape4(const Dims& d) {
+    Dims h = d;
+    h.nx = d.nx / 4;
+    ColShape s = col_shape(h);
+    return s;
+}
+
+bool fine4_ok(const Dims& d) { return d.nx % 4 == 0 && d.nx >= 16; }
+
+void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
+                         float* q, const RedArgs& ra, cudaStream_t s) {
+    ColShape sh = shape4(d);
+    k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra);
+}
+void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
+                      cudaStream_t s) {
+    ColShape sh = shape4(d);
+    k_residual4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res);
+}
+void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s) {
+    Dims h = c;
+    h.nx = c.nx / 2;
+    ColShape sh = col_shape(h);
+    k_restrict4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc);
+}
+void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s) {
+    ColShape sh = shape4(f);
+    k_prolong_add4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf);
+}
+void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s) {
+    ColShape sh = shape4(d);
+    k_smooth_zero4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z);
+}
+void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
+                       cudaStream_t s) {
+    ColShape sh = shape4(d);
+    k_rb_colour4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour);
+}
+
+}  // namespace fld

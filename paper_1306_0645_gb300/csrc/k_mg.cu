@@ -72,9 +72,8 @@ __device__ __forceinline__ T nbr_sum_prod(const Dims& d, const Op<T>& A, long lo
 // ------------------------------------------------------------ operators
 
 __global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
-    GRID_LOOP(c, cd.n) {
-        int I, J, K;
-        cell_ijk(c, cd, I, J, K);
+    COL_BEGIN(cd)
+        const int I = i, J = j, K = k;
         const long long fx = f.nx, fxy = (long long)f.nx * f.ny;
         const long long base = 2LL * I + fx * 2LL * J + fxy * 2LL * K;
         double ms = 0.0;
@@ -102,9 +101,7 @@ __global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
 
 template <class T>
 __global__ void k_invd(Dims d, Op<T> A, Op<double> A64) {
-    GRID_LOOP(c, d.n) {
-        int i, j, k;
-        cell_ijk(c, d, i, j, k);
+    COL_BEGIN(d)
         double swu, sw;
         // u unused: pass m as a harmless array for the weight sum only
         nbr_sums<double>(d, A64, c, i, j, k, A64.m, swu, sw);
@@ -129,9 +126,7 @@ __global__ void k_to_f32(Dims d, Op<double> A, Op<float> B) {
 // on the fly.
 template <class T>
 __global__ void k_smooth_zero(Dims d, Op<T> A, const T* __restrict__ r, T* __restrict__ z) {
-    GRID_LOOP(c, d.n) {
-        int i, j, k;
-        cell_ijk(c, d, i, j, k);
+    COL_BEGIN(d)
         if (((i + j + k) & 1) == 0) {
             z[c] = r[c] * A.invd[c];
         } else {
@@ -145,15 +140,15 @@ __global__ void k_smooth_zero(Dims d, Op<T> A, const T* __restrict__ r, T* __res
 // the colour.
 template <class T>
 __global__ void k_rb_colour(Dims d, Op<T> A, const T* __restrict__ r, T* z, int colour) {
-    const int hx = d.nx >> 1;
-    const long long nh = d.n >> 1;
-    GRID_LOOP(t, nh) {
-        const long long row = t / hx;
-        const int s = (int)(t - row * hx);
-        const int k = (int)(row / d.ny);
-        const int j = (int)(row - (long long)k * d.ny);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int kch = (d.nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int k0 = (int)blockIdx.z * kch, k1 = min(d.nz, k0 + kch);
+    if (s >= (d.nx >> 1) || j >= d.ny) return;
+    const long long nxy = (long long)d.nx * d.ny;
+    for (int k = k0; k < k1; k++) {
         const int i = 2 * s + ((j + k + colour) & 1);
-        const long long c = i + (long long)d.nx * row;
+        const long long c = (long long)k * nxy + (long long)j * d.nx + i;
         T swu, sw;
         nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
         z[c] = A.invd[c] * (r[c] + swu);
@@ -165,12 +160,10 @@ __global__ void k_rb_colour(Dims d, Op<T> A, const T* __restrict__ r, T* z, int 
 template <class T>
 __global__ void k_jacobi(Dims d, Op<T> A, const T* __restrict__ r, const T* __restrict__ z,
                          T* __restrict__ out, T omega, int zero_guess) {
-    GRID_LOOP(c, d.n) {
+    COL_BEGIN(d)
         if (zero_guess) {
             out[c] = omega * A.invd[c] * r[c];
         } else {
-            int i, j, k;
-            cell_ijk(c, d, i, j, k);
             T swu, sw;
             nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
             const T Az = A.m[c] * z[c] + sw * z[c] - swu;
@@ -182,9 +175,7 @@ __global__ void k_jacobi(Dims d, Op<T> A, const T* __restrict__ r, const T* __re
 template <class T>
 __global__ void k_residual(Dims d, Op<T> A, const T* __restrict__ r, const T* __restrict__ z,
                            T* __restrict__ res) {
-    GRID_LOOP(c, d.n) {
-        int i, j, k;
-        cell_ijk(c, d, i, j, k);
+    COL_BEGIN(d)
         T swu, sw;
         nbr_sums<T>(d, A, c, i, j, k, z, swu, sw);
         res[c] = r[c] - (A.m[c] * z[c] + sw * z[c] - swu);
@@ -205,9 +196,8 @@ __device__ __forceinline__ int fine_tap(int I, int t, int nf, int periodic) {
 template <class T>
 __global__ void k_restrict(Dims f, Dims cd, const T* __restrict__ rf, T* __restrict__ rc) {
     const T wt[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
-    GRID_LOOP(c, cd.n) {
-        int I, J, K;
-        cell_ijk(c, cd, I, J, K);
+    COL_BEGIN(cd)
+        const int I = i, J = j, K = k;
         int fi[4], fj[4], fk[4];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
@@ -244,9 +234,7 @@ __device__ __forceinline__ void coarse_pair(int i, int nc, int periodic, int& I0
 
 template <class T>
 __global__ void k_prolong_add(Dims f, Dims cd, const T* __restrict__ ec, T* __restrict__ zf) {
-    GRID_LOOP(c, f.n) {
-        int i, j, k;
-        cell_ijk(c, f, i, j, k);
+    COL_BEGIN(f)
         int Ix[2], Iy[2], Iz[2];
         coarse_pair(i, cd.nx, cd.px, Ix[0], Ix[1]);
         coarse_pair(j, cd.ny, cd.py, Iy[0], Iy[1]);
@@ -349,39 +337,49 @@ __global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* 
 static const int TPB = 256;
 
 void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s) {
-    k_coarsen<<<grid_blocks(c.n, TPB), TPB, 0, s>>>(f, c, F, C);
+    ColShape sh = col_shape(c);
+    k_coarsen<<<sh.grid, sh.block, 0, s>>>(f, c, F, C);
 }
 template <class T>
 void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s) {
-    k_invd<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, A64);
+    ColShape sh = col_shape(d);
+    k_invd<T><<<sh.grid, sh.block, 0, s>>>(d, A, A64);
 }
 void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s) {
     k_to_f32<<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, B);
 }
 template <class T>
 void launch_smooth_zero(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s) {
-    k_smooth_zero<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z);
+    ColShape sh = col_shape(d);
+    k_smooth_zero<T><<<sh.grid, sh.block, 0, s>>>(d, A, r, z);
 }
 template <class T>
 void launch_rb_colour(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s) {
-    k_rb_colour<T><<<grid_blocks(d.n / 2, TPB), TPB, 0, s>>>(d, A, r, z, colour);
+    Dims h = d;
+    h.nx = d.nx / 2;
+    ColShape sh = col_shape(h);
+    k_rb_colour<T><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour);
 }
 template <class T>
 void launch_jacobi(const Dims& d, Op<T> A, const T* r, const T* z, T* out, double omega,
                    bool zero_guess, cudaStream_t s) {
-    k_jacobi<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z, out, (T)omega, zero_guess ? 1 : 0);
+    ColShape sh = col_shape(d);
+    k_jacobi<T><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, out, (T)omega, zero_guess ? 1 : 0);
 }
 template <class T>
 void launch_residual(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s) {
-    k_residual<T><<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, r, z, res);
+    ColShape sh = col_shape(d);
+    k_residual<T><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res);
 }
 template <class T>
 void launch_restrict(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s) {
-    k_restrict<T><<<grid_blocks(c.n, TPB), TPB, 0, s>>>(f, c, rf, rc);
+    ColShape sh = col_shape(c);
+    k_restrict<T><<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc);
 }
 template <class T>
 void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s) {
-    k_prolong_add<T><<<grid_blocks(f.n, TPB), TPB, 0, s>>>(f, c, ec, zf);
+    ColShape sh = col_shape(f);
+    k_prolong_add<T><<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf);
 }
 void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc,
                          cudaStream_t s) {

@@ -10,6 +10,14 @@ struct PhysDev {
     double dt, c, Dmax, Rmin, sigma, adot;
     double h[3];        // cell widths
     double dt_h2[3];    // dt / h^2
+    double wmax[3];     // dt D_max / h^2, the weight of a capped face
+    double dtcs;        // dt c sigma
+    double one_dta;     // 1 + dt adot/a
+    double dta;         // dt adot/a
+    float wmax32[3];    // FP32 copy of wmax
+    float sigmaL32;     // sigma L_unit
+    float twoL_h32[3];  // 2 L_unit / h
+    float thr32;        // screen threshold on 9 (kappa_f L)^2 + (R L)^2
     int limiter;        // 0 paper, 1 Levermore-Pomraning
 };
 
@@ -19,16 +27,31 @@ struct Op {
     T *m, *wx, *wy, *wz, *invd;
 };
 
+// Per-block lists of the faces the FP32 screen could not settle, finished
+// by a compacted FP64 pass.  entries == nullptr disables the lists.
+struct FaceList {
+    unsigned* entries;   // block b owns entries[b * cap, (b + 1) * cap)
+    unsigned* counts;    // entries used per block
+    int cap;
+};
+
 // ---- assembly (k_assemble.cu)
 // Pass 1: opacity, face limiter and weights (FP64, plus FP32 copies of the
 // weights and mass term when op32.m != nullptr); flags invalid inputs.
 void launch_assemble_faces(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                            const double* eta, Op<double> op, Op<float> op32, double* sc,
-                           cudaStream_t s);
+                           FaceList fl, cudaStream_t s);
+// FP64 limiter for the listed faces (one block per list segment).
+void launch_assemble_fix(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
+                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s);
+// Size of the face lists for a level: blocks of the faces launch and
+// entries per block (0 when lists are not used).
+void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap);
 // Pass 2: right-hand side b, inverse diagonals (FP64 if op.invd, FP32 if
-// op32.invd) and ||b||^2 into sc[S_BB].
+// op32.invd), the FP64 diagonal if diag64, ||b||^2 into slot0 and max |b|
+// into slot1.
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
-                         const double* eta, Op<double> op, Op<float> op32, double* b,
+                         const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
                          const RedArgs& ra, cudaStream_t s);
 
 // ---- multigrid (k_mg.cu), T = float or double
@@ -66,20 +89,38 @@ void launch_cg_update(long long n, T* x, T* r, const T* p, const T* q, const Red
                       cudaStream_t s);
 template <class T>
 void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s);
-// r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.
-void launch_residual64(const Dims& d, Op<double> A, const double* b, const double* x, double* r,
-                       const RedArgs& ra, cudaStream_t s);
+// r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.  diag (may
+// be null) is the stored FP64 diagonal.
+void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
+                       double* r, const RedArgs& ra, cudaStream_t s);
 // r32 = r64 / sc[S_RMAX]; x32 = 0; ||r32||^2 -> S_R0 (and S_RR).
 void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
                      cudaStream_t s);
-// x64 += sc[S_RMAX] * x32
-void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, cudaStream_t s);
-// E_out = E + dE and the photon balance sums into S_BAL, S_EMIT, S_ABSORB.
+// x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32)
+void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
+                      cudaStream_t s);
+// E_out = max(E + dE, 0); photon balance sums into S_BAL, S_EMIT, S_ABSORB
+// and the floor's energy into S_FLOOR.
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
                      cudaStream_t s);
 void launch_opacity_update(long long n, const double* E, const double* nH, const double* nHI,
                            double* out, double dt, double c, double sigma, double hnu,
                            double alpha_B, cudaStream_t s);
+
+// ---- FP32 four-cells-per-thread sweeps (k_fine4.cu); need nx % 4 == 0
+bool fine4_ok(const Dims& d);
+void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
+                         float* q, const RedArgs& ra, cudaStream_t s);
+void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
+                      cudaStream_t s);
+void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s);
+void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
+                       cudaStream_t s);
+void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s);
+void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s);
+void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s);
+void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
+                       const RedArgs& ra, cudaStream_t s);
 
 }  // namespace fld

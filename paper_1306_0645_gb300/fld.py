@@ -50,7 +50,8 @@ class fld_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("balance_abs", ctypes.c_double),
                 ("balance_rel", ctypes.c_double), ("emitted", ctypes.c_double),
-                ("absorbed", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("absorbed", ctypes.c_double), ("floor_added", ctypes.c_double),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -156,6 +156,7 @@ def density_peaks(rho: np.ndarray, count: int, periodic: bool,
     maxima (topped up with the densest remaining cells if there are fewer)."""
     import torch
     import torch.nn.functional as F
+    count = min(count, rho.size)
     t = torch.from_numpy(np.ascontiguousarray(rho)).to(device)[None, None]
     if periodic:
         pad = F.pad(t, (1, 1, 1, 1, 1, 1), mode="circular")
