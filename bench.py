@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=256, help="grid of the CPU-baseline sample")
     ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference-arm sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving leg (Poisson stream, 0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -116,6 +120,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def max_over_ranks(ms, dist, device="cuda"):
+    """Max of a per-rank time over all ranks (the job is as slow as its
+    slowest rank)."""
+    import torch
+    if dist is None:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_hbm_peak():
@@ -253,11 +269,7 @@ def main():
     stats = fld.fld_profile_read(ctx)
     launches = int(sum(k["launches"] for k in stats))
     d = next(k for k in stats if k["cls"] == dom["cls"])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     value = cells * args.steps * world / (total_ms * 1e-3)
 
     peak, peak_kind = measured_hbm_peak()
@@ -306,6 +318,20 @@ def main():
         e2e = {"value": cells * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": 3 * cells * 8,
                "d2h_bytes_per_step": cells * 8}
 
+    # ---- serving: a Poisson stream of independent grids, continuous batching
+    serving_out = None
+    if args.serve_requests > 0:
+        from paper_1306_0645_gb300 import serving
+        reqs = synth.request_stream(count=args.serve_requests, rate=args.serve_rate, seed=5 + rank)
+        srv = serving.Server(budget_bytes=40e9, workers=args.serve_workers)
+        srv.run(synth.request_stream(count=4 * args.serve_workers, rate=1e9, seed=99), realtime=False)
+        res = srv.run(reqs, realtime=True)
+        srv.close()
+        serving_out = serving.summarize(res)
+        serving_out.update({"rate_per_s": args.serve_rate, "workers": args.serve_workers,
+                            "budget_GB": 40, "sizes": [16, 32, 48, 64, 96, 128],
+                            "precision": "mixed", "latency": "arrival to E^{n+1} on the host"})
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and args.cpu_n > 0:
         src = max(1, args.sources * args.cpu_n ** 3 // 512 ** 3)
@@ -327,6 +353,7 @@ def main():
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
             "roofline": roofline, "step_roofline_frac": step_frac, "kernel_breakdown_one_step": breakdown,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "serving": serving_out,
         }
         print(json.dumps(out), flush=True)
     ctx.close()

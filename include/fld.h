@@ -95,6 +95,9 @@ typedef struct {
     int pre, post;             /* smoothing sweeps per level (1, 1) */
     double inner_rtol;         /* mixed mode: inner FP32 solve target (1e-4) */
     int coarse_cap;            /* largest coarsest grid, cells (1024) */
+    int graphs;                /* CUDA graph per CG iteration: 1 on, 0 off,
+                                  -1 auto (grids up to 128^3; default).
+                                  Needs a non-NULL stream. */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -110,6 +113,7 @@ typedef struct {
     double emitted;            /* photons emitted in the step, V dt sum eta / h nu */
     double absorbed;           /* photons absorbed in the step */
     double floor_added;        /* photons added by flooring E^{n+1} at 0 */
+    double rel_change;         /* ||E^{n+1} - E^n||_2 / ||E^{n+1}||_2 */
     double ms;                 /* device time of the call, ms */
 } fld_info;
 
@@ -117,7 +121,8 @@ typedef struct fld_ctx fld_ctx;
 
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
- * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024.
+ * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
+ * graphs -1.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 
@@ -161,6 +166,37 @@ fld_status fld_step(fld_ctx* ctx, double* E, const double* n_HI,
  * or pinned; pinned memory gives full copy bandwidth. */
 fld_status fld_step_host(fld_ctx* ctx, double* E, const double* n_HI,
                          const double* eta, fld_info* info);
+
+/* Change the time step of the context (the operator depends on dt). */
+fld_status fld_set_dt(fld_ctx* ctx, double dt);
+
+/* Radiation subcycling (Sec. 3.3): advance E over t_span in substeps.
+ * A substep whose solve fails (FLD_ENOCONV or FLD_ENONFINITE) is retried at
+ * 0.1 of its time step, leaving E as it was; after a successful substep the
+ * next one is dt * clamp(tau_tol / rel_change, 0.1, growth) (rel_change of
+ * fld_info, the relative change per step in the RMS norm), within
+ * [dt_min, dt_max] and never past t_span.  Fails with the substep's status
+ * when dt falls below dt_min or after max_substeps substeps. */
+typedef struct {
+    double tau_tol;            /* target relative change per substep (1e-4) */
+    double dt_min, dt_max;     /* s; dt_max <= 0: no upper bound */
+    double growth;             /* largest factor between substeps (2) */
+    int max_substeps;          /* (10000) */
+} fld_advance_params;
+
+typedef struct {
+    int status;
+    int substeps;              /* successful substeps */
+    int retries;               /* failed attempts redone at 0.1 dt */
+    int iters;                 /* CG iterations summed over all attempts */
+    double t_done;             /* time advanced (t_span on success) */
+    double dt_next;            /* suggested first dt of the next call */
+    double ms;                 /* wall time of the call, ms */
+} fld_advance_info;
+
+fld_status fld_advance(fld_ctx* ctx, double* E, const double* n_HI, const double* eta,
+                       double t_span, double dt_first, const fld_advance_params* ap,
+                       fld_advance_info* info);
 
 /* Step n independent contexts whose work may overlap on the device.  Each
  * context runs on its own stream; infos[i] receives context i's result.

@@ -100,6 +100,8 @@ def _lib_handle():
                 ("or_prolong_add", [ctypes.POINTER(ctypes.c_int)] * 2 + [_P] * 2, ctypes.c_int),
                 ("or_restrict", [ctypes.POINTER(ctypes.c_int)] * 2 + [_P] * 2, ctypes.c_int),
                 ("or_opacity_update", [ctypes.c_size_t] + [_P] * 4 + [ctypes.c_double] * 5, ctypes.c_int),
+                ("or_advance", [ctypes.POINTER(_Grid), ctypes.POINTER(_Phys), ctypes.POINTER(_Solver)]
+                 + [_P] * 3 + [ctypes.c_double] * 6 + [ctypes.c_int, _P], ctypes.c_int),
             ]:
                 f = getattr(lib, name)
                 f.argtypes = args
@@ -254,7 +256,7 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
     sh = _shape(grid)
     E, nHI, eta = _arr(E, sh), _arr(nHI, sh), _arr(eta, sh)
     E_new = E.copy()
-    info = np.zeros(7)
+    info = np.zeros(8)
     g, p, s = _grid(grid), _phys(phys), _solver(solver or {})
     st = _lib_handle().or_step(ctypes.byref(g), ctypes.byref(p), ctypes.byref(s), _ptr(E),
                                _ptr(nHI), _ptr(eta), _ptr(E_new), _ptr(info))
@@ -262,7 +264,8 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
         raise OracleError(st, "step")
     return E_new, {"status": st, "iters": int(info[0]), "rel_res": info[1],
                    "balance_abs": info[2], "balance_rel": info[3],
-                   "emitted": info[4], "absorbed": info[5], "floor_added": info[6]}
+                   "emitted": info[4], "absorbed": info[5], "floor_added": info[6],
+                   "rel_change": info[7]}
 
 
 def num_levels(n):
@@ -310,3 +313,20 @@ def opacity_update(E, nH, nHI, dt, c, sigma, hnu, alpha_B):
     _lib_handle().or_opacity_update(nHI.size, _ptr(E), _ptr(nH), _ptr(nHI), _ptr(out),
                                     float(dt), float(c), float(sigma), float(hnu), float(alpha_B))
     return out
+
+
+def advance(grid, phys, solver, E, nHI, eta, t_span, dt_first, tau_tol=1e-4, dt_min=3.15576e1,
+            dt_max=0.0, growth=2.0, max_substeps=10000, allow_fail=False):
+    """Subcycled advance over t_span; returns (E, info dict)."""
+    sh = _shape(grid)
+    E = _arr(E, sh).copy()
+    nHI, eta = _arr(nHI, sh), _arr(eta, sh)
+    out = np.zeros(5)
+    g, p, s = _grid(grid), _phys(phys), _solver(solver or {})
+    st = _lib_handle().or_advance(ctypes.byref(g), ctypes.byref(p), ctypes.byref(s), _ptr(E), _ptr(nHI),
+                                  _ptr(eta), float(t_span), float(dt_first), float(tau_tol), float(dt_min),
+                                  float(dt_max), float(growth), int(max_substeps), _ptr(out))
+    if st and not allow_fail:
+        raise OracleError(st, "advance")
+    return E, {"status": st, "substeps": int(out[0]), "retries": int(out[1]), "iters": int(out[2]),
+               "t_done": out[3], "dt_next": out[4]}

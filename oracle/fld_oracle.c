@@ -692,7 +692,8 @@ int or_pcg(const or_grid* g, const double* m, const double* wx,
 /* info[0] iters, [1] true ||b - A dE|| / ||b||, [2] photon imbalance
  * (photons), [3] imbalance relative to the step's photon budget,
  * [4] photons emitted in the step, [5] photons absorbed in the step,
- * [6] photons added by the E >= 0 floor. */
+ * [6] photons added by the E >= 0 floor, [7] relative change of the step
+ * ||E^{n+1} - E^n||_2 / ||E^{n+1}||_2 (on the floored E^{n+1}). */
 int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
             const double* E, const double* nHI, const double* eta,
             double* E_new, double* info) {
@@ -708,7 +709,7 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
     st = or_pcg(g, m, wx, wy, wz, b, dE, s, &iters, &rel, NULL);
     if (st != OR_OK && st != OR_ENOCONV) { free(buf); return st; }
     double V = g->h[0] * g->h[1] * g->h[2];
-    double bal = 0.0, emit = 0.0, absorb = 0.0, floor_add = 0.0;
+    double bal = 0.0, emit = 0.0, absorb = 0.0, floor_add = 0.0, dsq = 0.0, esq = 0.0;
     for (size_t i = 0; i < n; i++) {
         double En = E[i] + dE[i];
         double sink = p->dt * (p->c * nHI[i] * p->sigma + p->adot) * En;
@@ -716,6 +717,9 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
         emit += p->dt * eta[i];
         absorb += sink;
         if (En < 0.0) floor_add -= En;
+        double Ef = En < 0.0 ? 0.0 : En;
+        dsq += dE[i] * dE[i];
+        esq += Ef * Ef;
     }
     if (st == OR_OK)
         for (size_t i = 0; i < n; i++) {
@@ -731,7 +735,59 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
     info[4] = emit * scale;
     info[5] = absorb * scale;
     info[6] = floor_add * scale;
+    info[7] = esq > 0.0 ? sqrt(dsq / esq) : 0.0;
     free(buf);
+    return st;
+}
+
+/* --------------------------------------------------- radiation subcycling */
+
+/* Advance E over t_span in substeps (Sec. 3.3): a substep whose solve does
+ * not converge is redone at 0.1 of its time step; after a successful one the
+ * next time step is dt * clamp(tau_tol / change, 0.1, growth), change being
+ * the relative change of the substep in the RMS norm (the estimator's
+ * target tau_tol), kept within [dt_min, dt_max] (dt_max <= 0: unbounded) and
+ * never past t_span.
+ * out[0] substeps, [1] retries, [2] CG iterations, [3] time advanced,
+ * [4] next time step. */
+int or_advance(const or_grid* g, const or_phys* p0, const or_solver* s, double* E,
+               const double* nHI, const double* eta, double t_span, double dt_first,
+               double tau_tol, double dt_min, double dt_max, double growth,
+               int max_substeps, double* out) {
+    size_t n = ncell(g->n);
+    double* En = (double*)malloc(n * sizeof(double));
+    if (!En) return OR_ENOMEM;
+    or_phys p = *p0;
+    double t = 0.0, dt = dt_first;
+    if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
+    int substeps = 0, retries = 0, iters = 0, st = OR_OK;
+    while (t < t_span) {
+        if (substeps + retries >= max_substeps) { st = OR_ENOCONV; break; }
+        double rest = t_span - t;
+        int last = dt >= rest * (1.0 - 1e-12);
+        double dt_try = last ? rest : dt;
+        p.dt = dt_try;
+        double info[8];
+        st = or_step(g, &p, s, E, nHI, eta, En, info);
+        iters += (int)info[0];
+        if (st == OR_ENOCONV) {
+            retries++;
+            dt = 0.1 * dt_try;
+            if (dt < dt_min) break;
+            st = OR_OK;
+            continue;
+        }
+        if (st) break;
+        memcpy(E, En, n * sizeof(double));
+        t = last ? t_span : t + dt_try;
+        substeps++;
+        double f = info[7] > 0.0 ? tau_tol / info[7] : growth;
+        dt = dt_try * (f < 0.1 ? 0.1 : (f > growth ? growth : f));
+        if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
+        if (dt < dt_min) dt = dt_min;
+    }
+    out[0] = substeps; out[1] = retries; out[2] = iters; out[3] = t; out[4] = dt;
+    free(En);
     return st;
 }
 

@@ -33,6 +33,9 @@ enum Slot {
     S_NONFINITE,  // > 0: a reduction produced NaN/Inf
     S_TRUE_RR,    // ||b - A x||^2 recomputed
     S_FLOOR,      // energy density added by the E >= 0 floor (after S_ABSORB)
+    S_FIRST,      // 1 before the first CG iteration (beta = 0), then 0
+    S_DE2,        // sum dE^2 of the step
+    S_EN2,        // sum (E^{n+1})^2
     NUM_SLOTS = 32
 };
 
@@ -43,12 +46,12 @@ enum RedOp {
     R_ALPHA,        // alpha = rho / v0
     R_STORE2,       // sc[slot0] = v0, sc[slot1] = v1
     R_STORE3,       // sc[slot0..2] = v0..v2 (slots consecutive from slot0)
-    R_STORE4_FIN,   // sc[S_BAL], sc[S_EMIT], sc[S_ABSORB], sc[S_FLOOR] = v0..v3
+    R_STORE6_FIN,   // sc[S_BAL], [S_EMIT], [S_ABSORB], [S_FLOOR], [S_DE2], [S_EN2] = v0..v5
     R_STORE_SUM_MAX // sc[slot0] = v0 (sum), sc[slot1] = v1 (max)
 };
 
 struct RedArgs {
-    double* partials;     // >= 4 * RED_MAX_BLOCKS doubles
+    double* partials;     // >= 6 * RED_MAX_BLOCKS doubles
     unsigned* counter;    // one counter, 0 between reductions
     double* sc;           // scalar slots
     int op;
@@ -105,7 +108,9 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
         break;
     case R_RHO: {
         double rho = v[0];
-        sc[S_BETA] = ra.first ? 0.0 : rho / sc[S_RHO_OLD];
+        const bool first = ra.first || sc[S_FIRST] != 0.0;
+        sc[S_FIRST] = 0.0;
+        sc[S_BETA] = first ? 0.0 : rho / sc[S_RHO_OLD];
         sc[S_RHO] = rho;
         sc[S_RHO_OLD] = rho;
         bad = !isfinite(rho);
@@ -122,12 +127,14 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
         sc[ra.slot1] = v[1];
         bad = !isfinite(v[0]) || !isfinite(v[1]);
         break;
-    case R_STORE4_FIN:
+    case R_STORE6_FIN:
         sc[S_BAL] = v[0];
         sc[S_EMIT] = v[1];
         sc[S_ABSORB] = v[2];
         sc[S_FLOOR] = v[3];
-        bad = !isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(v[3]);
+        sc[S_DE2] = v[4];
+        sc[S_EN2] = v[5];
+        for (int q = 0; q < 6; q++) bad = bad || !isfinite(v[q]);
         break;
     case R_STORE3:
         sc[ra.slot0] = v[0];

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -181,7 +182,7 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     const size_t nc = (size_t)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
     buf(0, "dense", 0, nc * nc * sizeof(double));
     buf(0, "dense", 1, nc * nc * sizeof(double));
-    buf(0, "red", 0, 4 * RED_MAX_BLOCKS * sizeof(double));
+    buf(0, "red", 0, 6 * RED_MAX_BLOCKS * sizeof(double));
     buf(0, "red", 1, 256);
     buf(0, "red", 2, NUM_SLOTS * sizeof(double));
 }
@@ -217,6 +218,15 @@ struct fld_ctx {
     std::vector<Pend> pend;
     std::vector<cudaEvent_t> pool;
     size_t pool_used;
+    // CUDA graphs of one CG iteration, per solver precision (0 FP64, 1 FP32)
+    // and p-buffer parity; the launches each graph holds, for accounting
+    bool use_graphs;
+    bool capturing;
+    bool graphs_broken;
+    cudaGraphExec_t gexec[2][2];
+    std::vector<std::pair<int, double>> glaunch[2][2];
+    std::vector<std::pair<int, double>>* grec;   // launch list being captured
+    double* h_one;   // pinned 1.0, to raise S_FIRST
 };
 
 namespace {
@@ -250,6 +260,10 @@ struct KScope {
     double bytes;
     cudaEvent_t a = nullptr, b = nullptr;
     KScope(fld_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+        if (c->capturing) {   // counted each time the graph is launched
+            c->grec->push_back({cls, bytes});
+            return;
+        }
         c->kstat[cls].launches++;
         c->kstat[cls].bytes += bytes;
         if ((c->tmask >> cls) & 1ULL) {
@@ -339,9 +353,11 @@ void prolong_any(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t 
     launch_prolong_add<T>(f, c, ec, zf, s);
 }
 
-// z = B r on level l (zero initial guess).
+// z = B r on level l (zero initial guess).  If dot is given and the last
+// post-smoothing sweep of this level can carry it, <r, z> goes there (with
+// reduction *dot) and *dot_done is set.
 template <class T>
-void vcycle(fld_ctx* c, int l, const T* r, T* z) {
+void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, bool* dot_done = nullptr) {
     Level& L = c->L[l];
     cudaStream_t s = c->s;
     const double n = (double)L.d.n, ts = sizeof(T);
@@ -386,6 +402,15 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z) {
     for (int it = 0; it < p.post; it++) {
         if (p.smoother == FLD_SMOOTH_RBGS) {
             for (int colour = 1; colour >= 0; colour--) {
+                const bool last = it == p.post - 1 && colour == 0;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (last && dot && use4<T>(L.d)) {
+                        KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
+                        launch_rb_colour4_dot(L.d, A, r, z, colour, *dot, s);
+                        *dot_done = true;
+                        continue;
+                    }
+                }
                 KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
                 rb_colour_any<T>(L.d, A, r, z, colour, s);
             }
@@ -412,17 +437,24 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
     *converged = false;
     *iters = 0;
     CUDA_TRY(cudaMemsetAsync(p[0], 0, n * sizeof(T), c->s));
-    int cur = 0;
-    for (int k = 1; k <= max_iter; k++) {
-        vcycle<T>(c, 0, r, z);
+    // beta = 0 in the first iteration, signalled on the device so that
+    // every iteration launches the same work
+    CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    const int prec = std::is_same<T, float>::value ? 1 : 0;
+    // one CG iteration: V-cycle, <r,z>, p and q = A p, x and r updates, and
+    // the scalars to the pinned host mirror
+    auto iteration = [&](int cur) {
+        const RedArgs dra = red(c, R_RHO);
+        bool dot_done = false;
+        vcycle<T>(c, 0, r, z, &dra, &dot_done);
         const double ts = sizeof(T);
-        {
+        if (!dot_done) {
             KScope ks(c, K_DOT, 2.0 * n * ts);
             if constexpr (std::is_same<T, float>::value) {
-                if (use4<T>(L0.d)) launch_dot4(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
-                else launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
+                if (use4<T>(L0.d)) launch_dot4(n, r, z, red(c, R_RHO), c->s);
+                else launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
             } else {
-                launch_dot<T>(n, r, z, red(c, R_RHO, 0, 0, k == 1), c->s);
+                launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
             }
         }
         {
@@ -443,9 +475,47 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
                 launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
             }
         }
+        cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    };
+    int cur = 0;
+    for (int k = 1; k <= max_iter; k++) {
+        bool launched = false;
+        if (c->use_graphs && !c->graphs_broken && c->tmask == 0) {
+            cudaGraphExec_t& ge = c->gexec[prec][cur];
+            if (!ge) {
+                // capture (records, does not run) and instantiate this parity
+                c->glaunch[prec][cur].clear();
+                c->grec = &c->glaunch[prec][cur];
+                cudaGraph_t g = nullptr;
+                bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    c->capturing = true;
+                    iteration(cur);
+                    c->capturing = false;
+                    ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && g;
+                }
+                if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+                if (!ok) {
+                    cudaGetLastError();
+                    ge = nullptr;
+                    c->graphs_broken = true;
+                }
+            }
+            if (ge) {
+                CUDA_TRY(cudaGraphLaunch(ge, c->s));
+                for (auto& e : c->glaunch[prec][cur]) {
+                    c->kstat[e.first].launches++;
+                    c->kstat[e.first].bytes += e.second;
+                }
+                launched = true;
+            }
+        }
+        if (!launched) iteration(cur);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(c->s));
+        harvest(c);
         cur ^= 1;
-        fld_status st = read_scalars(c);
-        if (st) return st;
         *iters = k;
         if (c->h_sc[S_NONFINITE] != 0.0)
             return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
@@ -509,6 +579,10 @@ void free_ctx(fld_ctx* c) {
         if (c->stage[q]) cudaFree(c->stage[q]);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            if (c->gexec[a][b]) cudaGraphExecDestroy(c->gexec[a][b]);
+    if (c->h_one) cudaFreeHost(c->h_one);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
     delete c;
@@ -630,6 +704,40 @@ fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const d
     return FLD_OK;
 }
 
+
+// Device constants of a step with time step dt (the operator depends on dt
+// through the face weights and the mass term).
+void fill_physdev(fld_ctx* c, double dt) {
+    const fld_params* p = &c->p;
+    const fld_grid* g = &c->g;
+    PhysDev& pd = c->pd;
+    c->p.dt = dt;
+    pd.dt = dt;
+    pd.c = p->c;
+    pd.Dmax = p->dmax_coef * p->c * p->L_unit;
+    pd.Rmin = p->rmin_coef / p->L_unit;
+    pd.sigma = p->sigma;
+    pd.adot = p->adot_over_a;
+    pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
+    for (int a = 0; a < 3; a++) {
+        pd.dt_h2[a] = dt / (pd.h[a] * pd.h[a]);
+        pd.wmax[a] = pd.dt_h2[a] * pd.Dmax;
+        pd.wmax32[a] = (float)pd.wmax[a];
+        pd.twoL_h32[a] = (float)(2.0 * p->L_unit / pd.h[a]);
+    }
+    pd.dtcs = dt * p->c * p->sigma;
+    pd.dta = dt * p->adot_over_a;
+    pd.one_dta = 1.0 + pd.dta;
+    pd.sigmaL32 = (float)(p->sigma * p->L_unit);
+    // D = D_max exactly when 9 (kappa_f L)^2 + (R L)^2 <= (c L / D_max)^2;
+    // the FP32 screen accepts a face only 1e-3 inside that bound
+    pd.thr32 = (float)((1.0 / (p->dmax_coef * p->dmax_coef)) * (1.0 - 1e-3));
+    // the FP32 error of (R L)^2 grows with L / h; beyond 1e5 the screen is off
+    for (int a = 0; a < 3; a++)
+        if (!(pd.twoL_h32[a] < 2e5f)) pd.thr32 = -1.0f;
+    pd.limiter = p->limiter;
+}
+
 fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
     fld_info inf{};
     CUDA_TRY(cudaEventRecord(c->e0, c->s));
@@ -646,7 +754,7 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
         return st;
     }
     const long long n = c->L[0].d.n;
-    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE4_FIN), c->s); }
+    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE6_FIN), c->s); }
     CUDA_TRY(cudaEventRecord(c->e1, c->s));
     if ((st = read_scalars(c))) return st;
     const double V = c->g.dx * c->g.dy * c->g.dz;
@@ -655,6 +763,7 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
     inf.emitted = c->h_sc[S_EMIT] * scale;
     inf.absorbed = c->h_sc[S_ABSORB] * scale;
     inf.floor_added = c->h_sc[S_FLOOR] * scale;
+    inf.rel_change = c->h_sc[S_EN2] > 0.0 ? std::sqrt(c->h_sc[S_DE2] / c->h_sc[S_EN2]) : 0.0;
     const double budget = inf.emitted > inf.absorbed ? inf.emitted : inf.absorbed;
     inf.balance_rel = budget > 0.0 ? std::fabs(inf.balance_abs) / budget : std::fabs(inf.balance_abs);
     float ms = 0.f;
@@ -690,6 +799,7 @@ fld_status fld_params_default(fld_params* p) {
     p->post = 1;
     p->inner_rtol = 1e-4;
     p->coarse_cap = 1024;
+    p->graphs = -1;
     return FLD_OK;
 }
 
@@ -749,36 +859,22 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
         return set_err(FLD_ENOMEM, "pinned scalar buffer or event creation failed");
     }
     memset(c->h_sc, 0, NUM_SLOTS * sizeof(double));
+    if (cudaMallocHost(&c->h_one, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return set_err(FLD_ENOMEM, "pinned allocation failed");
+    }
+    *c->h_one = 1.0;
+    // graphs need a capturable (non-legacy) stream; "auto" uses them where
+    // launch latency matters, grids up to 128^3
+    c->use_graphs = c->s != nullptr &&
+                    (p->graphs == 1 || (p->graphs < 0 && c->L[0].d.n <= (1LL << 21)));
     if (cudaMemsetAsync(c->counter, 0, 256, c->s) != cudaSuccess ||
         cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), c->s) != cudaSuccess) {
         free_ctx(c);
         return set_err(FLD_ECUDA, "initial memset failed");
     }
-    PhysDev& pd = c->pd;
-    pd.dt = p->dt;
-    pd.c = p->c;
-    pd.Dmax = p->dmax_coef * p->c * p->L_unit;
-    pd.Rmin = p->rmin_coef / p->L_unit;
-    pd.sigma = p->sigma;
-    pd.adot = p->adot_over_a;
-    pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
-    for (int a = 0; a < 3; a++) {
-        pd.dt_h2[a] = p->dt / (pd.h[a] * pd.h[a]);
-        pd.wmax[a] = pd.dt_h2[a] * pd.Dmax;
-        pd.wmax32[a] = (float)pd.wmax[a];
-        pd.twoL_h32[a] = (float)(2.0 * p->L_unit / pd.h[a]);
-    }
-    pd.dtcs = p->dt * p->c * p->sigma;
-    pd.dta = p->dt * p->adot_over_a;
-    pd.one_dta = 1.0 + pd.dta;
-    pd.sigmaL32 = (float)(p->sigma * p->L_unit);
-    // D = D_max exactly when 9 (kappa_f L)^2 + (R L)^2 <= (c L / D_max)^2;
-    // the FP32 screen accepts a face only 1e-3 inside that bound
-    pd.thr32 = (float)((1.0 / (p->dmax_coef * p->dmax_coef)) * (1.0 - 1e-3));
-    // the FP32 error of (R L)^2 grows with L / h; beyond 1e5 the screen is off
-    for (int a = 0; a < 3; a++)
-        if (!(pd.twoL_h32[a] < 2e5f)) pd.thr32 = -1.0f;
-    pd.limiter = p->limiter;
+    fill_physdev(c, p->dt);
     *out = c;
     return FLD_OK;
 }
@@ -835,6 +931,64 @@ fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double*
     CUDA_TRY(cudaMemcpyAsync(E, c->stage[0], bytes, cudaMemcpyDeviceToHost, c->s));
     CUDA_TRY(cudaStreamSynchronize(c->s));
     return FLD_OK;
+}
+
+fld_status fld_set_dt(fld_ctx* c, double dt) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!(std::isfinite(dt) && dt > 0.0)) return set_err(FLD_EINVAL, "dt must be finite and > 0");
+    fill_physdev(c, dt);
+    return FLD_OK;
+}
+
+fld_status fld_advance(fld_ctx* c, double* E, const double* nHI, const double* eta, double t_span,
+                       double dt_first, const fld_advance_params* ap, fld_advance_info* info) {
+    if (!c || !ap) return set_err(FLD_EINVAL, "null argument");
+    if (!(t_span > 0.0) || !(dt_first > 0.0) || !(ap->tau_tol > 0.0) || !(ap->growth >= 1.0) ||
+        !(ap->dt_min > 0.0) || ap->max_substeps < 1)
+        return set_err(FLD_EINVAL, "invalid subcycling parameters");
+    const auto t0 = std::chrono::steady_clock::now();
+    fld_advance_info ai{};
+    const double dt_orig = c->p.dt;
+    double t = 0.0, dt = dt_first;
+    if (ap->dt_max > 0.0 && dt > ap->dt_max) dt = ap->dt_max;
+    fld_status st = FLD_OK;
+    while (t < t_span) {
+        if (ai.substeps + ai.retries >= ap->max_substeps) {
+            st = set_err(FLD_ENOCONV, "subcycling stopped after %d substeps", ap->max_substeps);
+            break;
+        }
+        const double rest = t_span - t;
+        const bool last = dt >= rest * (1.0 - 1e-12);
+        const double dt_try = last ? rest : dt;
+        fill_physdev(c, dt_try);
+        fld_info inf{};
+        st = step_impl(c, E, nHI, eta, &inf);
+        ai.iters += inf.iters;
+        if (st == FLD_ENOCONV || st == FLD_ENONFINITE) {
+            ai.retries++;
+            dt = 0.1 * dt_try;
+            if (dt < ap->dt_min) {
+                set_err(st, "substep of %.3e s failed and 0.1 dt is below dt_min", dt_try);
+                break;
+            }
+            st = FLD_OK;
+            continue;
+        }
+        if (st) break;
+        t = last ? t_span : t + dt_try;
+        ai.substeps++;
+        const double f = inf.rel_change > 0.0 ? ap->tau_tol / inf.rel_change : ap->growth;
+        dt = dt_try * (f < 0.1 ? 0.1 : (f > ap->growth ? ap->growth : f));
+        if (ap->dt_max > 0.0 && dt > ap->dt_max) dt = ap->dt_max;
+        if (dt < ap->dt_min) dt = ap->dt_min;
+    }
+    fill_physdev(c, dt_orig);
+    ai.status = st;
+    ai.t_done = t;
+    ai.dt_next = dt;
+    ai.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = ai;
+    return st;
 }
 
 fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E, const double** nHI,

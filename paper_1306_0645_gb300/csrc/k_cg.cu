@@ -164,14 +164,14 @@ __global__ void k_ir_update(long long n, double* __restrict__ x64, const float* 
 }
 
 // E_out = max(E + dE, 0); photon balance sums of the unfloored update
-// (energy density units; the host scales by V / h nu) and the energy the
-// floor adds.
+// (energy density units; the host scales by V / h nu), the energy the
+// floor adds, and sum dE^2, sum E_out^2 for the relative change of the step.
 __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p, const double* __restrict__ E,
                                                           const double* __restrict__ dE,
                                                           const double* __restrict__ nHI,
                                                           const double* __restrict__ eta, double* E_out,
                                                           RedArgs ra) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     GRID_LOOP(c, n) {
         const double d = dE[c];
         const double En = E[c] + d;
@@ -181,10 +181,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p
         acc[1] += emit;
         acc[2] += sink;
         if (En < 0.0) acc[3] -= En;
-        E_out[c] = En < 0.0 ? 0.0 : En;
+        const double Eo = En < 0.0 ? 0.0 : En;
+        acc[4] = fma(d, d, acc[4]);
+        acc[5] = fma(Eo, Eo, acc[5]);
+        E_out[c] = Eo;
     }
-    const bool mx[4] = {false, false, false, false};
-    grid_reduce<4>(acc, mx, ra);
+    const bool mx[6] = {false, false, false, false, false, false};
+    grid_reduce<6>(acc, mx, ra);
 }
 
 // ---------------------------------------------------------------- launchers

@@ -281,45 +281,63 @@ __global__ void __launch_bounds__(256) k_smooth_zero4(Dims d, Op<float> A, const
 
 // One colour of a red/black Gauss-Seidel sweep, in place: the cells of the
 // other colour are read, never written, so the in-place update is exact.
+// With dot (the last sweep of a V-cycle's post-smoothing on the finest
+// level) it also forms <r, z> of the finished z for CG.
+template <bool DOT>
 __global__ void __launch_bounds__(256) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
-                                                    float* z, int colour) {
+                                                    float* z, int colour, RedArgs ra) {
     const Walk w = walk_of(d);
-    if (w.k0 >= w.k1) return;
-    Geo g = geo_of(d, w, w.k0);
-    float4 zc = ld4(z, g.c);
-    float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
-    float4 wzc = ld4(A.wz, g.c);
-    for (int k = w.k0; k < w.k1; k++) {
-        if (k > w.k0) g = geo_of(d, w, k);
-        const bool has_zu = k < d.nz - 1 || d.pz;
-        const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
-        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
-        const float4 wxc = ld4(A.wx, g.c);
-        const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
-        float L, R;
-        xnb(z, g, zc, L, R);
-        const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
-        const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
-        const bool e0_mine = ((w.j + k + colour) & 1) == 0;
-        float4 o = zc;
+    DotAcc<float> da;
+    if (w.k0 < w.k1) {
+        Geo g = geo_of(d, w, w.k0);
+        float4 zc = ld4(z, g.c);
+        float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
+        float4 wzc = ld4(A.wz, g.c);
+        for (int k = w.k0; k < w.k1; k++) {
+            if (k > w.k0) g = geo_of(d, w, k);
+            const bool has_zu = k < d.nz - 1 || d.pz;
+            const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
+            const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+            const float4 wxc = ld4(A.wx, g.c);
+            const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
+            float L, R;
+            xnb(z, g, zc, L, R);
+            const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
+            const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
+            const bool e0_mine = ((w.j + k + colour) & 1) == 0;
+            float4 o = zc;
 #define U1(X, LX, RX)                                                                       \
-        (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * zym.X + f.yu.X * zyp.X +  \
-                 f.zl.X * zd.X + f.zu.X * zu.X))
-        if (e0_mine) {
-            o.x = U1(x, L, zc.y);
-            o.z = U1(z, zc.y, zc.w);
-        } else {
-            o.y = U1(y, zc.x, zc.z);
-            o.w = U1(w, zc.z, R);
-        }
+            (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * zym.X + f.yu.X * zyp.X +  \
+                     f.zl.X * zd.X + f.zu.X * zu.X))
+            if (e0_mine) {
+                o.x = U1(x, L, zc.y);
+                o.z = U1(z, zc.y, zc.w);
+            } else {
+                o.y = U1(y, zc.x, zc.z);
+                o.w = U1(w, zc.z, R);
+            }
 #undef U1
-        // z-neighbour values are of the other colour in the planes k +- 1
-        // and are not modified by this sweep, so rotating the loaded values
-        // is exact
-        if (w.valid) st4(z, g.c, o);
-        zd = o;
-        zc = zu;
-        wzc = wzu;
+            // z-neighbour values are of the other colour in the planes k +- 1
+            // and are not modified by this sweep, so rotating the loaded
+            // values is exact
+            if (w.valid) {
+                st4(z, g.c, o);
+                if (DOT) {
+                    da.add(rc.x, o.x);
+                    da.add(rc.y, o.y);
+                    da.add(rc.z, o.z);
+                    da.add(rc.w, o.w);
+                }
+            }
+            zd = o;
+            zc = zu;
+            wzc = wzu;
+        }
+    }
+    if (DOT) {
+        double acc[1] = {da.value()};
+        const bool mx[1] = {false};
+        grid_reduce<1>(acc, mx, ra);
     }
 }
 
@@ -521,7 +539,12 @@ void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, c
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                        cudaStream_t s) {
     ColShape sh = shape4(d);
-    k_rb_colour4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour);
+    k_rb_colour4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{});
+}
+void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
+                           const RedArgs& ra, cudaStream_t s) {
+    ColShape sh = shape4(d);
+    k_rb_colour4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, ra);
 }
 
 }  // namespace fld

@@ -99,8 +99,9 @@ void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, con
 // x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32)
 void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
                       cudaStream_t s);
-// E_out = max(E + dE, 0); photon balance sums into S_BAL, S_EMIT, S_ABSORB
-// and the floor's energy into S_FLOOR.
+// E_out = max(E + dE, 0); photon balance sums into S_BAL, S_EMIT, S_ABSORB,
+// the floor's energy into S_FLOOR, sum dE^2 into S_DE2, sum E_out^2 into
+// S_EN2 (reduction R_STORE6_FIN).
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
                      cudaStream_t s);
@@ -118,6 +119,9 @@ void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, c
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                        cudaStream_t s);
 void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s);
+// one colour of a sweep followed by <r, z> of the result (reduction ra)
+void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
+                           const RedArgs& ra, cudaStream_t s);
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s);
 void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s);
 void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,

@@ -43,7 +43,7 @@ class fld_params(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("coarse_cap", ctypes.c_int)]
+                ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class fld_info(ctypes.Structure):
@@ -51,6 +51,20 @@ class fld_info(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("balance_abs", ctypes.c_double),
                 ("balance_rel", ctypes.c_double), ("emitted", ctypes.c_double),
                 ("absorbed", ctypes.c_double), ("floor_added", ctypes.c_double),
+                ("rel_change", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fld_advance_params(ctypes.Structure):
+    _fields_ = [("tau_tol", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("growth", ctypes.c_double), ("max_substeps", ctypes.c_int)]
+
+
+class fld_advance_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("substeps", ctypes.c_int), ("retries", ctypes.c_int),
+                ("iters", ctypes.c_int), ("t_done", ctypes.c_double), ("dt_next", ctypes.c_double),
                 ("ms", ctypes.c_double)]
 
     def as_dict(self):
@@ -85,6 +99,9 @@ _SIGS = {
     "fld_opacity_update": ([ctypes.c_size_t, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
     "fld_levels": ([ctypes.POINTER(fld_grid), ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
+    "fld_set_dt": ([_VP, ctypes.c_double], ctypes.c_int),
+    "fld_advance": ([_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                     ctypes.POINTER(fld_advance_params), ctypes.POINTER(fld_advance_info)], ctypes.c_int),
     "fld_profile": ([_VP, ctypes.c_ulonglong], ctypes.c_int),
     "fld_profile_read": ([_VP, ctypes.POINTER(fld_kernel_stat), ctypes.c_int], ctypes.c_int),
     "fld_last_error": ([], ctypes.c_char_p),
@@ -310,3 +327,22 @@ def fld_profile_read(ctx: Context) -> List[dict]:
         out.append({"cls": i, "name": k.name.decode(), "launches": k.launches, "timed": k.timed,
                     "ms": k.ms, "bytes": k.bytes, "timed_bytes": k.timed_bytes})
     return out
+
+
+def fld_set_dt(ctx: Context, dt: float):
+    _check(lib().fld_set_dt(ctx.handle, float(dt)), "fld_set_dt")
+
+
+def fld_advance(ctx: Context, E, nHI, eta, t_span: float, dt_first: float, tau_tol: float = 1e-4,
+                dt_min: float = 1e-6 * 3.15576e7, dt_max: float = 0.0, growth: float = 2.0,
+                max_substeps: int = 10000, check: bool = True) -> dict:
+    """Subcycled advance of E over t_span (see fld_advance in fld.h)."""
+    ap = fld_advance_params(float(tau_tol), float(dt_min), float(dt_max), float(growth), int(max_substeps))
+    info = fld_advance_info()
+    st = lib().fld_advance(ctx.handle, _dptr(E, ctx.n, "E"), _dptr(nHI, ctx.n, "n_HI"), _dptr(eta, ctx.n, "eta"),
+                           float(t_span), float(dt_first), ctypes.byref(ap), ctypes.byref(info))
+    if check:
+        _check(st, "fld_advance")
+    d = info.as_dict()
+    d["status"] = st
+    return d

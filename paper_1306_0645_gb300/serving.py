@@ -1,0 +1,196 @@
+"""Continuous-batching request loop for FLD steps on one GPU.
+
+Independent requests (grids of different sizes, each with its own sources)
+arrive over time.  Worker threads each own a CUDA stream and a set of
+resident contexts (multigrid hierarchies and work buffers, one per grid size
+they have served), so a request's step runs through the C ABI on that
+worker's stream while other requests run on the others: work from requests
+that arrived while others were on the GPU overlaps on the device.
+Admission is by HBM budget: a request is admitted once the device bytes of
+the requests in flight plus its own (context footprint from
+fld_footprint_bytes, plus its fields) fit the budget; a request that can
+never fit is rejected.
+
+Every kernel launch shape depends only on the grid size and parameters and
+every reduction adds in a fixed order, so a request's result is the same,
+bit for bit, whether it runs alone or in the mix.
+"""
+from __future__ import annotations
+
+import dataclasses
+import queue
+import threading
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import fld, synth
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    n: int
+    arrival: float          # s, stream time
+    start: float            # s, when a worker began it
+    finish: float           # s, when its E was back on the host
+    status: int
+    iters: int = 0
+    outer_iters: int = 0
+    rel_res: float = 0.0
+    E: Optional[np.ndarray] = None
+
+    @property
+    def latency_ms(self) -> float:
+        return (self.finish - self.arrival) * 1e3
+
+    @property
+    def wait_ms(self) -> float:
+        return (self.start - self.arrival) * 1e3
+
+
+class Server:
+    """A pool of worker threads stepping requests under an HBM budget."""
+
+    def __init__(self, budget_bytes: float = 40e9, workers: int = 8, keep_results: bool = False,
+                 params: Optional[synth.Params] = None, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.budget = float(budget_bytes)
+        self.workers = workers
+        self.keep = keep_results
+        self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED)
+        self._used = 0.0
+        self._cv = threading.Condition()
+        self._streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
+        self._ctx: List[Dict[int, fld.Context]] = [dict() for _ in range(workers)]
+        self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
+        self._fp_cache: Dict[int, int] = {}
+
+    # ---------------------------------------------------------- admission
+    def footprint(self, n: int) -> int:
+        if n not in self._fp_cache:
+            fp = fld.fld_footprint_bytes(synth.Grid.cube(n), self.params)
+            self._fp_cache[n] = fp + 3 * n ** 3 * 8 if fp else 0
+        return self._fp_cache[n]
+
+    def _admit(self, nbytes: float) -> bool:
+        if nbytes <= 0 or nbytes > self.budget:
+            return False
+        with self._cv:
+            while self._used + nbytes > self.budget:
+                self._cv.wait()
+            self._used += nbytes
+        return True
+
+    def _release(self, nbytes: float):
+        with self._cv:
+            self._used -= nbytes
+            self._cv.notify_all()
+
+    # ----------------------------------------------------------- one step
+    def _context(self, w: int, n: int) -> fld.Context:
+        ctx = self._ctx[w].get(n)
+        if ctx is None:
+            ctx = fld.fld_create(synth.Grid.cube(n), self.params, self._streams[w])
+            self._ctx[w][n] = ctx
+        return ctx
+
+    def _fields(self, r: synth.Request):
+        """E, n_HI and eta of a request on the current stream, built from its
+        payload (source cells and rates)."""
+        torch = self.torch
+        n = r.n
+        cells, rates = synth.request_sources(r)
+        g = synth.Grid.cube(n)
+        E = torch.full((n ** 3,), synth.E0, dtype=torch.float64, device="cuda")
+        nHI = torch.full((n ** 3,), 1e-3, dtype=torch.float64, device="cuda")
+        eta = torch.zeros((n ** 3,), dtype=torch.float64, device="cuda")
+        idx = torch.from_numpy(cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])).cuda()
+        val = torch.from_numpy(rates * synth.HNU_HI / g.volume).cuda()
+        eta.index_put_((idx,), val, accumulate=True)
+        return E, nHI, eta
+
+    def step_one(self, w: int, r: synth.Request, t0: float) -> Result:
+        torch = self.torch
+        start = time.perf_counter() - t0
+        nbytes = self.footprint(r.n)
+        if not self._admit(nbytes):
+            return Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, fld.FLD_ENOMEM)
+        try:
+            with torch.cuda.stream(self._streams[w]):
+                ctx = self._context(w, r.n)
+                E, nHI, eta = self._fields(r)
+                info = fld.fld_step(ctx, E, nHI, eta, check=False)
+                host = self._pinned[w].get(r.n)
+                if host is None:
+                    host = torch.empty(r.n ** 3, dtype=torch.float64, pin_memory=True)
+                    self._pinned[w][r.n] = host
+                host.copy_(E, non_blocking=True)
+                self._streams[w].synchronize()
+                out = host.numpy().copy() if self.keep else None
+        finally:
+            self._release(nbytes)
+        return Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, info["status"],
+                      info["iters"], info["outer_iters"], info["rel_res"], out)
+
+    # ------------------------------------------------------------ the loop
+    def run(self, requests: Sequence[synth.Request], realtime: bool = True) -> List[Result]:
+        """Serve requests as they arrive (arrival times in s from now when
+        realtime, else all at once); returns results in request order."""
+        self.torch.cuda.set_device(self.device)
+        q: "queue.Queue" = queue.Queue()
+        results: Dict[int, Result] = {}
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+
+        def worker(w):
+            self.torch.cuda.set_device(self.device)
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                res = self.step_one(w, item, t0)
+                with lock:
+                    results[item.rid] = res
+
+        threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
+        for t in threads:
+            t.start()
+        order = sorted(requests, key=lambda r: r.arrival)
+        for r in order:
+            if realtime:
+                delay = r.arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            else:
+                r = dataclasses.replace(r, arrival=time.perf_counter() - t0)
+            q.put(r)
+        for _ in threads:
+            q.put(None)
+        for t in threads:
+            t.join()
+        return [results[r.rid] for r in requests]
+
+    def close(self):
+        for d in self._ctx:
+            for ctx in d.values():
+                ctx.close()
+            d.clear()
+
+
+def summarize(results: Sequence[Result]) -> dict:
+    ok = [r for r in results if r.status == fld.FLD_OK]
+    lat = np.array([r.latency_ms for r in ok]) if ok else np.zeros(1)
+    wait = np.array([r.wait_ms for r in ok]) if ok else np.zeros(1)
+    span = (max(r.finish for r in results) - min(r.arrival for r in results)) if results else 0.0
+    cells = sum(r.n ** 3 for r in ok)
+    return {"requests": len(results), "ok": len(ok),
+            "failed": len(results) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "wait_p50_ms": float(np.percentile(wait, 50)), "wait_p99_ms": float(np.percentile(wait, 99)),
+            "solves_per_s": len(ok) / span if span > 0 else None,
+            "cell_solves_per_s": cells / span if span > 0 else None,
+            "span_s": span}

@@ -90,6 +90,7 @@ class Params:
     post: int = 1
     inner_rtol: float = 1e-4
     coarse_cap: int = 1024
+    graphs: int = -1
 
 
 @dataclasses.dataclass
@@ -309,10 +310,22 @@ def request_stream(count: int = 2000, rate: float = 500.0, seed: int = 5,
 
 
 def request_case(r: Request) -> Case:
+    """Host arrays of one request: a uniform neutral medium (n_H = 1e-3) with
+    the request's seeded sources of 5e48 photons/s, mixed precision."""
     c = config_uniform(n=r.n, sources=r.sources, seed=r.seed, centre=False,
                        limiter=LIMITER_PAPER, precision=PREC_MIXED)
     c.name = f"req{r.rid}_{r.n}"
     return c
+
+
+def request_sources(r: Request) -> Tuple[np.ndarray, np.ndarray]:
+    """The payload of one request: source cells (i, j, k) and photon rates,
+    the same ones request_case places."""
+    g = Grid.cube(r.n)
+    rng = np.random.default_rng(r.seed)
+    pick = rng.choice(g.cells, size=min(r.sources, g.cells), replace=False)
+    cells = np.stack([pick % r.n, (pick // r.n) % r.n, pick // (r.n * r.n)], axis=1)
+    return cells, np.full(len(cells), NDOT)
 
 
 def random_case(n: Sequence[int], seed: int, periodic=(False, False, False),

@@ -303,3 +303,63 @@ def test_opacity_update_parity(fld, oracle):
     ref = oracle.opacity_update(E, nH, nHI, synth.DT, synth.C_LIGHT, synth.SIGMA_HI, synth.HNU_HI,
                                 synth.ALPHA_B)
     np.testing.assert_allclose(host(out), ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("precision", [synth.PREC_FP64, synth.PREC_MIXED])
+def test_graph_replay_equals_direct_launches(fld, precision):
+    # one CUDA graph per CG iteration replays exactly the launches it holds
+    case = synth.config3(48, sources=16)
+    case.params.precision = precision
+    out = []
+    s = torch.cuda.Stream()
+    for graphs in (0, 1):
+        case.params.graphs = graphs
+        with torch.cuda.stream(s):
+            ctx = fld.fld_create(case.grid, case.params, s)
+            E = dev(case.E)
+            infos = [fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta)) for _ in range(3)]
+            s.synchronize()
+            out.append((host(E), [i["iters"] for i in infos]))
+            ctx.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_advance_parity_with_oracle(fld, oracle):
+    # radiation subcycling (Sec. 3.3): same substep sequence and result
+    case = synth.config1(32)
+    p = case.params
+    p.rtol, p.max_iter = 1e-12, 200
+    span = 5 * p.dt
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = fld.fld_create(case.grid, p, s)
+        E = dev(case.E)
+        info = fld.fld_advance(ctx, E, dev(case.nHI), dev(case.eta), span, 0.05 * p.dt, tau_tol=1e-2,
+                               dt_min=1e-6 * p.dt)
+        s.synchronize()
+        ctx.close()
+    Eref, iref = oracle.advance(case.grid, p, {"rtol": 1e-12, "max_iter": 200}, case.E, case.nHI, case.eta,
+                                span, 0.05 * p.dt, tau_tol=1e-2, dt_min=1e-6 * p.dt)
+    assert info["substeps"] == iref["substeps"] and info["retries"] == iref["retries"] == 0
+    assert info["t_done"] == span
+    assert rel_max(host(E).reshape(case.grid.shape), Eref) < 1e-9
+
+
+def test_advance_retries_on_failure(fld):
+    case = synth.config1(16)
+    p = case.params
+    p.max_iter = 2
+    ctx = fld.fld_create(case.grid, p)
+    E = dev(case.E)
+    info = fld.fld_advance(ctx, E, dev(case.nHI), dev(case.eta), p.dt, p.dt, tau_tol=1e3,
+                           dt_min=1e-8 * p.dt, check=False)
+    assert info["retries"] >= 1
+    p.max_iter, p.rtol = 1, 1e-14
+    ctx2 = fld.fld_create(case.grid, p)
+    E2 = dev(case.E)
+    info2 = fld.fld_advance(ctx2, E2, dev(case.nHI), dev(case.eta), p.dt, p.dt, tau_tol=1e3,
+                            dt_min=1e-3 * p.dt, check=False)
+    assert info2["status"] == fld.FLD_ENOCONV and info2["t_done"] < p.dt
+    ctx.close()
+    ctx2.close()

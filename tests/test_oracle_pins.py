@@ -413,3 +413,51 @@ def test_opacity_update_equilibrium_and_dark(oracle):
     # no radiation: pure recombination, clamped at fully neutral
     out = oracle.opacity_update(np.zeros(5), nH, x * nH, 1e3, C, synth.SIGMA_HI, synth.HNU_HI, synth.ALPHA_B)
     np.testing.assert_allclose(out, np.minimum(x + 1e3 * synth.ALPHA_B * 1e-3 * (1 - x) ** 2, 1.0) * nH, rtol=1e-14)
+
+
+# ------------------------------------------------ radiation subcycling (Sec. 3.3)
+
+def test_advance_reaches_t_span_and_adapts(oracle):
+    case = synth.config1(16)
+    p = case.params
+    span = 20 * p.dt
+    E, info = oracle.advance(case.grid, p, {}, case.E, case.nHI, case.eta, span, dt_first=0.01 * p.dt,
+                             tau_tol=1e-2, dt_min=1e-6 * p.dt)
+    assert info["status"] == 0 and info["t_done"] == span
+    assert info["retries"] == 0 and info["substeps"] >= 3
+    # time steps grew from the small first one
+    assert info["dt_next"] > 0.01 * p.dt
+
+
+def test_advance_retries_failed_substeps_at_a_tenth(oracle):
+    # a solver allowed 2 CG iterations fails on the first large substep,
+    # converges on the 0.1 dt retry
+    case = synth.config1(16)
+    p = case.params
+    s = {"max_iter": 2, "rtol": 1e-8}
+    E2, info = oracle.advance(case.grid, p, s, case.E, case.nHI, case.eta, p.dt, dt_first=p.dt,
+                              tau_tol=1e3, dt_min=1e-8 * p.dt, allow_fail=True)
+    assert info["retries"] >= 1
+    # and when every retry fails the status says so
+    E3, info3 = oracle.advance(case.grid, p, {"max_iter": 1, "rtol": 1e-14}, case.E, case.nHI, case.eta,
+                               p.dt, dt_first=p.dt, tau_tol=1e3, dt_min=1e-3 * p.dt, allow_fail=True)
+    assert info3["status"] == oracle.ENOCONV and info3["t_done"] < p.dt
+
+
+def test_advance_converges_to_small_fixed_steps(oracle):
+    # backward Euler is first order: the subcycled result approaches the
+    # result of many small fixed steps as tau_tol shrinks
+    case = synth.random_case((8, 8, 8), seed=3)
+    p = case.params
+    span = 2 * p.dt
+    ref = case.E.copy()
+    for _ in range(400):
+        p.dt = span / 400
+        ref, _ = oracle.step(case.grid, p, {"rtol": 1e-12, "max_iter": 100}, ref, case.nHI, case.eta)
+    p.dt = span
+    errs = []
+    for tol in (1e-1, 1e-2):
+        E, info = oracle.advance(case.grid, p, {"rtol": 1e-12, "max_iter": 100}, case.E, case.nHI, case.eta,
+                                 span, dt_first=span / 100, tau_tol=tol, dt_min=1e-9 * span, growth=2.0)
+        errs.append(np.linalg.norm(E - ref) / np.linalg.norm(ref))
+    assert errs[1] < errs[0]
