@@ -230,6 +230,26 @@ fld_status fld_opacity_update(size_t n, const double* E, const double* n_H,
                               double dt, double c, double sigma, double hnu,
                               double alpha_B, void* cuda_stream);
 
+/* FP64 residual r = b - A x of a 7-point operator (m, wx, wy, wz in the
+ * layout of fld_get_system) and, into norms[0] and norms[1], ||r||_2^2 and
+ * max |r|, for callers that cannot allocate device memory: programs whose
+ * device memory is owned by another allocator, and latency-critical loops
+ * where cudaMalloc may synchronise the device.  The paper has no
+ * counterpart; this is a service entry point of the library.
+ * Nothing is allocated: the reduction's scratch is a fixed file-scope device
+ * array (about 257 KB, held by every GPU that loads the library until exit)
+ * whose address the first call on each device looks up, with that device
+ * current; make that first call before any stream capture.  Grids with more
+ * than 4194304 cells in an x-y plane (or 2^33 cells) are rejected with
+ * FLD_EINVAL.  All device pointers: m, wx, wy, wz, b, x read (nx*ny*nz
+ * FP64 each), r written (may be NULL), norms written (2 FP64).  Work is
+ * enqueued on cuda_stream and is asynchronous.  All calls share the scratch
+ * and each clears what must start at zero; calls that overlap on the GPU
+ * race. */
+fld_status fld_residual_noalloc(const fld_grid* g, const double* m, const double* wx,
+                                const double* wy, const double* wz, const double* b,
+                                const double* x, double* r, double* norms, void* cuda_stream);
+
 /* Number of levels and their shapes (dims[3*l .. 3*l+2]) for grid g. */
 int fld_levels(const fld_grid* g, int* dims, int max_levels);
 

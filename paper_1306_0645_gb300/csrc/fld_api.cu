@@ -776,6 +776,11 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
 
 }  // namespace
 
+namespace fld {
+// Lets other translation units of the library set fld_last_error's message.
+void record_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace fld
+
 extern "C" {
 
 fld_status fld_params_default(fld_params* p) {

@@ -109,6 +109,9 @@ void launch_opacity_update(long long n, const double* E, const double* nH, const
                            double* out, double dt, double c, double sigma, double hnu,
                            double alpha_B, cudaStream_t s);
 
+// Sets the calling thread's fld_last_error message (fld_api.cu).
+void record_error(const char* msg);
+
 // ---- FP32 four-cells-per-thread sweeps (k_fine4.cu); need nx % 4 == 0
 bool fine4_ok(const Dims& d);
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,

@@ -100,6 +100,7 @@ _SIGS = {
                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
     "fld_levels": ([ctypes.POINTER(fld_grid), ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
     "fld_set_dt": ([_VP, ctypes.c_double], ctypes.c_int),
+    "fld_residual_noalloc": ([ctypes.POINTER(fld_grid)] + [_VP] * 9, ctypes.c_int),
     "fld_advance": ([_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                      ctypes.POINTER(fld_advance_params), ctypes.POINTER(fld_advance_info)], ctypes.c_int),
     "fld_profile": ([_VP, ctypes.c_ulonglong], ctypes.c_int),
@@ -346,3 +347,17 @@ def fld_advance(ctx: Context, E, nHI, eta, t_span: float, dt_first: float, tau_t
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def fld_residual_noalloc(grid, m, wx, wy, wz, b, x, r, norms, stream=None):
+    """r = b - A x and norms = [||r||^2, max |r|] with no device allocation
+    (see fld_residual_noalloc in fld.h); r may be None."""
+    import torch
+    g = make_grid(grid)
+    n = g.nx * g.ny * g.nz
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptrs = [_dptr(t, n, nm) for t, nm in ((m, "m"), (wx, "wx"), (wy, "wy"), (wz, "wz"), (b, "b"), (x, "x"))]
+    rp = None if r is None else _dptr(r, n, "r")
+    _check(lib().fld_residual_noalloc(ctypes.byref(g), *ptrs, rp, _dptr(norms, 2, "norms"),
+                                      _VP(stream.cuda_stream)), "fld_residual_noalloc")
