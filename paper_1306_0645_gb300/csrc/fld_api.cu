@@ -95,8 +95,17 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
         return set_err(FLD_EINVAL, "grid dimensions must be >= 1 (got %d %d %d)", g->nx, g->ny, g->nz);
     if ((long long)g->nx * g->ny * g->nz > (1LL << 33))
         return set_err(FLD_EINVAL, "grid too large");
-    if ((long long)g->nx * g->ny > (1LL << 22))
-        return set_err(FLD_EINVAL, "an x-y plane may hold at most 4194304 cells");
+    {
+        // the stencil launches tile an x-y plane with at most RED_MAX_BLOCKS
+        // thread blocks (about 4.2 M cells)
+        Dims d0;
+        d0.nx = g->nx; d0.ny = g->ny; d0.nz = g->nz;
+        d0.px = d0.py = d0.pz = 0;
+        d0.n = (long long)g->nx * g->ny * g->nz;
+        const ColShape sh = col_shape(d0);
+        if ((long long)sh.grid.x * sh.grid.y * sh.grid.z > RED_MAX_BLOCKS)
+            return set_err(FLD_EINVAL, "x-y plane too large: at most 16384 thread blocks of 256 cells");
+    }
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
         return set_err(FLD_EINVAL, "cell widths must be finite and > 0");
     for (int a = 0; a < 3; a++)
