@@ -648,7 +648,12 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
             if ((st = read_scalars(c))) return st;
             int it = 0;
             bool iconv = false;
-            st = pcg<float>(c, c->h_sc[S_R0], c->p.inner_rtol, c->p.max_iter - inner_total, &it, &iconv);
+            // the inner solve need not reduce its residual further than the
+            // outer target requires (with a factor 2 of margin)
+            double irtol = 0.5 * rtol / inf.rel_res;
+            if (irtol < c->p.inner_rtol) irtol = c->p.inner_rtol;
+            if (irtol > 0.5) irtol = 0.5;
+            st = pcg<float>(c, c->h_sc[S_R0], irtol, c->p.max_iter - inner_total, &it, &iconv);
             if (st) return st;
             inner_total += it;
             { KScope k(c, K_IR_UPDATE, (outer == 0 ? 12.0 : 20.0) * n);

@@ -255,12 +255,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
         const double Ec = E[c];
         double flux = 0.0, wsum = 0.0;
         float wsum32 = 0.0f;
-        const bool f64diag = op.invd != nullptr || diag64 != nullptr;
+        // flux = sum_f w_f (E_nbr - E) = sum_f w_f E_nbr - W E, W = sum_f w_f
+        // (W is the diagonal's weight sum as well)
+        double swe = 0.0;
 #define FACE(WARR, W32ARR, wi, nb)                                 \
         {                                                          \
             const double w_ = op.WARR[wi];                         \
-            flux = fma(w_, E[nb] - Ec, flux);                      \
-            if (f64diag) wsum += w_;                               \
+            swe = fma(w_, E[nb], swe);                             \
+            wsum += w_;                                            \
             if (op32.invd) wsum32 += op32.W32ARR[wi];              \
         }
         if (i > 0) FACE(wx, wx, c, c - 1) else if (d.px) FACE(wx, wx, c, c + d.nx - 1)
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
         if (k > 0) FACE(wz, wz, c, c - sz) else if (d.pz) FACE(wz, wz, c, c + (long long)(d.nz - 1) * sz)
         if (k < d.nz - 1) FACE(wz, wz, c + sz, c + sz) else if (d.pz) FACE(wz, wz, c - (long long)(d.nz - 1) * sz, c - (long long)(d.nz - 1) * sz)
 #undef FACE
+        flux = fma(-wsum, Ec, swe);
         const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
         const double bc = fma(p.dt, eta[c], -sink) + flux;
         b[c] = bc;

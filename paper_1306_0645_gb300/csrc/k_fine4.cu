@@ -124,7 +124,7 @@ __device__ __forceinline__ Faces4 faces_of(const Op<float>& A, const Geo& g, flo
 // ------------------------------------------------------------------ p, q
 
 // p_out = z + beta p_in;  q = A p_out;  <p_out, q>.
-__global__ void __launch_bounds__(256) k_cg_p_matvec4(Dims d, Op<float> A, const float* __restrict__ z,
+__global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, const float* __restrict__ z,
                                                       const float* __restrict__ p_in,
                                                       float* __restrict__ p_out, float* __restrict__ q,
                                                       RedArgs ra) {
