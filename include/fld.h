@@ -98,6 +98,10 @@ typedef struct {
     int graphs;                /* CUDA graph per CG iteration: 1 on, 0 off,
                                   -1 auto (grids up to 128^3; default).
                                   Needs a non-NULL stream. */
+    int fused_post;            /* mixed mode, RB-GS, post = 1: one fused
+                                  black+red post-sweep kernel (1) or two
+                                  colour sweeps (0, default, faster on
+                                  GB300); same arithmetic */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -122,7 +126,7 @@ typedef struct fld_ctx fld_ctx;
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
  * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
- * graphs -1.
+ * graphs -1, fused_post 0.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 

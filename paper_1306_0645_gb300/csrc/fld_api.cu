@@ -52,13 +52,13 @@ enum KClass {
     K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_TO_F32, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
-    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_NUM
+    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
     "assemble_faces", "assemble_rhs", "coarsen", "invd", "to_f32", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
-    "opacity_update", "coarse_levels", "assemble_fix"};
+    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth"};
 
 struct KStat {
     long long launches, timed;
@@ -407,6 +407,17 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     { KScope k(c, kc(K_RESIDUAL), 7.0 * n * ts); residual_any<T>(L.d, A, r, z, t, s); }
     { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
+    if constexpr (std::is_same<T, float>::value) {
+        // one fused post-sweep: t = z + P e_c, then black and red from t into z
+        if (p.fused_post && p.smoother == FLD_SMOOTH_RBGS && p.post == 1 && post4_ok(L.d)) {
+            { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts);
+              launch_prolong_to4(L.d, C.d, (const float*)C.z, z, t, s); }
+            KScope k(c, kc(K_POST_FUSED), 7.0 * n * ts);
+            launch_post_smooth4(L.d, A, r, t, z, dot, s);
+            if (dot) *dot_done = true;
+            return;
+        }
+    }
     { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts); prolong_any<T>(L.d, C.d, (const T*)C.z, z, s); }
     for (int it = 0; it < p.post; it++) {
         if (p.smoother == FLD_SMOOTH_RBGS) {
@@ -819,6 +830,7 @@ fld_status fld_params_default(fld_params* p) {
     p->inner_rtol = 1e-4;
     p->coarse_cap = 1024;
     p->graphs = -1;
+    p->fused_post = 0;
     return FLD_OK;
 }
 

@@ -341,6 +341,239 @@ __global__ void __launch_bounds__(256) k_rb_colour4(Dims d, Op<float> A, const f
     }
 }
 
+// ------------------------------------------------ fused post-smoothing sweep
+
+// One post-smoothing sweep, black then red (see k_rb_colour4), in a single
+// pass and out of place: zi holds the pre-smoothed z plus the coarse
+// correction, zo receives the smoothed z.  A block is 32 lanes (4 cells
+// each) by PBY + 2 rows; the first and last rows are halo rows that only
+// form black values.  A block walks its chunk of planes with a one-plane
+// lag: at plane p it forms the black values of plane p + 1 (all its rows,
+// from zi, which nothing writes) and then the red values of plane p (inner
+// rows), taking the black y-neighbours from shared memory and the black
+// z-neighbours from registers.  Reading only zi keeps blocks independent,
+// so the result equals the two separate colour sweeps.
+constexpr int PBY = 6;
+
+namespace {
+
+struct PostRow {
+    int j;              // row (wrapped on a periodic axis, clamped otherwise)
+    bool has_yp;        // upper y face exists
+    long long row_dn, row_up;   // offsets of the y-neighbour rows (0 if missing)
+};
+
+__device__ __forceinline__ int wrapc(int v, int n, int periodic) {
+    if (v < 0) return periodic ? v + n : 0;
+    if (v >= n) return periodic ? v - n : n - 1;
+    return v;
+}
+
+// plane index and presence of the upper z face for plane q
+__device__ __forceinline__ int plane_of(int q, const Dims& d) { return wrapc(q, d.nz, d.pz); }
+
+}  // namespace
+
+template <bool DOT>
+__global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, const float* __restrict__ r,
+                                                      const float* __restrict__ zi, float* __restrict__ zo,
+                                                      RedArgs ra) {
+    __shared__ float4 sB[2][PBY + 2][32];
+    const int nx4 = d.nx >> 2;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i4raw = blockIdx.x * blockDim.x + tx;
+    const int i4 = min(i4raw, nx4 - 1);
+    const int i0 = 4 * i4;
+    const int jraw = (int)blockIdx.y * PBY - 1 + ty;
+    const int j = wrapc(jraw, d.ny, d.py);
+    const bool inner = ty >= 1 && ty <= PBY && jraw < d.ny && i4raw < nx4;
+    const long long nxy = (long long)d.nx * d.ny;
+    const long long rowoff = (long long)j * d.nx;
+    const int jd = wrapc(j - 1, d.ny, d.py), ju = wrapc(j + 1, d.ny, d.py);
+    const bool has_yp = j < d.ny - 1 || d.py;
+    const bool load_l = tx == 0 || i0 == 0;
+    const bool load_r = tx == blockDim.x - 1 || i0 + 4 >= d.nx;
+    const bool has_xr = i0 + 4 < d.nx || d.px;
+    const int xl = i0 > 0 ? i0 - 1 : (d.px ? d.nx - 1 : 0);
+    const int xr = i0 + 4 < d.nx ? i0 + 4 : (d.px ? 0 : d.nx - 1);
+    const int kch = (d.nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int k0 = (int)blockIdx.z * kch, k1 = min(d.nz, k0 + kch);
+    DotAcc<float> da;
+
+    // face weights of the four cells of this thread on plane q
+    auto faces = [&](int q, Faces4& f) {
+        const long long c = (long long)q * nxy + rowoff + i0;
+        const float4 wxc = ld4(A.wx, c);
+        const float rsh = __shfl_down_sync(FULL, wxc.x, 1);
+        const float xu3 = !has_xr ? 0.0f : (load_r ? A.wx[(long long)q * nxy + rowoff + (i0 + 4 < d.nx ? i0 + 4 : 0)] : rsh);
+        f.xl = wxc;
+        f.xu = make_float4(wxc.y, wxc.z, wxc.w, xu3);
+        f.yl = ld4(A.wy, c);
+        f.yu = has_yp ? ld4(A.wy, (long long)q * nxy + (long long)ju * d.nx + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        f.zl = ld4(A.wz, c);
+        const bool has_zu = q < d.nz - 1 || d.pz;
+        f.zu = has_zu ? ld4(A.wz, (long long)plane_of(q + 1, d) * nxy + rowoff + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+
+    // black values of plane q (cells of the other colour copied) from zi;
+    // cd, cc, cu: zi of planes q-1, q, q+1 at this thread's cells
+    auto black = [&](int q, float4 cd, float4 cc, float4 cu) {
+        Faces4 f;
+        faces(q, f);
+        const long long c = (long long)q * nxy + rowoff + i0;
+        const float lsh = __shfl_up_sync(FULL, cc.w, 1);
+        const float rsh = __shfl_down_sync(FULL, cc.x, 1);
+        const float L = load_l ? zi[(long long)q * nxy + rowoff + xl] : lsh;
+        const float R = load_r ? zi[(long long)q * nxy + rowoff + xr] : rsh;
+        const float4 ym = ld4(zi, (long long)q * nxy + (long long)jd * d.nx + i0);
+        const float4 yp = ld4(zi, (long long)q * nxy + (long long)ju * d.nx + i0);
+        const float4 rc = ld4(r, c), iv = ld4(A.invd, c);
+        const bool e0_black = ((j + q) & 1) == 1;
+        float4 o = cc;
+#define U1(X, LX, RX)                                                                      \
+        (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * ym.X + f.yu.X * yp.X +   \
+                 f.zl.X * cd.X + f.zu.X * cu.X))
+        if (e0_black) {
+            o.x = U1(x, L, cc.y);
+            o.z = U1(z, cc.y, cc.w);
+        } else {
+            o.y = U1(y, cc.x, cc.z);
+            o.w = U1(w, cc.z, R);
+        }
+#undef U1
+        return o;
+    };
+
+    if (k0 < k1) {
+        // zi at planes p, p+1, p+2 (rolling) and black values at p-1, p, p+1
+        const int pm1 = plane_of(k0 - 1, d), pm2 = plane_of(k0 - 2, d);
+        float4 zq0 = ld4(zi, (long long)pm2 * nxy + rowoff + i0);   // plane k0-2
+        float4 zq1 = ld4(zi, (long long)pm1 * nxy + rowoff + i0);   // plane k0-1
+        float4 zq2 = ld4(zi, (long long)k0 * nxy + rowoff + i0);    // plane k0
+        float4 Bd = black(pm1, zq0, zq1, zq2);                      // B_{k0-1}
+        float4 zq3 = ld4(zi, (long long)plane_of(k0 + 1, d) * nxy + rowoff + i0);
+        float4 Bc = black(k0, zq1, zq2, zq3);                       // B_{k0}
+        sB[k0 & 1][ty][tx] = Bc;
+        // now zq2 = z_{k0}, zq3 = z_{k0+1}
+        for (int p = k0; p < k1; p++) {
+            const int pu = plane_of(p + 1, d);
+            const float4 zq4 = ld4(zi, (long long)plane_of(p + 2, d) * nxy + rowoff + i0);
+            const float4 Bu = black(pu, zq2, zq3, zq4);             // B_{p+1}
+            sB[(p + 1) & 1][ty][tx] = Bu;
+            // everything the red values need except the shared black rows is
+            // fetched before the barrier, so the loads overlap the wait
+            Faces4 f;
+            faces(p, f);
+            const long long c = (long long)p * nxy + rowoff + i0;
+            const float4 rc = ld4(r, c), iv = ld4(A.invd, c);
+            const bool e0_red = ((j + p) & 1) == 0;
+            const float lsh = __shfl_up_sync(FULL, Bc.w, 1);
+            const float rsh = __shfl_down_sync(FULL, Bc.x, 1);
+            float L = lsh, R = rsh;
+            // a black x-neighbour outside the lanes of this block row is
+            // formed here from zi (only element 0's left and element 3's
+            // right neighbour can be; they are black when the element is red)
+            auto black_cell = [&](int x) {
+                const long long cc = (long long)p * nxy + rowoff + x;
+                const int xm = x > 0 ? x - 1 : (d.px ? d.nx - 1 : x);
+                const int xp = x < d.nx - 1 ? x + 1 : (d.px ? 0 : x);
+                const float wl = A.wx[cc];
+                const float wu = (x < d.nx - 1 || d.px) ? A.wx[(long long)p * nxy + rowoff + (x < d.nx - 1 ? x + 1 : 0)] : 0.0f;
+                const float wyl = A.wy[cc];
+                const float wyu = has_yp ? A.wy[(long long)p * nxy + (long long)ju * d.nx + x] : 0.0f;
+                const float wzl = A.wz[cc];
+                const bool has_zu = p < d.nz - 1 || d.pz;
+                const float wzu = has_zu ? A.wz[(long long)pu * nxy + rowoff + x] : 0.0f;
+                const float s = r[cc] + wl * zi[(long long)p * nxy + rowoff + xm] +
+                                wu * zi[(long long)p * nxy + rowoff + xp] +
+                                wyl * zi[(long long)p * nxy + (long long)jd * d.nx + x] +
+                                wyu * zi[(long long)p * nxy + (long long)ju * d.nx + x] +
+                                wzl * zi[(long long)plane_of(p - 1, d) * nxy + rowoff + x] +
+                                wzu * zi[(long long)pu * nxy + rowoff + x];
+                return A.invd[cc] * s;
+            };
+            if (load_l && e0_red) L = (i0 > 0 || d.px) ? black_cell(xl) : Bc.x;
+            if (load_r && !e0_red) R = has_xr ? black_cell(xr) : Bc.w;
+            __syncthreads();
+            // red values of plane p from the black ones
+            {
+                const float4 ym = sB[p & 1][ty > 0 ? ty - 1 : 0][tx];
+                const float4 yp = sB[p & 1][ty < PBY + 1 ? ty + 1 : PBY + 1][tx];
+                float4 o = Bc;
+#define V1(X, LX, RX)                                                                      \
+                (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * ym.X + f.yu.X * yp.X +   \
+                         f.zl.X * Bd.X + f.zu.X * Bu.X))
+                if (e0_red) {
+                    o.x = V1(x, L, Bc.y);
+                    o.z = V1(z, Bc.y, Bc.w);
+                } else {
+                    o.y = V1(y, Bc.x, Bc.z);
+                    o.w = V1(w, Bc.z, R);
+                }
+#undef V1
+                if (inner) {
+                    st4(zo, c, o);
+                    if (DOT) {
+                        da.add(rc.x, o.x);
+                        da.add(rc.y, o.y);
+                        da.add(rc.z, o.z);
+                        da.add(rc.w, o.w);
+                    }
+                }
+            }
+            __syncthreads();
+            Bd = Bc;
+            Bc = Bu;
+            zq2 = zq3;
+            zq3 = zq4;
+        }
+    }
+    if (DOT) {
+        double acc[1] = {da.value()};
+        const bool mx[1] = {false};
+        grid_reduce<1>(acc, mx, ra);
+    }
+}
+
+// Out-of-place prolongation: zo = z + P ec (see k_prolong_add4).
+__global__ void __launch_bounds__(256) k_prolong_to4(Dims f, Dims cd, const float* __restrict__ ec,
+                                                     const float* __restrict__ z, float* __restrict__ zo) {
+    const Walk w = walk_of(f);
+    if (w.k0 >= w.k1) return;
+    const int I = 2 * w.i4;
+    const int xi[4] = {wrapc(I - 1, cd.nx, cd.px), I, I + 1, wrapc(I + 2, cd.nx, cd.px)};
+    const int J0 = w.j >> 1;
+    const int J1 = wrapc((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
+    const long long cxy = (long long)cd.nx * cd.ny;
+    for (int k = w.k0; k < w.k1; k++) {
+        const int K0 = k >> 1;
+        const int K1 = wrapc((k & 1) ? K0 + 1 : K0 - 1, cd.nz, cd.pz);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int Jq = (q & 1) ? J1 : J0;
+            const int Kq = (q & 2) ? K1 : K0;
+            const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
+            const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
+            const float cm = ec[row + xi[0]], c0 = ec[row + xi[1]], c1 = ec[row + xi[2]],
+                        cp = ec[row + xi[3]];
+            acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
+            acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
+            acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
+            acc.w = fmaf(wq, 0.75f * c1 + 0.25f * cp, acc.w);
+        }
+        const long long c = (long long)k * w.nxy + (long long)w.j * f.nx + 4 * w.i4;
+        if (w.valid) {
+            float4 v = ld4(z, c);
+            v.x += acc.x;
+            v.y += acc.y;
+            v.z += acc.z;
+            v.w += acc.w;
+            st4(zo, c, v);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- transfers
 
 // Full-weighting restriction rc = P^T rf / 8 (see k_restrict): per axis the
@@ -509,6 +742,43 @@ static ColShape shape4(const Dims& d) {
     ColShape s = col_shape(h);
     return s;
 }
+
+static ColShape shape_post4(const Dims& d) {
+    Dims h = d;
+    h.nx = d.nx / 4;
+    ColShape s;
+    const int bx = pow2ceil(h.nx) < 32 ? pow2ceil(h.nx) : 32;
+    const int gx = (h.nx + bx - 1) / bx, gy = (d.ny + PBY - 1) / PBY;
+    long long xy = (long long)gx * gy;
+    long long gz = (152LL * 8 + xy - 1) / xy;
+    if (gz > d.nz) gz = d.nz;
+    if (xy * gz > RED_MAX_BLOCKS) gz = RED_MAX_BLOCKS / xy;
+    if (gz < 1) gz = 1;
+    s.block = dim3(bx, PBY + 2, 1);
+    s.grid = dim3(gx, gy, (unsigned)gz);
+    return s;
+}
+
+bool post4_ok(const Dims& d) {
+    Dims h = d;
+    h.nx = d.nx / 4;
+    const int bx = pow2ceil(h.nx) < 32 ? pow2ceil(h.nx) : 32;
+    return fine4_ok(d) && (long long)((h.nx + bx - 1) / bx) * ((d.ny + PBY - 1) / PBY) <= RED_MAX_BLOCKS;
+}
+
+void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float* zi, float* zo,
+                         const RedArgs* dot, cudaStream_t s) {
+    ColShape sh = shape_post4(d);
+    if (dot) k_post_smooth4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, *dot);
+    else k_post_smooth4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, RedArgs{});
+}
+
+void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const float* z, float* zo,
+                        cudaStream_t s) {
+    ColShape sh = shape4(f);
+    k_prolong_to4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, z, zo);
+}
+
 
 bool fine4_ok(const Dims& d) { return d.nx % 4 == 0 && d.nx >= 16; }
 

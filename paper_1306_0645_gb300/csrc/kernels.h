@@ -126,6 +126,14 @@ void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra,
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                            const RedArgs& ra, cudaStream_t s);
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s);
+// Fused post-smoothing sweep (black then red), out of place zi -> zo, with
+// <r, zo> into *dot when dot is given; post4_ok tells if a level qualifies.
+bool post4_ok(const Dims& d);
+void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float* zi, float* zo,
+                         const RedArgs* dot, cudaStream_t s);
+// zo = z + P ec (out of place)
+void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const float* z, float* zo,
+                        cudaStream_t s);
 void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s);
 void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
                        const RedArgs& ra, cudaStream_t s);

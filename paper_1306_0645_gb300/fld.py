@@ -43,7 +43,7 @@ class fld_params(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int), ("fused_post", ctypes.c_int)]
 
 
 class fld_info(ctypes.Structure):

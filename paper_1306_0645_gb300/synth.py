@@ -91,6 +91,7 @@ class Params:
     inner_rtol: float = 1e-4
     coarse_cap: int = 1024
     graphs: int = -1
+    fused_post: int = 0
 
 
 @dataclasses.dataclass

@@ -363,3 +363,23 @@ def test_advance_retries_on_failure(fld):
     assert info2["status"] == fld.FLD_ENOCONV and info2["t_done"] < p.dt
     ctx.close()
     ctx2.close()
+
+
+@pytest.mark.parametrize("make", [lambda: synth.config4(64, sources=512), lambda: synth.config2(64),
+                                  lambda: synth.random_case((96, 48, 40), seed=12, periodic=(True, False, True)),
+                                  lambda: synth.random_case((16, 24, 20), seed=13, periodic=(False, True, True))])
+def test_fused_post_sweep_equals_colour_sweeps(fld, make):
+    # the fused black+red post-sweep does the arithmetic of the two colour
+    # sweeps, so the whole mixed step is bit-identical
+    case = make()
+    case.params.precision = synth.PREC_MIXED
+    out = []
+    for fused in (0, 1):
+        case.params.fused_post = fused
+        ctx = fld.fld_create(case.grid, case.params)
+        E = dev(case.E)
+        infos = [fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta)) for _ in range(2)]
+        out.append((host(E), [(i["iters"], i["outer_iters"]) for i in infos]))
+        ctx.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
