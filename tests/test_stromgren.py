@@ -1,0 +1,113 @@
+"""Isothermal ionisation of a static neutral hydrogen region (the paper's
+Sec. 4.1.1 verification test, after Iliev et al. Test 1): the FLD radiation
+step coupled with the hydrogen-only photoionisation/recombination update
+(loosely coupled, one linearly implicit step per radiation step).
+
+The ionisation front follows r(t) = r_s (1 - exp(-t/t_rec))^(1/3) with
+r_s = (3 N_dot / (4 pi alpha_B n_H^2))^(1/3) and t_rec = 1/(alpha_B n_H).
+Parameters of the test: N_dot = 5e48 photons/s, n_H = 1e-3 cm^-3,
+alpha_B = 2.59e-13 cm^3/s (1e4 K, the reading of the garbled unit), box
+6.6 kpc, source in the corner cell with reflecting (zero-gradient) walls so
+the box is one octant of the sphere and receives N_dot / 8, initial
+E = 1e-45 erg/cm^3 and ionised fraction 0.0012.
+
+The front radius is taken from the ionised volume, r = (3 * 8 V_ion / 4 pi)^(1/3).
+The oracle run pins the coupled method to the closed form on the CPU; the
+GPU runs are checked against the closed form and against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1306_0645_gb300 import synth
+
+MYR = 1e6 * synth.YEAR
+N_H = 1e-3
+ALPHA = synth.ALPHA_B
+R_S = (3 * synth.NDOT / (4 * math.pi * ALPHA * N_H ** 2)) ** (1 / 3)
+T_REC = 1 / (ALPHA * N_H)
+
+
+def r_analytic(t):
+    return R_S * (1 - math.exp(-t / T_REC)) ** (1 / 3)
+
+
+def setup(n):
+    g = synth.Grid.cube(n)
+    nH = np.full(g.shape, N_H)
+    nHI = (1 - 0.0012) * nH
+    E = np.full(g.shape, 1e-45)
+    eta = np.zeros(g.shape)
+    eta[0, 0, 0] = synth.NDOT / 8 * synth.HNU_HI / g.volume
+    return g, nH, nHI, E, eta
+
+
+def front_radius(g, nH, nHI):
+    v_ion = float(((1 - nHI / nH) * g.volume).sum())
+    return (3 * 8 * v_ion / (4 * math.pi)) ** (1 / 3)
+
+
+def test_stromgren_front_oracle(oracle):
+    n, dt, steps = 24, 1 * MYR, 300
+    g, nH, nHI, E, eta = setup(n)
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt)
+    checks = {}
+    for k in range(1, steps + 1):
+        E, _ = oracle.step(g, p, {}, E, nHI, eta)
+        nHI = oracle.opacity_update(E, nH, nHI, dt, p.c, p.sigma, p.hnu, ALPHA)
+        if k in (100, 200, 300):
+            checks[k] = front_radius(g, nH, nHI) / r_analytic(k * dt)
+    assert abs(checks[100] - 1) < 0.07, checks
+    assert abs(checks[200] - 1) < 0.03, checks
+    assert abs(checks[300] - 1) < 0.03, checks
+
+
+def gpu_run(fld, torch, n, dt, steps, precision, marks):
+    g, nH, nHI, E, eta = setup(n)
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt, precision=precision)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    ctx = fld.fld_create(g, p)
+    Eg, nHIg, nHg, etag = dev(E), dev(nHI), dev(nH), dev(eta)
+    out = {}
+    for k in range(1, steps + 1):
+        fld.fld_step(ctx, Eg, nHIg, etag)
+        fld.fld_opacity_update(Eg, nHg, nHIg, nHIg, dt, p.c, p.sigma, p.hnu, ALPHA)
+        if k in marks:
+            out[k] = (Eg.cpu().numpy().reshape(g.shape), nHIg.cpu().numpy().reshape(g.shape))
+    ctx.close()
+    return g, nH, out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [synth.PREC_FP64, synth.PREC_MIXED])
+def test_stromgren_front_gpu(precision):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_0645_gb300 import fld
+    dt = 0.5 * MYR
+    marks = (200, 400, 800)
+    g, nH, out = gpu_run(fld, torch, 64, dt, 800, precision, marks)
+    ratio = {k: front_radius(g, nH, out[k][1]) / r_analytic(k * dt) for k in marks}
+    assert abs(ratio[200] - 1) < 0.06, ratio      # 100 Myr
+    assert abs(ratio[400] - 1) < 0.03, ratio      # 200 Myr
+    assert abs(ratio[800] - 1) < 0.03, ratio      # 400 Myr
+
+
+@pytest.mark.gpu
+def test_stromgren_gpu_matches_oracle(oracle):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_0645_gb300 import fld
+    n, dt, steps = 24, 2 * MYR, 60
+    g, nH, out = gpu_run(fld, torch, n, dt, steps, synth.PREC_FP64, (steps,))
+    _, _, nHI, E, eta = setup(n)
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt)
+    for _ in range(steps):
+        E, _ = oracle.step(g, p, {}, E, nHI, eta)
+        nHI = oracle.opacity_update(E, nH, nHI, dt, p.c, p.sigma, p.hnu, ALPHA)
+    Eg, nHIg = out[steps]
+    # both sides run the same algorithm at rtol 1e-8 for 60 coupled steps
+    assert abs(front_radius(g, nH, nHIg) / front_radius(g, nH, nHI) - 1) < 1e-6
+    assert np.linalg.norm(Eg - E) / np.linalg.norm(E) < 1e-6
