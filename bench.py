@@ -238,6 +238,9 @@ def main():
     pm = case.params
     pm.precision = synth.PREC_MIXED
     ctx = fld.fld_create(case.grid, pm, stream)
+    tuning = fld.autotune(ctx)
+    kinds = ["smooth_zero", "rb_colour", "residual", "restrict", "prolong", "cg_p_matvec"]
+    tuned = {k: tuning[2 * q: 2 * q + 2] for q, k in enumerate(kinds)}
     E = E0.clone()
     for _ in range(args.warmup):
         fld.fld_step(ctx, E, nHI, eta)
@@ -346,7 +349,8 @@ def main():
             "dtype": "f32 inner / f64 outer (mixed)", "data": "synthetic (seeded generators, no dataset)",
             "config": {"workload": workload_desc(n, sources), "n": n, "sources": sources,
                        "precision": "mixed", "l2": "inputs larger than L2 (each field 1 GiB at 512^3)",
-                       "parallelism": f"{world} independent replica(s)"},
+                       "parallelism": f"{world} independent replica(s)",
+                       "tuned_finest_level": {k: {"threads": v[0], "blocks": v[1]} for k, v in tuned.items()}},
             "iters": [i["iters"] for i in infos], "outer_iters": [i["outer_iters"] for i in infos],
             "rel_res": [i["rel_res"] for i in infos],
             "fp64_mg": fp64,

@@ -257,6 +257,22 @@ fld_status fld_residual_noalloc(const fld_grid* g, const double* m, const double
 /* Number of levels and their shapes (dims[3*l .. 3*l+2]) for grid g. */
 int fld_levels(const fld_grid* g, int* dims, int max_levels);
 
+/* Autotuner: for each level of a mixed-precision context whose FP32 sweeps
+ * run four cells per thread, time every candidate launch shape (128 or 256
+ * threads per block; 608 to 9728 blocks, which sets the z-chunk each thread
+ * walks) of the pre-smoothing, colour-sweep, residual, restriction,
+ * prolongation and CG p/q kernels, reps launches each, on the context's
+ * buffers and stream, and keep the fastest.  No-op for FP64 contexts.
+ * Discards captured CUDA graphs and the device scalars; call it after
+ * fld_create and before stepping (the assembled operator is kept). */
+fld_status fld_autotune(fld_ctx* ctx, int reps);
+
+/* The tuning table (threads, target blocks) per level and kernel: its
+ * length, a copy, and a replacement (for caching tuned shapes). */
+int fld_tuning_size(fld_ctx* ctx);
+fld_status fld_get_tuning(fld_ctx* ctx, int* out, int n);
+fld_status fld_set_tuning(fld_ctx* ctx, const int* in, int n);
+
 /* Per-kernel-class launch statistics of one context.  bytes is the
  * algorithmic traffic of the launches (every array a kernel streams counted
  * once per cell of its level, in the array's word size); ms and timed_bytes

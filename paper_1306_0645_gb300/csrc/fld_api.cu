@@ -40,11 +40,15 @@ fld_status set_err(fld_status st, const char* fmt, ...) {
             return set_err(FLD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
+// Tuned launch shapes of a level's FP32 sweeps.
+enum TuneClass { TN_SMOOTH0 = 0, TN_RB, TN_RES, TN_RESTRICT, TN_PROLONG, TN_PMATVEC, NTUNE };
+
 struct Level {
     Dims d;
     Op<double> A64;
     Op<float> A32;
     void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
+    Tune tune[NTUNE];
 };
 
 // Kernel classes for launch counting and optional CUDA-event timing.
@@ -326,38 +330,38 @@ bool use4(const Dims& d) {
     return std::is_same<T, float>::value && fine4_ok(d);
 }
 template <class T>
-void smooth_zero_any(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s) {
+void smooth_zero_any(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s, const Tune& tn) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(d)) return launch_smooth_zero4(d, A, r, z, s);
+        if (fine4_ok(d)) return launch_smooth_zero4(d, A, r, z, s, tn);
     }
     launch_smooth_zero<T>(d, A, r, z, s);
 }
 template <class T>
-void rb_colour_any(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s) {
+void rb_colour_any(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStream_t s, const Tune& tn) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(d)) return launch_rb_colour4(d, A, r, z, colour, s);
+        if (fine4_ok(d)) return launch_rb_colour4(d, A, r, z, colour, s, tn);
     }
     launch_rb_colour<T>(d, A, r, z, colour, s);
 }
 template <class T>
-void residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s) {
+void residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s, const Tune& tn) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(d)) return launch_residual4(d, A, r, z, res, s);
+        if (fine4_ok(d)) return launch_residual4(d, A, r, z, res, s, tn);
     }
     launch_residual<T>(d, A, r, z, res, s);
 }
 
 template <class T>
-void restrict_any(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s) {
+void restrict_any(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s, const Tune& tn) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(f)) return launch_restrict4(f, c, rf, rc, s);
+        if (fine4_ok(f)) return launch_restrict4(f, c, rf, rc, s, tn);
     }
     launch_restrict<T>(f, c, rf, rc, s);
 }
 template <class T>
-void prolong_any(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s) {
+void prolong_any(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s, const Tune& tn) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(f)) return launch_prolong_add4(f, c, ec, zf, s);
+        if (fine4_ok(f)) return launch_prolong_add4(f, c, ec, zf, s, tn);
     }
     launch_prolong_add<T>(f, c, ec, zf, s);
 }
@@ -382,11 +386,11 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     const fld_params& p = c->p;
     if (p.smoother == FLD_SMOOTH_RBGS) {
         if (p.pre >= 1) {
-            { KScope k(c, kc(K_SMOOTH_ZERO), 6.0 * n * ts); smooth_zero_any<T>(L.d, A, r, z, s); }
+            { KScope k(c, kc(K_SMOOTH_ZERO), 6.0 * n * ts); smooth_zero_any<T>(L.d, A, r, z, s, L.tune[TN_SMOOTH0]); }
             for (int it = 1; it < p.pre; it++)
                 for (int colour = 0; colour < 2; colour++) {
                     KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
-                    rb_colour_any<T>(L.d, A, r, z, colour, s);
+                    rb_colour_any<T>(L.d, A, r, z, colour, s, L.tune[TN_RB]);
                 }
         } else {
             cudaMemsetAsync(z, 0, L.d.n * sizeof(T), s);
@@ -404,8 +408,8 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     }
     Level& C = c->L[l + 1];
     const double nc = (double)C.d.n;
-    { KScope k(c, kc(K_RESIDUAL), 7.0 * n * ts); residual_any<T>(L.d, A, r, z, t, s); }
-    { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s); }
+    { KScope k(c, kc(K_RESIDUAL), 7.0 * n * ts); residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES]); }
+    { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s, L.tune[TN_RESTRICT]); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
     if constexpr (std::is_same<T, float>::value) {
         // one fused post-sweep: t = z + P e_c, then black and red from t into z
@@ -418,7 +422,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
             return;
         }
     }
-    { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts); prolong_any<T>(L.d, C.d, (const T*)C.z, z, s); }
+    { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts); prolong_any<T>(L.d, C.d, (const T*)C.z, z, s, L.tune[TN_PROLONG]); }
     for (int it = 0; it < p.post; it++) {
         if (p.smoother == FLD_SMOOTH_RBGS) {
             for (int colour = 1; colour >= 0; colour--) {
@@ -426,13 +430,13 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
                 if constexpr (std::is_same<T, float>::value) {
                     if (last && dot && use4<T>(L.d)) {
                         KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
-                        launch_rb_colour4_dot(L.d, A, r, z, colour, *dot, s);
+                        launch_rb_colour4_dot(L.d, A, r, z, colour, *dot, s, L.tune[TN_RB]);
                         *dot_done = true;
                         continue;
                     }
                 }
                 KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
-                rb_colour_any<T>(L.d, A, r, z, colour, s);
+                rb_colour_any<T>(L.d, A, r, z, colour, s, L.tune[TN_RB]);
             }
         } else {
             { KScope k(c, kc(K_JACOBI), 8.0 * n * ts); launch_jacobi<T>(L.d, A, r, z, t, p.jacobi_omega, false, s); }
@@ -480,7 +484,7 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
         {
             KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
             if constexpr (std::is_same<T, float>::value) {
-                if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+                if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s, L0.tune[TN_PMATVEC]);
                 else launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
             } else {
                 launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
@@ -1091,6 +1095,130 @@ fld_status fld_opacity_update(size_t n, const double* E, const double* nH, const
     launch_opacity_update((long long)n, E, nH, nHI, out, dt, c, sigma, hnu, alpha_B,
                           (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
+    return FLD_OK;
+}
+
+fld_status fld_autotune(fld_ctx* c, int reps) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (reps < 1 || reps > 100) return set_err(FLD_EINVAL, "reps must lie in [1, 100]");
+    if (!c->mixed) return FLD_OK;   // FP64 sweeps have a single launch shape
+    cudaStream_t s = c->s;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    // captured graphs hold the old launch shapes
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            if (c->gexec[a][b]) {
+                cudaGraphExecDestroy(c->gexec[a][b]);
+                c->gexec[a][b] = nullptr;
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int threads_c[] = {128, 256};
+    const int target_c[] = {152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
+    fld_status st = FLD_OK;
+    for (int l = 0; l + 1 < c->nl && !st; l++) {
+        Level& L = c->L[l];
+        Level& C = c->L[l + 1];
+        if (!fine4_ok(L.d)) continue;
+        const size_t nb = L.d.n * sizeof(float), ncb = C.d.n * sizeof(float);
+        float* r = l == 0 ? (float*)c->cg[0] : (float*)L.r;
+        float* z = l == 0 ? (float*)c->cg[1] : (float*)L.z;
+        float* t = (float*)L.t;
+        // sweep inputs need finite values only; results are discarded
+        cudaMemsetAsync(r, 0, nb, s);
+        cudaMemsetAsync(z, 0, nb, s);
+        cudaMemsetAsync(t, 0, nb, s);
+        cudaMemsetAsync(C.t, 0, ncb, s);
+        cudaMemsetAsync(C.z, 0, ncb, s);
+        if (!c->assembled) {
+            cudaMemsetAsync(L.A32.m, 0, nb, s);
+            cudaMemsetAsync(L.A32.wx, 0, nb, s);
+            cudaMemsetAsync(L.A32.wy, 0, nb, s);
+            cudaMemsetAsync(L.A32.wz, 0, nb, s);
+            cudaMemsetAsync(L.A32.invd, 0, nb, s);
+        }
+        if (l == 0) {
+            cudaMemsetAsync(c->cg[2], 0, nb, s);
+            cudaMemsetAsync(c->cg[3], 0, nb, s);
+        }
+        for (int k = 0; k < NTUNE && !st; k++) {
+            if (k == TN_PMATVEC && l != 0) continue;
+            auto run = [&](const Tune& tn) {
+                switch (k) {
+                case TN_SMOOTH0: launch_smooth_zero4(L.d, L.A32, r, t, s, tn); break;
+                case TN_RB: launch_rb_colour4(L.d, L.A32, r, t, 0, s, tn); break;
+                case TN_RES: launch_residual4(L.d, L.A32, r, z, t, s, tn); break;
+                case TN_RESTRICT: launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn); break;
+                case TN_PROLONG: launch_prolong_add4(L.d, C.d, (const float*)C.z, t, s, tn); break;
+                case TN_PMATVEC:
+                    launch_cg_p_matvec4(L.d, L.A32, z, (const float*)c->cg[2], (float*)c->cg[3],
+                                        (float*)c->cg[4], red(c, R_ALPHA), s, tn);
+                    break;
+                }
+            };
+            float best = 1e30f;
+            for (int th : threads_c)
+                for (int tg : target_c) {
+                    Tune tn;
+                    tn.threads = th;
+                    tn.target = tg;
+                    run(tn);
+                    cudaEventRecord(e0, s);
+                    for (int q = 0; q < reps; q++) run(tn);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = set_err(FLD_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        L.tune[k] = tn;
+                    }
+                }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing launches left scalars behind
+    cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), s);
+    cudaMemsetAsync(c->counter, 0, 256, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+int fld_tuning_size(fld_ctx* c) { return c ? 2 * NTUNE * c->nl : 0; }
+
+fld_status fld_get_tuning(fld_ctx* c, int* out, int n) {
+    if (!c || !out || n < 2 * NTUNE * c->nl) return set_err(FLD_EINVAL, "buffer too small");
+    for (int l = 0; l < c->nl; l++)
+        for (int k = 0; k < NTUNE; k++) {
+            out[2 * (l * NTUNE + k)] = c->L[l].tune[k].threads;
+            out[2 * (l * NTUNE + k) + 1] = c->L[l].tune[k].target;
+        }
+    return FLD_OK;
+}
+
+fld_status fld_set_tuning(fld_ctx* c, const int* in, int n) {
+    if (!c || !in || n != 2 * NTUNE * c->nl) return set_err(FLD_EINVAL, "tuning table of the wrong size");
+    for (int q = 0; q < n; q += 2) {
+        const int th = in[q], tg = in[q + 1];
+        if (th < 32 || th > 256 || (th & (th - 1)) || tg < 1 || tg > RED_MAX_BLOCKS)
+            return set_err(FLD_EINVAL, "invalid launch shape in tuning table");
+    }
+    for (int l = 0; l < c->nl; l++)
+        for (int k = 0; k < NTUNE; k++) {
+            c->L[l].tune[k].threads = in[2 * (l * NTUNE + k)];
+            c->L[l].tune[k].target = in[2 * (l * NTUNE + k) + 1];
+        }
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            if (c->gexec[a][b]) {
+                cudaGraphExecDestroy(c->gexec[a][b]);
+                c->gexec[a][b] = nullptr;
+            }
     return FLD_OK;
 }
 

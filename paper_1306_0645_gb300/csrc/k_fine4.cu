@@ -736,10 +736,10 @@ void launch_cg_update4(long long n, float* x, float* r, const float* p, const fl
     k_cg_update4<<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, x, r, p, q, ra);
 }
 
-static ColShape shape4(const Dims& d) {
+static ColShape shape4(const Dims& d, const Tune& tn = Tune{}) {
     Dims h = d;
     h.nx = d.nx / 4;
-    ColShape s = col_shape(h);
+    ColShape s = col_shape(h, tn.threads, tn.target);
     return s;
 }
 
@@ -783,37 +783,40 @@ void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const flo
 bool fine4_ok(const Dims& d) { return d.nx % 4 == 0 && d.nx >= 16; }
 
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
-                         float* q, const RedArgs& ra, cudaStream_t s) {
-    ColShape sh = shape4(d);
+                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
     k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra);
 }
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s) {
-    ColShape sh = shape4(d);
+                      cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
     k_residual4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res);
 }
-void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s) {
+void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
+                      const Tune& tn) {
     Dims h = c;
     h.nx = c.nx / 2;
-    ColShape sh = col_shape(h);
+    ColShape sh = col_shape(h, tn.threads, tn.target);
     k_restrict4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc);
 }
-void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s) {
-    ColShape sh = shape4(f);
+void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s,
+                         const Tune& tn) {
+    ColShape sh = shape4(f, tn);
     k_prolong_add4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf);
 }
-void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s) {
-    ColShape sh = shape4(d);
+void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
+                         const Tune& tn) {
+    ColShape sh = shape4(d, tn);
     k_smooth_zero4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z);
 }
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
-                       cudaStream_t s) {
-    ColShape sh = shape4(d);
+                       cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
     k_rb_colour4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{});
 }
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
-                           const RedArgs& ra, cudaStream_t s) {
-    ColShape sh = shape4(d);
+                           const RedArgs& ra, cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
     k_rb_colour4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, ra);
 }
 

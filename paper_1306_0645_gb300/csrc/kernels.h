@@ -112,20 +112,30 @@ void launch_opacity_update(long long n, const double* E, const double* nH, const
 // Sets the calling thread's fld_last_error message (fld_api.cu).
 void record_error(const char* msg);
 
+// Launch shape of a four-cells-per-thread sweep: threads per block (a
+// power of two up to 256, x lanes first) and the total blocks aimed at (the
+// z-chunk length follows).  Chosen per level and kernel by fld_autotune.
+struct Tune {
+    int threads = 256;
+    int target = 152 * 8;
+};
+
 // ---- FP32 four-cells-per-thread sweeps (k_fine4.cu); need nx % 4 == 0
 bool fine4_ok(const Dims& d);
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
-                         float* q, const RedArgs& ra, cudaStream_t s);
+                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s);
-void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s);
+                      cudaStream_t s, const Tune& tn = Tune{});
+void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
+                         const Tune& tn = Tune{});
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
-                       cudaStream_t s);
+                       cudaStream_t s, const Tune& tn = Tune{});
 void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s);
 // one colour of a sweep followed by <r, z> of the result (reduction ra)
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
-                           const RedArgs& ra, cudaStream_t s);
-void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s);
+                           const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
+void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
+                      const Tune& tn = Tune{});
 // Fused post-smoothing sweep (black then red), out of place zi -> zo, with
 // <r, zo> into *dot when dot is given; post4_ok tells if a level qualifies.
 bool post4_ok(const Dims& d);
@@ -134,7 +144,8 @@ void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float
 // zo = z + P ec (out of place)
 void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const float* z, float* zo,
                         cudaStream_t s);
-void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s);
+void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s,
+                         const Tune& tn = Tune{});
 void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
                        const RedArgs& ra, cudaStream_t s);
 

@@ -103,6 +103,10 @@ _SIGS = {
     "fld_residual_noalloc": ([ctypes.POINTER(fld_grid)] + [_VP] * 9, ctypes.c_int),
     "fld_advance": ([_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                      ctypes.POINTER(fld_advance_params), ctypes.POINTER(fld_advance_info)], ctypes.c_int),
+    "fld_autotune": ([_VP, ctypes.c_int], ctypes.c_int),
+    "fld_tuning_size": ([_VP], ctypes.c_int),
+    "fld_get_tuning": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
+    "fld_set_tuning": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
     "fld_profile": ([_VP, ctypes.c_ulonglong], ctypes.c_int),
     "fld_profile_read": ([_VP, ctypes.POINTER(fld_kernel_stat), ctypes.c_int], ctypes.c_int),
     "fld_last_error": ([], ctypes.c_char_p),
@@ -361,3 +365,56 @@ def fld_residual_noalloc(grid, m, wx, wy, wz, b, x, r, norms, stream=None):
     rp = None if r is None else _dptr(r, n, "r")
     _check(lib().fld_residual_noalloc(ctypes.byref(g), *ptrs, rp, _dptr(norms, 2, "norms"),
                                       _VP(stream.cuda_stream)), "fld_residual_noalloc")
+
+
+def fld_autotune(ctx: Context, reps: int = 3):
+    _check(lib().fld_autotune(ctx.handle, int(reps)), "fld_autotune")
+
+
+def fld_tuning_size(ctx: Context) -> int:
+    return int(lib().fld_tuning_size(ctx.handle))
+
+
+def fld_get_tuning(ctx: Context) -> List[int]:
+    n = fld_tuning_size(ctx)
+    buf = (ctypes.c_int * n)()
+    _check(lib().fld_get_tuning(ctx.handle, buf, n), "fld_get_tuning")
+    return list(buf)
+
+
+def fld_set_tuning(ctx: Context, table: Sequence[int]):
+    buf = (ctypes.c_int * len(table))(*[int(v) for v in table])
+    _check(lib().fld_set_tuning(ctx.handle, buf, len(table)), "fld_set_tuning")
+
+
+def autotune(ctx: Context, cache_path: Optional[str] = None, reps: int = 3) -> List[int]:
+    """Tune the context's FP32 launch shapes, or load them from a JSON cache
+    keyed by grid, boundaries, precision and GPU name; returns the table."""
+    import json
+    import torch
+    g = ctx._g
+    key = "%dx%dx%d_bc%d%d%d_p%d_%s" % (g.nx, g.ny, g.nz, g.bc[0], g.bc[1], g.bc[2], ctx.params.precision,
+                                         torch.cuda.get_device_name().replace(" ", "_"))
+    if cache_path is None:
+        cache_path = os.environ.get("FLD_TUNE_CACHE",
+                                    os.path.join(os.path.expanduser("~"), ".cache", "fld_gb300_tuning.json"))
+    cache = {}
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    table = cache.get(key)
+    if table is not None and len(table) == fld_tuning_size(ctx):
+        fld_set_tuning(ctx, table)
+        return table
+    fld_autotune(ctx, reps)
+    table = fld_get_tuning(ctx)
+    cache[key] = table
+    try:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f)
+    except OSError:
+        pass
+    return table

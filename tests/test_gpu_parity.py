@@ -383,3 +383,23 @@ def test_fused_post_sweep_equals_colour_sweeps(fld, make):
         ctx.close()
     assert out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_autotune_cache_roundtrip_and_parity(fld, oracle, tmp_path):
+    case = synth.config4(64, sources=512)
+    case.params.precision = synth.PREC_MIXED
+    cache = str(tmp_path / "tune.json")
+    res = []
+    for _ in range(2):   # tuned, then loaded from the cache
+        ctx = fld.fld_create(case.grid, case.params)
+        table = fld.autotune(ctx, cache_path=cache)
+        assert len(table) == fld.fld_tuning_size(ctx) and fld.fld_get_tuning(ctx) == table
+        E = dev(case.E)
+        fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
+        res.append((table, host(E).reshape(case.grid.shape)))
+        ctx.close()
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+    Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200}, case.E, case.nHI, case.eta)
+    E = res[0][1]
+    assert np.linalg.norm(E - Eref) / np.linalg.norm(Eref) < 1e-6
