@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <chrono>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <type_traits>
@@ -237,6 +239,16 @@ struct fld_ctx {
     bool capturing;
     bool graphs_broken;
     cudaGraphExec_t gexec[2][2];
+    cudaGraph_t graph[2][2];       // the captured iterations (children of batch graphs)
+    unsigned long long id;         // unique per context, keys batch graphs
+    unsigned graph_gen;            // bumped whenever the iteration graphs change
+    cudaEvent_t ev_join;           // orders this stream with a batch stream
+    // state of the CG run in progress (see pcg_begin / pcg_after)
+    struct Run {
+        double thresh;
+        int max_iter, k, cur;
+        bool conv, done;
+    } run;
     std::vector<std::pair<int, double>> glaunch[2][2];
     std::vector<std::pair<int, double>>* grec;   // launch list being captured
     double* h_one;   // pinned 1.0, to raise S_FIRST
@@ -445,10 +457,11 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     }
 }
 
-// Preconditioned CG on the fine level in precision T: r holds the initial
-// residual (x = 0), r0sq = ||r||^2; stops when ||r||^2 <= rtol^2 r0sq.
+// One CG iteration on the fine level in precision T (p parity cur): the
+// V-cycle, <r,z>, p and q = A p, the x and r updates, and the scalars to the
+// pinned host mirror.
 template <class T>
-fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
+void pcg_iteration(fld_ctx* c, int cur) {
     T* r = (T*)c->cg[0];
     T* z = (T*)c->cg[1];
     T* p[2] = {(T*)c->cg[2], (T*)c->cg[3]};
@@ -457,97 +470,154 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
     Level& L0 = c->L[0];
     Op<T> A = op_of<T>(L0);
     const long long n = L0.d.n;
-    const double thresh = rtol * rtol * r0sq;
-    *converged = false;
-    *iters = 0;
-    CUDA_TRY(cudaMemsetAsync(p[0], 0, n * sizeof(T), c->s));
+    const RedArgs dra = red(c, R_RHO);
+    bool dot_done = false;
+    vcycle<T>(c, 0, r, z, &dra, &dot_done);
+    const double ts = sizeof(T);
+    if (!dot_done) {
+        KScope ks(c, K_DOT, 2.0 * n * ts);
+        if constexpr (std::is_same<T, float>::value) {
+            if (use4<T>(L0.d)) launch_dot4(n, r, z, red(c, R_RHO), c->s);
+            else launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
+        } else {
+            launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
+        }
+    }
+    {
+        KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
+        if constexpr (std::is_same<T, float>::value) {
+            if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s, L0.tune[TN_PMATVEC]);
+            else launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+        } else {
+            launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
+        }
+    }
+    {
+        KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
+        if constexpr (std::is_same<T, float>::value) {
+            if (use4<T>(L0.d)) launch_cg_update4(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+            else launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+        } else {
+            launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+        }
+    }
+    cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+}
+
+void drop_graphs(fld_ctx* c) {
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) {
+            if (c->gexec[a][b]) cudaGraphExecDestroy(c->gexec[a][b]);
+            if (c->graph[a][b]) cudaGraphDestroy(c->graph[a][b]);
+            c->gexec[a][b] = nullptr;
+            c->graph[a][b] = nullptr;
+        }
+    c->graph_gen++;
+}
+
+// The captured and instantiated iteration of precision T and parity cur
+// (capturing it on first use), or null when graphs are off or unavailable.
+template <class T>
+cudaGraphExec_t pcg_graph(fld_ctx* c, int cur) {
+    const int prec = std::is_same<T, float>::value ? 1 : 0;
+    if (!(c->use_graphs && !c->graphs_broken && c->tmask == 0)) return nullptr;
+    cudaGraphExec_t& ge = c->gexec[prec][cur];
+    if (!ge) {
+        // capture (records, does not run) and instantiate this parity
+        c->glaunch[prec][cur].clear();
+        c->grec = &c->glaunch[prec][cur];
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            c->capturing = true;
+            pcg_iteration<T>(c, cur);
+            c->capturing = false;
+            ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && g;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (!ok) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            ge = nullptr;
+            c->graphs_broken = true;
+            return nullptr;
+        }
+        c->graph[prec][cur] = g;
+        c->graph_gen++;
+    }
+    return ge;
+}
+
+// Count the launches a graph of this context holds, once per replay.
+void count_graph_launches(fld_ctx* c, int prec, int cur) {
+    for (auto& e : c->glaunch[prec][cur]) {
+        c->kstat[e.first].launches++;
+        c->kstat[e.first].bytes += e.second;
+    }
+}
+
+// Start preconditioned CG in precision T: r holds the initial residual
+// (x = 0), r0sq = ||r||^2; it stops when ||r||^2 <= rtol^2 r0sq.
+template <class T>
+fld_status pcg_begin(fld_ctx* c, double r0sq, double rtol, int max_iter) {
+    CUDA_TRY(cudaMemsetAsync(c->cg[2], 0, c->L[0].d.n * sizeof(T), c->s));
     // beta = 0 in the first iteration, signalled on the device so that
     // every iteration launches the same work
     CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    c->run.thresh = rtol * rtol * r0sq;
+    c->run.max_iter = max_iter;
+    c->run.k = 0;
+    c->run.cur = 0;
+    c->run.conv = false;
+    c->run.done = max_iter < 1;
+    return FLD_OK;
+}
+
+// Enqueue the next iteration: the captured graph, or the launches.
+template <class T>
+fld_status pcg_enqueue(fld_ctx* c) {
     const int prec = std::is_same<T, float>::value ? 1 : 0;
-    // one CG iteration: V-cycle, <r,z>, p and q = A p, x and r updates, and
-    // the scalars to the pinned host mirror
-    auto iteration = [&](int cur) {
-        const RedArgs dra = red(c, R_RHO);
-        bool dot_done = false;
-        vcycle<T>(c, 0, r, z, &dra, &dot_done);
-        const double ts = sizeof(T);
-        if (!dot_done) {
-            KScope ks(c, K_DOT, 2.0 * n * ts);
-            if constexpr (std::is_same<T, float>::value) {
-                if (use4<T>(L0.d)) launch_dot4(n, r, z, red(c, R_RHO), c->s);
-                else launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
-            } else {
-                launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
-            }
-        }
-        {
-            KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
-            if constexpr (std::is_same<T, float>::value) {
-                if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s, L0.tune[TN_PMATVEC]);
-                else launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
-            } else {
-                launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
-            }
-        }
-        {
-            KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
-            if constexpr (std::is_same<T, float>::value) {
-                if (use4<T>(L0.d)) launch_cg_update4(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
-                else launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
-            } else {
-                launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
-            }
-        }
-        cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
-    };
-    int cur = 0;
-    for (int k = 1; k <= max_iter; k++) {
-        bool launched = false;
-        if (c->use_graphs && !c->graphs_broken && c->tmask == 0) {
-            cudaGraphExec_t& ge = c->gexec[prec][cur];
-            if (!ge) {
-                // capture (records, does not run) and instantiate this parity
-                c->glaunch[prec][cur].clear();
-                c->grec = &c->glaunch[prec][cur];
-                cudaGraph_t g = nullptr;
-                bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-                if (ok) {
-                    c->capturing = true;
-                    iteration(cur);
-                    c->capturing = false;
-                    ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && g;
-                }
-                if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
-                if (g) cudaGraphDestroy(g);
-                if (!ok) {
-                    cudaGetLastError();
-                    ge = nullptr;
-                    c->graphs_broken = true;
-                }
-            }
-            if (ge) {
-                CUDA_TRY(cudaGraphLaunch(ge, c->s));
-                for (auto& e : c->glaunch[prec][cur]) {
-                    c->kstat[e.first].launches++;
-                    c->kstat[e.first].bytes += e.second;
-                }
-                launched = true;
-            }
-        }
-        if (!launched) iteration(cur);
-        CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaStreamSynchronize(c->s));
-        harvest(c);
-        cur ^= 1;
-        *iters = k;
-        if (c->h_sc[S_NONFINITE] != 0.0)
-            return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
-        if (c->h_sc[S_RR] <= thresh) {
-            *converged = true;
-            break;
-        }
+    cudaGraphExec_t ge = pcg_graph<T>(c, c->run.cur);
+    if (ge) {
+        CUDA_TRY(cudaGraphLaunch(ge, c->s));
+        count_graph_launches(c, prec, c->run.cur);
+    } else {
+        pcg_iteration<T>(c, c->run.cur);
     }
+    CUDA_TRY(cudaGetLastError());
+    return FLD_OK;
+}
+
+// After an iteration has completed (its scalars are in the host mirror).
+fld_status pcg_after(fld_ctx* c) {
+    harvest(c);
+    auto& R = c->run;
+    R.k++;
+    R.cur ^= 1;
+    if (c->h_sc[S_NONFINITE] != 0.0) {
+        R.done = true;
+        return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", R.k);
+    }
+    if (c->h_sc[S_RR] <= R.thresh) {
+        R.conv = true;
+        R.done = true;
+    } else if (R.k >= R.max_iter) {
+        R.done = true;
+    }
+    return FLD_OK;
+}
+
+template <class T>
+fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
+    fld_status st = pcg_begin<T>(c, r0sq, rtol, max_iter);
+    if (st) return st;
+    while (!c->run.done) {
+        if ((st = pcg_enqueue<T>(c))) return st;
+        CUDA_TRY(cudaStreamSynchronize(c->s));
+        if ((st = pcg_after(c))) return st;
+    }
+    *iters = c->run.k;
+    *converged = c->run.conv;
     return FLD_OK;
 }
 
@@ -603,9 +673,8 @@ void free_ctx(fld_ctx* c) {
         if (c->stage[q]) cudaFree(c->stage[q]);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            if (c->gexec[a][b]) cudaGraphExecDestroy(c->gexec[a][b]);
+    drop_graphs(c);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->h_one) cudaFreeHost(c->h_one);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
@@ -686,7 +755,9 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
     return FLD_OK;
 }
 
-fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+// Enqueue the assembly (Sec. 2 limiter, Sec. 3.2 system) and the multigrid
+// setup, then the scalars to the host mirror; assemble_finish reads them.
+fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
     if (!c) return set_err(FLD_EINVAL, "null context");
     if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
     cudaStream_t s = c->s;
@@ -721,8 +792,13 @@ fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const d
       KScope k(c, K_COARSE_SETUP, 16.0 * nc * nc);
       launch_coarse_setup(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, s); }
     CUDA_TRY(cudaGetLastError());
-    fld_status st = read_scalars(c);
-    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return FLD_OK;
+}
+
+// After the assembly's scalars arrived: input checks.
+fld_status assemble_finish(fld_ctx* c) {
+    harvest(c);
     if (c->h_sc[S_BAD] == 1.0)
         return set_err(FLD_EINVAL, "E, n_HI and eta must be finite and >= 0");
     if (c->h_sc[S_BAD] == 2.0)
@@ -731,6 +807,13 @@ fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const d
         return set_err(FLD_ENONFINITE, "non-finite right-hand side");
     c->assembled = true;
     return FLD_OK;
+}
+
+fld_status assemble_impl(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+    fld_status st = assemble_enqueue(c, E, nHI, eta);
+    if (st) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    return assemble_finish(c);
 }
 
 
@@ -767,6 +850,30 @@ void fill_physdev(fld_ctx* c, double dt) {
     pd.limiter = p->limiter;
 }
 
+void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* eta) {
+    const long long n = c->L[0].d.n;
+    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE6_FIN), c->s); }
+    cudaEventRecord(c->e1, c->s);
+    cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+}
+
+// The photon balance and relative change from the host mirror.
+void finalize_info(fld_ctx* c, fld_info* inf) {
+    harvest(c);
+    const double V = c->g.dx * c->g.dy * c->g.dz;
+    const double scale = V / c->p.hnu;
+    inf->balance_abs = c->h_sc[S_BAL] * scale;
+    inf->emitted = c->h_sc[S_EMIT] * scale;
+    inf->absorbed = c->h_sc[S_ABSORB] * scale;
+    inf->floor_added = c->h_sc[S_FLOOR] * scale;
+    inf->rel_change = c->h_sc[S_EN2] > 0.0 ? std::sqrt(c->h_sc[S_DE2] / c->h_sc[S_EN2]) : 0.0;
+    const double budget = inf->emitted > inf->absorbed ? inf->emitted : inf->absorbed;
+    inf->balance_rel = budget > 0.0 ? std::fabs(inf->balance_abs) / budget : std::fabs(inf->balance_abs);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->e0, c->e1);
+    inf->ms = ms;
+}
+
 fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
     fld_info inf{};
     CUDA_TRY(cudaEventRecord(c->e0, c->s));
@@ -782,25 +889,310 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
         if (info) *info = inf;
         return st;
     }
-    const long long n = c->L[0].d.n;
-    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE6_FIN), c->s); }
-    CUDA_TRY(cudaEventRecord(c->e1, c->s));
-    if ((st = read_scalars(c))) return st;
-    const double V = c->g.dx * c->g.dy * c->g.dz;
-    const double scale = V / c->p.hnu;
-    inf.balance_abs = c->h_sc[S_BAL] * scale;
-    inf.emitted = c->h_sc[S_EMIT] * scale;
-    inf.absorbed = c->h_sc[S_ABSORB] * scale;
-    inf.floor_added = c->h_sc[S_FLOOR] * scale;
-    inf.rel_change = c->h_sc[S_EN2] > 0.0 ? std::sqrt(c->h_sc[S_DE2] / c->h_sc[S_EN2]) : 0.0;
-    const double budget = inf.emitted > inf.absorbed ? inf.emitted : inf.absorbed;
-    inf.balance_rel = budget > 0.0 ? std::fabs(inf.balance_abs) / budget : std::fabs(inf.balance_abs);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->e0, c->e1);
-    inf.ms = ms;
+    finalize_enqueue(c, E, nHI, eta);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->s));
+    finalize_info(c, &inf);
     inf.status = FLD_OK;
     if (info) *info = inf;
     return FLD_OK;
+}
+
+
+// ------------------------------------------------------- batched stepping
+//
+// Independent contexts advance in lockstep rounds.  In a round every
+// context enqueues its next piece of work on its own stream (assembly,
+// refinement residual, scaling, update, finalise); the contexts inside CG
+// contribute their captured iteration graphs as independent branches of one
+// batch graph, so all their iterations, whatever the grid sizes, go to the
+// device in a single graph launch.  One synchronisation per round, then each
+// context takes its next state from its scalars.  Each context runs exactly
+// the kernels of a single fld_step, so results match it bit for bit.
+
+enum BState { BS_ASM, BS_SCALE, BS_ITER, BS_RESID, BS_TRUE_RES, BS_FINAL, BS_DONE };
+
+struct BItem {
+    fld_ctx* c;
+    double* E;
+    const double* nHI;
+    const double* eta;
+    fld_info inf;
+    fld_status st;
+    int state;
+    int prec;            // CG precision in progress (0 FP64, 1 FP32)
+    double bb;
+    int inner_total, outer;
+    bool conv;
+    std::string err;
+};
+
+std::mutex g_batch_lock;
+std::map<std::vector<unsigned long long>, cudaGraphExec_t> g_batch_graphs;
+unsigned long long g_next_ctx_id = 1;
+
+thread_local cudaStream_t tl_bs = nullptr;
+thread_local cudaEvent_t tl_bev = nullptr;
+thread_local int tl_dev = -1;
+
+fld_status batch_stream(cudaStream_t* bs, cudaEvent_t* bev) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (!tl_bs || tl_dev != dev) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&tl_bs, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&tl_bev, cudaEventDisableTiming));
+        tl_dev = dev;
+    }
+    *bs = tl_bs;
+    *bev = tl_bev;
+    return FLD_OK;
+}
+
+// One graph holding the current CG iteration of every item as a branch.
+cudaGraphExec_t batch_graph(const std::vector<BItem*>& its) {
+    std::vector<unsigned long long> key;
+    for (BItem* b : its) {
+        key.push_back(b->c->id);
+        key.push_back((unsigned long long)(b->prec * 2 + b->c->run.cur));
+        key.push_back(b->c->graph_gen);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_lock);
+    auto it = g_batch_graphs.find(key);
+    if (it != g_batch_graphs.end()) return it->second;
+    if (g_batch_graphs.size() >= 64) {
+        for (auto& kv : g_batch_graphs) cudaGraphExecDestroy(kv.second);
+        g_batch_graphs.clear();
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    bool ok = true;
+    for (BItem* b : its) {
+        cudaGraphNode_t node;
+        cudaGraph_t child = b->c->graph[b->prec][b->c->run.cur];
+        if (!child || cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child) != cudaSuccess) { ok = false; break; }
+    }
+    cudaGraphExec_t ge = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (!ok) { cudaGetLastError(); return nullptr; }
+    g_batch_graphs[key] = ge;
+    return ge;
+}
+
+// Forget batch graphs holding this context's iterations (it is going away).
+void forget_batch_graphs(unsigned long long id) {
+    std::lock_guard<std::mutex> lock(g_batch_lock);
+    for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
+        bool uses = false;
+        for (size_t q = 0; q < it->first.size(); q += 3) uses = uses || it->first[q] == id;
+        if (uses) {
+            cudaGraphExecDestroy(it->second);
+            it = g_batch_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+void bfail(BItem& b, fld_status st) {
+    b.st = st;
+    b.inf.status = st;
+    b.err = g_err;
+    b.state = BS_DONE;
+}
+
+// What a context does after the round's synchronisation.
+void batch_after(BItem& b) {
+    fld_ctx* c = b.c;
+    const long long n = c->L[0].d.n;
+    const double rtol = c->p.rtol;
+    fld_status st = FLD_OK;
+    switch (b.state) {
+    case BS_ASM: {
+        if ((st = assemble_finish(c))) return bfail(b, st);
+        b.bb = c->h_sc[S_BB];
+        if (b.bb == 0.0) {
+            cudaMemsetAsync(c->dE, 0, n * sizeof(double), c->s);
+            finalize_enqueue(c, b.E, b.nHI, b.eta);
+            b.conv = true;
+            b.state = BS_FINAL;
+        } else if (!c->mixed) {
+            cudaMemcpyAsync(c->cg[0], c->b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+            cudaMemsetAsync(c->cg[5], 0, n * sizeof(double), c->s);
+            b.prec = 0;
+            if ((st = pcg_begin<double>(c, b.bb, rtol, c->p.max_iter))) return bfail(b, st);
+            b.state = BS_ITER;
+        } else {
+            // the first refinement residual is b itself (x = 0)
+            b.inf.rel_res = 1.0;
+            { KScope k(c, K_IR_SCALE, 16.0 * n);
+              launch_ir_scale(n, c->b, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            b.state = BS_SCALE;
+        }
+        return;
+    }
+    case BS_SCALE: {
+        harvest(c);
+        double irtol = 0.5 * rtol / b.inf.rel_res;
+        if (irtol < c->p.inner_rtol) irtol = c->p.inner_rtol;
+        if (irtol > 0.5) irtol = 0.5;
+        b.prec = 1;
+        if ((st = pcg_begin<float>(c, c->h_sc[S_R0], irtol, c->p.max_iter - b.inner_total))) return bfail(b, st);
+        b.state = BS_ITER;
+        return;
+    }
+    case BS_ITER: {
+        if ((st = pcg_after(c))) return bfail(b, st);
+        if (!c->run.done) return;
+        if (!c->mixed) {
+            b.inf.iters = c->run.k;
+            b.conv = c->run.conv;
+            cudaMemcpyAsync(c->dE, c->cg[5], n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+            { KScope k(c, K_RESIDUAL64, 48.0 * n);
+              launch_residual64(c->L[0].d, c->L[0].A64, nullptr, c->b, c->dE, nullptr,
+                                red(c, R_STORE_SUM_MAX, S_TRUE_RR, S_RMAX), c->s); }
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            b.state = BS_TRUE_RES;
+        } else {
+            b.inner_total += c->run.k;
+            { KScope k(c, K_IR_UPDATE, (b.outer == 0 ? 12.0 : 20.0) * n);
+              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, b.outer == 0, c->s); }
+            b.outer++;
+            { KScope k(c, K_RESIDUAL64, 56.0 * n);
+              launch_residual64(c->L[0].d, c->L[0].A64, c->diag64, c->b, c->dE, c->r64,
+                                red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            b.state = BS_RESID;
+        }
+        return;
+    }
+    case BS_RESID: {
+        harvest(c);
+        if (c->h_sc[S_NONFINITE] != 0.0) {
+            set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", b.outer);
+            return bfail(b, FLD_ENONFINITE);
+        }
+        b.inf.rel_res = std::sqrt(c->h_sc[S_R64] / b.bb);
+        b.inf.iters = b.inner_total;
+        b.inf.outer_iters = b.outer;
+        if (b.inf.rel_res <= rtol) {
+            b.conv = true;
+            finalize_enqueue(c, b.E, b.nHI, b.eta);
+            b.state = BS_FINAL;
+        } else if (b.inner_total >= c->p.max_iter) {
+            set_err(FLD_ENOCONV, "no convergence: relative residual %.3e > rtol %.3e after %d iterations",
+                    b.inf.rel_res, rtol, b.inner_total);
+            return bfail(b, FLD_ENOCONV);
+        } else {
+            { KScope k(c, K_IR_SCALE, 16.0 * n);
+              launch_ir_scale(n, c->r64, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            b.state = BS_SCALE;
+        }
+        return;
+    }
+    case BS_TRUE_RES: {
+        harvest(c);
+        b.inf.rel_res = std::sqrt(c->h_sc[S_TRUE_RR] / b.bb);
+        if (!b.conv) {
+            set_err(FLD_ENOCONV, "no convergence: relative residual %.3e > rtol %.3e after %d iterations",
+                    b.inf.rel_res, rtol, b.inf.iters);
+            return bfail(b, FLD_ENOCONV);
+        }
+        finalize_enqueue(c, b.E, b.nHI, b.eta);
+        b.state = BS_FINAL;
+        return;
+    }
+    case BS_FINAL: {
+        finalize_info(c, &b.inf);
+        b.inf.status = FLD_OK;
+        b.st = FLD_OK;
+        b.state = BS_DONE;
+        return;
+    }
+    default:
+        return;
+    }
+}
+
+fld_status step_batched_impl(int n, fld_ctx** cs, double** E, const double** nHI, const double** eta,
+                             fld_info* infos) {
+    cudaStream_t bs = nullptr;
+    cudaEvent_t bev = nullptr;
+    fld_status st = batch_stream(&bs, &bev);
+    if (st) return st;
+    std::vector<BItem> items(n);
+    for (int i = 0; i < n; i++) {
+        BItem& b = items[i];
+        b.c = cs[i];
+        b.E = E[i];
+        b.nHI = nHI[i];
+        b.eta = eta[i];
+        b.inf = fld_info{};
+        b.st = FLD_OK;
+        b.prec = 0;
+        b.bb = 0.0;
+        b.inner_total = b.outer = 0;
+        b.conv = false;
+        b.state = BS_ASM;
+        cudaEventRecord(b.c->e0, b.c->s);
+        if ((st = assemble_enqueue(b.c, b.E, b.nHI, b.eta))) bfail(b, st);
+    }
+    for (;;) {
+        // contexts inside CG: their iterations as one batch-graph launch
+        std::vector<BItem*> iter, direct;
+        for (BItem& b : items)
+            if (b.state == BS_ITER) {
+                const bool g = b.prec ? pcg_graph<float>(b.c, b.c->run.cur) != nullptr
+                                      : pcg_graph<double>(b.c, b.c->run.cur) != nullptr;
+                (g ? iter : direct).push_back(&b);
+            }
+        cudaGraphExec_t ge = iter.size() > 1 ? batch_graph(iter) : nullptr;
+        if (ge) {
+            for (BItem* b : iter) {
+                cudaEventRecord(b->c->ev_join, b->c->s);
+                cudaStreamWaitEvent(bs, b->c->ev_join, 0);
+            }
+            cudaGraphLaunch(ge, bs);
+            cudaEventRecord(bev, bs);
+            for (BItem* b : iter) {
+                cudaStreamWaitEvent(b->c->s, bev, 0);
+                count_graph_launches(b->c, b->prec, b->c->run.cur);
+            }
+        } else {
+            for (BItem* b : iter) direct.push_back(b);
+        }
+        for (BItem* b : direct) {
+            st = b->prec ? pcg_enqueue<float>(b->c) : pcg_enqueue<double>(b->c);
+            if (st) bfail(*b, st);
+        }
+        bool any = false;
+        for (BItem& b : items) {
+            if (b.state == BS_DONE) continue;
+            any = true;
+            cudaError_t e = cudaStreamSynchronize(b.c->s);
+            if (e != cudaSuccess) {
+                set_err(FLD_ECUDA, "stream synchronisation failed: %s", cudaGetErrorString(e));
+                bfail(b, FLD_ECUDA);
+            }
+        }
+        if (!any) break;
+        for (BItem& b : items)
+            if (b.state != BS_DONE) batch_after(b);
+    }
+    fld_status first = FLD_OK;
+    std::string msg;
+    for (int i = 0; i < n; i++) {
+        infos[i] = items[i].inf;
+        infos[i].status = items[i].st;
+        if (items[i].st && !first) {
+            first = items[i].st;
+            msg = "batch item " + std::to_string(i) + ": " + items[i].err;
+        }
+    }
+    if (first) g_err = msg;
+    return first;
 }
 
 }  // namespace
@@ -900,6 +1292,15 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
         return set_err(FLD_ENOMEM, "pinned allocation failed");
     }
     *c->h_one = 1.0;
+    if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return set_err(FLD_ECUDA, "event creation failed");
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_batch_lock);
+        c->id = g_next_ctx_id++;
+    }
     // graphs need a capturable (non-legacy) stream; "auto" uses them where
     // launch latency matters, grids up to 128^3
     c->use_graphs = c->s != nullptr &&
@@ -914,7 +1315,10 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     return FLD_OK;
 }
 
-void fld_destroy(fld_ctx* c) { free_ctx(c); }
+void fld_destroy(fld_ctx* c) {
+    if (c) forget_batch_graphs(c->id);
+    free_ctx(c);
+}
 
 fld_status fld_assemble(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
     return assemble_impl(c, E, nHI, eta);
@@ -1032,24 +1436,10 @@ fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E, const double** nH
         return set_err(FLD_EINVAL, "invalid batch arguments");
     for (int i = 0; i < n; i++)
         if (!ctxs[i]) return set_err(FLD_EINVAL, "null context %d in batch", i);
-    std::vector<fld_status> st(n, FLD_OK);
-    std::vector<std::string> msg(n);
-    std::vector<std::thread> th;
-    th.reserve(n);
-    // Each context drives its own stream from its own host thread, so the
-    // steps' kernels overlap on the device.
     for (int i = 0; i < n; i++)
-        th.emplace_back([&, i] {
-            st[i] = step_impl(ctxs[i], E[i], nHI[i], eta[i], &infos[i]);
-            if (st[i]) msg[i] = g_err;
-        });
-    for (auto& t : th) t.join();
-    for (int i = 0; i < n; i++)
-        if (st[i]) {
-            g_err = "batch item " + std::to_string(i) + ": " + msg[i];
-            return st[i];
-        }
-    return FLD_OK;
+        for (int j = 0; j < i; j++)
+            if (ctxs[i] == ctxs[j]) return set_err(FLD_EINVAL, "context %d appears twice in the batch", i);
+    return step_batched_impl(n, ctxs, E, nHI, eta, infos);
 }
 
 fld_status fld_apply(fld_ctx* c, const double* x, double* y) {
@@ -1105,12 +1495,7 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
     cudaStream_t s = c->s;
     CUDA_TRY(cudaStreamSynchronize(s));
     // captured graphs hold the old launch shapes
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            if (c->gexec[a][b]) {
-                cudaGraphExecDestroy(c->gexec[a][b]);
-                c->gexec[a][b] = nullptr;
-            }
+    drop_graphs(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -1213,12 +1598,7 @@ fld_status fld_set_tuning(fld_ctx* c, const int* in, int n) {
             c->L[l].tune[k].threads = in[2 * (l * NTUNE + k)];
             c->L[l].tune[k].target = in[2 * (l * NTUNE + k) + 1];
         }
-    for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++)
-            if (c->gexec[a][b]) {
-                cudaGraphExecDestroy(c->gexec[a][b]);
-                c->gexec[a][b] = nullptr;
-            }
+    drop_graphs(c);
     return FLD_OK;
 }
 

@@ -54,18 +54,23 @@ class Server:
     """A pool of worker threads stepping requests under an HBM budget."""
 
     def __init__(self, budget_bytes: float = 40e9, workers: int = 8, keep_results: bool = False,
-                 params: Optional[synth.Params] = None, device: int = 0):
+                 params: Optional[synth.Params] = None, device: int = 0, batch: int = 1):
         import torch
         self.torch = torch
         self.device = device
         self.budget = float(budget_bytes)
         self.workers = workers
         self.keep = keep_results
+        # batch > 1: a free worker takes every request that has arrived (up
+        # to batch) and steps them together through fld_step_batched, whose
+        # CG iterations run as one graph launch for all of them
+        self.batch = max(1, int(batch))
         self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED)
         self._used = 0.0
         self._cv = threading.Condition()
         self._streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
         self._ctx: List[Dict[int, fld.Context]] = [dict() for _ in range(workers)]
+        self._bctx: List[Dict[int, List[fld.Context]]] = [dict() for _ in range(workers)]
         self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
         self._fp_cache: Dict[int, int] = {}
 
@@ -136,6 +141,56 @@ class Server:
         return Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, info["status"],
                       info["iters"], info["outer_iters"], info["rel_res"], out)
 
+    def step_batch(self, w: int, reqs: Sequence[synth.Request], t0: float) -> List[Result]:
+        """Step several arrived requests together on worker w."""
+        torch = self.torch
+        start = time.perf_counter() - t0
+        out: List[Result] = []
+        admitted = []
+        for r in reqs:
+            nb = self.footprint(r.n)
+            if nb <= 0 or nb > self.budget:
+                out.append(Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, fld.FLD_ENOMEM))
+            else:
+                admitted.append(r)
+        if not admitted:
+            return out
+        # the group is admitted as a whole (the worker loop keeps it within
+        # the budget), so workers never hold part of the budget while waiting
+        total = float(sum(self.footprint(r.n) for r in admitted))
+        self._admit(total)
+        nbytes = [total]
+        try:
+            with torch.cuda.stream(self._streams[w]):
+                used: Dict[int, int] = {}
+                ctxs, fields = [], []
+                for r in admitted:
+                    pool = self._bctx[w].setdefault(r.n, [])
+                    k = used.get(r.n, 0)
+                    used[r.n] = k + 1
+                    if k == len(pool):
+                        pool.append(fld.fld_create(synth.Grid.cube(r.n), self.params, self._streams[w]))
+                    ctxs.append(pool[k])
+                    fields.append(self._fields(r))
+                st, infos = fld.fld_step_batched(ctxs, [f[0] for f in fields], [f[1] for f in fields],
+                                                 [f[2] for f in fields], check=False)
+                hosts = []
+                for r, f in zip(admitted, fields):
+                    h = torch.empty(r.n ** 3, dtype=torch.float64, pin_memory=True) if self.keep else None
+                    if h is not None:
+                        h.copy_(f[0], non_blocking=True)
+                    hosts.append(h)
+                self._streams[w].synchronize()
+                now = time.perf_counter() - t0
+                for r, info, h in zip(admitted, infos, hosts):
+                    out.append(Result(r.rid, r.n, r.arrival, start, now, info["status"], info["iters"],
+                                      info["outer_iters"], info["rel_res"],
+                                      h.numpy().copy() if h is not None else None))
+        finally:
+            for nb in nbytes:
+                self._release(nb)
+        return out
+
     # ------------------------------------------------------------ the loop
     def run(self, requests: Sequence[synth.Request], realtime: bool = True) -> List[Result]:
         """Serve requests as they arrive (arrival times in s from now when
@@ -152,9 +207,31 @@ class Server:
                 item = q.get()
                 if item is None:
                     return
-                res = self.step_one(w, item, t0)
+                if self.batch == 1:
+                    res = [self.step_one(w, item, t0)]
+                else:
+                    group, stop = [item], False
+                    total = self.footprint(item.n)
+                    while len(group) < self.batch:
+                        try:
+                            nxt = q.get_nowait()
+                        except queue.Empty:
+                            break
+                        if nxt is None:
+                            stop = True
+                            break
+                        fp = self.footprint(nxt.n)
+                        if total + fp > self.budget:
+                            q.put(nxt)       # waits for a later group
+                            break
+                        group.append(nxt)
+                        total += fp
+                    res = self.step_batch(w, group, t0)
+                    if stop:
+                        q.put(None)
                 with lock:
-                    results[item.rid] = res
+                    for r in res:
+                        results[r.rid] = r
 
         threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
         for t in threads:
@@ -178,6 +255,11 @@ class Server:
         for d in self._ctx:
             for ctx in d.values():
                 ctx.close()
+            d.clear()
+        for d in self._bctx:
+            for pool in d.values():
+                for ctx in pool:
+                    ctx.close()
             d.clear()
 
 

@@ -79,3 +79,70 @@ def test_poisson_stream_latency_report(serving):
     srv.close()
     s = serving.summarize(res)
     assert s["ok"] == 200 and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_step_batched_uneven_grids_equal_single_steps():
+    """fld_step_batched: uneven grids in lockstep, every CG iteration of all
+    of them one batch-graph launch; each result is bit-identical to a single
+    fld_step of the same context, and a failing item leaves the others."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_0645_gb300 import fld
+    cases = [synth.config_uniform(16, sources=3, seed=1, centre=False, precision=synth.PREC_MIXED),
+             synth.random_case((24, 16, 32), seed=2, periodic=(True, False, False)),
+             synth.config_uniform(48, sources=9, seed=3, centre=False, precision=synth.PREC_MIXED),
+             synth.config4(64, sources=64),
+             synth.config2(32),
+             synth.config_uniform(32, sources=2, seed=4, centre=False, precision=synth.PREC_MIXED)]
+    cases[1].params.precision = synth.PREC_MIXED
+    cases[3].params.precision = synth.PREC_MIXED
+    cases[4].params.precision = synth.PREC_FP64
+    cases[5].params.max_iter = 1                      # fails: FLD_ENOCONV
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+
+    def make():
+        streams = [torch.cuda.Stream() for _ in cases]
+        ctxs = [fld.fld_create(c.grid, c.params, s) for c, s in zip(cases, streams)]
+        return streams, ctxs
+
+    # single steps
+    streams, ctxs = make()
+    single = []
+    for c, ctx, s in zip(cases, ctxs, streams):
+        E = dev(c.E)
+        with torch.cuda.stream(s):
+            info = fld.fld_step(ctx, E, dev(c.nHI), dev(c.eta), check=False)
+        s.synchronize()
+        single.append((E.cpu().numpy(), info))
+    for ctx in ctxs:
+        ctx.close()
+    # the batch, twice in a row (graphs are reused the second time)
+    for rep in range(2):
+        streams, ctxs = make()
+        Es = [dev(c.E) for c in cases]
+        st, infos = fld.fld_step_batched(ctxs, Es, [dev(c.nHI) for c in cases], [dev(c.eta) for c in cases],
+                                         check=False)
+        torch.cuda.synchronize()
+        assert st == fld.FLD_ENOCONV
+        for (Es_, info_s), E, info_b, c in zip(single, Es, infos, cases):
+            assert info_b["status"] == info_s["status"]
+            assert info_b["iters"] == info_s["iters"] and info_b["outer_iters"] == info_s["outer_iters"]
+            assert np.array_equal(E.cpu().numpy(), Es_)
+        assert infos[5]["status"] == fld.FLD_ENOCONV
+        assert np.array_equal(Es[5].cpu().numpy(), cases[5].E.ravel())   # unchanged on failure
+        for ctx in ctxs:
+            ctx.close()
+
+
+def test_batched_serving_equals_alone(serving):
+    # workers that step every arrived request together (fld_step_batched)
+    reqs = small_stream(24, seed=41)
+    alone = serving.Server(workers=1, keep_results=True)
+    ra = alone.run(reqs, realtime=False)
+    alone.close()
+    srv = serving.Server(workers=2, keep_results=True, batch=8)
+    rb = srv.run(reqs, realtime=False)
+    srv.close()
+    for a, b in zip(ra, rb):
+        assert a.status == 0 and b.status == 0
+        assert np.array_equal(a.E, b.E)
