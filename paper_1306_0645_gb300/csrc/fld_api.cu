@@ -773,7 +773,7 @@ fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, cons
         KScope k(c, K_ASM_FIX, 0.0);
         launch_assemble_fix(L0.d, c->pd, E, nHI, L0.A64, op32, c->flist, s);
     }
-    { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 4.0 : 8.0)));
+    { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 28.0 : 8.0)));
       launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr,
                           red(c, R_STORE_SUM_MAX, S_BB, S_RMAX), s); }
     for (int l = 1; l < c->nl; l++) {
