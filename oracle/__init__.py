@@ -6,7 +6,7 @@ imports this package, and this package imports nothing from the product.
 
 The arithmetic lives in ``fld_oracle.c`` (plain C, FP64, one OpenMP loop per
 stencil sweep, serial dot products); see that file's header for the paper
-passages it follows (Sec. 2 limiter, Sec. 3.2 backward-Euler correction
+passages it follows (Sec. 2 limiter, Sec. 3.2 theta-method correction
 system, Table 1 solver) and the readings taken where the paper is silent.
 
 Arrays are numpy float64, C-contiguous, shaped (nz, ny, nx) so that x is the
@@ -56,7 +56,8 @@ def build(force: bool = False) -> str:
 
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3),
-                ("periodic", ctypes.c_int * 3)]
+                ("periodic", ctypes.c_int * 3), ("dirichlet", ctypes.c_int * 6),
+                ("ebc", ctypes.c_double * 6)]
 
 
 class _Phys(ctypes.Structure):
@@ -64,7 +65,7 @@ class _Phys(ctypes.Structure):
                 ("L_unit", ctypes.c_double), ("dmax_coef", ctypes.c_double),
                 ("rmin_coef", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("adot", ctypes.c_double), ("hnu", ctypes.c_double),
-                ("limiter", ctypes.c_int)]
+                ("limiter", ctypes.c_int), ("theta", ctypes.c_double)]
 
 
 class _Solver(ctypes.Structure):
@@ -86,17 +87,18 @@ def _lib_handle():
                 ("or_num_threads", [], ctypes.c_int),
                 ("or_lp_lambda", [ctypes.c_double], ctypes.c_double),
                 ("or_face_D", [ctypes.c_double] * 5 + [ctypes.POINTER(_Phys)], ctypes.c_double),
-                ("or_assemble", [ctypes.POINTER(_Grid), ctypes.POINTER(_Phys)] + [_P] * 8, ctypes.c_int),
+                ("or_assemble", [ctypes.POINTER(_Grid), ctypes.POINTER(_Phys)] + [_P] * 9, ctypes.c_int),
+                ("or_bnd_size", [ctypes.POINTER(ctypes.c_int)], ctypes.c_size_t),
                 ("or_apply", [ctypes.POINTER(_Grid)] + [_P] * 6, None),
                 ("or_dense_matrix", [ctypes.POINTER(_Grid)] + [_P] * 5, ctypes.c_int),
                 ("or_dense_solve", [ctypes.POINTER(_Grid)] + [_P] * 6, ctypes.c_int),
-                ("or_vcycle", [ctypes.POINTER(_Grid)] + [_P] * 6 + [ctypes.POINTER(_Solver)], ctypes.c_int),
-                ("or_pcg", [ctypes.POINTER(_Grid)] + [_P] * 6 + [ctypes.POINTER(_Solver),
+                ("or_vcycle", [ctypes.POINTER(_Grid)] + [_P] * 7 + [ctypes.POINTER(_Solver)], ctypes.c_int),
+                ("or_pcg", [ctypes.POINTER(_Grid)] + [_P] * 7 + [ctypes.POINTER(_Solver),
                             ctypes.POINTER(ctypes.c_int), _P, _P], ctypes.c_int),
                 ("or_step", [ctypes.POINTER(_Grid), ctypes.POINTER(_Phys), ctypes.POINTER(_Solver)]
                  + [_P] * 5, ctypes.c_int),
                 ("or_num_levels", [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
-                ("or_coarsen", [ctypes.POINTER(ctypes.c_int)] * 2 + [_P] * 8, ctypes.c_int),
+                ("or_coarsen", [ctypes.POINTER(ctypes.c_int)] * 3 + [_P] * 10, ctypes.c_int),
                 ("or_prolong_add", [ctypes.POINTER(ctypes.c_int)] * 2 + [_P] * 2, ctypes.c_int),
                 ("or_restrict", [ctypes.POINTER(ctypes.c_int)] * 2 + [_P] * 2, ctypes.c_int),
                 ("or_opacity_update", [ctypes.c_size_t] + [_P] * 4 + [ctypes.c_double] * 5, ctypes.c_int),
@@ -116,20 +118,36 @@ def _get(obj, name, default=None):
     return getattr(obj, name, default)
 
 
+def _dirichlet(g):
+    """Per-side Dirichlet flags and values (x lo, x hi, y lo, y hi, z lo, z hi)
+    of a grid object: attributes ``dirichlet`` (6 flags) and ``ebc`` (6
+    values); absent means reflecting everywhere."""
+    d = _get(g, "dirichlet") or (0,) * 6
+    v = _get(g, "ebc") or (0.0,) * 6
+    return [1 if x else 0 for x in d], [float(x) for x in v]
+
+
+def _has_dirichlet(g) -> bool:
+    return any(_dirichlet(g)[0])
+
+
 def _grid(g) -> _Grid:
     n = _get(g, "n")
     h = _get(g, "h")
     per = _get(g, "periodic")
+    dflag, dval = _dirichlet(g)
     return _Grid((ctypes.c_int * 3)(*[int(v) for v in n]),
                  (ctypes.c_double * 3)(*[float(v) for v in h]),
-                 (ctypes.c_int * 3)(*[1 if v else 0 for v in per]))
+                 (ctypes.c_int * 3)(*[1 if v else 0 for v in per]),
+                 (ctypes.c_int * 6)(*dflag), (ctypes.c_double * 6)(*dval))
 
 
 def _phys(p) -> _Phys:
     return _Phys(float(_get(p, "dt")), float(_get(p, "c")), float(_get(p, "L_unit")),
                  float(_get(p, "dmax_coef", 0.006)), float(_get(p, "rmin_coef", 1e-20)),
                  float(_get(p, "sigma")), float(_get(p, "adot_over_a", 0.0)),
-                 float(_get(p, "hnu", 2.17896e-11)), int(_get(p, "limiter", LIMITER_PAPER)))
+                 float(_get(p, "hnu", 2.17896e-11)), int(_get(p, "limiter", LIMITER_PAPER)),
+                 float(_get(p, "theta", 1.0)))
 
 
 def _solver(s) -> _Solver:
@@ -148,6 +166,15 @@ def _arr(a, shape=None):
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
+
+
+def _optr(a):
+    return _ptr(a) if a is not None else None
+
+
+def bnd_size(n) -> int:
+    """Length of the packed Dirichlet face array of an n = (nx, ny, nz) grid."""
+    return int(_lib_handle().or_bnd_size((ctypes.c_int * 3)(*[int(v) for v in n])))
 
 
 def _shape(g):
@@ -170,14 +197,17 @@ def face_D(E1, E2, k1, k2, h, phys) -> float:
 
 
 def assemble(grid, phys, E, nHI, eta) -> dict:
-    """Operator (m, wx, wy, wz) and right-hand side b of A dE = b."""
+    """Operator (m, wx, wy, wz), the packed Dirichlet face weights "bnd" (None
+    when the grid has no Dirichlet side) and the right-hand side b of
+    A dE = b."""
     sh = _shape(grid)
     E, nHI, eta = _arr(E, sh), _arr(nHI, sh), _arr(eta, sh)
     out = {k: np.empty(sh) for k in ("m", "wx", "wy", "wz", "b")}
+    out["bnd"] = np.empty(bnd_size(_get(grid, "n"))) if _has_dirichlet(grid) else None
     g, p = _grid(grid), _phys(phys)
     st = _lib_handle().or_assemble(ctypes.byref(g), ctypes.byref(p), _ptr(E), _ptr(nHI), _ptr(eta),
                                    _ptr(out["m"]), _ptr(out["wx"]), _ptr(out["wy"]),
-                                   _ptr(out["wz"]), _ptr(out["b"]))
+                                   _ptr(out["wz"]), _ptr(out["b"]), _optr(out["bnd"]))
     if st:
         raise OracleError(st, "assemble")
     return out
@@ -186,6 +216,13 @@ def assemble(grid, phys, E, nHI, eta) -> dict:
 def _op(grid, op):
     sh = _shape(grid)
     return [_arr(op[k], sh) for k in ("m", "wx", "wy", "wz")]
+
+
+def _bnd(grid, op):
+    b = op.get("bnd") if isinstance(op, dict) else None
+    if b is None:
+        return None
+    return _arr(b).ravel()
 
 
 def apply(grid, op, x) -> np.ndarray:
@@ -226,8 +263,9 @@ def vcycle(grid, op, r, solver=None) -> np.ndarray:
     r = _arr(r, sh)
     z = np.empty(sh)
     g, s = _grid(grid), _solver(solver or {})
+    bnd = _bnd(grid, op)
     st = _lib_handle().or_vcycle(ctypes.byref(g), _ptr(m), _ptr(wx), _ptr(wy), _ptr(wz),
-                                 _ptr(r), _ptr(z), ctypes.byref(s))
+                                 _optr(bnd), _ptr(r), _ptr(z), ctypes.byref(s))
     if st:
         raise OracleError(st, "vcycle")
     return z
@@ -244,19 +282,21 @@ def pcg(grid, op, b, solver=None, allow_noconv=False):
     iters = ctypes.c_int(0)
     rel = np.zeros(1)
     hist = np.zeros(s.max_iter + 1)
-    st = _lib_handle().or_pcg(ctypes.byref(g), _ptr(m), _ptr(wx), _ptr(wy), _ptr(wz), _ptr(b),
-                              _ptr(x), ctypes.byref(s), ctypes.byref(iters), _ptr(rel), _ptr(hist))
+    bnd = _bnd(grid, op)
+    st = _lib_handle().or_pcg(ctypes.byref(g), _ptr(m), _ptr(wx), _ptr(wy), _ptr(wz), _optr(bnd),
+                              _ptr(b), _ptr(x), ctypes.byref(s), ctypes.byref(iters), _ptr(rel),
+                              _ptr(hist))
     if st and not (st == ENOCONV and allow_noconv):
         raise OracleError(st, "pcg")
     return x, iters.value, float(rel[0]), hist[: iters.value + 1]
 
 
 def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
-    """One FLD backward-Euler step: returns (E_new, info dict)."""
+    """One FLD theta-method step: returns (E_new, info dict)."""
     sh = _shape(grid)
     E, nHI, eta = _arr(E, sh), _arr(nHI, sh), _arr(eta, sh)
     E_new = E.copy()
-    info = np.zeros(8)
+    info = np.zeros(9)
     g, p, s = _grid(grid), _phys(phys), _solver(solver or {})
     st = _lib_handle().or_step(ctypes.byref(g), ctypes.byref(p), ctypes.byref(s), _ptr(E),
                                _ptr(nHI), _ptr(eta), _ptr(E_new), _ptr(info))
@@ -265,7 +305,7 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
     return E_new, {"status": st, "iters": int(info[0]), "rel_res": info[1],
                    "balance_abs": info[2], "balance_rel": info[3],
                    "emitted": info[4], "absorbed": info[5], "floor_added": info[6],
-                   "rel_change": info[7]}
+                   "rel_change": info[7], "outflow": info[8]}
 
 
 def num_levels(n):
@@ -279,13 +319,24 @@ def _ints(v):
     return (ctypes.c_int * 3)(*[int(x) for x in v])
 
 
-def coarsen(nf, periodic, op):
+def coarsen(nf, periodic, op, dirichlet=None):
+    """Coarse operator of a level; with dirichlet (6 flags) the op's packed
+    face weights "bnd" are coarsened too."""
     shf = (nf[2], nf[1], nf[0])
     shc = (nf[2] // 2, nf[1] // 2, nf[0] // 2)
     ins = [_arr(op[k], shf) for k in ("m", "wx", "wy", "wz")]
     outs = {k: np.empty(shc) for k in ("m", "wx", "wy", "wz")}
-    _lib_handle().or_coarsen(_ints(nf), _ints(periodic), *[_ptr(a) for a in ins],
-                             *[_ptr(outs[k]) for k in ("m", "wx", "wy", "wz")])
+    dflag = None
+    bnd = bndc = None
+    if dirichlet is not None and any(dirichlet):
+        dflag = (ctypes.c_int * 6)(*[1 if v else 0 for v in dirichlet])
+        bnd = _arr(op["bnd"]).ravel()
+        bndc = np.empty(bnd_size((nf[0] // 2, nf[1] // 2, nf[2] // 2)))
+    st = _lib_handle().or_coarsen(_ints(nf), _ints(periodic), dflag, *[_ptr(a) for a in ins], _optr(bnd),
+                                  *[_ptr(outs[k]) for k in ("m", "wx", "wy", "wz")], _optr(bndc))
+    if st:
+        raise OracleError(st, "coarsen")
+    outs["bnd"] = bndc
     return outs
 
 

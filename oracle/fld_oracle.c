@@ -19,9 +19,11 @@
  *     (Sec. 1, LevermorePomraning1981);
  *   - opacity kappa = n_HI sigma for a monochromatic grey source
  *     (Eq. "opacity" with a single species and a delta-function SED);
- *   - backward Euler (theta = 1) with D lagged at E^n, so the step is one
- *     linear system, posed for the correction dE = E^{n+1} - E^n
- *     (Sec. 3.2);
+ *   - the implicit theta-method of Sec. 3.2 (theta = 1 backward Euler,
+ *     theta = 1/2 the trapezoidal rule) with D lagged at E^n, so the step is
+ *     one linear system, posed for the correction dE = E^{n+1} - E^n:
+ *     with F(E) = div(D grad E) - (c kappa + adot/a) E + eta (eta and kappa
+ *     held at t^n), dE - theta dt L dE = dt F(E^n), L the linear part of F;
  *   - the solver of Table 1: PCG, at most 50 iterations, tolerance 1e-8,
  *     preconditioned by a geometric multigrid cycle with red/black
  *     Gauss-Seidel relaxation, 1 pre- and 1 post-sweep.
@@ -34,29 +36,43 @@
  *   - LP limiter: with x = R/kappa_f, D = c lambda(x)/kappa_f,
  *     lambda(x) = (coth x - 1/x)/x, series 1/3 - x^2/45 + 2x^4/945 for
  *     x < 1e-2, and D = c/R when kappa_f = 0 or x > 1e8;
- *   - zero-gradient boundaries carry no flux (face weight 0), periodic wrap;
+ *   - boundaries per face of the box: reflecting (zero gradient, no flux,
+ *     face weight 0), periodic (wrap; both faces of the axis), Dirichlet
+ *     (E fixed to E_b on the face, half a cell from the cell centre: the
+ *     face takes D from the limiter with face E = (E + E_b)/2, normal
+ *     difference |E - E_b| over h/2 and kappa_f = kappa of the cell, and
+ *     weight theta dt D / (h h/2) on the diagonal), and outflow read as
+ *     Dirichlet with E_b = 0, through which the limiter lets radiation
+ *     stream out at |F| = c E_face when the cell is optically thin;
  *   - multigrid: full 2x coarsening of cell-centred grids while every
  *     dimension is even and the smallest one exceeds 4; trilinear
  *     prolongation P (ghost cells per boundary condition), restriction
  *     R = P^T / 8; coarse operator by rediscretisation (coarse face weight =
- *     sum of the 4 fine face weights across the coarse face / 16, coarse
- *     mass term = mean of the 8 children); dense Cholesky on the coarsest
+ *     sum of the 4 fine face weights across the coarse face / 16, also for
+ *     Dirichlet boundary faces; coarse mass term = mean of the 8 children's
+ *     mass terms, the boundary weights apart); dense Cholesky on the coarsest
  *     grid; one V(pre,post) cycle per PCG iteration, red = (i+j+k) even,
  *     pre-sweeps red then black, post-sweeps black then red (symmetric);
  *     weighted Jacobi as the alternative smoother;
  *   - PCG from x0 = 0, stop when ||r||_2 / ||b||_2 <= rtol on the
  *     recursively updated residual; b = 0 gives dE = 0 in 0 iterations;
- *   - E^{n+1} = max(E^n + dE, 0): the exact solution is non-negative (A is
- *     an M-matrix and A E^{n+1} = E^n + dt eta >= 0), so negative values are
- *     solver-tolerance artefacts; the photon balance is taken on E^n + dE
- *     before the floor, and the floor's addition is reported.
+ *   - E^{n+1} = max(E^n + dE, 0): for backward Euler the exact solution is
+ *     non-negative (A is an M-matrix and A E^{n+1} = E^n + dt eta >= 0), so
+ *     negative values are solver-tolerance artefacts; the trapezoidal rule
+ *     can undershoot for large dt, which the floor also catches.  The photon
+ *     balance is taken on E^n + dE before the floor, and the floor's
+ *     addition is reported.
  *
  * Layout: every field is a contiguous FP64 array, x fastest,
  * idx = i + nx (j + ny k).  The operator of a level is stored as the mass
- * term m_i = 1 + dt (c kappa_i + adot/a) and three lower-face weights:
+ * term m_i = 1 + theta dt (c kappa_i + adot/a) + (the theta-scaled weights of
+ * the cell's Dirichlet boundary faces) and three lower-face weights
+ * theta dt D / h^2:
  * wx[idx] couples cell (i,j,k) with (i-1,j,k) (and with (nx-1,j,k) for i = 0
- * on a periodic axis; 0 on a zero-gradient boundary), likewise wy, wz.
+ * on a periodic axis; 0 on any other boundary), likewise wy, wz.
  * Row i of A:  (A u)_i = m_i u_i + sum_faces w_f (u_i - u_nbr).
+ * The weights of Dirichlet faces are also kept per face, in one packed
+ * boundary array (see side_offset), for the coarsening.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -69,10 +85,13 @@ enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ENOCONV = 3 };
 enum { OR_LIMITER_PAPER = 0, OR_LIMITER_LP = 1 };
 enum { OR_SMOOTH_RBGS = 0, OR_SMOOTH_JACOBI = 1 };
 
+/* Faces of the box, side s = 2 axis + (0 lower, 1 upper). */
 typedef struct {
     int n[3];          /* cells per axis */
     double h[3];       /* cell widths, cm */
-    int periodic[3];   /* 1 = periodic, 0 = zero-gradient */
+    int periodic[3];   /* 1 = periodic axis (both faces) */
+    int dirichlet[6];  /* per side: 1 = E fixed to ebc[side]; 0 = reflecting */
+    double ebc[6];     /* Dirichlet value of each side (outflow: 0) */
 } or_grid;
 
 typedef struct {
@@ -85,6 +104,7 @@ typedef struct {
     double adot;       /* adot/a, 1/s */
     double hnu;        /* erg per photon, for photon counts */
     int limiter;
+    double theta;      /* 1 backward Euler, 1/2 trapezoidal */
 } or_phys;
 
 typedef struct {
@@ -101,11 +121,50 @@ typedef struct {
     int periodic[3];
     double *m, *wx, *wy, *wz;
     int owned;
+    int dirichlet[6];
+    double* bnd;       /* packed Dirichlet face weights (NULL: none) */
 } or_level;
 
 #define OR_MAX_LEVELS 32
 
 static size_t ncell(const int n[3]) { return (size_t)n[0] * n[1] * n[2]; }
+
+/* Packed per-face boundary arrays: sides in the order x lo, x hi, y lo,
+ * y hi, z lo, z hi; the face of cell (i,j,k) on an x side has index
+ * j + ny k, on a y side i + nx k, on a z side i + nx j. */
+static size_t side_size(const int n[3], int s) {
+    int d = s / 2;
+    if (d == 0) return (size_t)n[1] * n[2];
+    if (d == 1) return (size_t)n[0] * n[2];
+    return (size_t)n[0] * n[1];
+}
+
+static size_t side_offset(const int n[3], int s) {
+    size_t o = 0;
+    for (int q = 0; q < s; q++) o += side_size(n, q);
+    return o;
+}
+
+size_t or_bnd_size(const int n[3]) { return side_offset(n, 6); }
+
+/* Index of cell (i,j,k)'s face on side s in the packed array, or -1 when
+ * the cell does not touch that side. */
+static long side_face(const int n[3], int s, int i, int j, int k) {
+    int d = s / 2, hi = s % 2;
+    int ijk[3] = {i, j, k};
+    if (ijk[d] != (hi ? n[d] - 1 : 0)) return -1;
+    size_t f;
+    if (d == 0) f = j + (size_t)n[1] * k;
+    else if (d == 1) f = i + (size_t)n[0] * k;
+    else f = i + (size_t)n[0] * j;
+    return (long)(side_offset(n, s) + f);
+}
+
+static int any_dirichlet(const int dir[6]) {
+    for (int s = 0; s < 6; s++)
+        if (dir[s]) return 1;
+    return 0;
+}
 
 int or_num_threads(void) {
 #ifdef _OPENMP
@@ -160,27 +219,38 @@ double or_face_D(double E1, double E2, double k1, double k2, double h,
 /* --------------------------------------------------------------- assembly */
 
 static int valid_grid(const or_grid* g) {
-    for (int d = 0; d < 3; d++)
+    for (int d = 0; d < 3; d++) {
         if (g->n[d] < 1 || !(g->h[d] > 0.0)) return 0;
+        if (g->periodic[d] && (g->dirichlet[2 * d] || g->dirichlet[2 * d + 1])) return 0;
+    }
+    for (int s = 0; s < 6; s++)
+        if (g->dirichlet[s] && !(isfinite(g->ebc[s]) && g->ebc[s] >= 0.0)) return 0;
     return 1;
 }
 
-/* Build m, wx, wy, wz and the right-hand side b of the backward-Euler
- * correction system A dE = b (Sec. 3.2):
- *   m_i  = 1 + dt (c kappa_i + adot/a)
- *   w_f  = dt D_f / h_d^2
- *   b_i  = dt eta_i - dt (c kappa_i + adot/a) E_i + sum_f w_f (E_nbr - E_i)
- */
+/* Build m, wx, wy, wz, the packed Dirichlet face weights bnd (may be NULL
+ * when the grid has no Dirichlet side) and the right-hand side b of the
+ * theta-method correction system A dE = b (Sec. 3.2):
+ *   w_f  = theta dt D_f / h_d^2                      (interior faces)
+ *   w_b  = theta dt D_b / (h_d h_d / 2)              (Dirichlet faces)
+ *   m_i  = 1 + theta dt (c kappa_i + adot/a) + sum of the cell's w_b
+ *   b_i  = dt eta_i - dt (c kappa_i + adot/a) E_i
+ *          + sum_f (w_f / theta) (E_nbr - E_i) + sum_b (w_b / theta) (E_b - E_i),
+ * i.e. b = dt F(E^n) with the unscaled weights and A = I - theta dt L. */
 int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                 const double* nHI, const double* eta, double* m, double* wx,
-                double* wy, double* wz, double* b) {
+                double* wy, double* wz, double* b, double* bnd) {
     if (!valid_grid(g) || !(p->dt > 0.0) || p->sigma < 0.0) return OR_EINVAL;
+    if (!(p->theta > 0.0 && p->theta <= 1.0)) return OR_EINVAL;
+    if (any_dirichlet(g->dirichlet) && !bnd) return OR_EINVAL;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const double th = p->theta;
     size_t N = ncell(g->n);
     for (size_t i = 0; i < N; i++)
         if (!(E[i] >= 0.0) || !(nHI[i] >= 0.0) || !(eta[i] >= 0.0) ||
             !isfinite(E[i]) || !isfinite(nHI[i]) || !isfinite(eta[i]))
             return OR_EINVAL;
+    if (bnd) memset(bnd, 0, or_bnd_size(g->n) * sizeof(double));
     double* w[3] = {wx, wy, wz};
     const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
 #pragma omp parallel for schedule(static)
@@ -190,7 +260,7 @@ int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                 int ijk[3] = {i, j, k};
                 size_t c = i + (size_t)nx * (j + (size_t)ny * k);
                 double kap = nHI[c] * p->sigma;
-                m[c] = 1.0 + p->dt * (p->c * kap + p->adot);
+                double mass = 1.0 + th * p->dt * (p->c * kap + p->adot);
                 for (int d = 0; d < 3; d++) {
                     size_t lo;
                     int has = 1;
@@ -200,8 +270,19 @@ int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                     if (!has) { w[d][c] = 0.0; continue; }
                     double D = or_face_D(E[lo], E[c], nHI[lo] * p->sigma, kap,
                                          g->h[d], p);
-                    w[d][c] = p->dt * D / (g->h[d] * g->h[d]);
+                    w[d][c] = th * p->dt * D / (g->h[d] * g->h[d]);
                 }
+                for (int sd = 0; sd < 6; sd++) {
+                    if (!g->dirichlet[sd]) continue;
+                    long f = side_face(g->n, sd, i, j, k);
+                    if (f < 0) continue;
+                    double h = g->h[sd / 2];
+                    double D = or_face_D(g->ebc[sd], E[c], kap, kap, 0.5 * h, p);
+                    double wb = th * p->dt * D / (h * 0.5 * h);
+                    bnd[f] = wb;
+                    mass += wb;
+                }
+                m[c] = mass;
             }
     /* b needs every face weight, so it is a second pass. */
 #pragma omp parallel for schedule(static)
@@ -215,16 +296,21 @@ int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                 for (int d = 0; d < 3; d++) {
                     /* lower face */
                     if (ijk[d] > 0)
-                        flux += w[d][c] * (E[c - stride[d]] - E[c]);
+                        flux += w[d][c] / th * (E[c - stride[d]] - E[c]);
                     else if (g->periodic[d])
-                        flux += w[d][c] * (E[c + (size_t)(g->n[d] - 1) * stride[d]] - E[c]);
+                        flux += w[d][c] / th * (E[c + (size_t)(g->n[d] - 1) * stride[d]] - E[c]);
                     /* upper face */
                     if (ijk[d] < g->n[d] - 1)
-                        flux += w[d][c + stride[d]] * (E[c + stride[d]] - E[c]);
+                        flux += w[d][c + stride[d]] / th * (E[c + stride[d]] - E[c]);
                     else if (g->periodic[d]) {
                         size_t up = c - (size_t)(g->n[d] - 1) * stride[d];
-                        flux += w[d][up] * (E[up] - E[c]);
+                        flux += w[d][up] / th * (E[up] - E[c]);
                     }
+                }
+                for (int sd = 0; sd < 6; sd++) {
+                    if (!g->dirichlet[sd]) continue;
+                    long f = side_face(g->n, sd, i, j, k);
+                    if (f >= 0) flux += bnd[f] / th * (g->ebc[sd] - E[c]);
                 }
                 b[c] = p->dt * eta[c] - p->dt * (p->c * kap + p->adot) * E[c] + flux;
             }
@@ -285,9 +371,12 @@ static double level_diag(const or_level* L, int i, int j, int k) {
 static or_level fine_level(const or_grid* g, const double* m, const double* wx,
                            const double* wy, const double* wz) {
     or_level L;
+    memset(&L, 0, sizeof(L));
     for (int d = 0; d < 3; d++) { L.n[d] = g->n[d]; L.periodic[d] = g->periodic[d]; }
+    for (int s = 0; s < 6; s++) L.dirichlet[s] = g->dirichlet[s];
     L.m = (double*)m; L.wx = (double*)wx; L.wy = (double*)wy; L.wz = (double*)wz;
     L.owned = 0;
+    L.bnd = NULL;
     return L;
 }
 
@@ -369,11 +458,50 @@ int or_dense_solve(const or_grid* g, const double* m, const double* wx,
 
 /* ------------------------------------------------------ multigrid pieces */
 
-/* Coarse operator by rediscretisation. */
+/* Sum of the Dirichlet face weights of cell (i,j,k) of a level. */
+static double cell_bnd(const or_level* L, int i, int j, int k) {
+    double sum = 0.0;
+    if (!L->bnd) return 0.0;
+    for (int s = 0; s < 6; s++) {
+        if (!L->dirichlet[s]) continue;
+        long f = side_face(L->n, s, i, j, k);
+        if (f >= 0) sum += L->bnd[f];
+    }
+    return sum;
+}
+
+/* Coarse operator by rediscretisation: every coarse face weight (interior
+ * or Dirichlet boundary) is the sum of the 4 fine weights across the coarse
+ * face / 16; the coarse mass term is the mean of the 8 children's mass
+ * terms (their m without their boundary weights) plus the coarse cell's own
+ * boundary weights. */
 static void coarsen(const or_level* F, or_level* C) {
     const int cx = C->n[0], cy = C->n[1], cz = C->n[2];
     const int fx = F->n[0], fy = F->n[1];
 #define FI(i, j, k) ((size_t)(i) + (size_t)fx * ((size_t)(j) + (size_t)fy * (size_t)(k)))
+    if (C->bnd) {
+        memset(C->bnd, 0, or_bnd_size(C->n) * sizeof(double));
+        for (int s = 0; s < 6; s++) {
+            if (!C->dirichlet[s]) continue;
+            int d = s / 2, hi = s % 2;
+            /* the two coarse axes spanning the face, and the fine layer */
+            int a0 = d == 0 ? 1 : 0, a1 = d == 2 ? 1 : 2;
+            for (int v = 0; v < C->n[a1]; v++)
+                for (int u = 0; u < C->n[a0]; u++) {
+                    int cc[3], ff[3];
+                    cc[d] = hi ? C->n[d] - 1 : 0;
+                    cc[a0] = u; cc[a1] = v;
+                    double sum = 0.0;
+                    for (int q = 0; q < 2; q++)
+                        for (int r = 0; r < 2; r++) {
+                            ff[d] = hi ? F->n[d] - 1 : 0;
+                            ff[a0] = 2 * u + q; ff[a1] = 2 * v + r;
+                            sum += F->bnd[side_face(F->n, s, ff[0], ff[1], ff[2])];
+                        }
+                    C->bnd[side_face(C->n, s, cc[0], cc[1], cc[2])] = sum / 16.0;
+                }
+        }
+    }
 #pragma omp parallel for schedule(static)
     for (int K = 0; K < cz; K++)
         for (int J = 0; J < cy; J++)
@@ -382,9 +510,11 @@ static void coarsen(const or_level* F, or_level* C) {
                 double msum = 0.0;
                 for (int dk = 0; dk < 2; dk++)
                     for (int dj = 0; dj < 2; dj++)
-                        for (int di = 0; di < 2; di++)
-                            msum += F->m[FI(2 * I + di, 2 * J + dj, 2 * K + dk)];
-                C->m[c] = msum / 8.0;
+                        for (int di = 0; di < 2; di++) {
+                            int fi = 2 * I + di, fj = 2 * J + dj, fk = 2 * K + dk;
+                            msum += F->m[FI(fi, fj, fk)] - cell_bnd(F, fi, fj, fk);
+                        }
+                C->m[c] = msum / 8.0 + cell_bnd(C, I, J, K);
                 double sx = 0.0, sy = 0.0, sz = 0.0;
                 for (int a = 0; a < 2; a++)
                     for (int bb = 0; bb < 2; bb++) {
@@ -497,6 +627,7 @@ static void hier_free(or_hier* H) {
     for (int l = 0; l < H->nl; l++) {
         if (H->lev[l].owned) {
             free(H->lev[l].m); free(H->lev[l].wx); free(H->lev[l].wy); free(H->lev[l].wz);
+            free(H->lev[l].bnd);
         }
         free(H->res[l]); free(H->rc[l]); free(H->zc[l]); free(H->tmp[l]);
     }
@@ -526,22 +657,27 @@ int or_num_levels(const int n[3], int* dims_out) {
 
 static int hier_build(or_hier* H, const or_grid* g, const double* m,
                       const double* wx, const double* wy, const double* wz,
-                      int coarse_cap) {
+                      const double* bnd, int coarse_cap) {
     memset(H, 0, sizeof(*H));
+    int dir = any_dirichlet(g->dirichlet);
+    if (dir && !bnd) return OR_EINVAL;
     H->lev[0] = fine_level(g, m, wx, wy, wz);
+    H->lev[0].bnd = (double*)bnd;
     H->nl = 1;
     while (coarsenable(H->lev[H->nl - 1].n) && H->nl < OR_MAX_LEVELS) {
         or_level* F = &H->lev[H->nl - 1];
         or_level* C = &H->lev[H->nl];
         for (int d = 0; d < 3; d++) { C->n[d] = F->n[d] / 2; C->periodic[d] = F->periodic[d]; }
+        for (int sd = 0; sd < 6; sd++) C->dirichlet[sd] = F->dirichlet[sd];
         size_t nc = ncell(C->n);
         C->m = (double*)malloc(nc * sizeof(double));
         C->wx = (double*)malloc(nc * sizeof(double));
         C->wy = (double*)malloc(nc * sizeof(double));
         C->wz = (double*)malloc(nc * sizeof(double));
+        C->bnd = dir ? (double*)malloc(or_bnd_size(C->n) * sizeof(double)) : NULL;
         C->owned = 1;
         H->nl++;
-        if (!C->m || !C->wx || !C->wy || !C->wz) { hier_free(H); return OR_ENOMEM; }
+        if (!C->m || !C->wx || !C->wy || !C->wz || (dir && !C->bnd)) { hier_free(H); return OR_ENOMEM; }
         coarsen(F, C);
     }
     for (int l = 0; l < H->nl; l++) {
@@ -592,40 +728,61 @@ static void vcycle(or_hier* H, int l, const double* r, double* z,
 
 /* One V-cycle with zero initial guess: z = B r. */
 int or_vcycle(const or_grid* g, const double* m, const double* wx,
-              const double* wy, const double* wz, const double* r, double* z,
-              const or_solver* s) {
+              const double* wy, const double* wz, const double* bnd,
+              const double* r, double* z, const or_solver* s) {
     or_hier H;
-    int st = hier_build(&H, g, m, wx, wy, wz, s->coarse_cap);
+    int st = hier_build(&H, g, m, wx, wy, wz, bnd, s->coarse_cap);
     if (st) return st;
     vcycle(&H, 0, r, z, s);
     hier_free(&H);
     return OR_OK;
 }
 
-/* Exposed pieces of the cycle, for tests of the transfer operators. */
-int or_coarsen(const int nf[3], const int periodic[3], const double* m,
-               const double* wx, const double* wy, const double* wz,
-               double* mc, double* wxc, double* wyc, double* wzc) {
-    or_level F = {{nf[0], nf[1], nf[2]}, {periodic[0], periodic[1], periodic[2]},
-                  (double*)m, (double*)wx, (double*)wy, (double*)wz, 0};
-    or_level C = {{nf[0] / 2, nf[1] / 2, nf[2] / 2}, {periodic[0], periodic[1], periodic[2]},
-                  mc, wxc, wyc, wzc, 0};
+/* Exposed pieces of the cycle, for tests of the transfer operators.
+ * dirichlet may be NULL (no Dirichlet side); bnd and bndc are the packed
+ * boundary weights of the fine and coarse level (used when dirichlet has a
+ * side set). */
+static or_level bare_level(const int n[3], const int periodic[3], const int* dirichlet) {
+    or_level L;
+    memset(&L, 0, sizeof(L));
+    for (int d = 0; d < 3; d++) { L.n[d] = n[d]; L.periodic[d] = periodic[d]; }
+    if (dirichlet)
+        for (int s = 0; s < 6; s++) L.dirichlet[s] = dirichlet[s];
+    return L;
+}
+
+int or_coarsen(const int nf[3], const int periodic[3], const int* dirichlet,
+               const double* m, const double* wx, const double* wy, const double* wz,
+               const double* bnd, double* mc, double* wxc, double* wyc, double* wzc,
+               double* bndc) {
+    const int nc[3] = {nf[0] / 2, nf[1] / 2, nf[2] / 2};
+    or_level F = bare_level(nf, periodic, dirichlet);
+    or_level C = bare_level(nc, periodic, dirichlet);
+    F.m = (double*)m; F.wx = (double*)wx; F.wy = (double*)wy; F.wz = (double*)wz;
+    C.m = mc; C.wx = wxc; C.wy = wyc; C.wz = wzc;
+    if (dirichlet && any_dirichlet(dirichlet)) {
+        if (!bnd || !bndc) return OR_EINVAL;
+        F.bnd = (double*)bnd;
+        C.bnd = bndc;
+    }
     coarsen(&F, &C);
     return OR_OK;
 }
 
 int or_prolong_add(const int nf[3], const int periodic[3], const double* ec,
                    double* zf) {
-    or_level F = {{nf[0], nf[1], nf[2]}, {periodic[0], periodic[1], periodic[2]}, 0, 0, 0, 0, 0};
-    or_level C = {{nf[0] / 2, nf[1] / 2, nf[2] / 2}, {periodic[0], periodic[1], periodic[2]}, 0, 0, 0, 0, 0};
+    const int nc[3] = {nf[0] / 2, nf[1] / 2, nf[2] / 2};
+    or_level F = bare_level(nf, periodic, NULL);
+    or_level C = bare_level(nc, periodic, NULL);
     prolong_add(&F, &C, ec, zf);
     return OR_OK;
 }
 
 int or_restrict(const int nf[3], const int periodic[3], const double* rf,
                 double* rc) {
-    or_level F = {{nf[0], nf[1], nf[2]}, {periodic[0], periodic[1], periodic[2]}, 0, 0, 0, 0, 0};
-    or_level C = {{nf[0] / 2, nf[1] / 2, nf[2] / 2}, {periodic[0], periodic[1], periodic[2]}, 0, 0, 0, 0, 0};
+    const int nc[3] = {nf[0] / 2, nf[1] / 2, nf[2] / 2};
+    or_level F = bare_level(nf, periodic, NULL);
+    or_level C = bare_level(nc, periodic, NULL);
     restrict_fw(&F, &C, rf, rc);
     return OR_OK;
 }
@@ -641,8 +798,8 @@ static double dot(const double* a, const double* b, size_t n) {
 /* Multigrid-preconditioned CG for A x = b (Table 1).  hist, if given,
  * receives ||r_k|| / ||b|| for k = 0..iters (max_iter + 1 entries). */
 int or_pcg(const or_grid* g, const double* m, const double* wx,
-           const double* wy, const double* wz, const double* b, double* x,
-           const or_solver* s, int* iters, double* rel_res, double* hist) {
+           const double* wy, const double* wz, const double* bnd, const double* b,
+           double* x, const or_solver* s, int* iters, double* rel_res, double* hist) {
     size_t n = ncell(g->n);
     memset(x, 0, n * sizeof(double));
     *iters = 0;
@@ -651,7 +808,7 @@ int or_pcg(const or_grid* g, const double* m, const double* wx,
     if (hist) hist[0] = bnorm > 0.0 ? 1.0 : 0.0;
     if (bnorm == 0.0) return OR_OK;
     or_hier H;
-    int st = hier_build(&H, g, m, wx, wy, wz, s->coarse_cap);
+    int st = hier_build(&H, g, m, wx, wy, wz, bnd, s->coarse_cap);
     if (st) return st;
     double* r = (double*)malloc(n * sizeof(double));
     double* z = (double*)malloc(n * sizeof(double));
@@ -693,26 +850,35 @@ int or_pcg(const or_grid* g, const double* m, const double* wx,
  * (photons), [3] imbalance relative to the step's photon budget,
  * [4] photons emitted in the step, [5] photons absorbed in the step,
  * [6] photons added by the E >= 0 floor, [7] relative change of the step
- * ||E^{n+1} - E^n||_2 / ||E^{n+1}||_2 (on the floored E^{n+1}). */
+ * ||E^{n+1} - E^n||_2 / ||E^{n+1}||_2 (on the floored E^{n+1}),
+ * [8] photons that left through Dirichlet faces (negative: entered).
+ * With the theta-method every loss term is taken at
+ * theta E^{n+1} + (1 - theta) E^n = E^n + theta dE, so the balance
+ *   sum_i [dE_i - dt eta_i + dt (c kappa_i + adot/a)(E^n_i + theta dE_i)]
+ *   + sum_b (w_b / theta)(E^n_i + theta dE_i - E_b)
+ * vanishes up to the solver residual (the interior fluxes telescope). */
 int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
             const double* E, const double* nHI, const double* eta,
             double* E_new, double* info) {
     size_t n = ncell(g->n);
-    double* buf = (double*)malloc(6 * n * sizeof(double));
+    size_t nb = any_dirichlet(g->dirichlet) ? or_bnd_size(g->n) : 0;
+    double* buf = (double*)malloc((6 * n + nb) * sizeof(double));
     if (!buf) return OR_ENOMEM;
     double *m = buf, *wx = buf + n, *wy = buf + 2 * n, *wz = buf + 3 * n,
-           *b = buf + 4 * n, *dE = buf + 5 * n;
-    int st = or_assemble(g, p, E, nHI, eta, m, wx, wy, wz, b);
+           *b = buf + 4 * n, *dE = buf + 5 * n, *bnd = nb ? buf + 6 * n : NULL;
+    int st = or_assemble(g, p, E, nHI, eta, m, wx, wy, wz, b, bnd);
     if (st) { free(buf); return st; }
     int iters = 0;
     double rel = 0.0;
-    st = or_pcg(g, m, wx, wy, wz, b, dE, s, &iters, &rel, NULL);
+    st = or_pcg(g, m, wx, wy, wz, bnd, b, dE, s, &iters, &rel, NULL);
     if (st != OR_OK && st != OR_ENOCONV) { free(buf); return st; }
+    const double th = p->theta;
     double V = g->h[0] * g->h[1] * g->h[2];
     double bal = 0.0, emit = 0.0, absorb = 0.0, floor_add = 0.0, dsq = 0.0, esq = 0.0;
+    double out = 0.0, gross = 0.0;
     for (size_t i = 0; i < n; i++) {
         double En = E[i] + dE[i];
-        double sink = p->dt * (p->c * nHI[i] * p->sigma + p->adot) * En;
+        double sink = p->dt * (p->c * nHI[i] * p->sigma + p->adot) * (E[i] + th * dE[i]);
         bal += dE[i] - (p->dt * eta[i] - sink);
         emit += p->dt * eta[i];
         absorb += sink;
@@ -721,6 +887,20 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
         dsq += dE[i] * dE[i];
         esq += Ef * Ef;
     }
+    if (bnd)
+        for (int k = 0; k < g->n[2]; k++)
+            for (int j = 0; j < g->n[1]; j++)
+                for (int i = 0; i < g->n[0]; i++)
+                    for (int sd = 0; sd < 6; sd++) {
+                        if (!g->dirichlet[sd]) continue;
+                        long f = side_face(g->n, sd, i, j, k);
+                        if (f < 0) continue;
+                        size_t c = i + (size_t)g->n[0] * (j + (size_t)g->n[1] * k);
+                        double fl = bnd[f] / th * (E[c] + th * dE[c] - g->ebc[sd]);
+                        out += fl;
+                        gross += fabs(fl);
+                    }
+    bal += out;
     if (st == OR_OK)
         for (size_t i = 0; i < n; i++) {
             double En = E[i] + dE[i];
@@ -728,6 +908,7 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
         }
     double scale = V / p->hnu;
     double budget = emit > absorb ? emit : absorb;
+    if (gross > budget) budget = gross;
     info[0] = iters;
     info[1] = rel;
     info[2] = bal * scale;
@@ -736,6 +917,7 @@ int or_step(const or_grid* g, const or_phys* p, const or_solver* s,
     info[5] = absorb * scale;
     info[6] = floor_add * scale;
     info[7] = esq > 0.0 ? sqrt(dsq / esq) : 0.0;
+    info[8] = out * scale;
     free(buf);
     return st;
 }
@@ -767,7 +949,7 @@ int or_advance(const or_grid* g, const or_phys* p0, const or_solver* s, double* 
         int last = dt >= rest * (1.0 - 1e-12);
         double dt_try = last ? rest : dt;
         p.dt = dt_try;
-        double info[8];
+        double info[9];
         st = or_step(g, &p, s, E, nHI, eta, En, info);
         iters += (int)info[0];
         if (st == OR_ENOCONV) {

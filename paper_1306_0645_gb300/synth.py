@@ -47,10 +47,20 @@ BC_ZERO_GRADIENT, BC_PERIODIC = 0, 1
 
 @dataclasses.dataclass
 class Grid:
-    """Uniform Cartesian grid: cells per axis, cell widths (cm), periodicity."""
+    """Uniform Cartesian grid: cells per axis, cell widths (cm), periodicity,
+    and the faces held at a fixed E (Dirichlet; value 0 = outflow), per side
+    in the order x lo, x hi, y lo, y hi, z lo, z hi.  Other non-periodic faces
+    reflect (zero gradient)."""
     n: Tuple[int, int, int]
     h: Tuple[float, float, float]
     periodic: Tuple[bool, bool, bool] = (False, False, False)
+    dirichlet: Tuple[bool, bool, bool, bool, bool, bool] = (False,) * 6
+    ebc: Tuple[float, float, float, float, float, float] = (0.0,) * 6
+
+    def outflow_upper(self) -> "Grid":
+        """The boundary set of the Sec. 4.1 tests: reflecting faces at x = 0,
+        y = 0, z = 0 and outflow at the three upper faces."""
+        return dataclasses.replace(self, dirichlet=(False, True) * 3, ebc=(0.0,) * 6)
 
     @property
     def shape(self):
@@ -92,6 +102,7 @@ class Params:
     coarse_cap: int = 1024
     graphs: int = -1
     fused_post: int = 0
+    theta: float = 1.0
 
 
 @dataclasses.dataclass
