@@ -5,9 +5,10 @@
  * The operation (Norman et al., arXiv:1306.0645):
  *   The radiation component of the operator split (Sec. 3.2, Eq. "fld"),
  *       dE/dt = div(D grad E) - (adot/a) E - c kappa E + eta,
- *   is advanced by backward Euler with the flux limiter D evaluated at E^n,
- *   which makes the step one linear system, posed for the correction
- *   dE = E^{n+1} - E^n (Sec. 3.2).  D is the limiter of Sec. 2,
+ *   is advanced by the implicit theta-method of Sec. 3.2 (theta = 1
+ *   backward Euler, the default; theta = 1/2 the trapezoidal rule) with the
+ *   flux limiter D evaluated at E^n, which makes the step one linear system,
+ *   posed for the correction dE = E^{n+1} - E^n.  D is the limiter of Sec. 2,
  *       D = min{ c (9 kappa_f^2 + R^2)^(-1/2), D_max },
  *       R = max{ |E_2 - E_1| / (h E_f), R_min },
  *   with face energy E_f the arithmetic mean and face opacity kappa_f the
@@ -21,13 +22,23 @@
  *
  * Discretisation (the library's reading where the paper is silent):
  *   cell-centred uniform grid, CGS units; face weight w_f = dt D_f / h_d^2;
- *   A dE = b with (A u)_i = m_i u_i + sum_f w_f (u_i - u_nbr),
- *   m_i = 1 + dt (c kappa_i + adot/a),
- *   b_i = dt eta_i - dt (c kappa_i + adot/a) E_i + sum_f w_f (E_nbr - E_i).
- *   Zero-gradient boundaries carry no flux; periodic axes wrap.
+ *   A dE = b with (A u)_i = m_i u_i + sum_f theta w_f (u_i - u_nbr),
+ *   m_i = 1 + theta dt (c kappa_i + adot/a) + sum_b theta w_b,
+ *   b_i = dt eta_i - dt (c kappa_i + adot/a) E_i + sum_f w_f (E_nbr - E_i)
+ *         + sum_b w_b (E_b - E_i),
+ *   the sums over b running over the cell's Dirichlet boundary faces.
+ *   Boundaries, per face of the box (the tests of Sec. 4.1 use reflecting
+ *   and outflow faces): reflecting (zero gradient) faces carry no flux;
+ *   periodic axes wrap; a Dirichlet face holds E = E_b half a cell from the
+ *   cell centre, its weight w_b = dt D_b / (h h/2) with D_b from the limiter
+ *   at face energy (E_i + E_b)/2, normal difference |E_i - E_b| over h/2 and
+ *   the cell's opacity; an outflow face is a Dirichlet face with E_b = 0,
+ *   through which the limiter lets optically thin radiation stream out at
+ *   |F| = c E_face.
  *   Multigrid: full 2x coarsening while all dimensions are even and the
  *   smallest exceeds 4; trilinear prolongation P, restriction P^T/8; coarse
- *   operators by rediscretisation; dense direct solve on the coarsest grid
+ *   operators by rediscretisation (boundary face weights included); dense
+ *   direct solve on the coarsest grid
  *   (at most fld_params.coarse_cap cells, else FLD_EINVAL).
  *
  * Conventions for every call:
@@ -63,15 +74,28 @@ typedef enum {
 } fld_status;
 
 typedef enum { FLD_LIMITER_PAPER = 0, FLD_LIMITER_LP = 1 } fld_limiter;
-typedef enum { FLD_BC_ZERO_GRADIENT = 0, FLD_BC_PERIODIC = 1 } fld_bc;
+typedef enum {
+    FLD_BC_ZERO_GRADIENT = 0,  /* reflecting: no flux through the face */
+    FLD_BC_PERIODIC = 1,       /* the axis wraps (both faces of the axis) */
+    FLD_BC_DIRICHLET = 2,      /* E fixed to fld_grid.bc_value on the face */
+    FLD_BC_OUTFLOW = 3         /* Dirichlet with E = 0: radiation leaves */
+} fld_bc;
 typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 } fld_precision;
 typedef enum { FLD_SMOOTH_RBGS = 0, FLD_SMOOTH_JACOBI = 1 } fld_smoother;
 
-/* Grid: cells per axis (>= 1), cell widths in cm (> 0), boundary per axis. */
+/* Grid: cells per axis (>= 1), cell widths in cm (> 0), boundary per face.
+ * An axis is periodic when bc[a] is FLD_BC_PERIODIC, and bc_hi[a] must
+ * then be FLD_BC_PERIODIC or 0.  Otherwise bc[a] governs the lower face
+ * (x = 0, ...) and bc_hi[a] (not periodic) the upper face; a
+ * zero-initialised bc_hi makes the upper faces reflecting. */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz;
-    int bc[3];                 /* fld_bc for x, y, z */
+    int bc[3];                 /* fld_bc of the lower faces (x, y, z) */
+    int bc_hi[3];              /* fld_bc of the upper faces */
+    double bc_value[6];        /* E_b of Dirichlet faces, erg/cm^3, finite
+                                  and >= 0, in the order x lo, x hi, y lo,
+                                  y hi, z lo, z hi (others ignored) */
 } fld_grid;
 
 /* Physical and solver parameters.  fld_params_default fills the values of
@@ -102,6 +126,9 @@ typedef struct {
                                   black+red post-sweep kernel (1) or two
                                   colour sweeps (0, default, faster on
                                   GB300); same arithmetic */
+    double theta;              /* time discretisation, in [1/2, 1]: 1
+                                  backward Euler (default), 1/2 trapezoidal
+                                  (Sec. 3.2) */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -112,13 +139,18 @@ typedef struct {
     double rel_res;            /* ||b - A dE||_2 / ||b||_2 of the result,
                                   recomputed in FP64 */
     double balance_abs;        /* photons: sum_i V [dE_i - dt (eta_i -
-                                  (c kappa_i + adot/a) E^{n+1}_i)] / h nu */
-    double balance_rel;        /* |balance_abs| / max(emitted, absorbed) */
+                                  (c kappa_i + adot/a) E^theta_i)] / h nu
+                                  + outflow, E^theta = E^n + theta dE */
+    double balance_rel;        /* |balance_abs| / max(emitted, absorbed,
+                                  photons through Dirichlet faces counted
+                                  face by face in absolute value) */
     double emitted;            /* photons emitted in the step, V dt sum eta / h nu */
     double absorbed;           /* photons absorbed in the step */
     double floor_added;        /* photons added by flooring E^{n+1} at 0 */
     double rel_change;         /* ||E^{n+1} - E^n||_2 / ||E^{n+1}||_2 */
     double ms;                 /* device time of the call, ms */
+    double outflow;            /* photons that left through Dirichlet and
+                                  outflow faces (negative: entered) */
 } fld_info;
 
 typedef struct fld_ctx fld_ctx;
@@ -126,7 +158,7 @@ typedef struct fld_ctx fld_ctx;
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
  * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
- * graphs -1, fused_post 0.
+ * graphs -1, fused_post 0, theta 1.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 

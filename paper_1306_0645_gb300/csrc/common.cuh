@@ -36,7 +36,11 @@ enum Slot {
     S_FIRST,      // 1 before the first CG iteration (beta = 0), then 0
     S_DE2,        // sum dE^2 of the step
     S_EN2,        // sum (E^{n+1})^2
-    NUM_SLOTS = 32
+    S_OUT0,       // photons out through the Dirichlet faces of side 0..5
+    S_OUT5 = S_OUT0 + 5,
+    S_OUTABS0,    // the same summed in absolute value per face, side 0..5
+    S_OUTABS5 = S_OUTABS0 + 5,
+    NUM_SLOTS = 40
 };
 
 // What the last block of a reduction does with the finished sums.
@@ -217,6 +221,10 @@ struct DotAcc<float> {
 };
 
 constexpr int FLAT_MAX_BLOCKS = 152 * 16;
+
+// Grid-stride loop over [0, n).
+#define GRID_LOOP(c, n) \
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
 
 inline int red_blocks(long long n, int threads = RED_THREADS) {
     long long b = (n + threads - 1) / threads;

@@ -49,6 +49,7 @@ struct Level {
     Dims d;
     Op<double> A64;
     Op<float> A32;
+    Bnd bnd;           // Dirichlet face weights (FP64)
     void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
     Tune tune[NTUNE];
 };
@@ -114,9 +115,19 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     }
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
         return set_err(FLD_EINVAL, "cell widths must be finite and > 0");
-    for (int a = 0; a < 3; a++)
-        if (g->bc[a] != FLD_BC_ZERO_GRADIENT && g->bc[a] != FLD_BC_PERIODIC)
-            return set_err(FLD_EINVAL, "unknown boundary condition %d on axis %d", g->bc[a], a);
+    for (int a = 0; a < 3; a++) {
+        const int lo = g->bc[a], hi = g->bc_hi[a];
+        if (lo < FLD_BC_ZERO_GRADIENT || lo > FLD_BC_OUTFLOW || hi < FLD_BC_ZERO_GRADIENT || hi > FLD_BC_OUTFLOW)
+            return set_err(FLD_EINVAL, "unknown boundary condition (%d, %d) on axis %d", lo, hi, a);
+        if (lo == FLD_BC_PERIODIC && hi != FLD_BC_PERIODIC && hi != FLD_BC_ZERO_GRADIENT)
+            return set_err(FLD_EINVAL, "axis %d is periodic but its upper face is %d", a, hi);
+        if (lo != FLD_BC_PERIODIC && hi == FLD_BC_PERIODIC)
+            return set_err(FLD_EINVAL, "axis %d: periodic upper face needs a periodic lower face", a);
+        for (int u = 0; u < 2; u++)
+            if ((u ? hi : lo) == FLD_BC_DIRICHLET && lo != FLD_BC_PERIODIC &&
+                !(std::isfinite(g->bc_value[2 * a + u]) && g->bc_value[2 * a + u] >= 0.0))
+                return set_err(FLD_EINVAL, "Dirichlet value of face %d must be finite and >= 0", 2 * a + u);
+    }
     if (!finite_pos(p->dt)) return set_err(FLD_EINVAL, "dt must be finite and > 0");
     if (!finite_pos(p->c)) return set_err(FLD_EINVAL, "c must be finite and > 0");
     if (!finite_pos(p->L_unit)) return set_err(FLD_EINVAL, "L_unit must be finite and > 0");
@@ -128,6 +139,8 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     if (!(std::isfinite(p->adot_over_a) && p->adot_over_a >= 0.0))
         return set_err(FLD_EINVAL, "adot_over_a must be finite and >= 0");
     if (!finite_pos(p->hnu)) return set_err(FLD_EINVAL, "hnu must be finite and > 0");
+    if (!(p->theta >= 0.5 && p->theta <= 1.0))
+        return set_err(FLD_EINVAL, "theta must lie in [1/2, 1] (1 backward Euler, 1/2 trapezoidal)");
     if (p->limiter != FLD_LIMITER_PAPER && p->limiter != FLD_LIMITER_LP)
         return set_err(FLD_EINVAL, "unknown limiter %d", p->limiter);
     if (p->precision != FLD_PREC_FP64 && p->precision != FLD_PREC_MIXED)
@@ -155,6 +168,17 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     return FLD_OK;
 }
 
+// Sides (bit 2 axis + upper) held at a fixed E: Dirichlet and outflow faces.
+int dirichlet_mask(const fld_grid* g) {
+    int m = 0;
+    for (int a = 0; a < 3; a++) {
+        if (g->bc[a] == FLD_BC_PERIODIC) continue;
+        if (g->bc[a] == FLD_BC_DIRICHLET || g->bc[a] == FLD_BC_OUTFLOW) m |= 1 << (2 * a);
+        if (g->bc_hi[a] == FLD_BC_DIRICHLET || g->bc_hi[a] == FLD_BC_OUTFLOW) m |= 1 << (2 * a + 1);
+    }
+    return m;
+}
+
 // Enumerates every device buffer a context needs, in a fixed order; the
 // same walk sizes the footprint and performs the allocation.
 template <class F>
@@ -174,6 +198,11 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
             buf(l, "vec", 1, n * ts);
         }
         buf(l, "vec", 2, n * ts);
+        if (dirichlet_mask(g)) {
+            const size_t nb = 2 * ((size_t)dims[l][1] * dims[l][2] + (size_t)dims[l][0] * dims[l][2] +
+                                   (size_t)dims[l][0] * dims[l][1]);
+            buf(l, "bnd", 0, nb * sizeof(double));
+        }
     }
     const size_t n0 = (size_t)g->nx * g->ny * g->nz;
     buf(0, "b", 0, n0 * sizeof(double));
@@ -646,6 +675,8 @@ fld_status alloc_ctx(fld_ctx* c) {
             else if (q == 3) L.A32.wz = f; else L.A32.invd = f;
         } else if (!strcmp(kind, "vec")) {
             if (q == 0) L.r = ptr; else if (q == 1) L.z = ptr; else L.t = ptr;
+        } else if (!strcmp(kind, "bnd")) {
+            L.bnd.w = (double*)ptr;
         } else if (!strcmp(kind, "b")) c->b = (double*)ptr;
         else if (!strcmp(kind, "dE")) c->dE = (double*)ptr;
         else if (!strcmp(kind, "r64")) c->r64 = (double*)ptr;
@@ -775,12 +806,17 @@ fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, cons
     }
     { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 28.0 : 8.0)));
       launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr,
-                          red(c, R_STORE_SUM_MAX, S_BB, S_RMAX), s); }
+                          L0.bnd, red(c, R_STORE_SUM_MAX, S_BB, S_RMAX), s); }
     for (int l = 1; l < c->nl; l++) {
         Level& F = c->L[l - 1];
         Level& C = c->L[l];
         const double nf = (double)F.d.n, nc = (double)C.d.n;
         { KScope k(c, K_COARSEN, 32.0 * (nf + nc)); launch_coarsen(F.d, C.d, F.A64, C.A64, s); }
+        for (int sd = 0; sd < 6; sd++)
+            if ((C.bnd.mask >> sd) & 1) {
+                KScope k(c, K_COARSEN, 0.0);
+                launch_coarsen_bnd(F.d, C.d, sd, F.bnd, C.bnd, C.A64, s);
+            }
         { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
         if (c->mixed) {
             { KScope k(c, K_TO_F32, 48.0 * nc); launch_to_f32(C.d, C.A64, C.A32, s); }
@@ -831,15 +867,23 @@ void fill_physdev(fld_ctx* c, double dt) {
     pd.sigma = p->sigma;
     pd.adot = p->adot_over_a;
     pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
+    pd.theta = p->theta;
+    pd.inv_theta = 1.0 / p->theta;
     for (int a = 0; a < 3; a++) {
-        pd.dt_h2[a] = dt / (pd.h[a] * pd.h[a]);
+        pd.dt_h2[a] = p->theta * dt / (pd.h[a] * pd.h[a]);
         pd.wmax[a] = pd.dt_h2[a] * pd.Dmax;
         pd.wmax32[a] = (float)pd.wmax[a];
         pd.twoL_h32[a] = (float)(2.0 * p->L_unit / pd.h[a]);
     }
     pd.dtcs = dt * p->c * p->sigma;
     pd.dta = dt * p->adot_over_a;
-    pd.one_dta = 1.0 + pd.dta;
+    pd.mdtcs = p->theta * pd.dtcs;
+    pd.one_dta = 1.0 + p->theta * pd.dta;
+    pd.dmask = dirichlet_mask(g);
+    for (int sd = 0; sd < 6; sd++) {
+        const int kind = (sd & 1) ? g->bc_hi[sd >> 1] : g->bc[sd >> 1];
+        pd.ebc[sd] = kind == FLD_BC_DIRICHLET ? g->bc_value[sd] : 0.0;
+    }
     pd.sigmaL32 = (float)(p->sigma * p->L_unit);
     // D = D_max exactly when 9 (kappa_f L)^2 + (R L)^2 <= (c L / D_max)^2;
     // the FP32 screen accepts a face only 1e-3 inside that bound
@@ -852,6 +896,13 @@ void fill_physdev(fld_ctx* c, double dt) {
 
 void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* eta) {
     const long long n = c->L[0].d.n;
+    // the flux through Dirichlet faces needs E^n, before the update below
+    for (int sd = 0; sd < 6; sd++)
+        if ((c->L[0].bnd.mask >> sd) & 1) {
+            KScope k(c, K_FINALIZE, 0.0);
+            launch_bnd_outflow(c->L[0].d, c->pd, sd, c->L[0].bnd, E, c->dE,
+                               red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd), c->s);
+        }
     { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE6_FIN), c->s); }
     cudaEventRecord(c->e1, c->s);
     cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
@@ -862,12 +913,20 @@ void finalize_info(fld_ctx* c, fld_info* inf) {
     harvest(c);
     const double V = c->g.dx * c->g.dy * c->g.dz;
     const double scale = V / c->p.hnu;
-    inf->balance_abs = c->h_sc[S_BAL] * scale;
+    double out = 0.0, gross = 0.0;
+    for (int sd = 0; sd < 6; sd++)
+        if ((c->L[0].bnd.mask >> sd) & 1) {
+            out += c->h_sc[S_OUT0 + sd];
+            gross += c->h_sc[S_OUTABS0 + sd];
+        }
+    inf->outflow = out * scale;
+    inf->balance_abs = (c->h_sc[S_BAL] + out) * scale;
     inf->emitted = c->h_sc[S_EMIT] * scale;
     inf->absorbed = c->h_sc[S_ABSORB] * scale;
     inf->floor_added = c->h_sc[S_FLOOR] * scale;
     inf->rel_change = c->h_sc[S_EN2] > 0.0 ? std::sqrt(c->h_sc[S_DE2] / c->h_sc[S_EN2]) : 0.0;
-    const double budget = inf->emitted > inf->absorbed ? inf->emitted : inf->absorbed;
+    double budget = inf->emitted > inf->absorbed ? inf->emitted : inf->absorbed;
+    if (gross * scale > budget) budget = gross * scale;
     inf->balance_rel = budget > 0.0 ? std::fabs(inf->balance_abs) / budget : std::fabs(inf->balance_abs);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->e0, c->e1);
@@ -1227,6 +1286,7 @@ fld_status fld_params_default(fld_params* p) {
     p->coarse_cap = 1024;
     p->graphs = -1;
     p->fused_post = 0;
+    p->theta = 1.0;
     return FLD_OK;
 }
 
@@ -1272,6 +1332,7 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     c->nc = (int)c->L[c->nl - 1].d.n;
     st = alloc_ctx(c);
     if (st) { free_ctx(c); return st; }
+    for (int l = 0; l < c->nl; l++) c->L[l].bnd.mask = c->L[l].bnd.w ? dirichlet_mask(g) : 0;
     {
         long long blocks = 0;
         int cap = 0;

@@ -1,13 +1,17 @@
 // k_assemble.cu -- per-cell opacity and per-face flux-limited diffusion
-// coefficients of the backward-Euler correction system (FP64).
+// coefficients of the theta-method correction system (FP64).
 //
 // Flux limiter (Sec. 2): D = min{ c (9 kappa_f^2 + R^2)^(-1/2), D_max },
 // R = max{ |E_2 - E_1| / (h E_f), R_min }, E_f arithmetic and kappa_f
 // harmonic face means; Levermore-Pomraning alternative (Sec. 1 citation)
 // with lambda(x) = (coth x - 1/x)/x, x = R/kappa_f.
-// System (Sec. 3.2, residual-correction form of backward Euler with the
-// limiter lagged at E^n): w_f = dt D_f / h^2, m = 1 + dt (c kappa + adot/a),
-// b = dt eta - dt (c kappa + adot/a) E + sum_f w_f (E_nbr - E).
+// System (Sec. 3.2, residual-correction form of the theta-method with the
+// limiter lagged at E^n): the operator's face weights theta dt D_f / h^2 and
+// mass term 1 + theta dt (c kappa + adot/a); the right-hand side
+// b = dt eta - dt (c kappa + adot/a) E + sum_f w_f (E_nbr - E) with the full
+// weights w_f = dt D_f / h^2.  A Dirichlet face of the box (E = E_b half a
+// cell out) adds theta w_b, w_b = dt D_b / (h h/2), to the mass term and
+// w_b (E_b - E) to b, with D_b from the limiter of the half-cell face.
 #include "kernels.h"
 
 namespace fld {
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(256) k_assemble_faces(Dims d, PhysDev p, const
         const double Ec = E[c], nc = nHI[c];
         bad |= !valid_bits(Ec) || !valid_bits(nc) || !valid_bits(eta[c]);
         const double kc = nc * p.sigma;
-        const double m = fma(p.dtcs, nc, p.one_dta);
+        const double m = fma(p.mdtcs, nc, p.one_dta);
         bool okc = true;
         const float kL32 = f32_trunc(nc, okc) * p.sigmaL32;
         double w[3];
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
                                                              const double* __restrict__ nHI,
                                                              const double* __restrict__ eta, Op<double> op,
                                                              Op<float> op32, double* __restrict__ b,
-                                                             double* __restrict__ diag64, RedArgs ra) {
+                                                             double* __restrict__ diag64, Bnd bnd, RedArgs ra) {
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     double acc[2] = {0.0, 0.0};
     COL_BEGIN(d)
@@ -273,14 +277,45 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
         if (k < d.nz - 1) FACE(wz, wz, c + sz, c + sz) else if (d.pz) FACE(wz, wz, c - (long long)(d.nz - 1) * sz, c - (long long)(d.nz - 1) * sz)
 #undef FACE
         flux = fma(-wsum, Ec, swe);
+        double m = op.m[c];
+        float m32 = op32.invd ? op32.m[c] : 0.0f;
+        if (p.dmask) {
+            // Dirichlet faces of the box touching this cell
+            const int ijk[3] = {i, j, k};
+            const int nn[3] = {d.nx, d.ny, d.nz};
+            const double kc = nHI[c] * p.sigma;
+            double wb_sum = 0.0;
+#pragma unroll
+            for (int sd = 0; sd < 6; sd++) {
+                const int a = sd >> 1;
+                if (!((p.dmask >> sd) & 1) || ijk[a] != ((sd & 1) ? nn[a] - 1 : 0)) continue;
+                const double Eb = p.ebc[sd];
+                const double wb = 2.0 * p.dt_h2[a] * face_D(Eb, Ec, kc, kc, 0.5 * p.h[a], p);
+                const long long f = a == 0 ? j + (long long)d.ny * k
+                                           : (a == 1 ? i + (long long)d.nx * k : i + (long long)d.nx * j);
+                bnd.w[bnd_offset(d, sd) + f] = wb;
+                wb_sum += wb;
+                flux = fma(wb, Eb - Ec, flux);
+            }
+            if (wb_sum != 0.0) {
+                m += wb_sum;
+                op.m[c] = m;
+                if (op32.m) {
+                    m32 = (float)m;
+                    op32.m[c] = m32;
+                }
+            }
+        }
+        // the right-hand side takes the full weights, the operator theta times them
+        flux *= p.inv_theta;
         const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
         const double bc = fma(p.dt, eta[c], -sink) + flux;
         b[c] = bc;
         acc[0] = fma(bc, bc, acc[0]);
         acc[1] = fmax(acc[1], fabs(bc));
-        if (op.invd) op.invd[c] = 1.0 / (op.m[c] + wsum);
-        if (diag64) diag64[c] = op.m[c] + wsum;
-        if (op32.invd) op32.invd[c] = 1.0f / (op32.m[c] + wsum32);
+        if (op.invd) op.invd[c] = 1.0 / (m + wsum);
+        if (diag64) diag64[c] = m + wsum;
+        if (op32.invd) op32.invd[c] = 1.0f / (m32 + wsum32);
     }
     const bool ismax[2] = {false, true};
     grid_reduce<2>(acc, ismax, ra);
@@ -312,9 +347,43 @@ void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap) {
 
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
-                         const RedArgs& ra, cudaStream_t s) {
+                         Bnd bnd, const RedArgs& ra, cudaStream_t s) {
     ColShape sh = col_shape(d);
-    k_assemble_rhs<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, ra);
+    k_assemble_rhs<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+}
+
+// Photons through the Dirichlet faces of side sd (sum, and sum of absolute
+// values per face): with the theta-method the
+// face flux is w_b [theta (E^{n+1} - E_b) + (1 - theta)(E^n - E_b)] / theta
+// per unit volume, i.e. w_b (inv_theta (E^n - E_b) + dE) with the stored
+// (theta-scaled) w_b.
+__global__ void __launch_bounds__(RED_THREADS) k_bnd_outflow(Dims d, PhysDev p, int sd, Bnd bnd,
+                                                            const double* __restrict__ E,
+                                                            const double* __restrict__ dE, RedArgs ra) {
+    const int a = sd >> 1, hi = sd & 1;
+    const long long nf = bnd_side_size(d, sd);
+    const long long off = bnd_offset(d, sd);
+    const long long nu = a == 0 ? d.ny : d.nx;
+    const double Eb = p.ebc[sd];
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(f, nf) {
+        const long long u = f % nu, v = f / nu;
+        long long i, j, k;
+        if (a == 0) { i = hi ? d.nx - 1 : 0; j = u; k = v; }
+        else if (a == 1) { i = u; j = hi ? d.ny - 1 : 0; k = v; }
+        else { i = u; j = v; k = hi ? d.nz - 1 : 0; }
+        const long long c = i + (long long)d.nx * (j + (long long)d.ny * k);
+        const double fl = bnd.w[off + f] * fma(p.inv_theta, E[c] - Eb, dE[c]);
+        acc[0] += fl;
+        acc[1] += fabs(fl);
+    }
+    const bool mx[2] = {false, false};
+    grid_reduce<2>(acc, mx, ra);
+}
+
+void launch_bnd_outflow(const Dims& d, const PhysDev& p, int sd, Bnd bnd, const double* E,
+                        const double* dE, const RedArgs& ra, cudaStream_t st) {
+    k_bnd_outflow<<<red_blocks(bnd_side_size(d, sd)), RED_THREADS, 0, st>>>(d, p, sd, bnd, E, dE, ra);
 }
 
 __global__ void k_opacity_update(long long n, const double* __restrict__ E, const double* __restrict__ nH,

@@ -9,8 +9,6 @@
 
 namespace fld {
 
-#define GRID_LOOP(c, n) \
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
 
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_dot(long long n, const T* __restrict__ a,
@@ -166,6 +164,8 @@ __global__ void k_ir_update(long long n, double* __restrict__ x64, const float* 
 // E_out = max(E + dE, 0); photon balance sums of the unfloored update
 // (energy density units; the host scales by V / h nu), the energy the
 // floor adds, and sum dE^2, sum E_out^2 for the relative change of the step.
+// BE: theta = 1, losses at E^{n+1} itself.
+template <bool BE>
 __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p, const double* __restrict__ E,
                                                           const double* __restrict__ dE,
                                                           const double* __restrict__ nHI,
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p
     GRID_LOOP(c, n) {
         const double d = dE[c];
         const double En = E[c] + d;
-        const double sink = fma(p.dtcs, nHI[c], p.dta) * En;
+        // losses at theta E^{n+1} + (1 - theta) E^n = E^n + theta dE
+        const double sink = fma(p.dtcs, nHI[c], p.dta) * (BE ? En : fma(p.theta, d, E[c]));
         const double emit = p.dt * eta[c];
         acc[0] += d - (emit - sink);
         acc[1] += emit;
@@ -228,7 +229,10 @@ void launch_ir_update(long long n, double* x64, const float* x32, const double* 
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
                      cudaStream_t s) {
-    k_finalize<<<red_blocks(n), RED_THREADS, 0, s>>>(n, p, E, dE, nHI, eta, E_out, ra);
+    if (p.theta == 1.0)
+        k_finalize<true><<<red_blocks(n), RED_THREADS, 0, s>>>(n, p, E, dE, nHI, eta, E_out, ra);
+    else
+        k_finalize<false><<<red_blocks(n), RED_THREADS, 0, s>>>(n, p, E, dE, nHI, eta, E_out, ra);
 }
 
 #define INST(T)                                                                                     \

@@ -66,8 +66,6 @@ __device__ __forceinline__ T nbr_sum_prod(const Dims& d, const Op<T>& A, long lo
     return a;
 }
 
-#define GRID_LOOP(c, n) \
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
 
 // ------------------------------------------------------------ operators
 
@@ -96,6 +94,30 @@ __global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
         C.wx[c] = sx * 0.0625;
         C.wy[c] = sy * 0.0625;
         C.wz[c] = sz * 0.0625;
+    }
+}
+
+// Coarse Dirichlet face weights of side sd: the sum of the 4 fine weights
+// across each coarse face / 16, as for interior faces.  k_coarsen set the
+// coarse mass term to the mean of the 8 children's m, which holds their
+// boundary weights / 8 = 2 w_c; the rediscretised mass term has w_c, so
+// w_c is taken back off.
+__global__ void k_coarsen_bnd(Dims f, Dims cd, int sd, Bnd F, Bnd C, Op<double> CA) {
+    const int a = sd >> 1, hi = sd & 1;
+    const long long nfc = bnd_side_size(cd, sd);
+    const long long offc = bnd_offset(cd, sd), offf = bnd_offset(f, sd);
+    const long long nuc = a == 0 ? cd.ny : cd.nx;
+    const long long nuf = 2 * nuc;
+    GRID_LOOP(fc, nfc) {
+        const long long u = fc % nuc, v = fc / nuc;
+        const long long f00 = offf + 2 * u + nuf * 2 * v;
+        const double wc = ((F.w[f00] + F.w[f00 + 1]) + (F.w[f00 + nuf] + F.w[f00 + nuf + 1])) * 0.0625;
+        C.w[offc + fc] = wc;
+        long long i, j, k;
+        if (a == 0) { i = hi ? cd.nx - 1 : 0; j = u; k = v; }
+        else if (a == 1) { i = u; j = hi ? cd.ny - 1 : 0; k = v; }
+        else { i = u; j = v; k = hi ? cd.nz - 1 : 0; }
+        CA.m[i + (long long)cd.nx * (j + (long long)cd.ny * k)] -= wc;
     }
 }
 
@@ -339,6 +361,10 @@ static const int TPB = 256;
 void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s) {
     ColShape sh = col_shape(c);
     k_coarsen<<<sh.grid, sh.block, 0, s>>>(f, c, F, C);
+}
+void launch_coarsen_bnd(const Dims& f, const Dims& c, int sd, Bnd F, Bnd C, Op<double> CA,
+                        cudaStream_t st) {
+    k_coarsen_bnd<<<grid_blocks(bnd_side_size(c, sd), 256), 256, 0, st>>>(f, c, sd, F, C, CA);
 }
 template <class T>
 void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s) {

@@ -5,15 +5,21 @@
 
 namespace fld {
 
-// Physical constants of one step, precomputed on the host.
+// Physical constants of one step, precomputed on the host.  theta is the
+// time discretisation of the theta-method: the operator A carries theta
+// times the face weights and loss rates, the right-hand side the full ones.
 struct PhysDev {
     double dt, c, Dmax, Rmin, sigma, adot;
     double h[3];        // cell widths
-    double dt_h2[3];    // dt / h^2
-    double wmax[3];     // dt D_max / h^2, the weight of a capped face
-    double dtcs;        // dt c sigma
-    double one_dta;     // 1 + dt adot/a
+    double dt_h2[3];    // theta dt / h^2 (face weights of A per unit D)
+    double wmax[3];     // theta dt D_max / h^2, the weight of a capped face
+    double dtcs;        // dt c sigma (right-hand side and photon balance)
+    double one_dta;     // 1 + theta dt adot/a (mass term of A)
     double dta;         // dt adot/a
+    double mdtcs;       // theta dt c sigma (mass term of A)
+    double theta, inv_theta;
+    double ebc[6];      // E_b of the Dirichlet faces: x lo, x hi, y lo, ...
+    int dmask;          // bit s set: side s (2 axis + upper) is Dirichlet
     float wmax32[3];    // FP32 copy of wmax
     float sigmaL32;     // sigma L_unit
     float twoL_h32[3];  // 2 L_unit / h
@@ -26,6 +32,25 @@ template <class T>
 struct Op {
     T *m, *wx, *wy, *wz, *invd;
 };
+
+// Weights of the Dirichlet faces of a level (theta-scaled, on the diagonal
+// of A), packed by side in the order x lo, x hi, y lo, y hi, z lo, z hi; the
+// face of cell (i,j,k) on an x side has index j + ny k, on a y side
+// i + nx k, on a z side i + nx j.  w == nullptr: no Dirichlet face.
+struct Bnd {
+    double* w;
+    int mask;           // Dirichlet sides, bit 2 axis + upper
+};
+
+__host__ __device__ inline long long bnd_side_size(const Dims& d, int s) {
+    const int a = s >> 1;
+    return a == 0 ? (long long)d.ny * d.nz : (a == 1 ? (long long)d.nx * d.nz : (long long)d.nx * d.ny);
+}
+__host__ __device__ inline long long bnd_offset(const Dims& d, int s) {
+    long long o = 0;
+    for (int q = 0; q < s; q++) o += bnd_side_size(d, q);
+    return o;
+}
 
 // Per-block lists of the faces the FP32 screen could not settle, finished
 // by a compacted FP64 pass.  entries == nullptr disables the lists.
@@ -49,13 +74,26 @@ void launch_assemble_fix(const Dims& d, const PhysDev& p, const double* E, const
 void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap);
 // Pass 2: right-hand side b, inverse diagonals (FP64 if op.invd, FP32 if
 // op32.invd), the FP64 diagonal if diag64, ||b||^2 into slot0 and max |b|
-// into slot1.
+// into slot1.  Cells on a Dirichlet face (p.dmask) also get the face's
+// limiter weight: stored in bnd, added to m (FP64 and FP32) and its flux
+// to b.
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
-                         const RedArgs& ra, cudaStream_t s);
+                         Bnd bnd, const RedArgs& ra, cudaStream_t s);
+// Photons through the Dirichlet faces of side s over the step (before the
+// finalisation overwrites E): sum of w_b (inv_theta (E - E_b) + dE) into
+// slot S_OUT0 + s and the sum of its absolute values into S_OUTABS0 + s
+// (reduction ra with op R_STORE2).
+void launch_bnd_outflow(const Dims& d, const PhysDev& p, int s, Bnd bnd, const double* E,
+                        const double* dE, const RedArgs& ra, cudaStream_t st);
 
 // ---- multigrid (k_mg.cu), T = float or double
 void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s);
+// Coarse Dirichlet face weights of side s (sum of the 4 fine ones / 16);
+// the coarse mass term, which k_coarsen took as the mean of the children's
+// full m, gives back the difference: m_c -= w_c.  After launch_coarsen.
+void launch_coarsen_bnd(const Dims& f, const Dims& c, int s, Bnd F, Bnd C, Op<double> CA,
+                        cudaStream_t st);
 template <class T>
 void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s);
 void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s);

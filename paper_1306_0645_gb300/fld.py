@@ -29,10 +29,13 @@ class FldError(RuntimeError):
         self.status = status
 
 
+FLD_BC_ZERO_GRADIENT, FLD_BC_PERIODIC, FLD_BC_DIRICHLET, FLD_BC_OUTFLOW = range(4)
+
+
 class fld_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
-                ("bc", ctypes.c_int * 3)]
+                ("bc", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("bc_value", ctypes.c_double * 6)]
 
 
 class fld_params(ctypes.Structure):
@@ -43,7 +46,8 @@ class fld_params(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int), ("fused_post", ctypes.c_int)]
+                ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int), ("fused_post", ctypes.c_int),
+                ("theta", ctypes.c_double)]
 
 
 class fld_info(ctypes.Structure):
@@ -51,7 +55,7 @@ class fld_info(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("balance_abs", ctypes.c_double),
                 ("balance_rel", ctypes.c_double), ("emitted", ctypes.c_double),
                 ("absorbed", ctypes.c_double), ("floor_added", ctypes.c_double),
-                ("rel_change", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("rel_change", ctypes.c_double), ("ms", ctypes.c_double), ("outflow", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -147,9 +151,24 @@ def _get(o, k, default=None):
 
 
 def make_grid(g) -> fld_grid:
+    """fld_grid of a grid record: n, h, periodic (3 flags) and optionally
+    dirichlet (6 flags, x lo, x hi, y lo, ...) with values ebc (6)."""
     n, h, per = _get(g, "n"), _get(g, "h"), _get(g, "periodic")
+    dflag = _get(g, "dirichlet") or (False,) * 6
+    dval = _get(g, "ebc") or (0.0,) * 6
+    lo, hi = [], []
+    for a in range(3):
+        if per[a]:
+            # a Dirichlet flag on a periodic axis is passed on for the
+            # library to reject
+            lo.append(FLD_BC_PERIODIC)
+            hi.append(FLD_BC_DIRICHLET if (dflag[2 * a] or dflag[2 * a + 1]) else FLD_BC_PERIODIC)
+        else:
+            lo.append(FLD_BC_DIRICHLET if dflag[2 * a] else FLD_BC_ZERO_GRADIENT)
+            hi.append(FLD_BC_DIRICHLET if dflag[2 * a + 1] else FLD_BC_ZERO_GRADIENT)
     return fld_grid(int(n[0]), int(n[1]), int(n[2]), float(h[0]), float(h[1]), float(h[2]),
-                    (ctypes.c_int * 3)(*[1 if v else 0 for v in per]))
+                    (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
+                    (ctypes.c_double * 6)(*[float(v) for v in dval]))
 
 
 def make_params(p=None, **overrides) -> fld_params:

@@ -236,6 +236,25 @@ def config_uniform(n: int = 32, sources: int = 1, seed: int = 0, periodic: bool 
                 eta=point_source_eta(g, cells, NDOT), nH=nH, sources=cells)
 
 
+def config_two_sources(nx: int = 128, theta: float = 1.0, precision: int = PREC_FP64) -> Case:
+    """Two sources of 5e48 photons/s 8 kpc apart in a uniform static medium
+    (n_H = 1e-3 cm^-3, neutral) filling a 20 x 10 x 10 kpc box resolved by
+    nx x nx/2 x nx/2 cubic cells (128 x 64 x 64 in the paper's test of two
+    merging HII regions, Sec. 4.1).  The sources sit on the long axis, 4 kpc
+    either side of the centre.  Radiation leaves through all six faces
+    (outflow), L_unit = 20 kpc."""
+    ny = nx // 2
+    h = 20.0 * KPC / nx
+    g = Grid((nx, ny, ny), (h, h, h), dirichlet=(True,) * 6, ebc=(0.0,) * 6)
+    p = Params(L_unit=20.0 * KPC, theta=theta, precision=precision)
+    centre = np.array([10.0, 5.0, 5.0]) * KPC
+    pos = [centre + np.array([dx, 0.0, 0.0]) * KPC for dx in (-4.0, 4.0)]
+    cells = np.array([[int(v // h) for v in q] for q in pos])
+    nH = np.full(g.shape, 1e-3)
+    return Case(name=f"two_sources{nx}", grid=g, params=p, E=np.full(g.shape, E0), nHI=nH.copy(),
+                eta=point_source_eta(g, cells, NDOT), nH=nH, sources=cells)
+
+
 def config_lognormal(n: int = 128, seed: int = 2, sigma_ln: float = 1.0,
                      mean_nH: float = 2e-4, sources: int = 256, periodic: bool = True,
                      tanh_ionised: bool = True, log_uniform_rates: Tuple[float, float] = (1e50, 1e53),

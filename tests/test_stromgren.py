@@ -62,9 +62,11 @@ def test_stromgren_front_oracle(oracle):
     assert abs(checks[300] - 1) < 0.03, checks
 
 
-def gpu_run(fld, torch, n, dt, steps, precision, marks):
+def gpu_run(fld, torch, n, dt, steps, precision, marks, outflow=False, theta=1.0):
     g, nH, nHI, E, eta = setup(n)
-    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt, precision=precision)
+    if outflow:
+        g = g.outflow_upper()
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt, precision=precision, theta=theta)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
     ctx = fld.fld_create(g, p)
     Eg, nHIg, nHg, etag = dev(E), dev(nHI), dev(nH), dev(eta)
@@ -92,6 +94,25 @@ def test_stromgren_front_gpu(precision):
     assert abs(ratio[200] - 1) < 0.06, ratio      # 100 Myr
     assert abs(ratio[400] - 1) < 0.03, ratio      # 200 Myr
     assert abs(ratio[800] - 1) < 0.03, ratio      # 400 Myr
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_stromgren_front_gpu_paper_boundaries(theta):
+    # the boundary set of the test: reflecting at x, y, z = 0 (the source's
+    # corner), outflow at the three far faces; backward Euler and the
+    # trapezoidal rule
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_0645_gb300 import fld
+    dt = 0.5 * MYR
+    marks = (200, 400, 800)
+    g, nH, out = gpu_run(fld, torch, 64, dt, 800, synth.PREC_MIXED, marks, outflow=True, theta=theta)
+    ratio = {k: front_radius(g, nH, out[k][1]) / r_analytic(k * dt) for k in marks}
+    assert abs(ratio[200] - 1) < 0.06, ratio
+    assert abs(ratio[400] - 1) < 0.03, ratio
+    assert abs(ratio[800] - 1) < 0.03, ratio
 
 
 @pytest.mark.gpu
