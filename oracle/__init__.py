@@ -65,7 +65,7 @@ class _Phys(ctypes.Structure):
                 ("L_unit", ctypes.c_double), ("dmax_coef", ctypes.c_double),
                 ("rmin_coef", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("adot", ctypes.c_double), ("hnu", ctypes.c_double),
-                ("limiter", ctypes.c_int), ("theta", ctypes.c_double)]
+                ("limiter", ctypes.c_int), ("theta", ctypes.c_double), ("a", ctypes.c_double)]
 
 
 class _Solver(ctypes.Structure):
@@ -147,7 +147,7 @@ def _phys(p) -> _Phys:
                  float(_get(p, "dmax_coef", 0.006)), float(_get(p, "rmin_coef", 1e-20)),
                  float(_get(p, "sigma")), float(_get(p, "adot_over_a", 0.0)),
                  float(_get(p, "hnu", 2.17896e-11)), int(_get(p, "limiter", LIMITER_PAPER)),
-                 float(_get(p, "theta", 1.0)))
+                 float(_get(p, "theta", 1.0)), float(_get(p, "scale_factor", 1.0)))
 
 
 def _solver(s) -> _Solver:

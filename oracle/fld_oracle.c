@@ -19,6 +19,11 @@
  *     (Sec. 1, LevermorePomraning1981);
  *   - opacity kappa = n_HI sigma for a monochromatic grey source
  *     (Eq. "opacity" with a single species and a delta-function SED);
+ *   - comoving coordinates for cosmological runs (Sec. 3.2, Eq. "fld"
+ *     with the adot/a term): cell widths are comoving, the gradients of the
+ *     equation proper, so the limiter and the face weights see the proper
+ *     widths a h, a the scale factor; E and eta are per comoving volume,
+ *     kappa proper;
  *   - the implicit theta-method of Sec. 3.2 (theta = 1 backward Euler,
  *     theta = 1/2 the trapezoidal rule) with D lagged at E^n, so the step is
  *     one linear system, posed for the correction dE = E^{n+1} - E^n:
@@ -105,6 +110,7 @@ typedef struct {
     double hnu;        /* erg per photon, for photon counts */
     int limiter;
     double theta;      /* 1 backward Euler, 1/2 trapezoidal */
+    double a;          /* cosmological scale factor (1: proper units) */
 } or_phys;
 
 typedef struct {
@@ -230,7 +236,8 @@ static int valid_grid(const or_grid* g) {
 
 /* Build m, wx, wy, wz, the packed Dirichlet face weights bnd (may be NULL
  * when the grid has no Dirichlet side) and the right-hand side b of the
- * theta-method correction system A dE = b (Sec. 3.2):
+ * theta-method correction system A dE = b (Sec. 3.2), with the proper cell
+ * widths h_d = a * (comoving width):
  *   w_f  = theta dt D_f / h_d^2                      (interior faces)
  *   w_b  = theta dt D_b / (h_d h_d / 2)              (Dirichlet faces)
  *   m_i  = 1 + theta dt (c kappa_i + adot/a) + sum of the cell's w_b
@@ -242,9 +249,11 @@ int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                 double* wy, double* wz, double* b, double* bnd) {
     if (!valid_grid(g) || !(p->dt > 0.0) || p->sigma < 0.0) return OR_EINVAL;
     if (!(p->theta > 0.0 && p->theta <= 1.0)) return OR_EINVAL;
+    if (!(p->a > 0.0 && isfinite(p->a))) return OR_EINVAL;
     if (any_dirichlet(g->dirichlet) && !bnd) return OR_EINVAL;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const double th = p->theta;
+    const double hp[3] = {p->a * g->h[0], p->a * g->h[1], p->a * g->h[2]};
     size_t N = ncell(g->n);
     for (size_t i = 0; i < N; i++)
         if (!(E[i] >= 0.0) || !(nHI[i] >= 0.0) || !(eta[i] >= 0.0) ||
@@ -269,14 +278,14 @@ int or_assemble(const or_grid* g, const or_phys* p, const double* E,
                     else { has = 0; lo = c; }
                     if (!has) { w[d][c] = 0.0; continue; }
                     double D = or_face_D(E[lo], E[c], nHI[lo] * p->sigma, kap,
-                                         g->h[d], p);
-                    w[d][c] = th * p->dt * D / (g->h[d] * g->h[d]);
+                                         hp[d], p);
+                    w[d][c] = th * p->dt * D / (hp[d] * hp[d]);
                 }
                 for (int sd = 0; sd < 6; sd++) {
                     if (!g->dirichlet[sd]) continue;
                     long f = side_face(g->n, sd, i, j, k);
                     if (f < 0) continue;
-                    double h = g->h[sd / 2];
+                    double h = hp[sd / 2];
                     double D = or_face_D(g->ebc[sd], E[c], kap, kap, 0.5 * h, p);
                     double wb = th * p->dt * D / (h * 0.5 * h);
                     bnd[f] = wb;

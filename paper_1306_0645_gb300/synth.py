@@ -103,6 +103,7 @@ class Params:
     graphs: int = -1
     fused_post: int = 0
     theta: float = 1.0
+    scale_factor: float = 1.0
 
 
 @dataclasses.dataclass

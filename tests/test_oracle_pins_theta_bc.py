@@ -269,3 +269,46 @@ def test_invalid_boundary_and_theta_rejected(oracle):
         oracle.step(g2, phys(), {}, E, E * 0, E * 0)        # negative E_b
     with pytest.raises(oracle.OracleError):
         oracle.step(synth.Grid.cube(4), phys(theta=0.0), {}, E, E * 0, E * 0)
+
+
+# ------------------------------------------------- comoving coordinates
+
+@pytest.mark.parametrize("theta", [0.5, 1.0])
+def test_comoving_widths_act_as_proper_widths(oracle, theta):
+    # a grid of comoving widths h at scale factor a is the grid of proper
+    # widths a h: same operator and right-hand side (the gradients of the
+    # equation are proper), whatever the limiter regime of each face
+    case = synth.random_case((12, 10, 8), seed=21, periodic=(True, False, False))
+    a = 0.2
+    p = case.params
+    p.theta, p.adot_over_a = theta, 3e-17
+    g_c = synth.Grid(case.grid.n, case.grid.h, case.grid.periodic,
+                     dirichlet=(False, False, True, False, False, True), ebc=(0, 0, 1e-19, 0, 0, 0))
+    g_p = synth.Grid(case.grid.n, tuple(a * h for h in case.grid.h), case.grid.periodic,
+                     dirichlet=g_c.dirichlet, ebc=g_c.ebc)
+    p.scale_factor = a
+    op_c = oracle.assemble(g_c, p, case.E, case.nHI, case.eta)
+    p.scale_factor = 1.0
+    op_p = oracle.assemble(g_p, p, case.E, case.nHI, case.eta)
+    for k in ("m", "wx", "wy", "wz", "b", "bnd"):
+        np.testing.assert_allclose(op_c[k], op_p[k], rtol=1e-14, atol=0)
+
+
+def test_comoving_mode_decays_with_proper_wavenumber(oracle):
+    # uniform medium, eta = eta0 + eps * mode: the mode's response carries
+    # the diffusion rate D lambda / (a h)^2 of the proper wavenumber
+    n = (16, 8, 12)
+    a = 0.25
+    kap = 1e-18
+    g = synth.Grid(n, (2e20, 3e20, 2.5e20))
+    p = phys(adot_over_a=1e-17, scale_factor=a, theta=0.5)
+    mode, lam = cosine_modes(n, (3, 1, 2), False)
+    E0, eta0, eps = 1e-18, 4e-24, 1e-24
+    D = min(C / (3 * kap), 0.006 * C * p.L_unit)
+    w = [p.dt * D / (a * h) ** 2 for h in g.h]
+    s = C * kap + p.adot_over_a
+    exact = p.dt * (eta0 - s * E0) / (1 + 0.5 * p.dt * s) \
+        + p.dt * eps * mode / (1 + 0.5 * (p.dt * s + sum(wd * ld for wd, ld in zip(w, lam))))
+    E1, _ = oracle.step(g, p, {"rtol": 1e-14, "max_iter": 200}, np.full(g.shape, E0),
+                        np.full(g.shape, kap / p.sigma), eta0 + eps * mode)
+    np.testing.assert_allclose(E1 - E0, exact, rtol=0, atol=1e-12 * np.abs(exact).max())
