@@ -129,6 +129,12 @@ typedef struct {
     double theta;              /* time discretisation, in [1/2, 1]: 1
                                   backward Euler (default), 1/2 trapezoidal
                                   (Sec. 3.2) */
+    double scale_factor;       /* cosmological expansion factor a (> 0,
+                                  default 1).  Cell widths are comoving, the
+                                  equation's gradients proper: the limiter
+                                  and face weights use a * dx etc.  E and eta
+                                  are per comoving volume (photon counts use
+                                  the comoving cell volume), kappa proper. */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -158,7 +164,7 @@ typedef struct fld_ctx fld_ctx;
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
  * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
- * graphs -1, fused_post 0, theta 1.
+ * graphs -1, fused_post 0, theta 1, scale_factor 1.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 
@@ -205,6 +211,12 @@ fld_status fld_step_host(fld_ctx* ctx, double* E, const double* n_HI,
 
 /* Change the time step of the context (the operator depends on dt). */
 fld_status fld_set_dt(fld_ctx* ctx, double dt);
+
+/* Cosmological expansion between steps (Sec. 3.2, the adot/a term of Eq.
+ * "fld" in comoving coordinates): set the scale factor a (> 0) and adot/a
+ * (>= 0, 1/s) for the following steps.  The hierarchy and buffers are kept;
+ * the next assembly takes the new values.  FLD_EINVAL leaves them unchanged. */
+fld_status fld_set_expansion(fld_ctx* ctx, double scale_factor, double adot_over_a);
 
 /* Radiation subcycling (Sec. 3.3): advance E over t_span in substeps.
  * A substep whose solve fails (FLD_ENOCONV or FLD_ENONFINITE) is retried at

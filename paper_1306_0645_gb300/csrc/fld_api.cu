@@ -141,6 +141,8 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     if (!finite_pos(p->hnu)) return set_err(FLD_EINVAL, "hnu must be finite and > 0");
     if (!(p->theta >= 0.5 && p->theta <= 1.0))
         return set_err(FLD_EINVAL, "theta must lie in [1/2, 1] (1 backward Euler, 1/2 trapezoidal)");
+    if (!(std::isfinite(p->scale_factor) && p->scale_factor > 0.0))
+        return set_err(FLD_EINVAL, "scale_factor must be finite and > 0");
     if (p->limiter != FLD_LIMITER_PAPER && p->limiter != FLD_LIMITER_LP)
         return set_err(FLD_EINVAL, "unknown limiter %d", p->limiter);
     if (p->precision != FLD_PREC_FP64 && p->precision != FLD_PREC_MIXED)
@@ -866,7 +868,10 @@ void fill_physdev(fld_ctx* c, double dt) {
     pd.Rmin = p->rmin_coef / p->L_unit;
     pd.sigma = p->sigma;
     pd.adot = p->adot_over_a;
-    pd.h[0] = g->dx; pd.h[1] = g->dy; pd.h[2] = g->dz;
+    // the equation's gradients are proper: widths a * (comoving width)
+    pd.h[0] = p->scale_factor * g->dx;
+    pd.h[1] = p->scale_factor * g->dy;
+    pd.h[2] = p->scale_factor * g->dz;
     pd.theta = p->theta;
     pd.inv_theta = 1.0 / p->theta;
     for (int a = 0; a < 3; a++) {
@@ -1287,6 +1292,7 @@ fld_status fld_params_default(fld_params* p) {
     p->graphs = -1;
     p->fused_post = 0;
     p->theta = 1.0;
+    p->scale_factor = 1.0;
     return FLD_OK;
 }
 
@@ -1437,6 +1443,17 @@ fld_status fld_set_dt(fld_ctx* c, double dt) {
     if (!c) return set_err(FLD_EINVAL, "null context");
     if (!(std::isfinite(dt) && dt > 0.0)) return set_err(FLD_EINVAL, "dt must be finite and > 0");
     fill_physdev(c, dt);
+    return FLD_OK;
+}
+
+fld_status fld_set_expansion(fld_ctx* c, double a, double adot_over_a) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!(std::isfinite(a) && a > 0.0)) return set_err(FLD_EINVAL, "scale factor must be finite and > 0");
+    if (!(std::isfinite(adot_over_a) && adot_over_a >= 0.0))
+        return set_err(FLD_EINVAL, "adot_over_a must be finite and >= 0");
+    c->p.scale_factor = a;
+    c->p.adot_over_a = adot_over_a;
+    fill_physdev(c, c->p.dt);
     return FLD_OK;
 }
 

@@ -47,7 +47,7 @@ class fld_params(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int), ("fused_post", ctypes.c_int),
-                ("theta", ctypes.c_double)]
+                ("theta", ctypes.c_double), ("scale_factor", ctypes.c_double)]
 
 
 class fld_info(ctypes.Structure):
@@ -104,6 +104,7 @@ _SIGS = {
                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP], ctypes.c_int),
     "fld_levels": ([ctypes.POINTER(fld_grid), ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
     "fld_set_dt": ([_VP, ctypes.c_double], ctypes.c_int),
+    "fld_set_expansion": ([_VP, ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "fld_residual_noalloc": ([ctypes.POINTER(fld_grid)] + [_VP] * 9, ctypes.c_int),
     "fld_advance": ([_VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                      ctypes.POINTER(fld_advance_params), ctypes.POINTER(fld_advance_info)], ctypes.c_int),
@@ -355,6 +356,11 @@ def fld_profile_read(ctx: Context) -> List[dict]:
 
 def fld_set_dt(ctx: Context, dt: float):
     _check(lib().fld_set_dt(ctx.handle, float(dt)), "fld_set_dt")
+
+
+def fld_set_expansion(ctx: Context, scale_factor: float, adot_over_a: float):
+    _check(lib().fld_set_expansion(ctx.handle, float(scale_factor), float(adot_over_a)),
+           "fld_set_expansion")
 
 
 def fld_advance(ctx: Context, E, nHI, eta, t_span: float, dt_first: float, tau_tol: float = 1e-4,

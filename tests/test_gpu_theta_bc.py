@@ -167,3 +167,32 @@ def test_theta_validation(fld):
     g3 = synth.Grid((8, 8, 8), (1e20,) * 3, dirichlet=(True,) + (False,) * 5, ebc=(math.inf,) + (0.0,) * 5)
     with pytest.raises(fld.FldError):
         fld.fld_create(g3, synth.Params())
+
+
+def test_comoving_scale_factor_parity(fld, oracle):
+    # comoving widths at scale factor a, changed between steps through
+    # fld_set_expansion; FP64 steps solved tightly against the oracle
+    case = with_faces(synth.random_case((24, 16, 20), seed=31), (False, True) * 3, theta=0.5)
+    p = case.params
+    p.rtol, p.max_iter = 1e-13, 200
+    p.scale_factor, p.adot_over_a = 0.25, 4e-17
+    ctx = fld.fld_create(case.grid, p)
+    fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
+    out = {k: torch.empty(case.grid.cells, dtype=torch.float64, device="cuda") for k in ("m", "wx", "wy", "wz", "b")}
+    fld.fld_get_system(ctx, **out)
+    ref = oracle.assemble(case.grid, p, case.E, case.nHI, case.eta)
+    sh = case.grid.shape
+    for k in ("m", "wx", "wy", "wz"):
+        np.testing.assert_allclose(host(out[k], sh), ref[k], rtol=1e-13, atol=0)
+    E = dev(case.E)
+    Eref = case.E.copy()
+    for a, h in ((0.25, 4e-17), (0.3, 3e-17), (0.5, 1e-17)):
+        fld.fld_set_expansion(ctx, a, h)
+        p.scale_factor, p.adot_over_a = a, h
+        info = fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
+        Eref, _ = oracle.step(case.grid, p, {"rtol": 1e-13, "max_iter": 200}, Eref, case.nHI, case.eta)
+        assert info["rel_res"] <= 1e-13
+    with pytest.raises(fld.FldError):
+        fld.fld_set_expansion(ctx, 0.0, 1e-17)
+    ctx.close()
+    np.testing.assert_allclose(host(E, sh), Eref, rtol=1e-10, atol=1e-10 * np.abs(Eref).max())

@@ -132,3 +132,138 @@ def test_stromgren_gpu_matches_oracle(oracle):
     # both sides run the same algorithm at rtol 1e-8 for 60 coupled steps
     assert abs(front_radius(g, nH, nHIg) / front_radius(g, nH, nHI) - 1) < 1e-6
     assert np.linalg.norm(Eg - E) / np.linalg.norm(E) < 1e-6
+
+
+# --------------------------------------------- cosmological I-front (Sec. 4.1.2)
+#
+# The same source in an expanding Einstein-de Sitter universe (q0 = 1/2,
+# H0 = 50 km/s/Mpc), from z = 4, in a comoving box of 80 kpc with the
+# initial proper density 1.175e-28 g/cm^3 of hydrogen.  E and eta are per
+# comoving volume, the cell widths comoving (scale factor a through
+# fld_set_expansion), n_H proper and falling as a^-3; the photoionisation
+# rate takes the proper E / a^3.  The luminosity is 5e46 photons/s (the
+# test's 5e48 /s front leaves this box within 100 Myr, before the expansion
+# matters), so the front stays inside for 2 Gyr while a doubles.
+#
+# Closed form: photon counting for the comoving ionised volume V of the
+# octant, n_c dV/dt = N_dot/8 - alpha_B n_c^2 V / a^3 with n_c = n_H a^3
+# constant (the sharp-front model behind the Shapiro-Giroux solution),
+# integrated numerically.  The ionised volume of the run counts each cell's
+# ionisation beyond that of gas no photon reached (the 0.0012 initial
+# ionisation recombines meanwhile).
+
+H0_EDS = 50e5 / (1e3 * synth.KPC)
+A0 = 0.2
+NH_Z4 = 1.175e-28 / 1.6726e-24
+NDOT_COSMO = 5e46
+L_COSMO = 80 * synth.KPC
+
+
+def eds_a(t):
+    return (1.5 * H0_EDS * t) ** (2.0 / 3.0)
+
+
+def eds_t(a):
+    return 2.0 / (3.0 * H0_EDS) * a ** 1.5
+
+
+def cosmo_front_closed_form(t_end, expanding=True):
+    from scipy.integrate import solve_ivp
+    nc = NH_Z4 * A0 ** 3
+    t0 = eds_t(A0)
+
+    def rhs(t, V):
+        a = eds_a(t) if expanding else A0
+        return [NDOT_COSMO / (8 * nc) - ALPHA * nc * V[0] / a ** 3]
+
+    sol = solve_ivp(rhs, (t0, t0 + t_end), [0.0], rtol=1e-10, atol=1e30)
+    return (3 * 8 * sol.y[0][-1] / (4 * math.pi)) ** (1 / 3)
+
+
+def cosmo_setup(n):
+    g = synth.Grid.cube(n, box=L_COSMO).outflow_upper()
+    E = np.full(g.shape, 1e-45 * A0 ** 3)
+    eta = np.zeros(g.shape)
+    eta[0, 0, 0] = NDOT_COSMO / 8 * synth.HNU_HI / g.volume
+    return g, E, eta
+
+
+def cosmo_radius(g, x, x_dark):
+    v = float((np.maximum(x_dark - x, 0.0) * g.volume).sum())
+    return (3 * 8 * v / (4 * math.pi)) ** (1 / 3)
+
+
+COSMO_MARKS_MYR = (200, 1000, 2000)
+
+
+def test_cosmological_front_oracle(oracle):
+    n, dt = 24, 5 * MYR
+    g, E, eta = cosmo_setup(n)
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt, L_unit=L_COSMO)
+    x = np.full(g.shape, 1 - 0.0012)
+    xd = np.full(1, 1 - 0.0012)
+    t0 = eds_t(A0)
+    t = t0
+    got = {}
+    for k in range(1, int(COSMO_MARKS_MYR[-1] * MYR / dt) + 1):
+        a = eds_a(t + 0.5 * dt)
+        p.scale_factor, p.adot_over_a = a, H0_EDS * a ** -1.5
+        nHp = NH_Z4 * (A0 / a) ** 3
+        E, _ = oracle.step(g, p, {}, E, x * nHp, eta)
+        ae = eds_a(t + dt)
+        nHe = NH_Z4 * (A0 / ae) ** 3
+        cp = synth.C_LIGHT / ae ** 3          # proper E = comoving E / a^3
+        x = oracle.opacity_update(E, np.full(g.shape, nHe), x * nHe, dt, cp, p.sigma, p.hnu, ALPHA) / nHe
+        xd = oracle.opacity_update(np.zeros(1), np.full(1, nHe), xd * nHe, dt, cp, p.sigma, p.hnu, ALPHA) / nHe
+        t += dt
+        tm = round((t - t0) / MYR)
+        if tm in COSMO_MARKS_MYR:
+            got[tm] = cosmo_radius(g, x, xd[0]) / cosmo_front_closed_form(t - t0)
+    assert all(abs(r - 1) < 0.04 for r in got.values()), got
+    # the expansion matters: a static universe's front is 13% behind by 2 Gyr
+    T = COSMO_MARKS_MYR[-1] * MYR
+    assert cosmo_front_closed_form(T, expanding=False) < 0.9 * cosmo_front_closed_form(T)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_cosmological_front_gpu(theta):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_0645_gb300 import fld
+    n, dt = 64, 2.5 * MYR
+    g, E0, eta0 = cosmo_setup(n)
+    p = synth.Params(limiter=synth.LIMITER_PAPER, dt=dt, L_unit=L_COSMO, precision=synth.PREC_MIXED,
+                     theta=theta)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    ctx = fld.fld_create(g, p)
+    E, eta = dev(E0), dev(eta0)
+    x = torch.full((g.cells,), 1 - 0.0012, dtype=torch.float64, device="cuda")
+    xd = torch.full((1,), 1 - 0.0012, dtype=torch.float64, device="cuda")
+    zero1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t0 = eds_t(A0)
+    t = t0
+    got = {}
+    for k in range(1, int(COSMO_MARKS_MYR[-1] * MYR / dt) + 1):
+        a = eds_a(t + 0.5 * dt)
+        fld.fld_set_expansion(ctx, a, H0_EDS * a ** -1.5)
+        nHp = NH_Z4 * (A0 / a) ** 3
+        fld.fld_step(ctx, E, x * nHp, eta)
+        ae = eds_a(t + dt)
+        nHe = NH_Z4 * (A0 / ae) ** 3
+        cp = synth.C_LIGHT / ae ** 3
+        nH = torch.full_like(x, nHe)
+        nHI = x * nHe
+        fld.fld_opacity_update(E, nH, nHI, nHI, dt, cp, p.sigma, p.hnu, ALPHA)
+        x = nHI / nHe
+        nHd = xd * nHe
+        fld.fld_opacity_update(zero1, torch.full_like(xd, nHe), nHd, nHd, dt, cp, p.sigma, p.hnu, ALPHA)
+        xd = nHd / nHe
+        t += dt
+        tm = round((t - t0) / MYR)
+        if tm in COSMO_MARKS_MYR:
+            xh = x.cpu().numpy().reshape(g.shape)
+            got[tm] = cosmo_radius(g, xh, float(xd[0])) / cosmo_front_closed_form(t - t0)
+    ctx.close()
+    assert all(abs(r - 1) < 0.04 for r in got.values()), got
