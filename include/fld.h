@@ -298,6 +298,78 @@ fld_status fld_residual_noalloc(const fld_grid* g, const double* m, const double
                                 const double* wy, const double* wz, const double* b,
                                 const double* x, double* r, double* norms, void* cuda_stream);
 
+/* ---- Spectral model (Sec. 2, "Model coupling"): grey and multigroup
+ * integrals of the assumed spectrum chi(nu) and the fields built from them.
+ *
+ * For frequency groups g = [edges[g], edges[g+1]] (a grey field is the one
+ * group [nu_1, nu_max]; nu_max reads the paper's "infinity") and species
+ * i = HI, HeI, HeII with thresholds nu_i, row g of the coefficient table is
+ *   K_g0..2 = int sigma_i chi dnu / N_g              (Eq. "opacity")
+ *   P_g0..2 = int sigma_i chi / nu dnu / N_g         (Eq. "photoionization")
+ *   H_g0..2 = int sigma_i chi (1 - nu_i/nu) dnu / N_g (Eq. "photoheating")
+ *   F_g     = N_g / N                                (share of the emissivity)
+ * with N_g = int_g chi dnu, N = int over all groups, the species integrals
+ * from max(edges[g], nu_i).  The normalisation starts at the group's lower
+ * edge for all three (the paper prints nu_i in the opacity's denominator;
+ * photons below nu_i are part of E but species i cannot absorb them).
+ * Cross sections: sigma_0 [beta (nu/nu_i)^-s + (1-beta) (nu/nu_i)^(-s-1)],
+ * nu >= nu_i (defaults: the Osterbrock 1989 fits the paper cites). */
+typedef enum { FLD_SED_MONO = 0, FLD_SED_BLACKBODY = 1, FLD_SED_POWERLAW = 2 } fld_sed_kind;
+#define FLD_MAX_GROUPS 16
+#define FLD_SED_NCOEF 10
+
+typedef struct {
+    double nu_threshold;       /* Hz */
+    double sigma0;             /* cm^2 at threshold */
+    double beta, s;            /* shape of the fit */
+} fld_xsec;
+
+typedef struct {
+    int kind;                  /* fld_sed_kind */
+    double nu_mono;            /* Hz, line frequency (FLD_SED_MONO) */
+    double T;                  /* K, blackbody chi ~ nu^3 / (exp(h nu/kT) - 1) */
+    double alpha;              /* power law chi ~ nu^-alpha */
+    fld_xsec species[3];       /* HI, HeI, HeII */
+} fld_sed;
+
+/* Blackbody at 1e5 K (alpha 1.5, nu_mono = nu_HI for the other kinds) with
+ * the Osterbrock fits: HI (13.6 eV, 6.30e-18, 1.34, 2.99), HeI (24.6 eV,
+ * 7.83e-18, 1.66, 2.05), HeII (54.4 eV, 1.58e-18, 1.34, 2.99). */
+fld_status fld_sed_default(fld_sed* sed);
+
+/* The coefficient table of `groups` groups (1 .. FLD_MAX_GROUPS; edges is a
+ * HOST array of groups + 1 increasing frequencies in Hz) into the HOST
+ * array coef[groups * FLD_SED_NCOEF], row g = (K_g0..2, P_g0..2, H_g0..2,
+ * F_g).  Computed on the GPU (composite Simpson in ln nu, 2^14 intervals per
+ * integral; a line is evaluated at its frequency) on cuda_stream, which is
+ * synchronised before the call returns.  Allocates a small device scratch
+ * (stream-ordered) and frees it. */
+fld_status fld_sed_integrals(const fld_sed* sed, const double* edges, int groups, double* coef,
+                             void* cuda_stream);
+
+/* Group opacities and emissivities in one pass over the cells:
+ * kappa[g][c] = sum_i n_i[c] K_gi and eta_out[g][c] = F_g eta[c].
+ * coef: HOST table of fld_sed_integrals.  n_HI, n_HeI, n_HeII, eta: DEVICE
+ * arrays of n cells (n_HeI, n_HeII may be NULL for 0; eta may be NULL when
+ * eta_out is NULL).  kappa, eta_out: HOST arrays of `groups` DEVICE
+ * pointers (eta_out may be NULL).  A group opacity field passed to
+ * fld_step as n_HI with fld_params.sigma = 1 makes it the step's kappa.
+ * Asynchronous on cuda_stream. */
+fld_status fld_group_fields(size_t n, int groups, const double* coef, const double* n_HI,
+                            const double* n_HeI, const double* n_HeII, const double* eta,
+                            double* const* kappa, double* const* eta_out, void* cuda_stream);
+
+/* Photoionisation and photoheating rates from the group energies:
+ * gamma_i[c] = sum_g (c_light / h) P_gi E_g[c] (1/s) and
+ * heating[c] = sum_g c_light E_g[c] sum_i n_i[c] H_gi / rho_b[c] (erg/s/g).
+ * E: HOST array of `groups` DEVICE pointers; the density and output arrays
+ * are DEVICE arrays of n cells, any output may be NULL (heating needs
+ * rho_b).  Asynchronous on cuda_stream. */
+fld_status fld_photo_rates(size_t n, int groups, const double* coef, const double* const* E,
+                           const double* n_HI, const double* n_HeI, const double* n_HeII,
+                           const double* rho_b, double c_light, double* gamma_HI, double* gamma_HeI,
+                           double* gamma_HeII, double* heating, void* cuda_stream);
+
 /* Number of levels and their shapes (dims[3*l .. 3*l+2]) for grid g. */
 int fld_levels(const fld_grid* g, int* dims, int max_levels);
 

@@ -75,6 +75,21 @@ class fld_advance_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+FLD_SED_MONO, FLD_SED_BLACKBODY, FLD_SED_POWERLAW = range(3)
+FLD_MAX_GROUPS = 16
+FLD_SED_NCOEF = 10
+
+
+class fld_xsec(ctypes.Structure):
+    _fields_ = [("nu_threshold", ctypes.c_double), ("sigma0", ctypes.c_double), ("beta", ctypes.c_double),
+                ("s", ctypes.c_double)]
+
+
+class fld_sed(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nu_mono", ctypes.c_double), ("T", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("species", fld_xsec * 3)]
+
+
 class fld_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
                 ("timed", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
@@ -114,6 +129,11 @@ _SIGS = {
     "fld_set_tuning": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int], ctypes.c_int),
     "fld_profile": ([_VP, ctypes.c_ulonglong], ctypes.c_int),
     "fld_profile_read": ([_VP, ctypes.POINTER(fld_kernel_stat), ctypes.c_int], ctypes.c_int),
+    "fld_sed_default": ([ctypes.POINTER(fld_sed)], ctypes.c_int),
+    "fld_sed_integrals": ([ctypes.POINTER(fld_sed), _VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "fld_group_fields": ([ctypes.c_size_t, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "fld_photo_rates": ([ctypes.c_size_t, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double,
+                         _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "fld_last_error": ([], ctypes.c_char_p),
     "fld_destroy": ([_VP], None),
 }
@@ -443,3 +463,71 @@ def autotune(ctx: Context, cache_path: Optional[str] = None, reps: int = 3) -> L
     except OSError:
         pass
     return table
+
+
+# ------------------------------------------------------------ spectral model
+
+def fld_sed_default(**overrides) -> fld_sed:
+    """SED record: the library's defaults with fields overridden by keyword
+    (kind, nu_mono, T, alpha)."""
+    sed = fld_sed()
+    _check(lib().fld_sed_default(ctypes.byref(sed)), "fld_sed_default")
+    for k, v in overrides.items():
+        setattr(sed, k, type(getattr(sed, k))(v))
+    return sed
+
+
+def fld_sed_integrals(sed: fld_sed, edges: Sequence[float], stream=None) -> np.ndarray:
+    """Coefficient table (groups x FLD_SED_NCOEF) for frequency-group edges (Hz)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    groups = e.size - 1
+    coef = np.zeros((max(groups, 1), FLD_SED_NCOEF))
+    st = lib().fld_sed_integrals(ctypes.byref(sed), ctypes.c_void_p(e.ctypes.data), int(groups),
+                                 ctypes.c_void_p(coef.ctypes.data), _stream(stream))
+    _check(st, "fld_sed_integrals")
+    return coef
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _VP(s.cuda_stream)
+
+
+def _ptrs(ts, n, what):
+    arr = (_VP * len(ts))()
+    for g, t in enumerate(ts):
+        arr[g] = _dptr(t, n, f"{what}[{g}]").value
+    return arr
+
+
+def _opt(t, n, what):
+    return _dptr(t, n, what) if t is not None else None
+
+
+def fld_group_fields(coef: np.ndarray, n_HI, kappas, n_HeI=None, n_HeII=None, eta=None, etas=None,
+                     stream=None):
+    """kappa_g = sum_i n_i K_gi and eta_g = F_g eta into the given tensors."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    groups = coef.shape[0]
+    n = n_HI.numel()
+    st = lib().fld_group_fields(n, groups, ctypes.c_void_p(coef.ctypes.data), _dptr(n_HI, n, "n_HI"),
+                                _opt(n_HeI, n, "n_HeI"), _opt(n_HeII, n, "n_HeII"), _opt(eta, n, "eta"),
+                                ctypes.cast(_ptrs(kappas, n, "kappa"), _VP),
+                                ctypes.cast(_ptrs(etas, n, "eta_out"), _VP) if etas is not None else None,
+                                _stream(stream))
+    _check(st, "fld_group_fields")
+
+
+def fld_photo_rates(coef: np.ndarray, E_groups, n_HI=None, n_HeI=None, n_HeII=None, rho_b=None,
+                    c_light=2.99792458e10, gamma_HI=None, gamma_HeI=None, gamma_HeII=None, heating=None,
+                    stream=None):
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    groups = coef.shape[0]
+    n = E_groups[0].numel()
+    st = lib().fld_photo_rates(n, groups, ctypes.c_void_p(coef.ctypes.data),
+                               ctypes.cast(_ptrs(E_groups, n, "E"), _VP), _opt(n_HI, n, "n_HI"),
+                               _opt(n_HeI, n, "n_HeI"), _opt(n_HeII, n, "n_HeII"), _opt(rho_b, n, "rho_b"),
+                               float(c_light), _opt(gamma_HI, n, "gamma_HI"), _opt(gamma_HeI, n, "gamma_HeI"),
+                               _opt(gamma_HeII, n, "gamma_HeII"), _opt(heating, n, "heating"), _stream(stream))
+    _check(st, "fld_photo_rates")
