@@ -47,6 +47,7 @@ TRAFFIC_OVER_ALGORITHMIC = {
     "smooth_zero": 24.2 / 24.0,
     "residual": 27.9 / 28.0,
     "restrict": 4.5 / 4.5,
+    "prolong_add": 6.7 / 8.5,
     "cg_update": 22.6 / 24.0,
     "assemble_faces": 71.6 / 72.0,
     "residual64": 56.0 / 56.0,
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (Poisson stream, 0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--variant-steps", type=int, default=3,
+                    help="timed steps of each method variant (trapezoidal rule, outflow faces, "
+                         "comoving units) on the same workload; 0 skips them")
     ap.add_argument("--serve-workers", type=int, default=8)
     return ap.parse_args()
 
@@ -324,6 +328,77 @@ def main():
         ctx64.close()
         del E64
 
+    # ---- method variants on the same workload and tuned launch shapes
+    variants = None
+    if args.variant_steps > 0:
+        import dataclasses
+        table = fld.fld_get_tuning(ctx)
+        grid_out = case.grid.outflow_upper()
+        variants = {}
+        for name, grid_v, changes in (
+                ("trapezoidal", case.grid, {"theta": 0.5}),
+                ("outflow_faces", grid_out, {}),
+                ("comoving_a0.5", case.grid, {"scale_factor": 0.5, "adot_over_a": 1.0e-17})):
+            pv = dataclasses.replace(pm, **changes)
+            ctxv = fld.fld_create(grid_v, pv, stream)
+            fld.fld_set_tuning(ctxv, table)
+            Ev = E0.clone()
+            fld.fld_step(ctxv, Ev, nHI, eta)
+            msv, perv, infv = time_steps(fld, torch, ctxv, Ev, nHI, eta, args.variant_steps)
+            variants[name] = {"value": cells * args.variant_steps / (msv * 1e-3), "unit": UNIT,
+                              "ms_per_step": msv / args.variant_steps,
+                              "iters": [i["iters"] for i in infv], "outer_iters": [i["outer_iters"] for i in infv],
+                              "rel_res": [i["rel_res"] for i in infv],
+                              "balance_rel": [i["balance_rel"] for i in infv],
+                              "what": {"trapezoidal": "theta = 1/2 (Sec. 3.2)",
+                                       "outflow_faces": "reflecting at x, y, z = 0, outflow at the upper faces "
+                                                        "(Sec. 4.1 boundary set)",
+                                       "comoving_a0.5": "comoving widths at scale factor 0.5, adot/a 1e-17 /s"}[name]}
+            ctxv.close()
+            del Ev
+        # multigroup: four groups of a 1e5 K blackbody (edges at the HI,
+        # HeI, HeII thresholds, 100 nu_HI and 1000 nu_HI), each an FLD system
+        # with its group opacity and share of the emissivity; a step is the
+        # group fields plus all groups through the batched driver
+        G = 4
+        hnu_hi = synth.HNU_HI
+        h_pl = 6.62607015e-27
+        nu1 = hnu_hi / h_pl
+        edges = [nu1, 24.6 / 13.6 * nu1, 54.4 / 13.6 * nu1, 100 * nu1, 1000 * nu1]
+        coef = fld.fld_sed_integrals(fld.fld_sed_default(kind=fld.FLD_SED_BLACKBODY, T=1e5), edges)
+        pg = dataclasses.replace(pm, sigma=1.0)
+        gstreams = [torch.cuda.Stream() for _ in range(G)]
+        gctx = [fld.fld_create(case.grid, pg, st) for st in gstreams]
+        for c_ in gctx:
+            fld.fld_set_tuning(c_, table)
+        kap = [torch.empty_like(E0) for _ in range(G)]
+        etg = [torch.empty_like(E0) for _ in range(G)]
+        Eg = [E0 * float(coef[k, 9]) for k in range(G)]
+
+        def mg_step():
+            fld.fld_group_fields(coef, nHI, kap, eta=eta, etas=etg)
+            torch.cuda.synchronize()
+            return fld.fld_step_batched(gctx, Eg, kap, etg)
+
+        mg_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        minf = []
+        for _ in range(args.variant_steps):
+            minf.append(mg_step()[1])
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        variants["multigroup4"] = {
+            "value": cells * G * args.variant_steps / el, "unit": "cell-group-solves/s",
+            "ms_per_step": el * 1e3 / args.variant_steps,
+            "iters": [[i["iters"] for i in st_] for st_ in minf],
+            "what": "4 groups of a 1e5 K blackbody (edges nu_HI, nu_HeI, nu_HeII, 100, 1000 nu_HI), "
+                    "group opacities and emissivities by fld_group_fields, groups stepped together by "
+                    "fld_step_batched; wall time of whole steps (host clock)"}
+        for c_ in gctx:
+            c_.close()
+        del kap, etg, Eg
+
     # ---- end to end through the host-buffer entry point
     e2e = None
     if args.e2e_steps > 0:
@@ -378,7 +453,7 @@ def main():
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
             "roofline": roofline, "step_roofline_frac": step_frac, "kernel_breakdown_one_step": breakdown,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "serving": serving_out,
+            "serving": serving_out, "variants": variants,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
