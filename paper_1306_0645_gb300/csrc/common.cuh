@@ -40,6 +40,7 @@ enum Slot {
     S_OUT5 = S_OUT0 + 5,
     S_OUTABS0,    // the same summed in absolute value per face, side 0..5
     S_OUTABS5 = S_OUTABS0 + 5,
+    S_ESUM,       // sum of the loss-weighted energies E^n + theta dE (finalise)
     NUM_SLOTS = 40
 };
 
@@ -50,12 +51,12 @@ enum RedOp {
     R_ALPHA,        // alpha = rho / v0
     R_STORE2,       // sc[slot0] = v0, sc[slot1] = v1
     R_STORE3,       // sc[slot0..2] = v0..v2 (slots consecutive from slot0)
-    R_STORE6_FIN,   // sc[S_BAL], [S_EMIT], [S_ABSORB], [S_FLOOR], [S_DE2], [S_EN2] = v0..v5
+    R_STORE7_FIN,   // sc[S_BAL], [S_EMIT], [S_ABSORB], [S_FLOOR], [S_DE2], [S_EN2], [S_ESUM] = v0..v6
     R_STORE_SUM_MAX // sc[slot0] = v0 (sum), sc[slot1] = v1 (max)
 };
 
 struct RedArgs {
-    double* partials;     // >= 6 * RED_MAX_BLOCKS doubles
+    double* partials;     // >= 8 * RED_MAX_BLOCKS doubles
     unsigned* counter;    // one counter, 0 between reductions
     double* sc;           // scalar slots
     int op;
@@ -131,14 +132,15 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
         sc[ra.slot1] = v[1];
         bad = !isfinite(v[0]) || !isfinite(v[1]);
         break;
-    case R_STORE6_FIN:
+    case R_STORE7_FIN:
         sc[S_BAL] = v[0];
         sc[S_EMIT] = v[1];
         sc[S_ABSORB] = v[2];
         sc[S_FLOOR] = v[3];
         sc[S_DE2] = v[4];
         sc[S_EN2] = v[5];
-        for (int q = 0; q < 6; q++) bad = bad || !isfinite(v[q]);
+        sc[S_ESUM] = v[6];
+        for (int q = 0; q < 7; q++) bad = bad || !isfinite(v[q]);
         break;
     case R_STORE3:
         sc[ra.slot0] = v[0];

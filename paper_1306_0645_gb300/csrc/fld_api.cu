@@ -228,7 +228,7 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     const size_t nc = (size_t)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
     buf(0, "dense", 0, nc * nc * sizeof(double));
     buf(0, "dense", 1, nc * nc * sizeof(double));
-    buf(0, "red", 0, 6 * RED_MAX_BLOCKS * sizeof(double));
+    buf(0, "red", 0, 8 * RED_MAX_BLOCKS * sizeof(double));
     buf(0, "red", 1, 256);
     buf(0, "red", 2, NUM_SLOTS * sizeof(double));
 }
@@ -908,7 +908,7 @@ void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* et
             launch_bnd_outflow(c->L[0].d, c->pd, sd, c->L[0].bnd, E, c->dE,
                                red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd), c->s);
         }
-    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE6_FIN), c->s); }
+    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE7_FIN), c->s); }
     cudaEventRecord(c->e1, c->s);
     cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
 }
@@ -924,10 +924,15 @@ void finalize_info(fld_ctx* c, fld_info* inf) {
             out += c->h_sc[S_OUT0 + sd];
             gross += c->h_sc[S_OUTABS0 + sd];
         }
+    // the finalisation sums dE, eta, n_HI E^theta and E^theta over the cells
+    // (E^theta = E^n + theta dE); emission and absorption follow by the
+    // step's constants
+    const double emit = c->pd.dt * c->h_sc[S_EMIT];
+    const double absorb = c->pd.dtcs * c->h_sc[S_ABSORB] + c->pd.dta * c->h_sc[S_ESUM];
     inf->outflow = out * scale;
-    inf->balance_abs = (c->h_sc[S_BAL] + out) * scale;
-    inf->emitted = c->h_sc[S_EMIT] * scale;
-    inf->absorbed = c->h_sc[S_ABSORB] * scale;
+    inf->balance_abs = ((c->h_sc[S_BAL] - emit) + absorb + out) * scale;
+    inf->emitted = emit * scale;
+    inf->absorbed = absorb * scale;
     inf->floor_added = c->h_sc[S_FLOOR] * scale;
     inf->rel_change = c->h_sc[S_EN2] > 0.0 ? std::sqrt(c->h_sc[S_DE2] / c->h_sc[S_EN2]) : 0.0;
     double budget = inf->emitted > inf->absorbed ? inf->emitted : inf->absorbed;

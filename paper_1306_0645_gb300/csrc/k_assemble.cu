@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(256) k_assemble_fix(Dims d, PhysDev p, const d
 }
 
 // Right-hand side and inverse diagonal.  In mixed mode the FP32 diagonal
-// comes from the FP32 weights, so no FP64 division is needed.
+// comes from the FP32 weights, so no FP64 division is needed.  BE: theta = 1
+// (no rescaling of the flux).
+template <bool BE>
 __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p, const double* __restrict__ E,
                                                              const double* __restrict__ nHI,
                                                              const double* __restrict__ eta, Op<double> op,
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
             }
         }
         // the right-hand side takes the full weights, the operator theta times them
-        flux *= p.inv_theta;
+        if (!BE) flux *= p.inv_theta;
         const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
         const double bc = fma(p.dt, eta[c], -sink) + flux;
         b[c] = bc;
@@ -349,7 +351,10 @@ void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
                          Bnd bnd, const RedArgs& ra, cudaStream_t s) {
     ColShape sh = col_shape(d);
-    k_assemble_rhs<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+    if (p.theta == 1.0)
+        k_assemble_rhs<true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+    else
+        k_assemble_rhs<false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
 }
 
 // Photons through the Dirichlet faces of side sd (sum, and sum of absolute

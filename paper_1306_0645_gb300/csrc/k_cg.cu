@@ -161,34 +161,38 @@ __global__ void k_ir_update(long long n, double* __restrict__ x64, const float* 
     }
 }
 
-// E_out = max(E + dE, 0); photon balance sums of the unfloored update
-// (energy density units; the host scales by V / h nu), the energy the
+// E_out = max(E + dE, 0) and the sums of the photon balance of the
+// unfloored update (energy density units; the host applies dt, dt c sigma,
+// dt adot/a and V / h nu): sum dE, sum eta, sum n_HI E^theta, sum E^theta
+// with E^theta = E^n + theta dE (E^{n+1} for backward Euler), the energy the
 // floor adds, and sum dE^2, sum E_out^2 for the relative change of the step.
-// BE: theta = 1, losses at E^{n+1} itself.
+// Seven FP64 operations per cell (the FP64 pipe bounds this kernel); the
+// sign test and the floor run on the integer pipe.  BE: theta = 1.
 template <bool BE>
 __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p, const double* __restrict__ E,
                                                           const double* __restrict__ dE,
                                                           const double* __restrict__ nHI,
                                                           const double* __restrict__ eta, double* E_out,
                                                           RedArgs ra) {
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     GRID_LOOP(c, n) {
         const double d = dE[c];
-        const double En = E[c] + d;
-        // losses at theta E^{n+1} + (1 - theta) E^n = E^n + theta dE
-        const double sink = fma(p.dtcs, nHI[c], p.dta) * (BE ? En : fma(p.theta, d, E[c]));
-        const double emit = p.dt * eta[c];
-        acc[0] += d - (emit - sink);
-        acc[1] += emit;
-        acc[2] += sink;
-        if (En < 0.0) acc[3] -= En;
-        const double Eo = En < 0.0 ? 0.0 : En;
+        const double Ec = E[c];
+        const double En = Ec + d;
+        const double Et = BE ? En : fma(p.theta, d, Ec);
+        acc[0] += d;
+        acc[1] += eta[c];
+        acc[2] = fma(nHI[c], Et, acc[2]);
+        acc[6] += Et;
+        const bool neg = __double_as_longlong(En) < 0;   // sign bit (also -0)
+        if (neg) acc[3] -= En;
+        const double Eo = neg ? 0.0 : En;
         acc[4] = fma(d, d, acc[4]);
         acc[5] = fma(Eo, Eo, acc[5]);
         E_out[c] = Eo;
     }
-    const bool mx[6] = {false, false, false, false, false, false};
-    grid_reduce<6>(acc, mx, ra);
+    const bool mx[7] = {false, false, false, false, false, false, false};
+    grid_reduce<7>(acc, mx, ra);
 }
 
 // ---------------------------------------------------------------- launchers

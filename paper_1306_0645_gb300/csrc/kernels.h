@@ -137,9 +137,10 @@ void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, con
 // x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32)
 void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
                       cudaStream_t s);
-// E_out = max(E + dE, 0); photon balance sums into S_BAL, S_EMIT, S_ABSORB,
-// the floor's energy into S_FLOOR, sum dE^2 into S_DE2, sum E_out^2 into
-// S_EN2 (reduction R_STORE6_FIN).
+// E_out = max(E + dE, 0); sums for the photon balance into S_BAL (dE),
+// S_EMIT (eta), S_ABSORB (n_HI E^theta), S_ESUM (E^theta), the floor's
+// energy into S_FLOOR, sum dE^2 into S_DE2, sum E_out^2 into S_EN2
+// (reduction R_STORE7_FIN).
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,
                      cudaStream_t s);
