@@ -135,6 +135,12 @@ typedef struct {
                                   and face weights use a * dx etc.  E and eta
                                   are per comoving volume (photon counts use
                                   the comoving cell volume), kappa proper. */
+    int tail_cells;            /* red/black Gauss-Seidel: the levels from the
+                                  first one with at most tail_cells cells
+                                  down to the coarsest run as one persistent
+                                  thread-block-cluster kernel per V-cycle
+                                  (default 32768; 0 = one launch per sweep);
+                                  same arithmetic as the per-level kernels */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -164,7 +170,7 @@ typedef struct fld_ctx fld_ctx;
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
  * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
- * graphs -1, fused_post 0, theta 1, scale_factor 1.
+ * graphs -1, fused_post 0, theta 1, scale_factor 1, tail_cells 32768.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 

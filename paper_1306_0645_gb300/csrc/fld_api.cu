@@ -59,13 +59,13 @@ enum KClass {
     K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_TO_F32, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
-    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_NUM
+    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
     "assemble_faces", "assemble_rhs", "coarsen", "invd", "to_f32", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
-    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth"};
+    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail"};
 
 struct KStat {
     long long launches, timed;
@@ -159,6 +159,7 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
         return set_err(FLD_EINVAL, "inner_rtol must lie in (0, 1)");
     if (p->coarse_cap < 1 || p->coarse_cap > COARSE_CAP_MAX)
         return set_err(FLD_EINVAL, "coarse_cap must lie in [1, %d]", COARSE_CAP_MAX);
+    if (p->tail_cells < 0) return set_err(FLD_EINVAL, "tail_cells must be >= 0");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
@@ -283,6 +284,7 @@ struct fld_ctx {
     std::vector<std::pair<int, double>> glaunch[2][2];
     std::vector<std::pair<int, double>>* grec;   // launch list being captured
     double* h_one;   // pinned 1.0, to raise S_FIRST
+    int tail_from;   // first level of the persistent coarse tail (-1: none)
 };
 
 namespace {
@@ -422,6 +424,29 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     if (l == c->nl - 1) {
         KScope k(c, kc(K_COARSE_APPLY), n * n * 8.0 + 2.0 * n * ts);
         launch_coarse_apply<T>((int)L.d.n, c->ainv, r, z, s);
+        return;
+    }
+    if (l == c->tail_from) {
+        // this level and all coarser ones in one cluster launch
+        TailArgs<T> ta{};
+        ta.nlev = c->nl - l;
+        ta.pre = c->p.pre;
+        ta.post = c->p.post;
+        ta.ainv = c->ainv;
+        double bytes = 0.0;
+        for (int q = 0; q < ta.nlev; q++) {
+            Level& Q = c->L[l + q];
+            TailLevel<T>& t = ta.L[q];
+            t.d = Q.d;
+            t.A = op_of<T>(Q);
+            t.r = q == 0 ? const_cast<T*>(r) : (T*)Q.r;
+            t.z = q == 0 ? z : (T*)Q.z;
+            t.t = (T*)Q.t;
+            // smoothing, residual, transfers: about 30 words per cell
+            bytes += 30.0 * (double)Q.d.n * ts;
+        }
+        KScope k(c, K_VTAIL, bytes);
+        launch_vtail<T>(ta, s);
         return;
     }
     Op<T> A = op_of<T>(L);
@@ -1298,6 +1323,7 @@ fld_status fld_params_default(fld_params* p) {
     p->fused_post = 0;
     p->theta = 1.0;
     p->scale_factor = 1.0;
+    p->tail_cells = 32768;
     return FLD_OK;
 }
 
@@ -1344,6 +1370,16 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     st = alloc_ctx(c);
     if (st) { free_ctx(c); return st; }
     for (int l = 0; l < c->nl; l++) c->L[l].bnd.mask = c->L[l].bnd.w ? dirichlet_mask(g) : 0;
+    // persistent coarse tail: from the first level with at most tail_cells
+    // cells (red/black Gauss-Seidel only), if at least one level lies above
+    // the coarsest one and a cluster of the tail kernel fits on the device
+    c->tail_from = -1;
+    if (p->tail_cells > 0 && p->smoother == FLD_SMOOTH_RBGS && c->nl >= 2) {
+        int l0 = 0;
+        while (l0 < c->nl - 1 && c->L[l0].d.n > p->tail_cells) l0++;
+        const bool ok = c->mixed ? vtail_supported<float>() : vtail_supported<double>();
+        if (l0 < c->nl - 1 && c->nl - l0 <= TAIL_MAX_LEVELS && ok) c->tail_from = l0;
+    }
     {
         long long blocks = 0;
         int cap = 0;

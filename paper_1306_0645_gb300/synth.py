@@ -104,6 +104,7 @@ class Params:
     fused_post: int = 0
     theta: float = 1.0
     scale_factor: float = 1.0
+    tail_cells: int = 32768
 
 
 @dataclasses.dataclass

@@ -403,3 +403,58 @@ def test_autotune_cache_roundtrip_and_parity(fld, oracle, tmp_path):
     Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200}, case.E, case.nHI, case.eta)
     E = res[0][1]
     assert np.linalg.norm(E - Eref) / np.linalg.norm(Eref) < 1e-6
+
+
+TAIL_CASES = [
+    ((32, 32, 32), (False,) * 3),
+    ((64, 48, 32), (True, False, True)),
+    ((24, 16, 40), (False, True, False)),
+    ((128, 64, 64), (False,) * 3),
+]
+
+
+@pytest.mark.parametrize("n,per", TAIL_CASES)
+def test_persistent_tail_vcycle(fld, oracle, n, per):
+    # the coarse levels as one cluster kernel: the FP64 V-cycle matches the
+    # per-level kernels and the oracle to rounding (the FP32 tail is covered
+    # by the mixed steps below)
+    case = synth.random_case(n, seed=300 + sum(n), periodic=per)
+    x = np.random.default_rng(8).standard_normal(case.grid.shape)
+    out = {}
+    for tail in (32768, 0):
+        p = synth.Params(tail_cells=tail)
+        ctx = fld.fld_create(case.grid, p)
+        fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
+        z = torch.empty(case.grid.cells, dtype=torch.float64, device="cuda")
+        fld.fld_vcycle(ctx, dev(x), z)
+        out[tail] = host(z).reshape(x.shape)
+        ctx.close()
+    op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
+    zref = oracle.vcycle(case.grid, op, x)
+    errs = (rel_max(out[32768], zref), rel_max(out[0], zref), rel_max(out[32768], out[0]))
+    assert max(errs) < 1e-12, errs
+
+
+@pytest.mark.parametrize("n", [32, 64])
+@pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
+def test_persistent_tail_step(fld, oracle, prec, n):
+    # whole steps with and without the tail, and against the oracle (at 32^3
+    # the whole V-cycle is the tail)
+    case = synth.config3(n, sources=64)
+    case.params.precision = prec
+    Es = {}
+    for tail in (32768, 0):
+        case.params.tail_cells = tail
+        ctx = fld.fld_create(case.grid, case.params)
+        E = dev(case.E)
+        info = fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
+        ctx.close()
+        assert info["rel_res"] <= 1e-8
+        Es[tail] = host(E).reshape(case.grid.shape)
+    Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200}, case.E, case.nHI, case.eta)
+    for E in Es.values():
+        el2 = np.linalg.norm(E - Eref) / np.linalg.norm(Eref)
+        einf = np.abs(E - Eref).max() / np.abs(Eref).max()
+        assert el2 < 1e-6 and einf < 1e-6, (el2, einf)
+    if prec == synth.PREC_FP64:
+        assert rel_max(Es[32768] - case.E, Es[0] - case.E) < 1e-10
