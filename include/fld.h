@@ -139,7 +139,8 @@ typedef struct {
                                   first one with at most tail_cells cells
                                   down to the coarsest run as one persistent
                                   thread-block-cluster kernel per V-cycle
-                                  (default 32768; 0 = one launch per sweep);
+                                  (default 32768, at most 2^24; 0 = one
+                                  launch per sweep);
                                   same arithmetic as the per-level kernels */
 } fld_params;
 

@@ -159,7 +159,8 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
         return set_err(FLD_EINVAL, "inner_rtol must lie in (0, 1)");
     if (p->coarse_cap < 1 || p->coarse_cap > COARSE_CAP_MAX)
         return set_err(FLD_EINVAL, "coarse_cap must lie in [1, %d]", COARSE_CAP_MAX);
-    if (p->tail_cells < 0) return set_err(FLD_EINVAL, "tail_cells must be >= 0");
+    if (p->tail_cells < 0 || p->tail_cells > (1 << 24))
+        return set_err(FLD_EINVAL, "tail_cells must lie in [0, 2^24]");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
@@ -285,6 +286,7 @@ struct fld_ctx {
     std::vector<std::pair<int, double>>* grec;   // launch list being captured
     double* h_one;   // pinned 1.0, to raise S_FIRST
     int tail_from;   // first level of the persistent coarse tail (-1: none)
+    int tail_cluster;   // CTAs of the tail's cluster
 };
 
 namespace {
@@ -446,7 +448,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
             bytes += 30.0 * (double)Q.d.n * ts;
         }
         KScope k(c, K_VTAIL, bytes);
-        launch_vtail<T>(ta, s);
+        launch_vtail<T>(ta, c->tail_cluster, s);
         return;
     }
     Op<T> A = op_of<T>(L);
@@ -1377,8 +1379,8 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
     if (p->tail_cells > 0 && p->smoother == FLD_SMOOTH_RBGS && c->nl >= 2) {
         int l0 = 0;
         while (l0 < c->nl - 1 && c->L[l0].d.n > p->tail_cells) l0++;
-        const bool ok = c->mixed ? vtail_supported<float>() : vtail_supported<double>();
-        if (l0 < c->nl - 1 && c->nl - l0 <= TAIL_MAX_LEVELS && ok) c->tail_from = l0;
+        c->tail_cluster = c->mixed ? vtail_cluster<float>() : vtail_cluster<double>();
+        if (l0 < c->nl - 1 && c->nl - l0 <= TAIL_MAX_LEVELS && c->tail_cluster > 0) c->tail_from = l0;
     }
     {
         long long blocks = 0;

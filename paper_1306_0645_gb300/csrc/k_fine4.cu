@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
 // ---------------------------------------------------------------- residual
 
 // res = r - A z
-__global__ void __launch_bounds__(256) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
+__global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
                                                    const float* __restrict__ z, float* __restrict__ res) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_residual4(Dims d, Op<float> A, const fl
 
 // First red/black Gauss-Seidel sweep from z = 0 (see k_smooth_zero): red
 // cells r / diag; black cells (r + sum_f w_f r_nbr / diag_nbr) / diag.
-__global__ void __launch_bounds__(256) k_smooth_zero4(Dims d, Op<float> A, const float* __restrict__ r,
+__global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, const float* __restrict__ r,
                                                       float* __restrict__ z) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) k_smooth_zero4(Dims d, Op<float> A, const
 // With dot (the last sweep of a V-cycle's post-smoothing on the finest
 // level) it also forms <r, z> of the finished z for CG.
 template <bool DOT>
-__global__ void __launch_bounds__(256) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
+__global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
                                                     float* z, int colour, RedArgs ra) {
     const Walk w = walk_of(d);
     DotAcc<float> da;

@@ -27,7 +27,7 @@ namespace fld {
 
 namespace {
 
-constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_THREADS = 1024;
 
 template <class T>
 __device__ __forceinline__ T ldw(const T* p, long long i) { return __ldcg(p + i); }
@@ -84,12 +84,16 @@ __device__ __forceinline__ T tail_nbr_sum_prod(const Dims& d, const Op<T>& A, lo
     return a;
 }
 
+// Cell coordinates by 32-bit unsigned division (tail levels hold fewer
+// than 2^24 cells; 64-bit division would cost far more than the sweep).
 __device__ __forceinline__ void tail_ijk(long long c, const Dims& d, int& i, int& j, int& k) {
-    const long long nxy = (long long)d.nx * d.ny;
-    k = (int)(c / nxy);
-    const long long rem = c - (long long)k * nxy;
-    j = (int)(rem / d.nx);
-    i = (int)(rem - (long long)j * d.nx);
+    const unsigned cu = (unsigned)c, nx = (unsigned)d.nx, nxy = (unsigned)d.nx * (unsigned)d.ny;
+    const unsigned kk = cu / nxy;
+    const unsigned rem = cu - kk * nxy;
+    const unsigned jj = rem / nx;
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(rem - jj * nx);
 }
 
 __device__ __forceinline__ int tail_fine_tap(int I, int t, int nf, int periodic) {
@@ -248,47 +252,55 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
 
 }  // namespace
 
-template <class T>
-cudaError_t launch_vtail(const TailArgs<T>& a, cudaStream_t s) {
+namespace {
+
+cudaLaunchConfig_t tail_config(int cluster, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(TAIL_CLUSTER, 1, 1);
+    cfg.gridDim = dim3(cluster, 1, 1);
     cfg.blockDim = dim3(TAIL_THREADS, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = TAIL_CLUSTER;
+    attr[0].val.clusterDim.x = cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_vtail(const TailArgs<T>& a, int cluster, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config(cluster, s, attr);
     return cudaLaunchKernelEx(&cfg, k_vtail<T>, a);
 }
 
+// The largest cluster (16 CTAs, a non-portable size, else the portable 8)
+// of which at least one can be resident; 0 if none.
 template <class T>
-bool vtail_supported() {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(TAIL_CLUSTER, 1, 1);
-    cfg.blockDim = dim3(TAIL_THREADS, 1, 1);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = TAIL_CLUSTER;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, k_vtail<T>, &cfg);
-    if (e != cudaSuccess) {
+int vtail_cluster() {
+    if (cudaFuncSetAttribute(k_vtail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         cudaGetLastError();
-        return false;
+    for (int cluster : {16, 8}) {
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = tail_config(cluster, nullptr, attr);
+        int n = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_vtail<T>, &cfg);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (n > 0) return cluster;
     }
-    return clusters > 0;
+    return 0;
 }
 
-template cudaError_t launch_vtail<float>(const TailArgs<float>&, cudaStream_t);
-template cudaError_t launch_vtail<double>(const TailArgs<double>&, cudaStream_t);
-template bool vtail_supported<float>();
-template bool vtail_supported<double>();
+template cudaError_t launch_vtail<float>(const TailArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_vtail<double>(const TailArgs<double>&, int, cudaStream_t);
+template int vtail_cluster<float>();
+template int vtail_cluster<double>();
 
 }  // namespace fld

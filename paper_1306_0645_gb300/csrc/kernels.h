@@ -150,9 +150,8 @@ void launch_opacity_update(long long n, const double* E, const double* nH, const
 
 // ---- persistent coarse tail of the V-cycle (k_tail.cu): levels L[0] (the
 // first level at or below the size threshold) to L[nlev - 1] (the coarsest)
-// in one launch of one cluster of TAIL_CLUSTER CTAs.  L[0].r is the input,
+// in one launch of one cluster of `cluster` CTAs.  L[0].r is the input,
 // L[0].z the output; the other r, z, t are the levels' work vectors.
-constexpr int TAIL_CLUSTER = 8;
 constexpr int TAIL_MAX_LEVELS = 12;
 template <class T>
 struct TailLevel {
@@ -167,10 +166,11 @@ struct TailArgs {
     TailLevel<T> L[TAIL_MAX_LEVELS];
 };
 template <class T>
-cudaError_t launch_vtail(const TailArgs<T>& a, cudaStream_t s);
-// whether a cluster of the tail kernel can be resident on this device
+cudaError_t launch_vtail(const TailArgs<T>& a, int cluster, cudaStream_t s);
+// the cluster size to launch the tail with (16 or 8 CTAs), 0 if no cluster
+// of the tail kernel can be resident on this device
 template <class T>
-bool vtail_supported();
+int vtail_cluster();
 
 // Sets the calling thread's fld_last_error message (fld_api.cu).
 void record_error(const char* msg);
