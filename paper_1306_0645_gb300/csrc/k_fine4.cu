@@ -346,22 +346,20 @@ __global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, cons
 // One post-smoothing sweep, black then red (see k_rb_colour4), in a single
 // pass and out of place: zi holds the pre-smoothed z plus the coarse
 // correction, zo receives the smoothed z.  A block is 32 lanes (4 cells
-// each) by PBY + 2 rows; the first and last rows are halo rows that only
-// form black values.  A block walks its chunk of planes with a one-plane
-// lag: at plane p it forms the black values of plane p + 1 (all its rows,
-// from zi, which nothing writes) and then the red values of plane p (inner
-// rows), taking the black y-neighbours from shared memory and the black
-// z-neighbours from registers.  Reading only zi keeps blocks independent,
-// so the result equals the two separate colour sweeps.
+// each) by PBY + 2 rows.  Lanes 0 and 31 and the first and last rows are
+// halo threads that only form black values: every red cell of the inner
+// lanes and rows then finds its black neighbours in the block (x by warp
+// shuffle, y in shared memory, z in registers), and no cell is formed
+// twice by one thread.  A block walks its chunk of planes with a one-plane
+// lag: at plane p it forms the black values of plane p + 1 (from zi, which
+// nothing writes) and the red values of plane p.  The black values are
+// double-buffered in shared memory, so one barrier per plane suffices.
+// Reading only zi keeps blocks independent, so the result equals the two
+// separate colour sweeps.
 constexpr int PBY = 6;
+constexpr int PLANES_X = 30;   // inner lanes of a block row
 
 namespace {
-
-struct PostRow {
-    int j;              // row (wrapped on a periodic axis, clamped otherwise)
-    bool has_yp;        // upper y face exists
-    long long row_dn, row_up;   // offsets of the y-neighbour rows (0 if missing)
-};
 
 __device__ __forceinline__ int wrapc(int v, int n, int periodic) {
     if (v < 0) return periodic ? v + n : 0;
@@ -369,7 +367,7 @@ __device__ __forceinline__ int wrapc(int v, int n, int periodic) {
     return v;
 }
 
-// plane index and presence of the upper z face for plane q
+// plane index of plane q with the boundary rule of the z axis
 __device__ __forceinline__ int plane_of(int q, const Dims& d) { return wrapc(q, d.nz, d.pz); }
 
 }  // namespace
@@ -381,18 +379,19 @@ __global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, co
     __shared__ float4 sB[2][PBY + 2][32];
     const int nx4 = d.nx >> 2;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i4raw = blockIdx.x * blockDim.x + tx;
-    const int i4 = min(i4raw, nx4 - 1);
+    const int i4raw = (int)blockIdx.x * PLANES_X - 1 + tx;
+    const int i4 = wrapc(i4raw, nx4, d.px);
     const int i0 = 4 * i4;
     const int jraw = (int)blockIdx.y * PBY - 1 + ty;
     const int j = wrapc(jraw, d.ny, d.py);
-    const bool inner = ty >= 1 && ty <= PBY && jraw < d.ny && i4raw < nx4;
+    const bool inner = tx >= 1 && tx <= PLANES_X && ty >= 1 && ty <= PBY && i4raw < nx4 && jraw < d.ny;
     const long long nxy = (long long)d.nx * d.ny;
     const long long rowoff = (long long)j * d.nx;
     const int jd = wrapc(j - 1, d.ny, d.py), ju = wrapc(j + 1, d.ny, d.py);
     const bool has_yp = j < d.ny - 1 || d.py;
-    const bool load_l = tx == 0 || i0 == 0;
-    const bool load_r = tx == blockDim.x - 1 || i0 + 4 >= d.nx;
+    // the halo lanes take their outer x-neighbour from memory
+    const bool load_l = tx == 0;
+    const bool load_r = tx == 31;
     const bool has_xr = i0 + 4 < d.nx || d.px;
     const int xl = i0 > 0 ? i0 - 1 : (d.px ? d.nx - 1 : 0);
     const int xr = i0 + 4 < d.nx ? i0 + 4 : (d.px ? 0 : d.nx - 1);
@@ -454,71 +453,44 @@ __global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, co
         float4 zq3 = ld4(zi, (long long)plane_of(k0 + 1, d) * nxy + rowoff + i0);
         float4 Bc = black(k0, zq1, zq2, zq3);                       // B_{k0}
         sB[k0 & 1][ty][tx] = Bc;
+        __syncthreads();
         // now zq2 = z_{k0}, zq3 = z_{k0+1}
         for (int p = k0; p < k1; p++) {
             const int pu = plane_of(p + 1, d);
             const float4 zq4 = ld4(zi, (long long)plane_of(p + 2, d) * nxy + rowoff + i0);
             const float4 Bu = black(pu, zq2, zq3, zq4);             // B_{p+1}
+            // buffer (p+1) & 1 was last read in the previous plane, before
+            // the barrier that ended it
             sB[(p + 1) & 1][ty][tx] = Bu;
-            // everything the red values need except the shared black rows is
-            // fetched before the barrier, so the loads overlap the wait
+            // red values of plane p from the black ones (inner threads)
             Faces4 f;
             faces(p, f);
             const long long c = (long long)p * nxy + rowoff + i0;
             const float4 rc = ld4(r, c), iv = ld4(A.invd, c);
             const bool e0_red = ((j + p) & 1) == 0;
-            const float lsh = __shfl_up_sync(FULL, Bc.w, 1);
-            const float rsh = __shfl_down_sync(FULL, Bc.x, 1);
-            float L = lsh, R = rsh;
-            // a black x-neighbour outside the lanes of this block row is
-            // formed here from zi (only element 0's left and element 3's
-            // right neighbour can be; they are black when the element is red)
-            auto black_cell = [&](int x) {
-                const long long cc = (long long)p * nxy + rowoff + x;
-                const int xm = x > 0 ? x - 1 : (d.px ? d.nx - 1 : x);
-                const int xp = x < d.nx - 1 ? x + 1 : (d.px ? 0 : x);
-                const float wl = A.wx[cc];
-                const float wu = (x < d.nx - 1 || d.px) ? A.wx[(long long)p * nxy + rowoff + (x < d.nx - 1 ? x + 1 : 0)] : 0.0f;
-                const float wyl = A.wy[cc];
-                const float wyu = has_yp ? A.wy[(long long)p * nxy + (long long)ju * d.nx + x] : 0.0f;
-                const float wzl = A.wz[cc];
-                const bool has_zu = p < d.nz - 1 || d.pz;
-                const float wzu = has_zu ? A.wz[(long long)pu * nxy + rowoff + x] : 0.0f;
-                const float s = r[cc] + wl * zi[(long long)p * nxy + rowoff + xm] +
-                                wu * zi[(long long)p * nxy + rowoff + xp] +
-                                wyl * zi[(long long)p * nxy + (long long)jd * d.nx + x] +
-                                wyu * zi[(long long)p * nxy + (long long)ju * d.nx + x] +
-                                wzl * zi[(long long)plane_of(p - 1, d) * nxy + rowoff + x] +
-                                wzu * zi[(long long)pu * nxy + rowoff + x];
-                return A.invd[cc] * s;
-            };
-            if (load_l && e0_red) L = (i0 > 0 || d.px) ? black_cell(xl) : Bc.x;
-            if (load_r && !e0_red) R = has_xr ? black_cell(xr) : Bc.w;
-            __syncthreads();
-            // red values of plane p from the black ones
-            {
-                const float4 ym = sB[p & 1][ty > 0 ? ty - 1 : 0][tx];
-                const float4 yp = sB[p & 1][ty < PBY + 1 ? ty + 1 : PBY + 1][tx];
-                float4 o = Bc;
+            const float L = __shfl_up_sync(FULL, Bc.w, 1);
+            const float R = __shfl_down_sync(FULL, Bc.x, 1);
+            const float4 ym = sB[p & 1][ty > 0 ? ty - 1 : 0][tx];
+            const float4 yp = sB[p & 1][ty < PBY + 1 ? ty + 1 : PBY + 1][tx];
+            float4 o = Bc;
 #define V1(X, LX, RX)                                                                      \
-                (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * ym.X + f.yu.X * yp.X +   \
-                         f.zl.X * Bd.X + f.zu.X * Bu.X))
-                if (e0_red) {
-                    o.x = V1(x, L, Bc.y);
-                    o.z = V1(z, Bc.y, Bc.w);
-                } else {
-                    o.y = V1(y, Bc.x, Bc.z);
-                    o.w = V1(w, Bc.z, R);
-                }
+            (iv.X * (rc.X + f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * ym.X + f.yu.X * yp.X +   \
+                     f.zl.X * Bd.X + f.zu.X * Bu.X))
+            if (e0_red) {
+                o.x = V1(x, L, Bc.y);
+                o.z = V1(z, Bc.y, Bc.w);
+            } else {
+                o.y = V1(y, Bc.x, Bc.z);
+                o.w = V1(w, Bc.z, R);
+            }
 #undef V1
-                if (inner) {
-                    st4(zo, c, o);
-                    if (DOT) {
-                        da.add(rc.x, o.x);
-                        da.add(rc.y, o.y);
-                        da.add(rc.z, o.z);
-                        da.add(rc.w, o.w);
-                    }
+            if (inner) {
+                st4(zo, c, o);
+                if (DOT) {
+                    da.add(rc.x, o.x);
+                    da.add(rc.y, o.y);
+                    da.add(rc.z, o.z);
+                    da.add(rc.w, o.w);
                 }
             }
             __syncthreads();
@@ -743,27 +715,27 @@ static ColShape shape4(const Dims& d, const Tune& tn = Tune{}) {
     return s;
 }
 
-static ColShape shape_post4(const Dims& d) {
-    Dims h = d;
-    h.nx = d.nx / 4;
+// Blocks of 32 lanes (30 inner) by PBY + 2 rows (PBY inner); the z chunk
+// follows from the target number of blocks.
+static ColShape shape_post4(const Dims& d, int target = 152 * 8) {
+    const int nx4 = d.nx / 4;
     ColShape s;
-    const int bx = pow2ceil(h.nx) < 32 ? pow2ceil(h.nx) : 32;
-    const int gx = (h.nx + bx - 1) / bx, gy = (d.ny + PBY - 1) / PBY;
+    const int gx = (nx4 + PLANES_X - 1) / PLANES_X, gy = (d.ny + PBY - 1) / PBY;
     long long xy = (long long)gx * gy;
-    long long gz = (152LL * 8 + xy - 1) / xy;
+    long long gz = (target + xy - 1) / xy;
     if (gz > d.nz) gz = d.nz;
     if (xy * gz > RED_MAX_BLOCKS) gz = RED_MAX_BLOCKS / xy;
     if (gz < 1) gz = 1;
-    s.block = dim3(bx, PBY + 2, 1);
+    s.block = dim3(32, PBY + 2, 1);
     s.grid = dim3(gx, gy, (unsigned)gz);
     return s;
 }
 
+// the fused sweep needs full warps of lanes: at least 32 float4 columns
 bool post4_ok(const Dims& d) {
-    Dims h = d;
-    h.nx = d.nx / 4;
-    const int bx = pow2ceil(h.nx) < 32 ? pow2ceil(h.nx) : 32;
-    return fine4_ok(d) && (long long)((h.nx + bx - 1) / bx) * ((d.ny + PBY - 1) / PBY) <= RED_MAX_BLOCKS;
+    const int nx4 = d.nx / 4;
+    return fine4_ok(d) && nx4 >= 32 &&
+           (long long)((nx4 + PLANES_X - 1) / PLANES_X) * ((d.ny + PBY - 1) / PBY) <= RED_MAX_BLOCKS;
 }
 
 void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float* zi, float* zo,

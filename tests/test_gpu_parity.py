@@ -365,12 +365,15 @@ def test_advance_retries_on_failure(fld):
     ctx2.close()
 
 
-@pytest.mark.parametrize("make", [lambda: synth.config4(64, sources=512), lambda: synth.config2(64),
-                                  lambda: synth.random_case((96, 48, 40), seed=12, periodic=(True, False, True)),
-                                  lambda: synth.random_case((16, 24, 20), seed=13, periodic=(False, True, True))])
+@pytest.mark.parametrize("make", [lambda: synth.config4(128, sources=1024), lambda: synth.config2(128),
+                                  lambda: synth.random_case((128, 40, 24), seed=12, periodic=(True, False, True)),
+                                  lambda: synth.random_case((160, 32, 24), seed=13, periodic=(False, True, False)),
+                                  lambda: synth.random_case((96, 48, 40), seed=14, periodic=(True, False, True))])
 def test_fused_post_sweep_equals_colour_sweeps(fld, make):
     # the fused black+red post-sweep does the arithmetic of the two colour
-    # sweeps, so the whole mixed step is bit-identical
+    # sweeps, so the whole mixed step is bit-identical (rows of 128 cells
+    # and more take the fused kernel: periodic and reflecting axes, a
+    # partial last block of lanes, rows that are not a multiple of PBY)
     case = make()
     case.params.precision = synth.PREC_MIXED
     out = []
