@@ -248,8 +248,9 @@ __global__ void __launch_bounds__(256) k_assemble_fix(Dims d, PhysDev p, const d
 
 // Right-hand side and inverse diagonal.  In mixed mode the FP32 diagonal
 // comes from the FP32 weights, so no FP64 division is needed.  BE: theta = 1
-// (no rescaling of the flux).
-template <bool BE>
+// (no rescaling of the flux); DIR: the grid has Dirichlet faces (the
+// variant without them carries none of their code or registers).
+template <bool BE, bool DIR>
 __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p, const double* __restrict__ E,
                                                              const double* __restrict__ nHI,
                                                              const double* __restrict__ eta, Op<double> op,
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
         flux = fma(-wsum, Ec, swe);
         double m = op.m[c];
         float m32 = op32.invd ? op32.m[c] : 0.0f;
-        if (p.dmask) {
+        if (DIR) {
             // Dirichlet faces of the box touching this cell
             const int ijk[3] = {i, j, k};
             const int nn[3] = {d.nx, d.ny, d.nz};
@@ -351,10 +352,15 @@ void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
                          Bnd bnd, const RedArgs& ra, cudaStream_t s) {
     ColShape sh = col_shape(d);
-    if (p.theta == 1.0)
-        k_assemble_rhs<true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+    const bool be = p.theta == 1.0, dir = p.dmask != 0;
+    if (be && !dir)
+        k_assemble_rhs<true, false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+    else if (be)
+        k_assemble_rhs<true, true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+    else if (!dir)
+        k_assemble_rhs<false, false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
     else
-        k_assemble_rhs<false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+        k_assemble_rhs<false, true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
 }
 
 // Photons through the Dirichlet faces of side sd (sum, and sum of absolute
