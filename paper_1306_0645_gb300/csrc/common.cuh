@@ -41,6 +41,9 @@ enum Slot {
     S_OUTABS0,    // the same summed in absolute value per face, side 0..5
     S_OUTABS5 = S_OUTABS0 + 5,
     S_ESUM,       // sum of the loss-weighted energies E^n + theta dE (finalise)
+    S_THRESH,     // device-side CG loop: stop when ||r||^2 <= this,
+    S_MAXIT,      //   or after this many iterations;
+    S_KITER,      //   iterations done
     NUM_SLOTS = 40
 };
 

@@ -284,9 +284,14 @@ struct fld_ctx {
     } run;
     std::vector<std::pair<int, double>> glaunch[2][2];
     std::vector<std::pair<int, double>>* grec;   // launch list being captured
-    double* h_one;   // pinned 1.0, to raise S_FIRST
+    double* h_one;   // pinned: [0] = 1.0 to raise S_FIRST, [1..3] loop slots
     int tail_from;   // first level of the persistent coarse tail (-1: none)
     int tail_cluster;   // CTAs of the tail's cluster
+    // device-side CG loop per solver precision: a while-node graph whose
+    // body is one iteration, the p copy and the convergence test
+    cudaGraph_t loop_graph[2];
+    cudaGraphExec_t loop_exec[2];
+    std::vector<std::pair<int, double>> loop_launch[2];
 };
 
 namespace {
@@ -519,7 +524,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
 // V-cycle, <r,z>, p and q = A p, the x and r updates, and the scalars to the
 // pinned host mirror.
 template <class T>
-void pcg_iteration(fld_ctx* c, int cur) {
+void pcg_iteration(fld_ctx* c, int cur, bool mirror = true) {
     T* r = (T*)c->cg[0];
     T* z = (T*)c->cg[1];
     T* p[2] = {(T*)c->cg[2], (T*)c->cg[3]};
@@ -559,18 +564,74 @@ void pcg_iteration(fld_ctx* c, int cur) {
             launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
         }
     }
-    cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    if (mirror) cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
 }
 
 void drop_graphs(fld_ctx* c) {
-    for (int a = 0; a < 2; a++)
+    for (int a = 0; a < 2; a++) {
         for (int b = 0; b < 2; b++) {
             if (c->gexec[a][b]) cudaGraphExecDestroy(c->gexec[a][b]);
             if (c->graph[a][b]) cudaGraphDestroy(c->graph[a][b]);
             c->gexec[a][b] = nullptr;
             c->graph[a][b] = nullptr;
         }
+        if (c->loop_exec[a]) cudaGraphExecDestroy(c->loop_exec[a]);
+        if (c->loop_graph[a]) cudaGraphDestroy(c->loop_graph[a]);
+        c->loop_exec[a] = nullptr;
+        c->loop_graph[a] = nullptr;
+    }
     c->graph_gen++;
+}
+
+// The device-side CG loop of precision T (built on first use), or null when
+// graphs are off or unavailable.  Its body, captured into the while node,
+// is one iteration at p parity 0, the copy of the new p into the old one,
+// and the convergence test that sets the node's condition; one launch runs
+// the whole solve, and the host synchronises once instead of per iteration.
+template <class T>
+cudaGraphExec_t loop_graph(fld_ctx* c) {
+    const int prec = std::is_same<T, float>::value ? 1 : 0;
+    if (!(c->use_graphs && !c->graphs_broken && c->tmask == 0)) return nullptr;
+    cudaGraphExec_t& ge = c->loop_exec[prec];
+    if (ge) return ge;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraph_t body = nullptr;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+        if (ok) body = np.conditional.phGraph_out[0];
+    }
+    if (ok) ok = cudaStreamBeginCaptureToGraph(c->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+    if (ok) {
+        c->loop_launch[prec].clear();
+        c->grec = &c->loop_launch[prec];
+        c->capturing = true;
+        pcg_iteration<T>(c, 0, false);
+        cudaMemcpyAsync(c->cg[2], c->cg[3], c->L[0].d.n * sizeof(T), cudaMemcpyDeviceToDevice, c->s);
+        launch_cg_check(h, c->sc, c->s);
+        c->capturing = false;
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(c->s, &out) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    if (!ok) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        ge = nullptr;
+        c->graphs_broken = true;
+        return nullptr;
+    }
+    c->loop_graph[prec] = g;
+    return ge;
 }
 
 // The captured and instantiated iteration of precision T and parity cur
@@ -669,6 +730,33 @@ template <class T>
 fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
     fld_status st = pcg_begin<T>(c, r0sq, rtol, max_iter);
     if (st) return st;
+    cudaGraphExec_t le = c->run.done ? nullptr : loop_graph<T>(c);
+    if (le) {
+        // the whole loop on the device: threshold, iteration cap and counter
+        // to their slots, one graph launch, one synchronisation
+        const int prec = std::is_same<T, float>::value ? 1 : 0;
+        c->h_one[1] = c->run.thresh;
+        c->h_one[2] = (double)max_iter;
+        c->h_one[3] = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(c->sc + S_THRESH, c->h_one + 1, 3 * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        CUDA_TRY(cudaGraphLaunch(le, c->s));
+        CUDA_TRY(cudaGetLastError());
+        if ((st = read_scalars(c))) return st;
+        const int k = (int)c->h_sc[S_KITER];
+        for (int q = 0; q < k; q++)
+            for (auto& e : c->loop_launch[prec]) {
+                c->kstat[e.first].launches++;
+                c->kstat[e.first].bytes += e.second;
+            }
+        c->run.k = k;
+        c->run.done = true;
+        if (c->h_sc[S_NONFINITE] != 0.0)
+            return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
+        c->run.conv = c->h_sc[S_RR] <= c->run.thresh;
+        *iters = k;
+        *converged = c->run.conv;
+        return FLD_OK;
+    }
     while (!c->run.done) {
         if ((st = pcg_enqueue<T>(c))) return st;
         CUDA_TRY(cudaStreamSynchronize(c->s));
@@ -1396,7 +1484,7 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
         return set_err(FLD_ENOMEM, "pinned scalar buffer or event creation failed");
     }
     memset(c->h_sc, 0, NUM_SLOTS * sizeof(double));
-    if (cudaMallocHost(&c->h_one, sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost(&c->h_one, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         return set_err(FLD_ENOMEM, "pinned allocation failed");

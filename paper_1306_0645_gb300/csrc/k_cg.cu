@@ -195,7 +195,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p
     grid_reduce<7>(acc, mx, ra);
 }
 
+// Convergence test of a CG loop run on the device as the body of a
+// conditional (while) graph node: count the iteration and continue while
+// ||r||^2 > threshold, fewer than the allowed iterations are done and no
+// reduction produced a non-finite value.
+__global__ void k_cg_check(cudaGraphConditionalHandle h, double* sc) {
+    const double k = sc[S_KITER] + 1.0;
+    sc[S_KITER] = k;
+    const bool cont = !(sc[S_RR] <= sc[S_THRESH]) && k < sc[S_MAXIT] && sc[S_NONFINITE] == 0.0;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- launchers
+
+void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s) {
+    k_cg_check<<<1, 1, 0, s>>>(h, sc);
+}
+
 
 template <class T>
 void launch_dot(long long n, const T* a, const T* b, const RedArgs& ra, cudaStream_t s) {

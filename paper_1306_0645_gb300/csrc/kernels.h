@@ -127,6 +127,10 @@ void launch_cg_update(long long n, T* x, T* r, const T* p, const T* q, const Red
                       cudaStream_t s);
 template <class T>
 void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s);
+// Device-side CG convergence test: sc[S_KITER] += 1 and the conditional h
+// set to continue while sc[S_RR] > sc[S_THRESH], S_KITER < S_MAXIT and no
+// non-finite reduction (one thread).
+void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s);
 // r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.  diag (may
 // be null) is the stored FP64 diagonal.
 void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
