@@ -943,7 +943,7 @@ fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, cons
     Level& Lc = c->L[c->nl - 1];
     { const double nc = (double)Lc.d.n;
       KScope k(c, K_COARSE_SETUP, 16.0 * nc * nc);
-      launch_coarse_setup(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, s); }
+      launch_coarse_setup(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, c->mixed, s); }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, s));
     return FLD_OK;

@@ -344,6 +344,60 @@ __global__ void k_chol_inverse(int n, double* M, double* Ainv, double* sc) {
     }
 }
 
+// Coarsest-grid setup for small grids, one CTA with the matrix in shared
+// memory: Cholesky M = L L^T in precision T (the trailing update spread over
+// all threads), X = L^-1 by forward substitution (one column per thread),
+// and the inverse Ainv = X^T X, written as FP64 (exactly symmetric).  The
+// mixed-precision solver takes T = float: its whole V-cycle is FP32.  A
+// non-positive pivot sets sc[S_BAD] = 2.
+template <class T>
+__global__ void __launch_bounds__(1024) k_chol_inverse_smem(int n, const double* __restrict__ M,
+                                                            double* __restrict__ Ainv, double* sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* L = reinterpret_cast<T*>(smem_raw);   // n x n, row-major
+    T* X = L + (long long)n * n;             // n x n, row-major, lower triangle
+    __shared__ int fail;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) fail = 0;
+    for (int q = tid; q < n * n; q += nt) {
+        L[q] = (T)M[q];
+        X[q] = T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        if (tid == 0) {
+            const T piv = L[j * n + j];
+            if (!(piv > T(0))) { fail = 1; L[j * n + j] = T(1); }
+            else L[j * n + j] = sqrt(piv);
+        }
+        __syncthreads();
+        const T ljj = L[j * n + j];
+        for (int i = j + 1 + tid; i < n; i += nt) L[i * n + j] /= ljj;
+        __syncthreads();
+        // trailing update of the lower triangle: (i, k) with j < k <= i
+        const int m = n - j - 1;
+        for (int q = tid; q < m * m; q += nt) {
+            const int i = j + 1 + q / m, k = j + 1 + q % m;
+            if (k <= i) L[i * n + k] -= L[i * n + j] * L[k * n + j];
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < n; t += nt)
+        for (int i = t; i < n; i++) {
+            T v = (i == t) ? T(1) : T(0);
+            for (int k = t; k < i; k++) v -= L[i * n + k] * X[k * n + t];
+            X[i * n + t] = v / L[i * n + i];
+        }
+    __syncthreads();
+    for (int q = tid; q < n * n; q += nt) {
+        const int a = q / n, b = q - a * n;
+        T v = T(0);
+        for (int i = a > b ? a : b; i < n; i++) v += X[i * n + a] * X[i * n + b];
+        Ainv[q] = (double)v;
+    }
+    if (fail && tid == 0) sc[S_BAD] = 2.0;
+}
+
 template <class T>
 __global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* __restrict__ r,
                                T* __restrict__ z) {
@@ -407,9 +461,26 @@ void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaSt
     ColShape sh = col_shape(f);
     k_prolong_add<T><<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf);
 }
-void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc,
+// shared memory of the in-CTA setup for an n x n matrix in precision T
+// (factor and inverse), and whether it fits
+static size_t chol_smem_bytes(long long n, size_t ts) { return 2 * (size_t)n * (size_t)n * ts; }
+static const size_t CHOL_SMEM_MAX = 200 * 1024;
+
+void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc, bool fp32,
                          cudaStream_t s) {
     k_dense_build<<<1, TPB, 0, s>>>(d, A, dense);
+    const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+    const size_t bytes = chol_smem_bytes(d.n, ts);
+    if (bytes <= CHOL_SMEM_MAX) {
+        if (fp32) {
+            cudaFuncSetAttribute(k_chol_inverse_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            k_chol_inverse_smem<float><<<1, 1024, bytes, s>>>((int)d.n, dense, ainv, sc);
+        } else {
+            cudaFuncSetAttribute(k_chol_inverse_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            k_chol_inverse_smem<double><<<1, 1024, bytes, s>>>((int)d.n, dense, ainv, sc);
+        }
+        return;
+    }
     const int threads = d.n < 1024 ? (int)((d.n + 31) / 32 * 32) : 1024;
     k_chol_inverse<<<1, threads, 0, s>>>((int)d.n, dense, ainv, sc);
 }

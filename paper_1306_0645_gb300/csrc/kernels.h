@@ -110,8 +110,9 @@ template <class T>
 void launch_restrict(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s);
 template <class T>
 void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s);
-// Coarsest grid: dense matrix, Cholesky, explicit inverse (one CTA).
-void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc,
+// Coarsest grid: dense matrix, Cholesky, explicit inverse (one CTA; in
+// shared memory and in FP32 when fp32 and the matrix fits, else FP64).
+void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc, bool fp32,
                          cudaStream_t s);
 template <class T>
 void launch_coarse_apply(int n, const double* ainv, const T* r, T* z, cudaStream_t s);
