@@ -452,6 +452,15 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
             // smoothing, residual, transfers: about 30 words per cell
             bytes += 30.0 * (double)Q.d.n * ts;
         }
+        // the small levels in one CTA's shared memory, if their vectors fit
+        ta.small_from = ta.nlev;
+        for (int q = 0; q < ta.nlev; q++)
+            if (ta.L[q].d.n <= TAIL_SMALL_CELLS) {
+                size_t cells = 0;
+                for (int u = q; u < ta.nlev; u++) cells += (size_t)ta.L[u].d.n;
+                if (3 * cells * sizeof(T) <= TAIL_SMEM_MAX) ta.small_from = q;
+                break;
+            }
         KScope k(c, K_VTAIL, bytes);
         launch_vtail<T>(ta, c->tail_cluster, s);
         return;

@@ -158,6 +158,11 @@ void launch_opacity_update(long long n, const double* E, const double* nH, const
 // in one launch of one cluster of `cluster` CTAs.  L[0].r is the input,
 // L[0].z the output; the other r, z, t are the levels' work vectors.
 constexpr int TAIL_MAX_LEVELS = 12;
+// small levels of the tail run in one CTA with their vectors (r, z, t) in
+// shared memory: from the first level with at most this many cells, when
+// their vectors fit TAIL_SMEM_MAX bytes
+constexpr long long TAIL_SMALL_CELLS = 512;
+constexpr size_t TAIL_SMEM_MAX = 160 * 1024;
 template <class T>
 struct TailLevel {
     Dims d;
@@ -167,6 +172,7 @@ struct TailLevel {
 template <class T>
 struct TailArgs {
     int nlev, pre, post;
+    int small_from;   // first level run by one CTA in shared memory (nlev: none)
     const double* ainv;
     TailLevel<T> L[TAIL_MAX_LEVELS];
 };
