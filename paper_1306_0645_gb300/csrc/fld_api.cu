@@ -292,6 +292,10 @@ struct fld_ctx {
     cudaGraph_t loop_graph[2];
     cudaGraphExec_t loop_exec[2];
     std::vector<std::pair<int, double>> loop_launch[2];
+    // host-buffer steps: side streams that split the copies over several
+    // copy engines, forked from and joined to the context's stream
+    cudaStream_t cstream[4];
+    cudaEvent_t cfork, cjoin[4];
 };
 
 namespace {
@@ -832,6 +836,11 @@ void free_ctx(fld_ctx* c) {
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     drop_graphs(c);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int q = 0; q < 4; q++) {
+        if (c->cstream[q]) cudaStreamDestroy(c->cstream[q]);
+        if (c->cjoin[q]) cudaEventDestroy(c->cjoin[q]);
+    }
+    if (c->cfork) cudaEventDestroy(c->cfork);
     if (c->h_one) cudaFreeHost(c->h_one);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
@@ -1557,6 +1566,35 @@ fld_status fld_step(fld_ctx* c, double* E, const double* nHI, const double* eta,
     return step_impl(c, E, nHI, eta, info);
 }
 
+// Copies of host-buffer steps: each array in chunks spread over the side
+// streams (several copy engines share the host link), ordered after the
+// context stream's work so far and joined back into it.
+fld_status split_copies(fld_ctx* c, int narr, void* const* dst, const void* const* src, size_t bytes,
+                        cudaMemcpyKind kind) {
+    constexpr int NS = 4;
+    if (!c->cstream[0]) {
+        for (int q = 0; q < NS; q++) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream[q], cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->cjoin[q], cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaEventCreateWithFlags(&c->cfork, cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventRecord(c->cfork, c->s));
+    for (int q = 0; q < NS; q++) CUDA_TRY(cudaStreamWaitEvent(c->cstream[q], c->cfork, 0));
+    const size_t chunk = ((bytes + NS - 1) / NS + 255) / 256 * 256;
+    int k = 0;
+    for (int a = 0; a < narr; a++)
+        for (size_t off = 0; off < bytes; off += chunk, k++) {
+            const size_t len = bytes - off < chunk ? bytes - off : chunk;
+            CUDA_TRY(cudaMemcpyAsync((char*)dst[a] + off, (const char*)src[a] + off, len, kind, c->cstream[k % NS]));
+        }
+    for (int q = 0; q < NS; q++) {
+        CUDA_TRY(cudaEventRecord(c->cjoin[q], c->cstream[q]));
+        CUDA_TRY(cudaStreamWaitEvent(c->s, c->cjoin[q], 0));
+    }
+    return FLD_OK;
+}
+
 fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
     if (!c) return set_err(FLD_EINVAL, "null context");
     if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
@@ -1569,12 +1607,19 @@ fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double*
                 return set_err(FLD_ENOMEM, "staging allocation failed");
             }
         }
-    CUDA_TRY(cudaMemcpyAsync(c->stage[0], E, bytes, cudaMemcpyHostToDevice, c->s));
-    CUDA_TRY(cudaMemcpyAsync(c->stage[1], nHI, bytes, cudaMemcpyHostToDevice, c->s));
-    CUDA_TRY(cudaMemcpyAsync(c->stage[2], eta, bytes, cudaMemcpyHostToDevice, c->s));
+    {
+        void* dst[3] = {c->stage[0], c->stage[1], c->stage[2]};
+        const void* src[3] = {E, nHI, eta};
+        fld_status st = split_copies(c, 3, dst, src, bytes, cudaMemcpyHostToDevice);
+        if (st) return st;
+    }
     fld_status st = step_impl(c, c->stage[0], c->stage[1], c->stage[2], info);
     if (st) return st;
-    CUDA_TRY(cudaMemcpyAsync(E, c->stage[0], bytes, cudaMemcpyDeviceToHost, c->s));
+    {
+        void* dst[1] = {E};
+        const void* src[1] = {c->stage[0]};
+        if ((st = split_copies(c, 1, dst, src, bytes, cudaMemcpyDeviceToHost))) return st;
+    }
     CUDA_TRY(cudaStreamSynchronize(c->s));
     return FLD_OK;
 }

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
         if (k > 0) FACE(wz, wz, c, c - sz) else if (d.pz) FACE(wz, wz, c, c + (long long)(d.nz - 1) * sz)
         if (k < d.nz - 1) FACE(wz, wz, c + sz, c + sz) else if (d.pz) FACE(wz, wz, c - (long long)(d.nz - 1) * sz, c - (long long)(d.nz - 1) * sz)
 #undef FACE
-        flux = fma(-wsum, Ec, swe);
+        if (!(BE && !DIR)) flux = fma(-wsum, Ec, swe);
         double m = op.m[c];
         float m32 = op32.invd ? op32.m[c] : 0.0f;
         if (DIR) {
@@ -309,10 +309,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
                 }
             }
         }
-        // the right-hand side takes the full weights, the operator theta times them
-        if (!BE) flux *= p.inv_theta;
-        const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
-        const double bc = fma(p.dt, eta[c], -sink) + flux;
+        double bc;
+        if (BE && !DIR) {
+            // b = dt eta + sum_f w_f E_nbr - (W + dt (c kappa + adot/a)) E
+            const double sc = fma(p.dtcs, nHI[c], p.dta);
+            bc = fma(-(wsum + sc), Ec, fma(p.dt, eta[c], swe));
+        } else {
+            // the right-hand side takes the full weights, the operator theta times them
+            if (!BE) flux *= p.inv_theta;
+            const double sink = fma(p.dtcs, nHI[c], p.dta) * Ec;
+            bc = fma(p.dt, eta[c], -sink) + flux;
+        }
         b[c] = bc;
         acc[0] = fma(bc, bc, acc[0]);
         acc[1] = fmax(acc[1], fabs(bc));

@@ -105,14 +105,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual64(Dims d, Op<double> A
         const double xc = x[c];
         double Ax;
         if (diag) {
-            double s = 0.0;
+            // b + sum_f w_f x_nbr, then r = b - (diag x - sum) in one FMA
+            double s = b[c];
             if (i > 0) s = fma(A.wx[c], x[c - 1], s); else if (d.px) s = fma(A.wx[c], x[c + d.nx - 1], s);
             if (i < d.nx - 1) s = fma(A.wx[c + 1], x[c + 1], s); else if (d.px) s = fma(A.wx[c - (d.nx - 1)], x[c - (d.nx - 1)], s);
             if (j > 0) s = fma(A.wy[c], x[c - sy], s); else if (d.py) s = fma(A.wy[c], x[c + (long long)(d.ny - 1) * sy], s);
             if (j < d.ny - 1) s = fma(A.wy[c + sy], x[c + sy], s); else if (d.py) s = fma(A.wy[c - (long long)(d.ny - 1) * sy], x[c - (long long)(d.ny - 1) * sy], s);
             if (k > 0) s = fma(A.wz[c], x[c - sz], s); else if (d.pz) s = fma(A.wz[c], x[c + (long long)(d.nz - 1) * sz], s);
             if (k < d.nz - 1) s = fma(A.wz[c + sz], x[c + sz], s); else if (d.pz) s = fma(A.wz[c - (long long)(d.nz - 1) * sz], x[c - (long long)(d.nz - 1) * sz], s);
-            Ax = fma(diag[c], xc, -s);
+            Ax = 0.0;
+            const double rd = fma(-diag[c], xc, s);
+            if (r) r[c] = rd;
+            acc[0] = fma(rd, rd, acc[0]);
+            acc[1] = fmax(acc[1], fabs(rd));
+            continue;
         } else {
             Ax = A.m[c] * xc;
             if (i > 0) Ax += A.wx[c] * (xc - x[c - 1]); else if (d.px) Ax += A.wx[c] * (xc - x[c + d.nx - 1]);
