@@ -264,8 +264,10 @@ fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E,
 /* Apply the assembled operator: y = A x (device, FP64).  For tests. */
 fld_status fld_apply(fld_ctx* ctx, const double* x, double* y);
 
-/* One multigrid V-cycle with zero initial guess, z = B r, on the
- * assembled FP64 hierarchy (device, FP64).  For tests. */
+/* One multigrid V-cycle with zero initial guess, z = B r, on the assembled
+ * hierarchy in the context's solver precision (device, FP64 arguments; a
+ * mixed-precision context runs its FP32 cycle on r rounded to FP32 and uses
+ * its CG work vectors).  For tests. */
 fld_status fld_vcycle(fld_ctx* ctx, const double* r, double* z);
 
 /* Copy the assembled fine-level operator and right-hand side to caller

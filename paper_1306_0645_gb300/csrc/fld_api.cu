@@ -1718,8 +1718,18 @@ fld_status fld_apply(fld_ctx* c, const double* x, double* y) {
 fld_status fld_vcycle(fld_ctx* c, const double* r, double* z) {
     if (!c || !r || !z) return set_err(FLD_EINVAL, "null argument");
     if (!c->assembled) return set_err(FLD_EINVAL, "fld_vcycle before fld_assemble");
-    if (c->mixed) return set_err(FLD_EINVAL, "fld_vcycle needs an FP64 context");
-    vcycle<double>(c, 0, r, z);
+    if (c->mixed) {
+        // the FP32 cycle of the mixed solver on r rounded to FP32 (the CG
+        // work vectors r and z serve as its input and output)
+        const long long n = c->L[0].d.n;
+        float* r32 = (float*)c->cg[0];
+        float* z32 = (float*)c->cg[1];
+        launch_f64_to_f32(n, r, r32, c->s);
+        vcycle<float>(c, 0, r32, z32);
+        launch_f32_to_f64(n, z32, z, c->s);
+    } else {
+        vcycle<double>(c, 0, r, z);
+    }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(c->s));
     harvest(c);

@@ -201,6 +201,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(long long n, PhysDev p
     grid_reduce<7>(acc, mx, ra);
 }
 
+__global__ void k_f64_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    GRID_LOOP(c, n) b[c] = (float)a[c];
+}
+__global__ void k_f32_to_f64(long long n, const float* __restrict__ a, double* __restrict__ b) {
+    GRID_LOOP(c, n) b[c] = (double)a[c];
+}
+
 // Convergence test of a CG loop run on the device as the body of a
 // conditional (while) graph node: count the iteration and continue while
 // ||r||^2 > threshold, fewer than the allowed iterations are done and no
@@ -213,6 +220,13 @@ __global__ void k_cg_check(cudaGraphConditionalHandle h, double* sc) {
 }
 
 // ---------------------------------------------------------------- launchers
+
+void launch_f64_to_f32(long long n, const double* a, float* b, cudaStream_t s) {
+    k_f64_to_f32<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);
+}
+void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s) {
+    k_f32_to_f64<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);
+}
 
 void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s) {
     k_cg_check<<<1, 1, 0, s>>>(h, sc);

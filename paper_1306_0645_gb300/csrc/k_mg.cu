@@ -398,6 +398,64 @@ __global__ void __launch_bounds__(1024) k_chol_inverse_smem(int n, const double*
     if (fail && tid == 0) sc[S_BAD] = 2.0;
 }
 
+// Coarsest-grid inverse for n <= 128, one CTA of 32 x 32 threads with the
+// matrix in shared memory: in-place Gauss-Jordan elimination without
+// pivoting (stable for the symmetric positive definite operator).  Step k
+// replaces the matrix M by
+//   M'[k][k] = 1/p,  M'[k][j] = M[k][j]/p,  M'[i][k] = -M[i][k]/p,
+//   M'[i][j] = M[i][j] - M[i][k] M[k][j]/p      (p = M[k][k] > 0),
+// every entry at once (read phase, barrier, write phase); after n steps M
+// holds the inverse.  Each thread owns the entries (ty + 32 a, tx + 32 b).
+// The result is written as FP64.  A non-positive pivot sets sc[S_BAD] = 2.
+constexpr int GJ_MAX = 128;
+template <class T, int PT>   // PT = entries per thread and axis, n <= 32 PT
+__global__ void __launch_bounds__(1024) k_gj_inverse_smem(int n, const double* __restrict__ M,
+                                                          double* __restrict__ Ainv, double* sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A = reinterpret_cast<T*>(smem_raw);
+    __shared__ int fail;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x == 0) fail = 0;
+    for (int q = threadIdx.x; q < n * n; q += 1024) A[q] = (T)M[q];
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        T p = A[k * n + k];
+        if (!(p > T(0))) {
+            if (threadIdx.x == 0) fail = 1;
+            p = T(1);
+        }
+        const T ip = T(1) / p;
+        T nv[PT][PT];
+#pragma unroll
+        for (int a = 0; a < PT; a++) {
+            const int i = ty + 32 * a;
+#pragma unroll
+            for (int b = 0; b < PT; b++) {
+                const int j = tx + 32 * b;
+                if (i < n && j < n) {
+                    if (i == k && j == k) nv[a][b] = ip;
+                    else if (i == k) nv[a][b] = A[k * n + j] * ip;
+                    else if (j == k) nv[a][b] = -A[i * n + k] * ip;
+                    else nv[a][b] = A[i * n + j] - A[i * n + k] * (A[k * n + j] * ip);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < PT; a++) {
+            const int i = ty + 32 * a;
+#pragma unroll
+            for (int b = 0; b < PT; b++) {
+                const int j = tx + 32 * b;
+                if (i < n && j < n) A[i * n + j] = nv[a][b];
+            }
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < n * n; q += 1024) Ainv[q] = (double)A[q];
+    if (fail && threadIdx.x == 0) sc[S_BAD] = 2.0;
+}
+
 template <class T>
 __global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* __restrict__ r,
                                T* __restrict__ z) {
@@ -470,6 +528,24 @@ void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ain
                          cudaStream_t s) {
     k_dense_build<<<1, TPB, 0, s>>>(d, A, dense);
     const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+    if (d.n <= GJ_MAX) {
+        const size_t gb = (size_t)d.n * (size_t)d.n * ts;
+        const int n = (int)d.n;
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gb);
+            kern<<<1, 1024, gb, s>>>(n, dense, ainv, sc);
+        };
+        if (fp32) {
+            if (n <= 32) go(k_gj_inverse_smem<float, 1>);
+            else if (n <= 64) go(k_gj_inverse_smem<float, 2>);
+            else go(k_gj_inverse_smem<float, 4>);
+        } else {
+            if (n <= 32) go(k_gj_inverse_smem<double, 1>);
+            else if (n <= 64) go(k_gj_inverse_smem<double, 2>);
+            else go(k_gj_inverse_smem<double, 4>);
+        }
+        return;
+    }
     const size_t bytes = chol_smem_bytes(d.n, ts);
     if (bytes <= CHOL_SMEM_MAX) {
         if (fp32) {

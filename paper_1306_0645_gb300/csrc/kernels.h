@@ -128,6 +128,9 @@ void launch_cg_update(long long n, T* x, T* r, const T* p, const T* q, const Red
                       cudaStream_t s);
 template <class T>
 void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s);
+// element-wise precision conversions (test hooks)
+void launch_f64_to_f32(long long n, const double* a, float* b, cudaStream_t s);
+void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s);
 // Device-side CG convergence test: sc[S_KITER] += 1 and the conditional h
 // set to continue while sc[S_RR] > sc[S_THRESH], S_KITER < S_MAXIT and no
 // non-finite reduction (one thread).

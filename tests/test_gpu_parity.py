@@ -461,3 +461,31 @@ def test_persistent_tail_step(fld, oracle, prec, n):
         assert el2 < 1e-6 and einf < 1e-6, (el2, einf)
     if prec == synth.PREC_FP64:
         assert rel_max(Es[32768] - case.E, Es[0] - case.E) < 1e-10
+
+
+def test_results_do_not_depend_on_launch_shapes(fld):
+    # race check without a sanitizer: the FP32 sweeps must give the same
+    # values whatever the tile order of their launch shapes.  One V-cycle
+    # (no reductions) is bit-identical under two tuning tables far apart
+    # (128-thread blocks with the fewest blocks, 256-thread blocks with the
+    # most); whole steps agree to the rounding of the CG reductions, whose
+    # block order does follow the shape.
+    case = synth.config4(128, sources=1024)
+    case.params.precision = synth.PREC_MIXED
+    x = np.random.default_rng(9).standard_normal(case.grid.cells)
+    zs, steps = [], []
+    for threads, blocks in ((128, 152 * 4), (256, 152 * 64)):
+        ctx = fld.fld_create(case.grid, case.params)
+        fld.fld_set_tuning(ctx, [threads, blocks] * (fld.fld_tuning_size(ctx) // 2))
+        fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
+        z = torch.empty(case.grid.cells, dtype=torch.float64, device="cuda")
+        fld.fld_vcycle(ctx, dev(x), z)
+        zs.append(host(z))
+        E = dev(case.E)
+        info = fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
+        steps.append((host(E), info["iters"], info["outer_iters"]))
+        ctx.close()
+    assert np.array_equal(zs[0], zs[1])
+    assert steps[0][1:] == steps[1][1:]
+    e0 = case.E.ravel()
+    assert rel_max(steps[0][0].ravel() - e0, steps[1][0].ravel() - e0) < 1e-6
