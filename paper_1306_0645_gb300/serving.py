@@ -14,6 +14,10 @@ never fit is rejected.
 Every kernel launch shape depends only on the grid size and parameters and
 every reduction adds in a fixed order, so a request's result is the same,
 bit for bit, whether it runs alone or in the mix.
+
+A request can be cancelled (``Server.cancel``) until a worker takes it: it
+is then returned with status ``CANCELLED`` and never stepped.  A step in
+progress is not interrupted.
 """
 from __future__ import annotations
 
@@ -26,6 +30,8 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 
 from . import fld, synth
+
+CANCELLED = -1   # Result.status of a request cancelled before it was stepped
 
 
 @dataclasses.dataclass
@@ -73,6 +79,21 @@ class Server:
         self._bctx: List[Dict[int, List[fld.Context]]] = [dict() for _ in range(workers)]
         self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
         self._fp_cache: Dict[int, int] = {}
+        self._cancelled = set()
+        self._cancel_lock = threading.Lock()
+
+    def cancel(self, rid: int) -> None:
+        """Cancel request rid if no worker has taken it yet."""
+        with self._cancel_lock:
+            self._cancelled.add(rid)
+
+    def _take(self, r: synth.Request) -> bool:
+        """True if r may be stepped (it was not cancelled); marks it taken."""
+        with self._cancel_lock:
+            if r.rid in self._cancelled:
+                return False
+            self._cancelled.discard(r.rid)
+            return True
 
     # ---------------------------------------------------------- admission
     def footprint(self, n: int) -> int:
@@ -207,7 +228,10 @@ class Server:
                 item = q.get()
                 if item is None:
                     return
-                if self.batch == 1:
+                if not self._take(item):
+                    now = time.perf_counter() - t0
+                    res = [Result(item.rid, item.n, item.arrival, now, now, CANCELLED)]
+                elif self.batch == 1:
                     res = [self.step_one(w, item, t0)]
                 else:
                     group, stop = [item], False
@@ -221,6 +245,11 @@ class Server:
                             stop = True
                             break
                         fp = self.footprint(nxt.n)
+                        if not self._take(nxt):
+                            now = time.perf_counter() - t0
+                            with lock:
+                                results[nxt.rid] = Result(nxt.rid, nxt.n, nxt.arrival, now, now, CANCELLED)
+                            continue
                         if total + fp > self.budget:
                             q.put(nxt)       # waits for a later group
                             break
@@ -265,12 +294,13 @@ class Server:
 
 def summarize(results: Sequence[Result]) -> dict:
     ok = [r for r in results if r.status == fld.FLD_OK]
+    cancelled = sum(1 for r in results if r.status == CANCELLED)
     lat = np.array([r.latency_ms for r in ok]) if ok else np.zeros(1)
     wait = np.array([r.wait_ms for r in ok]) if ok else np.zeros(1)
     span = (max(r.finish for r in results) - min(r.arrival for r in results)) if results else 0.0
     cells = sum(r.n ** 3 for r in ok)
     return {"requests": len(results), "ok": len(ok),
-            "failed": len(results) - len(ok),
+            "failed": len(results) - len(ok) - cancelled, "cancelled": cancelled,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "wait_p50_ms": float(np.percentile(wait, 50)), "wait_p99_ms": float(np.percentile(wait, 99)),
             "solves_per_s": len(ok) / span if span > 0 else None,

@@ -146,3 +146,22 @@ def test_batched_serving_equals_alone(serving):
     for a, b in zip(ra, rb):
         assert a.status == 0 and b.status == 0
         assert np.array_equal(a.E, b.E)
+
+
+def test_cancellation_before_a_worker_takes_the_request(serving):
+    # requests cancelled before they are taken come back CANCELLED, never
+    # stepped; the others are served as usual, and the summary counts both
+    reqs = synth.request_stream(count=40, rate=200.0, seed=51, sizes=(16, 32))
+    srv = serving.Server(workers=2, keep_results=True)
+    drop = {r.rid for r in reqs[::3]}
+    for rid in drop:
+        srv.cancel(rid)
+    res = srv.run(reqs, realtime=True)
+    srv.close()
+    for r in res:
+        if r.rid in drop:
+            assert r.status == serving.CANCELLED and r.E is None and r.iters == 0
+        else:
+            assert r.status == 0 and r.E is not None
+    s = serving.summarize(res)
+    assert s["cancelled"] == len(drop) and s["ok"] == len(reqs) - len(drop) and s["failed"] == 0
