@@ -263,7 +263,7 @@ def main():
     ctx = fld.fld_create(case.grid, pm, stream)
     tuning = fld.autotune(ctx)
     kinds = ["smooth_zero", "rb_colour", "residual", "restrict", "prolong", "cg_p_matvec"]
-    tuned = {k: tuning[2 * q: 2 * q + 2] for q, k in enumerate(kinds)}
+    tuned = {k: tuning[3 * q: 3 * q + 3] for q, k in enumerate(kinds)}   # threads, blocks, prefetch
     E = E0.clone()
     for _ in range(args.warmup):
         fld.fld_step(ctx, E, nHI, eta)

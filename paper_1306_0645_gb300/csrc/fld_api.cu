@@ -1774,6 +1774,8 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
     CUDA_TRY(cudaEventCreate(&e1));
     const int threads_c[] = {128, 256};
     const int target_c[] = {152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
+    const int pf_c[] = {0, 1, 2};
+    constexpr int NCAND = 2 * 5 * 3;
     fld_status st = FLD_OK;
     for (int l = 0; l + 1 < c->nl && !st; l++) {
         Level& L = c->L[l];
@@ -1816,26 +1818,28 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 }
             };
             float best = 1e30f;
-            for (int th : threads_c)
-                for (int tg : target_c) {
-                    Tune tn;
-                    tn.threads = th;
-                    tn.target = tg;
-                    run(tn);
-                    cudaEventRecord(e0, s);
-                    for (int q = 0; q < reps; q++) run(tn);
-                    cudaEventRecord(e1, s);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        st = set_err(FLD_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                        break;
-                    }
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best) {
-                        best = ms;
-                        L.tune[k] = tn;
-                    }
+            const bool has_pf = k == TN_SMOOTH0 || k == TN_RB || k == TN_RES || k == TN_PMATVEC;
+            for (int q = 0; q < NCAND && !st; q++) {
+                Tune tn;
+                tn.threads = threads_c[q % 2];
+                tn.target = target_c[(q / 2) % 5];
+                tn.pf = pf_c[q / 10];
+                if (tn.pf && !has_pf) continue;
+                run(tn);
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < reps; rep++) run(tn);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = set_err(FLD_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                    break;
                 }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    L.tune[k] = tn;
+                }
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -1847,29 +1851,34 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
     return st;
 }
 
-int fld_tuning_size(fld_ctx* c) { return c ? 2 * NTUNE * c->nl : 0; }
+int fld_tuning_size(fld_ctx* c) { return c ? TUNE_FIELDS * NTUNE * c->nl : 0; }
 
 fld_status fld_get_tuning(fld_ctx* c, int* out, int n) {
-    if (!c || !out || n < 2 * NTUNE * c->nl) return set_err(FLD_EINVAL, "buffer too small");
+    if (!c || !out || n < TUNE_FIELDS * NTUNE * c->nl) return set_err(FLD_EINVAL, "buffer too small");
     for (int l = 0; l < c->nl; l++)
         for (int k = 0; k < NTUNE; k++) {
-            out[2 * (l * NTUNE + k)] = c->L[l].tune[k].threads;
-            out[2 * (l * NTUNE + k) + 1] = c->L[l].tune[k].target;
+            int* e = out + TUNE_FIELDS * (l * NTUNE + k);
+            e[0] = c->L[l].tune[k].threads;
+            e[1] = c->L[l].tune[k].target;
+            e[2] = c->L[l].tune[k].pf;
         }
     return FLD_OK;
 }
 
 fld_status fld_set_tuning(fld_ctx* c, const int* in, int n) {
-    if (!c || !in || n != 2 * NTUNE * c->nl) return set_err(FLD_EINVAL, "tuning table of the wrong size");
-    for (int q = 0; q < n; q += 2) {
-        const int th = in[q], tg = in[q + 1];
-        if (th < 32 || th > 256 || (th & (th - 1)) || tg < 1 || tg > RED_MAX_BLOCKS)
+    if (!c || !in || n != TUNE_FIELDS * NTUNE * c->nl)
+        return set_err(FLD_EINVAL, "tuning table of the wrong size");
+    for (int q = 0; q < n; q += TUNE_FIELDS) {
+        const int th = in[q], tg = in[q + 1], pf = in[q + 2];
+        if (th < 32 || th > 256 || (th & (th - 1)) || tg < 1 || tg > RED_MAX_BLOCKS || pf < 0 || pf > TUNE_PF_MAX)
             return set_err(FLD_EINVAL, "invalid launch shape in tuning table");
     }
     for (int l = 0; l < c->nl; l++)
         for (int k = 0; k < NTUNE; k++) {
-            c->L[l].tune[k].threads = in[2 * (l * NTUNE + k)];
-            c->L[l].tune[k].target = in[2 * (l * NTUNE + k) + 1];
+            const int* e = in + TUNE_FIELDS * (l * NTUNE + k);
+            c->L[l].tune[k].threads = e[0];
+            c->L[l].tune[k].target = e[1];
+            c->L[l].tune[k].pf = e[2];
         }
     drop_graphs(c);
     return FLD_OK;

@@ -22,6 +22,13 @@ __device__ __forceinline__ float4 ld4(const float* __restrict__ p, long long i) 
 __device__ __forceinline__ void st4(float* p, long long i, float4 v) {
     *reinterpret_cast<float4*>(p + i) = v;
 }
+// Prefetch of the 16 bytes at p + i into L2.  The sweeps issue it for the
+// plane pf ahead of the one they compute, so that plane's loads hit L2:
+// bytes are requested from HBM without holding registers or scoreboard
+// entries while the current plane waits on its own loads.
+__device__ __forceinline__ void pf2(const float* p, long long i) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p + i)));
+}
 
 // Geometry of one 4-cell vector on one plane.  Indices of missing
 // neighbours (zero-gradient boundary) point at the cell itself; the matching
@@ -127,7 +134,7 @@ __device__ __forceinline__ Faces4 faces_of(const Op<float>& A, const Geo& g, flo
 __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, const float* __restrict__ z,
                                                       const float* __restrict__ p_in,
                                                       float* __restrict__ p_out, float* __restrict__ q,
-                                                      RedArgs ra) {
+                                                      RedArgs ra, int pf) {
     const float beta = (float)ra.sc[S_BETA];
     const Walk w = walk_of(d);
     DotAcc<float> da;
@@ -144,6 +151,15 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
         float4 wzc = ld4(A.wz, g.c);
         for (int k = w.k0; k < w.k1; k++) {
             if (k > w.k0) g = geo_of(d, w, k);
+            if (pf > 0 && k + pf < w.k1) {
+                const long long o = g.c + (long long)pf * w.nxy;
+                pf2(z, o);
+                pf2(p_in, o);
+                pf2(A.m, o);
+                pf2(A.wx, o);
+                pf2(A.wy, o);
+                pf2(A.wz, o);
+            }
             const long long up = zup(d, k, w.nxy);
             const bool has_zu = k < d.nz - 1 || d.pz;
             const float4 pu = P(g.c + up);
@@ -189,7 +205,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
 
 // res = r - A z
 __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
-                                                   const float* __restrict__ z, float* __restrict__ res) {
+                                                   const float* __restrict__ z, float* __restrict__ res, int pf) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
     Geo g = geo_of(d, w, w.k0);
@@ -198,6 +214,15 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
     float4 wzc = ld4(A.wz, g.c);
     for (int k = w.k0; k < w.k1; k++) {
         if (k > w.k0) g = geo_of(d, w, k);
+        if (pf > 0 && k + pf < w.k1) {
+            const long long o = g.c + (long long)pf * w.nxy;
+            pf2(z, o);
+            pf2(r, o);
+            pf2(A.m, o);
+            pf2(A.wx, o);
+            pf2(A.wy, o);
+            pf2(A.wz, o);
+        }
         const bool has_zu = k < d.nz - 1 || d.pz;
         const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
         const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
@@ -229,7 +254,7 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
 // First red/black Gauss-Seidel sweep from z = 0 (see k_smooth_zero): red
 // cells r / diag; black cells (r + sum_f w_f r_nbr / diag_nbr) / diag.
 __global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, const float* __restrict__ r,
-                                                      float* __restrict__ z) {
+                                                      float* __restrict__ z, int pf) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
     auto U = [&](long long i) {
@@ -243,6 +268,14 @@ __global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, co
     float4 wzc = ld4(A.wz, g.c);
     for (int k = w.k0; k < w.k1; k++) {
         if (k > w.k0) g = geo_of(d, w, k);
+        if (pf > 0 && k + pf < w.k1) {
+            const long long o = g.c + (long long)pf * w.nxy;
+            pf2(r, o);
+            pf2(A.invd, o);
+            pf2(A.wx, o);
+            pf2(A.wy, o);
+            pf2(A.wz, o);
+        }
         const bool has_zu = k < d.nz - 1 || d.pz;
         const float4 uu = U(g.c + zup(d, k, w.nxy));
         const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
@@ -285,7 +318,7 @@ __global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, co
 // level) it also forms <r, z> of the finished z for CG.
 template <bool DOT>
 __global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
-                                                    float* z, int colour, RedArgs ra) {
+                                                    float* z, int colour, RedArgs ra, int pf) {
     const Walk w = walk_of(d);
     DotAcc<float> da;
     if (w.k0 < w.k1) {
@@ -295,6 +328,15 @@ __global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, cons
         float4 wzc = ld4(A.wz, g.c);
         for (int k = w.k0; k < w.k1; k++) {
             if (k > w.k0) g = geo_of(d, w, k);
+            if (pf > 0 && k + pf < w.k1) {
+                const long long o = g.c + (long long)pf * w.nxy;
+                pf2(z, o);
+                pf2(r, o);
+                pf2(A.invd, o);
+                pf2(A.wx, o);
+                pf2(A.wy, o);
+                pf2(A.wz, o);
+            }
             const bool has_zu = k < d.nz - 1 || d.pz;
             const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
             const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
@@ -757,12 +799,12 @@ bool fine4_ok(const Dims& d) { return d.nx % 4 == 0 && d.nx >= 16; }
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
                          float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn) {
     ColShape sh = shape4(d, tn);
-    k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra);
+    k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra, tn.pf);
 }
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
                       cudaStream_t s, const Tune& tn) {
     ColShape sh = shape4(d, tn);
-    k_residual4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res);
+    k_residual4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
 }
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
                       const Tune& tn) {
@@ -779,17 +821,17 @@ void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* z
 void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
                          const Tune& tn) {
     ColShape sh = shape4(d, tn);
-    k_smooth_zero4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z);
+    k_smooth_zero4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, tn.pf);
 }
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                        cudaStream_t s, const Tune& tn) {
     ColShape sh = shape4(d, tn);
-    k_rb_colour4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{});
+    k_rb_colour4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{}, tn.pf);
 }
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                            const RedArgs& ra, cudaStream_t s, const Tune& tn) {
     ColShape sh = shape4(d, tn);
-    k_rb_colour4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, ra);
+    k_rb_colour4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, ra, tn.pf);
 }
 
 }  // namespace fld

@@ -195,7 +195,10 @@ void record_error(const char* msg);
 struct Tune {
     int threads = 256;
     int target = 152 * 8;
+    int pf = 1;             // L2 prefetch distance in planes (0: none; FP32 sweeps)
 };
+constexpr int TUNE_FIELDS = 3;      // entries of one tuning-table record
+constexpr int TUNE_PF_MAX = 8;
 
 // ---- FP32 four-cells-per-thread sweeps (k_fine4.cu); need nx % 4 == 0
 bool fine4_ok(const Dims& d);

@@ -403,6 +403,17 @@ def test_autotune_cache_roundtrip_and_parity(fld, oracle, tmp_path):
         ctx.close()
     assert res[0][0] == res[1][0]
     assert np.array_equal(res[0][1], res[1][1])
+    # records are (threads, blocks, prefetch distance); a bad record is refused
+    ctx = fld.fld_create(case.grid, case.params)
+    n = fld.fld_tuning_size(ctx)
+    assert n == len(res[0][0]) and n % 3 == 0
+    for bad in ((96, 608, 1), (256, 0, 1), (256, 608, -1), (256, 608, 9)):
+        with pytest.raises(fld.FldError):
+            fld.fld_set_tuning(ctx, list(bad) * (n // 3))
+    with pytest.raises(fld.FldError):
+        fld.fld_set_tuning(ctx, [256, 608] * (n // 3))
+    assert fld.fld_get_tuning(ctx) == [256, 152 * 8, 1] * (n // 3)
+    ctx.close()
     Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200}, case.E, case.nHI, case.eta)
     E = res[0][1]
     assert np.linalg.norm(E - Eref) / np.linalg.norm(Eref) < 1e-6
@@ -467,16 +478,17 @@ def test_results_do_not_depend_on_launch_shapes(fld):
     # race check without a sanitizer: the FP32 sweeps must give the same
     # values whatever the tile order of their launch shapes.  One V-cycle
     # (no reductions) is bit-identical under two tuning tables far apart
-    # (128-thread blocks with the fewest blocks, 256-thread blocks with the
-    # most); whole steps agree to the rounding of the CG reductions, whose
-    # block order does follow the shape.
+    # (128-thread blocks with the fewest blocks and no prefetch, 256-thread
+    # blocks with the most and the longest prefetch distance); whole steps
+    # agree to the rounding of the CG reductions, whose block order does
+    # follow the shape.
     case = synth.config4(128, sources=1024)
     case.params.precision = synth.PREC_MIXED
     x = np.random.default_rng(9).standard_normal(case.grid.cells)
     zs, steps = [], []
-    for threads, blocks in ((128, 152 * 4), (256, 152 * 64)):
+    for threads, blocks, pf in ((128, 152 * 4, 0), (256, 152 * 64, 8)):
         ctx = fld.fld_create(case.grid, case.params)
-        fld.fld_set_tuning(ctx, [threads, blocks] * (fld.fld_tuning_size(ctx) // 2))
+        fld.fld_set_tuning(ctx, [threads, blocks, pf] * (fld.fld_tuning_size(ctx) // 3))
         fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
         z = torch.empty(case.grid.cells, dtype=torch.float64, device="cuda")
         fld.fld_vcycle(ctx, dev(x), z)
