@@ -42,10 +42,10 @@ UNIT = "cell-solves/s"
 # ratio times its algorithmic bytes.  A class whose kernel changed since
 # the capture is left out (its traffic is then reported as null).
 TRAFFIC_OVER_ALGORITHMIC = {
-    "rb_colour": 28.2 / 26.0,
-    "cg_p_matvec": 32.5 / 32.0,
+    "rb_colour": 28.0 / 26.0,
+    "cg_p_matvec": 32.7 / 32.0,
     "smooth_zero": 24.7 / 24.0,
-    "residual": 28.4 / 28.0,
+    "residual": 28.3 / 28.0,
     "restrict": 4.5 / 4.5,
     "prolong_add": 6.7 / 8.5,
     "cg_update": 22.6 / 24.0,
