@@ -262,7 +262,7 @@ def main():
     pm.precision = synth.PREC_MIXED
     ctx = fld.fld_create(case.grid, pm, stream)
     tuning = fld.autotune(ctx)
-    kinds = ["smooth_zero", "rb_colour", "residual", "restrict", "prolong", "cg_p_matvec"]
+    kinds = ["smooth_zero", "rb_colour", "residual", "restrict", "prolong", "cg_p_matvec", "post_smooth"]
     tuned = {k: tuning[3 * q: 3 * q + 3] for q, k in enumerate(kinds)}   # threads, blocks, prefetch
     E = E0.clone()
     for _ in range(args.warmup):

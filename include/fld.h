@@ -396,7 +396,7 @@ fld_status fld_autotune(fld_ctx* ctx, int reps);
 /* The tuning table: per level and kernel one record of three ints
  * (threads per block, a power of two in [32, 256]; target blocks in
  * [1, 9728]; prefetch distance in planes, [0, 8], used by the stencil
- * sweeps only); its length (3 x 6 kernels x levels), a copy, and a
+ * sweeps only); its length (3 x 7 kernels x levels), a copy, and a
  * replacement (for caching tuned shapes).  fld_set_tuning checks every
  * record and changes nothing on FLD_EINVAL; the launch shape never changes
  * a result beyond the order of the CG reductions. */

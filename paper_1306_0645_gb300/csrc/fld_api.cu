@@ -43,7 +43,7 @@ fld_status set_err(fld_status st, const char* fmt, ...) {
     } while (0)
 
 // Tuned launch shapes of a level's FP32 sweeps.
-enum TuneClass { TN_SMOOTH0 = 0, TN_RB, TN_RES, TN_RESTRICT, TN_PROLONG, TN_PMATVEC, NTUNE };
+enum TuneClass { TN_SMOOTH0 = 0, TN_RB, TN_RES, TN_RESTRICT, TN_PROLONG, TN_PMATVEC, TN_POST, NTUNE };
 
 struct Level {
     Dims d;
@@ -505,7 +505,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
             { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts);
               launch_prolong_to4(L.d, C.d, (const float*)C.z, z, t, s); }
             KScope k(c, kc(K_POST_FUSED), 7.0 * n * ts);
-            launch_post_smooth4(L.d, A, r, t, z, dot, s);
+            launch_post_smooth4(L.d, A, r, t, z, dot, s, L.tune[TN_POST]);
             if (dot) *dot_done = true;
             return;
         }
@@ -1804,6 +1804,7 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
         }
         for (int k = 0; k < NTUNE && !st; k++) {
             if (k == TN_PMATVEC && l != 0) continue;
+            if (k == TN_POST && !(c->p.fused_post && post4_ok(L.d))) continue;
             auto run = [&](const Tune& tn) {
                 switch (k) {
                 case TN_SMOOTH0: launch_smooth_zero4(L.d, L.A32, r, t, s, tn); break;
@@ -1811,6 +1812,7 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 case TN_RES: launch_residual4(L.d, L.A32, r, z, t, s, tn); break;
                 case TN_RESTRICT: launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn); break;
                 case TN_PROLONG: launch_prolong_add4(L.d, C.d, (const float*)C.z, t, s, tn); break;
+                case TN_POST: launch_post_smooth4(L.d, L.A32, r, z, t, nullptr, s, tn); break;
                 case TN_PMATVEC:
                     launch_cg_p_matvec4(L.d, L.A32, z, (const float*)c->cg[2], (float*)c->cg[3],
                                         (float*)c->cg[4], red(c, R_ALPHA), s, tn);
@@ -1818,13 +1820,14 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 }
             };
             float best = 1e30f;
-            const bool has_pf = k == TN_SMOOTH0 || k == TN_RB || k == TN_RES || k == TN_PMATVEC;
+            const bool has_pf = k == TN_SMOOTH0 || k == TN_RB || k == TN_RES || k == TN_PMATVEC || k == TN_POST;
             for (int q = 0; q < NCAND && !st; q++) {
                 Tune tn;
                 tn.threads = threads_c[q % 2];
                 tn.target = target_c[(q / 2) % 5];
                 tn.pf = pf_c[q / 10];
                 if (tn.pf && !has_pf) continue;
+                if (k == TN_POST && tn.threads != 256) continue;   // fixed block of 32 x 8
                 run(tn);
                 cudaEventRecord(e0, s);
                 for (int rep = 0; rep < reps; rep++) run(tn);

@@ -417,7 +417,7 @@ __device__ __forceinline__ int plane_of(int q, const Dims& d) { return wrapc(q, 
 template <bool DOT>
 __global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, const float* __restrict__ r,
                                                       const float* __restrict__ zi, float* __restrict__ zo,
-                                                      RedArgs ra) {
+                                                      RedArgs ra, int pf) {
     __shared__ float4 sB[2][PBY + 2][32];
     const int nx4 = d.nx >> 2;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -499,6 +499,17 @@ __global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, co
         // now zq2 = z_{k0}, zq3 = z_{k0+1}
         for (int p = k0; p < k1; p++) {
             const int pu = plane_of(p + 1, d);
+            // the black front reads zi of plane p + 2 and the operator of
+            // plane p + 1: prefetch those pf planes further on
+            if (pf > 0 && p + 2 + pf < d.nz && p + 1 + pf <= k1) {
+                const long long o = (long long)(p + 1 + pf) * nxy + rowoff + i0;
+                pf2(zi, o + nxy);
+                pf2(r, o);
+                pf2(A.invd, o);
+                pf2(A.wx, o);
+                pf2(A.wy, o);
+                pf2(A.wz, o + nxy);
+            }
             const float4 zq4 = ld4(zi, (long long)plane_of(p + 2, d) * nxy + rowoff + i0);
             const float4 Bu = black(pu, zq2, zq3, zq4);             // B_{p+1}
             // buffer (p+1) & 1 was last read in the previous plane, before
@@ -781,10 +792,10 @@ bool post4_ok(const Dims& d) {
 }
 
 void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float* zi, float* zo,
-                         const RedArgs* dot, cudaStream_t s) {
-    ColShape sh = shape_post4(d);
-    if (dot) k_post_smooth4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, *dot);
-    else k_post_smooth4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, RedArgs{});
+                         const RedArgs* dot, cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape_post4(d, tn.target);
+    if (dot) k_post_smooth4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, *dot, tn.pf);
+    else k_post_smooth4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, zi, zo, RedArgs{}, tn.pf);
 }
 
 void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const float* z, float* zo,

@@ -220,7 +220,7 @@ void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, 
 // <r, zo> into *dot when dot is given; post4_ok tells if a level qualifies.
 bool post4_ok(const Dims& d);
 void launch_post_smooth4(const Dims& d, Op<float> A, const float* r, const float* zi, float* zo,
-                         const RedArgs* dot, cudaStream_t s);
+                         const RedArgs* dot, cudaStream_t s, const Tune& tn = Tune{});
 // zo = z + P ec (out of place)
 void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const float* z, float* zo,
                         cudaStream_t s);
