@@ -41,6 +41,16 @@ UNIT = "cell-solves/s"
 # Traffic grows with the cells of a launch, so a launch's traffic is this
 # ratio times its algorithmic bytes.  A class whose kernel changed since
 # the capture is left out (its traffic is then reported as null).
+# Compulsory bytes per cell of a mixed step under the fused-schedule model
+# (FP32 inner vectors and operator, FP64 outer): assembly reads E, n_HI, eta
+# and writes m, three face weights and b in FP64 plus the FP32 operator;
+# one preconditioned CG iteration streams 36 FP32 words (pre-smooth fused
+# with residual and restriction 12, prolongation with post-smoothing 7,
+# coarse levels about 2.7, p/q/<p,q> 8, x/r update 6); one outer refinement
+# reads x, b and the FP64 operator and writes the FP32 residual; finalize
+# reads E and dE and writes E.
+MODEL_ASM, MODEL_ITER, MODEL_IR, MODEL_FIN = 80.0, 144.0, 52.0, 24.0
+
 TRAFFIC_OVER_ALGORITHMIC = {
     "rb_colour": 28.0 / 26.0,
     "cg_p_matvec": 32.7 / 32.0,
@@ -313,6 +323,14 @@ def main():
     # whole-step algorithmic bytes over step time (all kernels)
     step_bytes = sum(k["bytes"] for k in stats) / args.steps
     step_frac = step_bytes / (total_ms / args.steps * 1e-3) / (peak * 1e9)
+    # the same fraction under the compulsory-traffic model of a fully fused
+    # schedule (bytes per cell: assembly 80, per inner iteration 144, per
+    # outer refinement 52, finalize 24, with the measured iteration counts)
+    model_cell = np.mean([MODEL_ASM + i["iters"] * MODEL_ITER + i["outer_iters"] * MODEL_IR + MODEL_FIN
+                          for i in infos])
+    step_model = {"bytes_per_cell": float(model_cell),
+                  "frac": float(model_cell * cells / (total_ms / args.steps * 1e-3) / (peak * 1e9)),
+                  "own_bytes_per_cell": float(step_bytes / cells)}
 
     # ---- plain FP64 multigrid on the same input
     fp64 = None
@@ -453,7 +471,8 @@ def main():
             "rel_res": [i["rel_res"] for i in infos],
             "fp64_mg": fp64,
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
-            "roofline": roofline, "step_roofline_frac": step_frac, "kernel_breakdown_one_step": breakdown,
+            "roofline": roofline, "step_roofline_frac": step_frac, "step_roofline_model": step_model,
+            "kernel_breakdown_one_step": breakdown,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "serving": serving_out, "variants": variants,
         }
