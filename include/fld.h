@@ -385,18 +385,19 @@ int fld_levels(const fld_grid* g, int* dims, int max_levels);
 /* Autotuner: for each level of a mixed-precision context whose FP32 sweeps
  * run four cells per thread, time every candidate launch shape (128 or 256
  * threads per block; 608 to 9728 blocks, which sets the z-chunk each thread
- * walks; for the stencil sweeps also an L2 prefetch distance of 0, 1 or 2
- * planes) of the pre-smoothing, colour-sweep, residual, restriction,
- * prolongation and CG p/q kernels, reps launches each, on the context's
- * buffers and stream, and keep the fastest.  No-op for FP64 contexts.
+ * walks; and an L2 prefetch distance of 0, 1 or 2 planes) of the
+ * pre-smoothing, colour-sweep, residual, restriction, prolongation and CG
+ * p/q kernels (and of the fused post-sweep when fused_post is set), reps
+ * launches each, on the context's buffers and stream, and keep the
+ * fastest.  No-op for FP64 contexts.
  * Discards captured CUDA graphs and the device scalars; call it after
  * fld_create and before stepping (the assembled operator is kept). */
 fld_status fld_autotune(fld_ctx* ctx, int reps);
 
 /* The tuning table: per level and kernel one record of three ints
  * (threads per block, a power of two in [32, 256]; target blocks in
- * [1, 9728]; prefetch distance in planes, [0, 8], used by the stencil
- * sweeps only); its length (3 x 7 kernels x levels), a copy, and a
+ * [1, 9728]; L2 prefetch distance in planes, [0, 8]); its length
+ * (3 x 7 kernels x levels), a copy, and a
  * replacement (for caching tuned shapes).  fld_set_tuning checks every
  * record and changes nothing on FLD_EINVAL; the launch shape never changes
  * a result beyond the order of the CG reductions. */

@@ -1820,13 +1820,11 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 }
             };
             float best = 1e30f;
-            const bool has_pf = k == TN_SMOOTH0 || k == TN_RB || k == TN_RES || k == TN_PMATVEC || k == TN_POST;
             for (int q = 0; q < NCAND && !st; q++) {
                 Tune tn;
                 tn.threads = threads_c[q % 2];
                 tn.target = target_c[(q / 2) % 5];
                 tn.pf = pf_c[q / 10];
-                if (tn.pf && !has_pf) continue;
                 if (k == TN_POST && tn.threads != 256) continue;   // fixed block of 32 x 8
                 run(tn);
                 cudaEventRecord(e0, s);

@@ -638,7 +638,7 @@ __device__ __forceinline__ float2 xy_sum(const Dims& f, const float* __restrict_
 }
 
 __global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float* __restrict__ rf,
-                                                   float* __restrict__ rc) {
+                                                   float* __restrict__ rc, int pf) {
     const int ht = cd.nx >> 1;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int J0 = blockIdx.y * blockDim.y + threadIdx.y;
@@ -654,6 +654,17 @@ __global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float*
     float2 s0 = xy_sum(f, rf, t, J, fold(2 * K0 - 1, f.nz, f.pz), load_l, load_r);
     float2 s1 = xy_sum(f, rf, t, J, 2 * K0, load_l, load_r);
     for (int K = K0; K < K1; K++) {
+        // this thread's own fine rows 2J, 2J + 1 of the two fine planes the
+        // walk reads pf coarse planes on
+        if (pf > 0 && K + pf < K1) {
+            const long long o = (long long)(2 * (K + pf) + 1) * f.nx * f.ny + (long long)(2 * J) * f.nx + 4 * t;
+            pf2(rf, o);
+            pf2(rf, o + f.nx);
+            if (2 * (K + pf) + 2 < f.nz) {
+                pf2(rf, o + (long long)f.nx * f.ny);
+                pf2(rf, o + (long long)f.nx * f.ny + f.nx);
+            }
+        }
         const float2 s2 = xy_sum(f, rf, t, J, 2 * K + 1, load_l, load_r);
         const float2 s3 = xy_sum(f, rf, t, J, fold(2 * K + 2, f.nz, f.pz), load_l, load_r);
         float2 o;
@@ -670,7 +681,7 @@ __global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float*
 // thread owns four fine cells along x, which interpolate from coarse cells
 // 2 i4 - 1 .. 2 i4 + 2 of two coarse rows in two coarse planes.
 __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const float* __restrict__ ec,
-                                                      float* __restrict__ zf) {
+                                                      float* __restrict__ zf, int pf) {
     const Walk w = walk_of(f);
     if (w.k0 >= w.k1) return;
     const int I = 2 * w.i4;
@@ -679,6 +690,8 @@ __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const flo
     const int J1 = fold((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
     const long long cxy = (long long)cd.nx * cd.ny;
     for (int k = w.k0; k < w.k1; k++) {
+        if (pf > 0 && k + pf < w.k1)
+            pf2(zf, (long long)(k + pf) * w.nxy + (long long)w.j * f.nx + 4 * w.i4);
         const int K0 = k >> 1;
         const int K1 = fold((k & 1) ? K0 + 1 : K0 - 1, cd.nz, cd.pz);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -822,12 +835,12 @@ void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, 
     Dims h = c;
     h.nx = c.nx / 2;
     ColShape sh = col_shape(h, tn.threads, tn.target);
-    k_restrict4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc);
+    k_restrict4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc, tn.pf);
 }
 void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s,
                          const Tune& tn) {
     ColShape sh = shape4(f, tn);
-    k_prolong_add4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf);
+    k_prolong_add4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf, tn.pf);
 }
 void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
                          const Tune& tn) {
