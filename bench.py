@@ -265,7 +265,11 @@ def main():
     cells = case.grid.cells
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
     E0, nHI, eta = dev(case.E), dev(case.nHI), dev(case.eta)
-    stream = torch.cuda.current_stream()
+    # a stream of its own (the legacy default stream cannot hold the CUDA
+    # graphs of the solve); torch work below is ordered on it as well
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)
 
     # ---- mixed precision (the measured path)
     pm = case.params

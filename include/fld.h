@@ -119,9 +119,12 @@ typedef struct {
     int pre, post;             /* smoothing sweeps per level (1, 1) */
     double inner_rtol;         /* mixed mode: inner FP32 solve target (1e-4) */
     int coarse_cap;            /* largest coarsest grid, cells (1024) */
-    int graphs;                /* CUDA graph per CG iteration: 1 on, 0 off,
-                                  -1 auto (grids up to 128^3; default).
-                                  Needs a non-NULL stream. */
+    int graphs;                /* CUDA graphs (the whole CG solve as one
+                                  device-side loop; per-iteration graphs in
+                                  fld_step_batched): 1 on, 0 off, -1 auto
+                                  (on; default).  Need a non-NULL stream:
+                                  with the legacy default stream the solve
+                                  launches its kernels one by one. */
     int fused_post;            /* mixed mode, RB-GS, post = 1: one fused
                                   black+red post-sweep kernel (1) or two
                                   colour sweeps (0, default, faster on

@@ -598,9 +598,10 @@ void drop_graphs(fld_ctx* c) {
 
 // The device-side CG loop of precision T (built on first use), or null when
 // graphs are off or unavailable.  Its body, captured into the while node,
-// is one iteration at p parity 0, the copy of the new p into the old one,
-// and the convergence test that sets the node's condition; one launch runs
-// the whole solve, and the host synchronises once instead of per iteration.
+// is one iteration at p parity 0 and its convergence test, then an IF node
+// holding the iteration at p parity 1 and its test; the tests set the
+// conditions.  One launch runs the whole solve, and the host synchronises
+// once instead of per iteration.
 template <class T>
 cudaGraphExec_t loop_graph(fld_ctx* c) {
     const int prec = std::is_same<T, float>::value ? 1 : 0;
@@ -622,6 +623,11 @@ cudaGraphExec_t loop_graph(fld_ctx* c) {
         ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
         if (ok) body = np.conditional.phGraph_out[0];
     }
+    // the body holds two iterations, p parity 0 then (under an IF node whose
+    // condition the first test sets as well) parity 1, so the new p never
+    // has to be copied into the old one
+    cudaGraphConditionalHandle hi = 0;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault) == cudaSuccess;
     if (ok) ok = cudaStreamBeginCaptureToGraph(c->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
                  cudaSuccess;
     if (ok) {
@@ -629,11 +635,46 @@ cudaGraphExec_t loop_graph(fld_ctx* c) {
         c->grec = &c->loop_launch[prec];
         c->capturing = true;
         pcg_iteration<T>(c, 0, false);
-        cudaMemcpyAsync(c->cg[2], c->cg[3], c->L[0].d.n * sizeof(T), cudaMemcpyDeviceToDevice, c->s);
-        launch_cg_check(h, c->sc, c->s);
+        launch_cg_check(h, c->sc, c->s, &hi);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        ok = cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &cg, &deps, &ed, &nd) == cudaSuccess &&
+             cs == cudaStreamCaptureStatusActive;
+        cudaGraphNode_t ifnode = nullptr;
+        cudaGraph_t ifbody = nullptr;
+        if (ok) {
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = hi;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            ok = cudaGraphAddNode(&ifnode, cg, deps, ed, nd, &ip) == cudaSuccess;
+            if (ok) ifbody = ip.conditional.phGraph_out[0];
+        }
+        if (ok)
+            ok = cudaStreamUpdateCaptureDependencies(c->s, &ifnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                 cudaSuccess;
         c->capturing = false;
         cudaGraph_t out = nullptr;
-        ok = cudaStreamEndCapture(c->s, &out) == cudaSuccess;
+        const bool ended = cudaStreamEndCapture(c->s, &out) == cudaSuccess;
+        ok = ok && ended;
+        if (ok) ok = cudaStreamBeginCaptureToGraph(c->s, ifbody, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            // its launches are the same as the first iteration's, which the
+            // host counts once per executed iteration
+            std::vector<std::pair<int, double>> second;
+            c->grec = &second;
+            c->capturing = true;
+            pcg_iteration<T>(c, 1, false);
+            launch_cg_check(h, c->sc, c->s);
+            c->capturing = false;
+            cudaGraph_t out2 = nullptr;
+            ok = cudaStreamEndCapture(c->s, &out2) == cudaSuccess;
+        }
     }
     if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
     if (!ok) {
@@ -1517,10 +1558,9 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
         std::lock_guard<std::mutex> lock(g_batch_lock);
         c->id = g_next_ctx_id++;
     }
-    // graphs need a capturable (non-legacy) stream; "auto" uses them where
-    // launch latency matters, grids up to 128^3
-    c->use_graphs = c->s != nullptr &&
-                    (p->graphs == 1 || (p->graphs < 0 && c->L[0].d.n <= (1LL << 21)));
+    // graphs need a capturable (non-legacy) stream; "auto" uses them at any
+    // size (the device-side CG loop saves the host round trip per iteration)
+    c->use_graphs = c->s != nullptr && p->graphs != 0;
     if (cudaMemsetAsync(c->counter, 0, 256, c->s) != cudaSuccess ||
         cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), c->s) != cudaSuccess) {
         free_ctx(c);

@@ -212,11 +212,12 @@ __global__ void k_f32_to_f64(long long n, const float* __restrict__ a, double* _
 // conditional (while) graph node: count the iteration and continue while
 // ||r||^2 > threshold, fewer than the allowed iterations are done and no
 // reduction produced a non-finite value.
-__global__ void k_cg_check(cudaGraphConditionalHandle h, double* sc) {
+__global__ void k_cg_check(cudaGraphConditionalHandle h, cudaGraphConditionalHandle h2, int both, double* sc) {
     const double k = sc[S_KITER] + 1.0;
     sc[S_KITER] = k;
     const bool cont = !(sc[S_RR] <= sc[S_THRESH]) && k < sc[S_MAXIT] && sc[S_NONFINITE] == 0.0;
     cudaGraphSetConditional(h, cont ? 1u : 0u);
+    if (both) cudaGraphSetConditional(h2, cont ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -228,8 +229,9 @@ void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s) {
     k_f32_to_f64<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);
 }
 
-void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s) {
-    k_cg_check<<<1, 1, 0, s>>>(h, sc);
+void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s,
+                     const cudaGraphConditionalHandle* h2) {
+    k_cg_check<<<1, 1, 0, s>>>(h, h2 ? *h2 : h, h2 ? 1 : 0, sc);
 }
 
 

@@ -134,7 +134,8 @@ void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s);
 // Device-side CG convergence test: sc[S_KITER] += 1 and the conditional h
 // set to continue while sc[S_RR] > sc[S_THRESH], S_KITER < S_MAXIT and no
 // non-finite reduction (one thread).
-void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s);
+void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s,
+                     const cudaGraphConditionalHandle* h2 = nullptr);
 // r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.  diag (may
 // be null) is the stored FP64 diagonal.
 void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
