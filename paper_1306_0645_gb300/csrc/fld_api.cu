@@ -194,7 +194,9 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     for (int l = 0; l < nl; l++) {
         const size_t n = (size_t)dims[l][0] * dims[l][1] * dims[l][2];
         for (int q = 0; q < 4; q++) buf(l, "A64", q, n * sizeof(double));
-        if (!(mixed && l == 0)) buf(l, "A64", 4, n * sizeof(double));
+        // the FP64 inverse diagonal serves the FP64 cycle only (the mixed
+        // solver's cycle is FP32 on every level)
+        if (!mixed) buf(l, "A64", 4, n * sizeof(double));
         if (mixed)
             for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
         if (l > 0) {
@@ -993,7 +995,7 @@ fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, cons
                 KScope k(c, K_COARSEN, 0.0);
                 launch_coarsen_bnd(F.d, C.d, sd, F.bnd, C.bnd, C.A64, s);
             }
-        { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
+        if (!c->mixed) { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
         if (c->mixed) {
             { KScope k(c, K_TO_F32, 48.0 * nc); launch_to_f32(C.d, C.A64, C.A32, s); }
             { KScope k(c, K_INVD, 36.0 * nc); launch_invd<float>(C.d, C.A32, C.A64, s); }
