@@ -401,12 +401,18 @@ void rb_colour_any(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStr
     }
     launch_rb_colour<T>(d, A, r, z, colour, s);
 }
+// Returns whether the residual took the form after one zero-guess sweep.
 template <class T>
-void residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s, const Tune& tn) {
+bool residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s, const Tune& tn,
+                  bool after_zero_sweep) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(d)) return launch_residual4(d, A, r, z, res, s, tn);
+        if (fine4_ok(d)) {
+            launch_residual4(d, A, r, z, res, s, tn, after_zero_sweep);
+            return after_zero_sweep;
+        }
     }
     launch_residual<T>(d, A, r, z, res, s);
+    return false;
 }
 
 template <class T>
@@ -498,7 +504,14 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     }
     Level& C = c->L[l + 1];
     const double nc = (double)C.d.n;
-    { KScope k(c, kc(K_RESIDUAL), 7.0 * n * ts); residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES]); }
+    {
+        // one red/black sweep from zero (black last) leaves a residual that
+        // needs neither r nor m (see k_residual4)
+        const bool zg = p.smoother == FLD_SMOOTH_RBGS && p.pre == 1 && std::is_same<T, float>::value &&
+                        fine4_ok(L.d);
+        KScope k(c, kc(K_RESIDUAL), (zg ? 5.0 : 7.0) * n * ts);
+        residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg);
+    }
     { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s, L.tune[TN_RESTRICT]); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
     if constexpr (std::is_same<T, float>::value) {
@@ -1851,7 +1864,10 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 switch (k) {
                 case TN_SMOOTH0: launch_smooth_zero4(L.d, L.A32, r, t, s, tn); break;
                 case TN_RB: launch_rb_colour4(L.d, L.A32, r, t, 0, s, tn); break;
-                case TN_RES: launch_residual4(L.d, L.A32, r, z, t, s, tn); break;
+                case TN_RES:
+                    launch_residual4(L.d, L.A32, r, z, t, s, tn,
+                                     c->p.smoother == FLD_SMOOTH_RBGS && c->p.pre == 1);
+                    break;
                 case TN_RESTRICT: launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn); break;
                 case TN_PROLONG: launch_prolong_add4(L.d, C.d, (const float*)C.z, t, s, tn); break;
                 case TN_POST: launch_post_smooth4(L.d, L.A32, r, z, t, nullptr, s, tn); break;

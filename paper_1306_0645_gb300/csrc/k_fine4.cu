@@ -203,7 +203,13 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
 
 // ---------------------------------------------------------------- residual
 
-// res = r - A z
+// res = r - A z.  ZG: z is the result of one red/black sweep from z = 0
+// (k_smooth_zero4), black cells last.  Then, in exact arithmetic, the
+// residual vanishes at black cells (their update solved their own row) and
+// at a red cell, where d z = r, it is the weighted sum of the black
+// neighbours, sum_f w_f z_nbr: neither r nor m is read (20 instead of 28
+// bytes per cell), and the result differs from r - A z only by rounding.
+template <bool ZG>
 __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
                                                    const float* __restrict__ z, float* __restrict__ res, int pf) {
     const Walk w = walk_of(d);
@@ -217,8 +223,10 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
         if (pf > 0 && k + pf < w.k1) {
             const long long o = g.c + (long long)pf * w.nxy;
             pf2(z, o);
-            pf2(r, o);
-            pf2(A.m, o);
+            if (!ZG) {
+                pf2(r, o);
+                pf2(A.m, o);
+            }
             pf2(A.wx, o);
             pf2(A.wy, o);
             pf2(A.wz, o);
@@ -231,17 +239,37 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
         float L, R;
         xnb(z, g, zc, L, R);
         const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
-        const float4 m = ld4(A.m, g.c), rc = ld4(r, g.c);
         float4 o;
+        if (ZG) {
+            // red = (i + j + k) even; element 0 has i even
+            const bool e0_red = ((w.j + k) & 1) == 0;
+#define S1(X, LX, RX)                                                                    \
+            (f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * zym.X + f.yu.X * zyp.X + f.zl.X * zd.X + \
+             f.zu.X * zu.X)
+            if (e0_red) {
+                o.x = S1(x, L, zc.y);
+                o.y = 0.0f;
+                o.z = S1(z, zc.y, zc.w);
+                o.w = 0.0f;
+            } else {
+                o.x = 0.0f;
+                o.y = S1(y, zc.x, zc.z);
+                o.z = 0.0f;
+                o.w = S1(w, zc.z, R);
+            }
+#undef S1
+        } else {
+            const float4 m = ld4(A.m, g.c), rc = ld4(r, g.c);
 #define R1(X, LX, RX)                                                                   \
-        o.X = rc.X - (m.X * zc.X + f.xl.X * (zc.X - (LX)) + f.xu.X * (zc.X - (RX)) +    \
-                      f.yl.X * (zc.X - zym.X) + f.yu.X * (zc.X - zyp.X) +               \
-                      f.zl.X * (zc.X - zd.X) + f.zu.X * (zc.X - zu.X));
-        R1(x, L, zc.y)
-        R1(y, zc.x, zc.z)
-        R1(z, zc.y, zc.w)
-        R1(w, zc.z, R)
+            o.X = rc.X - (m.X * zc.X + f.xl.X * (zc.X - (LX)) + f.xu.X * (zc.X - (RX)) +    \
+                          f.yl.X * (zc.X - zym.X) + f.yu.X * (zc.X - zyp.X) +               \
+                          f.zl.X * (zc.X - zd.X) + f.zu.X * (zc.X - zu.X));
+            R1(x, L, zc.y)
+            R1(y, zc.x, zc.z)
+            R1(z, zc.y, zc.w)
+            R1(w, zc.z, R)
 #undef R1
+        }
         if (w.valid) st4(res, g.c, o);
         zd = zc;
         zc = zu;
@@ -826,9 +854,10 @@ void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float
     k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra, tn.pf);
 }
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s, const Tune& tn) {
+                      cudaStream_t s, const Tune& tn, bool after_zero_sweep) {
     ColShape sh = shape4(d, tn);
-    k_residual4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+    if (after_zero_sweep) k_residual4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+    else k_residual4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
 }
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
                       const Tune& tn) {

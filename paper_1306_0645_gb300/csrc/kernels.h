@@ -205,8 +205,10 @@ constexpr int TUNE_PF_MAX = 8;
 bool fine4_ok(const Dims& d);
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
                          float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
+// after_zero_sweep: z comes from one red/black sweep from z = 0 (black
+// last), so the residual is sum_f w_f z_nbr at red cells and 0 at black ones
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s, const Tune& tn = Tune{});
+                      cudaStream_t s, const Tune& tn = Tune{}, bool after_zero_sweep = false);
 void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
                          const Tune& tn = Tune{});
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,

@@ -129,6 +129,32 @@ def test_vcycle_smoother_variants(fld, oracle, smoother, prepost):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,per", [((64, 32, 48), (False, False, False)), ((128, 64, 32), (True, False, True)),
+                                   ((96, 96, 64), (False, True, False))])
+@pytest.mark.parametrize("pre", [1, 2])
+def test_mixed_vcycle_parity(fld, oracle, n, per, pre):
+    # the FP32 cycle of a mixed context against the oracle's FP64 cycle.  With
+    # one pre-sweep the residual takes the zero-guess form (the weighted sum
+    # of the black neighbours at red cells, 0 at black cells), which equals
+    # r - A z in exact arithmetic; with two pre-sweeps it is r - A z itself.
+    # Both agree with the oracle to FP32 rounding of the cycle.
+    case = synth.random_case(n, seed=400 + sum(n), periodic=per, E_decades=(-20, -14))
+    op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
+    p = case.params
+    p.precision, p.pre, p.post = synth.PREC_MIXED, pre, 1
+    ctx = fld.fld_create(case.grid, p)
+    fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
+    x = np.random.default_rng(11).standard_normal(case.grid.shape)
+    z = torch.empty(case.grid.cells, dtype=torch.float64, device="cuda")
+    fld.fld_vcycle(ctx, dev(x), z)
+    ctx.close()
+    zg = host(z).reshape(x.shape)
+    zref = oracle.vcycle(case.grid, op, x, {"pre": pre, "post": 1})
+    el2 = np.linalg.norm(zg - zref) / np.linalg.norm(zref)
+    einf = np.abs(zg - zref).max() / np.abs(zref).max()
+    assert el2 < 1e-5 and einf < 1e-5, (el2, einf)
+
+
 def fp64_step_pair(fld, oracle, case, rtol=1e-13, max_iter=200):
     p = case.params
     p.rtol, p.max_iter = rtol, max_iter
