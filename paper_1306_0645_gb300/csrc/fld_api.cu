@@ -401,24 +401,22 @@ void rb_colour_any(const Dims& d, Op<T> A, const T* r, T* z, int colour, cudaStr
     }
     launch_rb_colour<T>(d, A, r, z, colour, s);
 }
-// Returns whether the residual took the form after one zero-guess sweep.
 template <class T>
-bool residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s, const Tune& tn,
-                  bool after_zero_sweep) {
+void residual_any(const Dims& d, Op<T> A, const T* r, const T* z, T* res, cudaStream_t s, const Tune& tn,
+                  bool after_zero_sweep, bool red_compressed) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(d)) {
-            launch_residual4(d, A, r, z, res, s, tn, after_zero_sweep);
-            return after_zero_sweep;
-        }
+        if (fine4_ok(d)) return launch_residual4(d, A, r, z, res, s, tn, after_zero_sweep, red_compressed);
     }
     launch_residual<T>(d, A, r, z, res, s);
-    return false;
 }
 
+// red_compressed (FP32 levels where red_compress_ok): rf as k_residual4
+// stores it after a zero-guess sweep
 template <class T>
-void restrict_any(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s, const Tune& tn) {
+void restrict_any(const Dims& f, const Dims& c, const T* rf, T* rc, cudaStream_t s, const Tune& tn,
+                  bool red_compressed) {
     if constexpr (std::is_same<T, float>::value) {
-        if (fine4_ok(f)) return launch_restrict4(f, c, rf, rc, s, tn);
+        if (fine4_ok(f)) return launch_restrict4(f, c, rf, rc, s, tn, red_compressed);
     }
     launch_restrict<T>(f, c, rf, rc, s);
 }
@@ -504,15 +502,16 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     }
     Level& C = c->L[l + 1];
     const double nc = (double)C.d.n;
-    {
-        // one red/black sweep from zero (black last) leaves a residual that
-        // needs neither r nor m (see k_residual4)
-        const bool zg = p.smoother == FLD_SMOOTH_RBGS && p.pre == 1 && std::is_same<T, float>::value &&
-                        fine4_ok(L.d);
-        KScope k(c, kc(K_RESIDUAL), (zg ? 5.0 : 7.0) * n * ts);
-        residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg);
-    }
-    { KScope k(c, kc(K_RESTRICT), (n + nc) * ts); restrict_any<T>(L.d, C.d, t, (T*)C.r, s, L.tune[TN_RESTRICT]); }
+    // one red/black sweep from zero (black last) leaves a residual that
+    // needs neither r nor m and vanishes at black cells; where the x extent
+    // allows it is stored red-compressed (see k_residual4)
+    const bool zg = p.smoother == FLD_SMOOTH_RBGS && p.pre == 1 && std::is_same<T, float>::value &&
+                    fine4_ok(L.d);
+    const bool cmp = zg && red_compress_ok(L.d);
+    { KScope k(c, kc(K_RESIDUAL), (cmp ? 4.5 : (zg ? 5.0 : 7.0)) * n * ts);
+      residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg, cmp); }
+    { KScope k(c, kc(K_RESTRICT), ((cmp ? 0.5 : 1.0) * n + nc) * ts);
+      restrict_any<T>(L.d, C.d, t, (T*)C.r, s, L.tune[TN_RESTRICT], cmp); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
     if constexpr (std::is_same<T, float>::value) {
         // one fused post-sweep: t = z + P e_c, then black and red from t into z
@@ -1831,6 +1830,8 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
     const int target_c[] = {152 * 4, 152 * 8, 152 * 16, 152 * 32, 152 * 64};
     const int pf_c[] = {0, 1, 2};
     constexpr int NCAND = 2 * 5 * 3;
+    // the residual and restriction forms the V-cycle will launch
+    const bool zg_cfg = c->p.smoother == FLD_SMOOTH_RBGS && c->p.pre == 1;
     fld_status st = FLD_OK;
     for (int l = 0; l + 1 < c->nl && !st; l++) {
         Level& L = c->L[l];
@@ -1865,10 +1866,11 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
                 case TN_SMOOTH0: launch_smooth_zero4(L.d, L.A32, r, t, s, tn); break;
                 case TN_RB: launch_rb_colour4(L.d, L.A32, r, t, 0, s, tn); break;
                 case TN_RES:
-                    launch_residual4(L.d, L.A32, r, z, t, s, tn,
-                                     c->p.smoother == FLD_SMOOTH_RBGS && c->p.pre == 1);
+                    launch_residual4(L.d, L.A32, r, z, t, s, tn, zg_cfg, zg_cfg && red_compress_ok(L.d));
                     break;
-                case TN_RESTRICT: launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn); break;
+                case TN_RESTRICT:
+                    launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn, zg_cfg && red_compress_ok(L.d));
+                    break;
                 case TN_PROLONG: launch_prolong_add4(L.d, C.d, (const float*)C.z, t, s, tn); break;
                 case TN_POST: launch_post_smooth4(L.d, L.A32, r, z, t, nullptr, s, tn); break;
                 case TN_PMATVEC:

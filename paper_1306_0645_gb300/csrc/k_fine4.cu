@@ -207,9 +207,13 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
 // (k_smooth_zero4), black cells last.  Then, in exact arithmetic, the
 // residual vanishes at black cells (their update solved their own row) and
 // at a red cell, where d z = r, it is the weighted sum of the black
-// neighbours, sum_f w_f z_nbr: neither r nor m is read (20 instead of 28
-// bytes per cell), and the result differs from r - A z only by rounding.
-template <bool ZG>
+// neighbours, sum_f w_f z_nbr: neither r nor m is read, and the result
+// differs from r - A z only by rounding (20 instead of 28 bytes per cell).
+// CMP: only the red values are stored, red-compressed: every pair of cells
+// (2m, 2m + 1) along x holds one red cell, whose residual goes to res[m],
+// so cell l has residual res[l >> 1] if it is red and 0 if it is black
+// (18 bytes per cell; k_restrict_red4 reads this form).
+template <bool ZG, bool CMP>
 __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
                                                    const float* __restrict__ z, float* __restrict__ res, int pf) {
     const Walk w = walk_of(d);
@@ -239,27 +243,28 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
         float L, R;
         xnb(z, g, zc, L, R);
         const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
-        float4 o;
         if (ZG) {
             // red = (i + j + k) even; element 0 has i even
             const bool e0_red = ((w.j + k) & 1) == 0;
 #define S1(X, LX, RX)                                                                    \
             (f.xl.X * (LX) + f.xu.X * (RX) + f.yl.X * zym.X + f.yu.X * zyp.X + f.zl.X * zd.X + \
              f.zu.X * zu.X)
+            float2 h;
             if (e0_red) {
-                o.x = S1(x, L, zc.y);
-                o.y = 0.0f;
-                o.z = S1(z, zc.y, zc.w);
-                o.w = 0.0f;
+                h.x = S1(x, L, zc.y);
+                h.y = S1(z, zc.y, zc.w);
             } else {
-                o.x = 0.0f;
-                o.y = S1(y, zc.x, zc.z);
-                o.z = 0.0f;
-                o.w = S1(w, zc.z, R);
+                h.x = S1(y, zc.x, zc.z);
+                h.y = S1(w, zc.z, R);
             }
 #undef S1
+            if (w.valid) {
+                if (CMP) *reinterpret_cast<float2*>(res + (g.c >> 1)) = h;
+                else st4(res, g.c, e0_red ? make_float4(h.x, 0.f, h.y, 0.f) : make_float4(0.f, h.x, 0.f, h.y));
+            }
         } else {
             const float4 m = ld4(A.m, g.c), rc = ld4(r, g.c);
+            float4 o;
 #define R1(X, LX, RX)                                                                   \
             o.X = rc.X - (m.X * zc.X + f.xl.X * (zc.X - (LX)) + f.xu.X * (zc.X - (RX)) +    \
                           f.yl.X * (zc.X - zym.X) + f.yu.X * (zc.X - zyp.X) +               \
@@ -269,8 +274,8 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
             R1(z, zc.y, zc.w)
             R1(w, zc.z, R)
 #undef R1
+            if (w.valid) st4(res, g.c, o);
         }
-        if (w.valid) st4(res, g.c, o);
         zd = zc;
         zc = zu;
         wzc = wzu;
@@ -665,6 +670,49 @@ __device__ __forceinline__ float2 xy_sum(const Dims& f, const float* __restrict_
     return acc;
 }
 
+// Residual of fine cell `row + x` from its red-compressed form.
+__device__ __forceinline__ float red_res(const float* __restrict__ rf, long long row, int x, int fy, int fz) {
+    return ((x + fy + fz) & 1) == 0 ? rf[(row + x) >> 1] : 0.0f;
+}
+
+// x-y weighted sums of fine plane fz for coarse cells 4t .. 4t+3 of row J
+// from a red-compressed residual: one float4 per fine row holds the red
+// values of fine cells 8t .. 8t+7.
+__device__ __forceinline__ float4 xy_sum_red(const Dims& f, const float* __restrict__ rf, int t, int J,
+                                             int fz, bool load_l, bool load_r) {
+    const float wv[4] = {0.25f, 0.75f, 0.75f, 0.25f};
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long plane = (long long)fz * f.nx * f.ny;
+    const int x0 = 8 * t;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int fy = fold(2 * J - 1 + q, f.ny, f.py);
+        const long long row = plane + (long long)fy * f.nx;
+        const float4 h = ld4(rf, (row + x0) >> 1);
+        // fine cell x0 is red when x0 + fy + fz is even (x0 is)
+        const bool even_red = ((fy + fz) & 1) == 0;
+        float v[8];
+        v[0] = even_red ? h.x : 0.f; v[1] = even_red ? 0.f : h.x;
+        v[2] = even_red ? h.y : 0.f; v[3] = even_red ? 0.f : h.y;
+        v[4] = even_red ? h.z : 0.f; v[5] = even_red ? 0.f : h.z;
+        v[6] = even_red ? h.w : 0.f; v[7] = even_red ? 0.f : h.w;
+        // fine cell x0 - 1 is red when the odd cells are, x0 + 8 when the even ones are
+        const float lsh = __shfl_up_sync(FULL, h.w, 1);
+        const float rsh = __shfl_down_sync(FULL, h.x, 1);
+        const float L = load_l ? red_res(rf, row, fold(x0 - 1, f.nx, f.px), fy, fz) : (even_red ? 0.f : lsh);
+        const float R = load_r ? red_res(rf, row, fold(x0 + 8, f.nx, f.px), fy, fz) : (even_red ? rsh : 0.f);
+        const float c0 = 0.25f * L + 0.75f * v[0] + 0.75f * v[1] + 0.25f * v[2];
+        const float c1 = 0.25f * v[1] + 0.75f * v[2] + 0.75f * v[3] + 0.25f * v[4];
+        const float c2 = 0.25f * v[3] + 0.75f * v[4] + 0.75f * v[5] + 0.25f * v[6];
+        const float c3 = 0.25f * v[5] + 0.75f * v[6] + 0.75f * v[7] + 0.25f * R;
+        acc.x = fmaf(wv[q], c0, acc.x);
+        acc.y = fmaf(wv[q], c1, acc.y);
+        acc.z = fmaf(wv[q], c2, acc.z);
+        acc.w = fmaf(wv[q], c3, acc.w);
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float* __restrict__ rf,
                                                    float* __restrict__ rc, int pf) {
     const int ht = cd.nx >> 1;
@@ -700,6 +748,46 @@ __global__ void __launch_bounds__(256) k_restrict4(Dims f, Dims cd, const float*
         o.y = 0.125f * (0.25f * s0.y + 0.75f * s1.y + 0.75f * s2.y + 0.25f * s3.y);
         if (valid)
             *reinterpret_cast<float2*>(rc + (long long)K * cd.nx * cd.ny + (long long)J * cd.nx + 2 * t) = o;
+        s0 = s2;
+        s1 = s3;
+    }
+}
+
+// k_restrict4 for a red-compressed residual (k_residual4 after a
+// zero-guess sweep): a thread owns coarse cells 4t .. 4t+3 of a row, one
+// float4 of compressed values per fine row (fine nx a multiple of 8).
+__global__ void __launch_bounds__(256) k_restrict_red4(Dims f, Dims cd, const float* __restrict__ rf,
+                                                       float* __restrict__ rc, int pf) {
+    const int qt = cd.nx >> 2;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J0 = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = t0 < qt && J0 < cd.ny;
+    const int t = min(t0, qt - 1), J = min(J0, cd.ny - 1);
+    const int kch = (cd.nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int K0 = (int)blockIdx.z * kch, K1 = min(cd.nz, K0 + kch);
+    if (K0 >= K1) return;
+    const bool load_l = threadIdx.x == 0 || t == 0;
+    const bool load_r = threadIdx.x == blockDim.x - 1 || t == qt - 1;
+    float4 s0 = xy_sum_red(f, rf, t, J, fold(2 * K0 - 1, f.nz, f.pz), load_l, load_r);
+    float4 s1 = xy_sum_red(f, rf, t, J, 2 * K0, load_l, load_r);
+    for (int K = K0; K < K1; K++) {
+        if (pf > 0 && K + pf < K1) {
+            const long long o = (long long)(2 * (K + pf) + 1) * f.nx * f.ny + (long long)(2 * J) * f.nx + 8 * t;
+            pf2(rf, o >> 1);
+            pf2(rf, (o + f.nx) >> 1);
+            if (2 * (K + pf) + 2 < f.nz) {
+                pf2(rf, (o + (long long)f.nx * f.ny) >> 1);
+                pf2(rf, (o + (long long)f.nx * f.ny + f.nx) >> 1);
+            }
+        }
+        const float4 s2 = xy_sum_red(f, rf, t, J, 2 * K + 1, load_l, load_r);
+        const float4 s3 = xy_sum_red(f, rf, t, J, fold(2 * K + 2, f.nz, f.pz), load_l, load_r);
+        float4 o;
+        o.x = 0.125f * (0.25f * s0.x + 0.75f * s1.x + 0.75f * s2.x + 0.25f * s3.x);
+        o.y = 0.125f * (0.25f * s0.y + 0.75f * s1.y + 0.75f * s2.y + 0.25f * s3.y);
+        o.z = 0.125f * (0.25f * s0.z + 0.75f * s1.z + 0.75f * s2.z + 0.25f * s3.z);
+        o.w = 0.125f * (0.25f * s0.w + 0.75f * s1.w + 0.75f * s2.w + 0.25f * s3.w);
+        if (valid) st4(rc, (long long)K * cd.nx * cd.ny + (long long)J * cd.nx + 4 * t, o);
         s0 = s2;
         s1 = s3;
     }
@@ -854,14 +942,26 @@ void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float
     k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra, tn.pf);
 }
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s, const Tune& tn, bool after_zero_sweep) {
+                      cudaStream_t s, const Tune& tn, bool after_zero_sweep, bool red_compressed) {
     ColShape sh = shape4(d, tn);
-    if (after_zero_sweep) k_residual4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
-    else k_residual4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+    if (after_zero_sweep && red_compressed)
+        k_residual4<true, true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+    else if (after_zero_sweep)
+        k_residual4<true, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+    else
+        k_residual4<false, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
 }
+bool red_compress_ok(const Dims& f) { return fine4_ok(f) && f.nx % 8 == 0; }
+
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
-                      const Tune& tn) {
+                      const Tune& tn, bool red_compressed) {
     Dims h = c;
+    if (red_compressed) {
+        h.nx = c.nx / 4;
+        ColShape sh = col_shape(h, tn.threads, tn.target);
+        k_restrict_red4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc, tn.pf);
+        return;
+    }
     h.nx = c.nx / 2;
     ColShape sh = col_shape(h, tn.threads, tn.target);
     k_restrict4<<<sh.grid, sh.block, 0, s>>>(f, c, rf, rc, tn.pf);

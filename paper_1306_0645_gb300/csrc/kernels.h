@@ -206,9 +206,13 @@ bool fine4_ok(const Dims& d);
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
                          float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
 // after_zero_sweep: z comes from one red/black sweep from z = 0 (black
-// last), so the residual is sum_f w_f z_nbr at red cells and 0 at black ones
+// last), so the residual is sum_f w_f z_nbr at red cells and 0 at black
+// ones; red_compressed (with after_zero_sweep, where red_compress_ok):
+// stored red-compressed, res[l >> 1] for red cell l
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
-                      cudaStream_t s, const Tune& tn = Tune{}, bool after_zero_sweep = false);
+                      cudaStream_t s, const Tune& tn = Tune{}, bool after_zero_sweep = false,
+                      bool red_compressed = false);
+bool red_compress_ok(const Dims& f);
 void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
                          const Tune& tn = Tune{});
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
@@ -217,8 +221,10 @@ void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra,
 // one colour of a sweep followed by <r, z> of the result (reduction ra)
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                            const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
+// red_compressed: rf is a red-compressed residual (k_residual4 after a
+// zero-guess sweep), cell l red ? rf[l >> 1] : 0
 void launch_restrict4(const Dims& f, const Dims& c, const float* rf, float* rc, cudaStream_t s,
-                      const Tune& tn = Tune{});
+                      const Tune& tn = Tune{}, bool red_compressed = false);
 // Fused post-smoothing sweep (black then red), out of place zi -> zo, with
 // <r, zo> into *dot when dot is given; post4_ok tells if a level qualifies.
 bool post4_ok(const Dims& d);
