@@ -599,7 +599,11 @@ __global__ void __launch_bounds__(256) k_prolong_to4(Dims f, Dims cd, const floa
     const Walk w = walk_of(f);
     if (w.k0 >= w.k1) return;
     const int I = 2 * w.i4;
-    const int xi[4] = {wrapc(I - 1, cd.nx, cd.px), I, I + 1, wrapc(I + 2, cd.nx, cd.px)};
+    const int xm = wrapc(I - 1, cd.nx, cd.px), xp = wrapc(I + 2, cd.nx, cd.px);
+    // coarse cells I, I+1 as one float2, I-1 and I+2 from the adjacent lanes
+    // (see k_prolong_add4)
+    const bool load_l = threadIdx.x == 0 || I == 0;
+    const bool load_r = threadIdx.x == blockDim.x - 1 || I + 2 >= cd.nx;
     const int J0 = w.j >> 1;
     const int J1 = wrapc((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
     const long long cxy = (long long)cd.nx * cd.ny;
@@ -613,8 +617,12 @@ __global__ void __launch_bounds__(256) k_prolong_to4(Dims f, Dims cd, const floa
             const int Kq = (q & 2) ? K1 : K0;
             const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
             const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
-            const float cm = ec[row + xi[0]], c0 = ec[row + xi[1]], c1 = ec[row + xi[2]],
-                        cp = ec[row + xi[3]];
+            const float2 cc = *reinterpret_cast<const float2*>(ec + row + I);
+            const float c0 = cc.x, c1 = cc.y;
+            const float lsh = __shfl_up_sync(FULL, c1, 1);
+            const float rsh = __shfl_down_sync(FULL, c0, 1);
+            const float cm = load_l ? ec[row + xm] : lsh;
+            const float cp = load_r ? ec[row + xp] : rsh;
             acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
             acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
             acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
@@ -801,7 +809,12 @@ __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const flo
     const Walk w = walk_of(f);
     if (w.k0 >= w.k1) return;
     const int I = 2 * w.i4;
-    const int xi[4] = {fold(I - 1, cd.nx, cd.px), I, I + 1, fold(I + 2, cd.nx, cd.px)};
+    const int xm = fold(I - 1, cd.nx, cd.px), xp = fold(I + 2, cd.nx, cd.px);
+    // coarse cells I, I+1 are one aligned float2 (cd.nx is even); I-1 and
+    // I+2 are the neighbouring lanes' unless this lane starts or ends its
+    // block row or the coarse row
+    const bool load_l = threadIdx.x == 0 || I == 0;
+    const bool load_r = threadIdx.x == blockDim.x - 1 || I + 2 >= cd.nx;
     const int J0 = w.j >> 1;
     const int J1 = fold((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
     const long long cxy = (long long)cd.nx * cd.ny;
@@ -817,8 +830,12 @@ __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const flo
             const int Kq = (q & 2) ? K1 : K0;
             const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
             const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
-            const float cm = ec[row + xi[0]], c0 = ec[row + xi[1]], c1 = ec[row + xi[2]],
-                        cp = ec[row + xi[3]];
+            const float2 cc = *reinterpret_cast<const float2*>(ec + row + I);
+            const float c0 = cc.x, c1 = cc.y;
+            const float lsh = __shfl_up_sync(FULL, c1, 1);
+            const float rsh = __shfl_down_sync(FULL, c0, 1);
+            const float cm = load_l ? ec[row + xm] : lsh;
+            const float cp = load_r ? ec[row + xp] : rsh;
             acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
             acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
             acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
