@@ -550,6 +550,14 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
 // One CG iteration on the fine level in precision T (p parity cur): the
 // V-cycle, <r,z>, p and q = A p, the x and r updates, and the scalars to the
 // pinned host mirror.
+// Whether the CG of precision T defers each update of x to the next
+// iteration (FP32 four-cell kernels): the last one is then applied by
+// launch_ir_update with the p of the last iteration, p[run.cur].
+template <class T>
+bool defers_x(fld_ctx* c) {
+    return std::is_same<T, float>::value && use4<T>(c->L[0].d);
+}
+
 template <class T>
 void pcg_iteration(fld_ctx* c, int cur, bool mirror = true) {
     T* r = (T*)c->cg[0];
@@ -573,19 +581,23 @@ void pcg_iteration(fld_ctx* c, int cur, bool mirror = true) {
             launch_dot<T>(n, r, z, red(c, R_RHO), c->s);
         }
     }
+    // the FP32 four-cell kernels defer x += alpha p to the next iteration's
+    // p/q kernel, which reads that p anyway (see defers_x)
+    const bool defer = defers_x<T>(c);
     {
-        KScope ks(c, K_CG_PMATVEC, 8.0 * n * ts);
+        KScope ks(c, K_CG_PMATVEC, (defer ? 10.0 : 8.0) * n * ts);
         if constexpr (std::is_same<T, float>::value) {
-            if (use4<T>(L0.d)) launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s, L0.tune[TN_PMATVEC]);
+            if (defer)
+                launch_cg_p_matvec4(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s, L0.tune[TN_PMATVEC], x);
             else launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
         } else {
             launch_cg_p_matvec<T>(L0.d, A, z, p[cur], p[cur ^ 1], q, red(c, R_ALPHA), c->s);
         }
     }
     {
-        KScope ks(c, K_CG_UPDATE, 6.0 * n * ts);
+        KScope ks(c, K_CG_UPDATE, (defer ? 3.0 : 6.0) * n * ts);
         if constexpr (std::is_same<T, float>::value) {
-            if (use4<T>(L0.d)) launch_cg_update4(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
+            if (defer) launch_cg_update4(n, nullptr, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
             else launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
         } else {
             launch_cg_update<T>(n, x, r, p[cur ^ 1], q, red(c, R_STORE1, S_RR), c->s);
@@ -749,8 +761,10 @@ template <class T>
 fld_status pcg_begin(fld_ctx* c, double r0sq, double rtol, int max_iter) {
     CUDA_TRY(cudaMemsetAsync(c->cg[2], 0, c->L[0].d.n * sizeof(T), c->s));
     // beta = 0 in the first iteration, signalled on the device so that
-    // every iteration launches the same work
+    // every iteration launches the same work; alpha = 0 before it, so that
+    // a deferred update of x adds nothing there
     CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    CUDA_TRY(cudaMemsetAsync(c->sc + S_ALPHA, 0, sizeof(double), c->s));
     c->run.thresh = rtol * rtol * r0sq;
     c->run.max_iter = max_iter;
     c->run.k = 0;
@@ -817,6 +831,7 @@ fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, b
                 c->kstat[e.first].bytes += e.second;
             }
         c->run.k = k;
+        c->run.cur = k & 1;   // as after k single iterations: the last p is p[cur]
         c->run.done = true;
         if (c->h_sc[S_NONFINITE] != 0.0)
             return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
@@ -961,8 +976,9 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
             st = pcg<float>(c, c->h_sc[S_R0], irtol, c->p.max_iter - inner_total, &it, &iconv);
             if (st) return st;
             inner_total += it;
-            { KScope k(c, K_IR_UPDATE, (outer == 0 ? 12.0 : 20.0) * n);
-              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, outer == 0, c->s); }
+            { KScope k(c, K_IR_UPDATE, ((outer == 0 ? 12.0 : 20.0) + (defers_x<float>(c) ? 4.0 : 0.0)) * n);
+              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, outer == 0, c->s,
+                               defers_x<float>(c) ? (const float*)c->cg[2 + c->run.cur] : nullptr); }
             outer++;
         }
         inf.iters = inner_total;
@@ -1313,8 +1329,9 @@ void batch_after(BItem& b) {
             b.state = BS_TRUE_RES;
         } else {
             b.inner_total += c->run.k;
-            { KScope k(c, K_IR_UPDATE, (b.outer == 0 ? 12.0 : 20.0) * n);
-              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, b.outer == 0, c->s); }
+            { KScope k(c, K_IR_UPDATE, ((b.outer == 0 ? 12.0 : 20.0) + (defers_x<float>(c) ? 4.0 : 0.0)) * n);
+              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, b.outer == 0, c->s,
+                               defers_x<float>(c) ? (const float*)c->cg[2 + c->run.cur] : nullptr); }
             b.outer++;
             { KScope k(c, K_RESIDUAL64, 56.0 * n);
               launch_residual64(c->L[0].d, c->L[0].A64, c->diag64, c->b, c->dE, c->r64,

@@ -156,14 +156,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_ir_scale(long long n, const dou
     grid_reduce<2>(acc, mx, ra);
 }
 
-// x64 += s x32 (assign: x64 = s x32, the first refinement from x64 = 0)
+// x64 += s x32 (assign: x64 = s x32, the first refinement from x64 = 0).
+// p_last: the inner solve deferred its last update of x, x32 + alpha p_last
+// (the FP32 operation the update kernel would have done) takes its place.
 __global__ void k_ir_update(long long n, double* __restrict__ x64, const float* __restrict__ x32,
-                            const double* __restrict__ sc, int assign) {
+                            const double* __restrict__ sc, int assign, const float* __restrict__ p_last) {
     const double s = sc[S_RMAX];
-    if (assign) {
-        GRID_LOOP(c, n) x64[c] = s * (double)x32[c];
-    } else {
-        GRID_LOOP(c, n) x64[c] = fma(s, (double)x32[c], x64[c]);
+    const float alpha = (float)sc[S_ALPHA];
+    GRID_LOOP(c, n) {
+        const float xf = p_last ? fmaf(alpha, p_last[c], x32[c]) : x32[c];
+        x64[c] = assign ? s * (double)xf : fma(s, (double)xf, x64[c]);
     }
 }
 
@@ -265,8 +267,8 @@ void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, con
     k_ir_scale<<<red_blocks(n), RED_THREADS, 0, s>>>(n, r64, r32, x32, ra);
 }
 void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
-                      cudaStream_t s) {
-    k_ir_update<<<grid_blocks(n, 256), 256, 0, s>>>(n, x64, x32, sc, assign ? 1 : 0);
+                      cudaStream_t s, const float* p_last) {
+    k_ir_update<<<grid_blocks(n, 256), 256, 0, s>>>(n, x64, x32, sc, assign ? 1 : 0, p_last);
 }
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,

@@ -130,12 +130,16 @@ __device__ __forceinline__ Faces4 faces_of(const Op<float>& A, const Geo& g, flo
 
 // ------------------------------------------------------------------ p, q
 
-// p_out = z + beta p_in;  q = A p_out;  <p_out, q>.
+// p_out = z + beta p_in;  q = A p_out;  <p_out, q>.  With x: also the
+// previous iteration's solution update x += alpha_prev p_in (alpha_prev is
+// the alpha slot when the kernel starts; its own reduction replaces it only
+// after every block has read it), which k_cg_update4 then leaves out.
 __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, const float* __restrict__ z,
                                                       const float* __restrict__ p_in,
                                                       float* __restrict__ p_out, float* __restrict__ q,
-                                                      RedArgs ra, int pf) {
+                                                      float* __restrict__ x, RedArgs ra, int pf) {
     const float beta = (float)ra.sc[S_BETA];
+    const float alpha_prev = x ? (float)ra.sc[S_ALPHA] : 0.0f;
     const Walk w = walk_of(d);
     DotAcc<float> da;
     auto P = [&](long long i) {
@@ -186,6 +190,14 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
             if (w.valid) {
                 st4(p_out, g.c, pc);
                 st4(q, g.c, qv);
+                if (x) {
+                    // p_in of this plane was read one plane ago (L1)
+                    const float4 pv = ld4(p_in, g.c);
+                    float4 xv = ld4(x, g.c);
+                    xv.x = fmaf(alpha_prev, pv.x, xv.x); xv.y = fmaf(alpha_prev, pv.y, xv.y);
+                    xv.z = fmaf(alpha_prev, pv.z, xv.z); xv.w = fmaf(alpha_prev, pv.w, xv.w);
+                    st4(x, g.c, xv);
+                }
                 da.add(pc.x, qv.x);
                 da.add(pc.y, qv.y);
                 da.add(pc.z, qv.z);
@@ -872,6 +884,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot4(long long n4, const float*
 }
 
 // x += alpha p;  r -= alpha q;  ||r||^2
+// x += alpha p (X; without it the update of x is deferred to the next
+// k_cg_p_matvec4), r -= alpha q, ||r||^2.
+template <bool X>
 __global__ void __launch_bounds__(RED_THREADS) k_cg_update4(long long n4, float* __restrict__ x,
                                                             float* __restrict__ r, const float* __restrict__ p,
                                                             const float* __restrict__ q, RedArgs ra) {
@@ -879,13 +894,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_update4(long long n4, float*
     DotAcc<float> da;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n4;
          c += (long long)gridDim.x * blockDim.x) {
-        float4 xv = ld4(x, 4 * c), rv = ld4(r, 4 * c);
-        const float4 pv = ld4(p, 4 * c), qv = ld4(q, 4 * c);
-        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+        float4 rv = ld4(r, 4 * c);
+        const float4 qv = ld4(q, 4 * c);
+        if (X) {
+            float4 xv = ld4(x, 4 * c);
+            const float4 pv = ld4(p, 4 * c);
+            xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+            xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+            st4(x, 4 * c, xv);
+        }
         rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
         rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
-        st4(x, 4 * c, xv);
         st4(r, 4 * c, rv);
         da.add(rv.x, rv.x);
         da.add(rv.y, rv.y);
@@ -904,7 +923,8 @@ void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra,
 }
 void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
                        const RedArgs& ra, cudaStream_t s) {
-    k_cg_update4<<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, x, r, p, q, ra);
+    if (x) k_cg_update4<true><<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, x, r, p, q, ra);
+    else k_cg_update4<false><<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, x, r, p, q, ra);
 }
 
 static ColShape shape4(const Dims& d, const Tune& tn = Tune{}) {
@@ -954,9 +974,9 @@ void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const flo
 bool fine4_ok(const Dims& d) { return d.nx % 4 == 0 && d.nx >= 16; }
 
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
-                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn) {
+                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn, float* x) {
     ColShape sh = shape4(d, tn);
-    k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, ra, tn.pf);
+    k_cg_p_matvec4<<<sh.grid, sh.block, 0, s>>>(d, A, z, p_in, p_out, q, x, ra, tn.pf);
 }
 void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z, float* res,
                       cudaStream_t s, const Tune& tn, bool after_zero_sweep, bool red_compressed) {

@@ -143,9 +143,11 @@ void launch_residual64(const Dims& d, Op<double> A, const double* diag, const do
 // r32 = r64 / sc[S_RMAX]; x32 = 0; ||r32||^2 -> S_R0 (and S_RR).
 void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
                      cudaStream_t s);
-// x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32)
+// x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32); p_last (optional):
+// x32 still lacks the last CG iteration's update, x32 + sc[S_ALPHA] p_last
+// in FP32 is used
 void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
-                      cudaStream_t s);
+                      cudaStream_t s, const float* p_last = nullptr);
 // E_out = max(E + dE, 0); sums for the photon balance into S_BAL (dE),
 // S_EMIT (eta), S_ABSORB (n_HI E^theta), S_ESUM (E^theta), the floor's
 // energy into S_FLOOR, sum dE^2 into S_DE2, sum E_out^2 into S_EN2
@@ -203,8 +205,11 @@ constexpr int TUNE_PF_MAX = 8;
 
 // ---- FP32 four-cells-per-thread sweeps (k_fine4.cu); need nx % 4 == 0
 bool fine4_ok(const Dims& d);
+// x (optional): also x += alpha_prev p_in, the previous iteration's update
+// of x (see launch_cg_update4 with x null)
 void launch_cg_p_matvec4(const Dims& d, Op<float> A, const float* z, const float* p_in, float* p_out,
-                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
+                         float* q, const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{},
+                         float* x = nullptr);
 // after_zero_sweep: z comes from one red/black sweep from z = 0 (black
 // last), so the residual is sum_f w_f z_nbr at red cells and 0 at black
 // ones; red_compressed (with after_zero_sweep, where red_compress_ok):
@@ -235,6 +240,8 @@ void launch_prolong_to4(const Dims& f, const Dims& c, const float* ec, const flo
                         cudaStream_t s);
 void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* zf, cudaStream_t s,
                          const Tune& tn = Tune{});
+// x null: r -= alpha q only, the update of x deferred to the next
+// launch_cg_p_matvec4 (and the last one to launch_ir_update)
 void launch_cg_update4(long long n, float* x, float* r, const float* p, const float* q,
                        const RedArgs& ra, cudaStream_t s);
 

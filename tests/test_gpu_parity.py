@@ -129,10 +129,16 @@ def test_vcycle_smoother_variants(fld, oracle, smoother, prepost):
     ctx.close()
 
 
-@pytest.mark.parametrize("n,per", [((64, 32, 48), (False, False, False)), ((128, 64, 32), (True, False, True)),
-                                   ((96, 96, 64), (False, True, False))])
+@pytest.mark.parametrize("n,per,tail", [((64, 32, 48), (False, False, False), 32768),
+                                        ((128, 64, 32), (True, False, True), 32768),
+                                        ((96, 96, 64), (False, True, False), 32768),
+                                        # nx = 4 mod 8: the zero-guess residual in the full layout
+                                        ((100, 24, 24), (False, False, False), 32768),
+                                        ((100, 24, 24), (True, True, False), 32768),
+                                        # no persistent tail: four-cell kernels on the coarse levels too
+                                        ((128, 96, 64), (False, False, True), 0)])
 @pytest.mark.parametrize("pre", [1, 2])
-def test_mixed_vcycle_parity(fld, oracle, n, per, pre):
+def test_mixed_vcycle_parity(fld, oracle, n, per, tail, pre):
     # the FP32 cycle of a mixed context against the oracle's FP64 cycle.  With
     # one pre-sweep the residual takes the zero-guess form (the weighted sum
     # of the black neighbours at red cells, 0 at black cells), which equals
@@ -141,7 +147,7 @@ def test_mixed_vcycle_parity(fld, oracle, n, per, pre):
     case = synth.random_case(n, seed=400 + sum(n), periodic=per, E_decades=(-20, -14))
     op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
     p = case.params
-    p.precision, p.pre, p.post = synth.PREC_MIXED, pre, 1
+    p.precision, p.pre, p.post, p.tail_cells = synth.PREC_MIXED, pre, 1, tail
     ctx = fld.fld_create(case.grid, p)
     fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
     x = np.random.default_rng(11).standard_normal(case.grid.shape)
