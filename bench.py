@@ -451,7 +451,8 @@ def main():
         from paper_1306_0645_gb300 import serving
         reqs = synth.request_stream(count=args.serve_requests, rate=args.serve_rate, seed=5 + rank)
         srv = serving.Server(budget_bytes=40e9, workers=args.serve_workers)
-        srv.run(synth.request_stream(count=4 * args.serve_workers, rate=1e9, seed=99), realtime=False)
+        # every worker's resident context and solve graphs for every size
+        srv.warm([16, 32, 48, 64, 96, 128])
         res = srv.run(reqs, realtime=True)
         srv.close()
         serving_out = serving.summarize(res)

@@ -213,6 +213,24 @@ class Server:
         return out
 
     # ------------------------------------------------------------ the loop
+    def warm(self, sizes: Sequence[int], sources: int = 4) -> List[Result]:
+        """Build every worker's resident context for each grid size (and, when
+        batching, the first context of its batch pool) and step it once, so
+        that allocations and the captured CUDA graphs of the solve exist before
+        requests arrive; returns the warm-up results."""
+        self.torch.cuda.set_device(self.device)
+        t0 = time.perf_counter()
+        out: List[Result] = []
+        for w in range(self.workers):
+            for i, n in enumerate(sizes):
+                r = synth.Request(-1 - i, 0.0, int(n), seed=1000 * w + i, sources=sources)
+                if self.footprint(r.n) <= 0 or self.footprint(r.n) > self.budget:
+                    continue
+                out.append(self.step_one(w, r, t0))
+                if self.batch > 1:
+                    out.extend(self.step_batch(w, [r], t0))
+        return out
+
     def run(self, requests: Sequence[synth.Request], realtime: bool = True) -> List[Result]:
         """Serve requests as they arrive (arrival times in s from now when
         realtime, else all at once); returns results in request order."""

@@ -165,3 +165,25 @@ def test_cancellation_before_a_worker_takes_the_request(serving):
             assert r.status == 0 and r.E is not None
     s = serving.summarize(res)
     assert s["cancelled"] == len(drop) and s["ok"] == len(reqs) - len(drop) and s["failed"] == 0
+
+
+@pytest.mark.parametrize("batch", [1, 3])
+def test_warm_builds_every_resident_context(serving, batch):
+    # warm(): one step per worker and size, so no request pays for a context
+    # or graph build; a warmed server gives the same results as a cold one
+    sizes = (16, 32, 48)
+    reqs = small_stream(12, seed=21)
+    cold = serving.Server(workers=2, keep_results=True)
+    rc = cold.run(reqs, realtime=False)
+    cold.close()
+    srv = serving.Server(workers=2, keep_results=True, batch=batch)
+    warm = srv.warm(sizes)
+    assert len(warm) == 2 * len(sizes) * (2 if batch > 1 else 1)
+    assert all(r.status == 0 and r.iters > 0 for r in warm)
+    for w in range(2):
+        assert sorted(srv._ctx[w]) == list(sizes)
+    rw = srv.run(reqs, realtime=False)
+    srv.close()
+    for a, b in zip(rc, rw):
+        assert a.status == 0 and b.status == 0
+        assert np.array_equal(a.E, b.E)
