@@ -288,6 +288,20 @@ inline ColShape col_shape(const Dims& d, int threads = 256, int target_blocks = 
         const long long c = (long long)k * nxy_ + (long long)j * (d).nx + i;
 #define COL_END }
 
+// The same walk over z-blocks zb0 .. zb0 + gridDim.z - 1 of a decomposition
+// of the planes into blocks of kch planes (a launch that covers a range of
+// whole z-blocks of a larger grid; zb0 = 0 and kch = ceil(nz / gridDim.z)
+// is COL_BEGIN).
+#define COL_BEGIN_ZB(d, zb0, kch)                                                       \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;                                \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;                                \
+    const int k0_ = ((zb0) + (int)blockIdx.z) * (kch);                                  \
+    const int k1_ = min((d).nz, k0_ + (kch));                                           \
+    const bool inb_ = i < (d).nx && j < (d).ny;                                         \
+    const long long nxy_ = (long long)(d).nx * (d).ny;                                  \
+    for (int k = inb_ ? k0_ : k1_; k < k1_; k++) {                                      \
+        const long long c = (long long)k * nxy_ + (long long)j * (d).nx + i;
+
 // Decompose a flat cell index.
 __device__ __forceinline__ void cell_ijk(long long c, const Dims& d, int& i, int& j, int& k) {
     long long t = c / d.nx;

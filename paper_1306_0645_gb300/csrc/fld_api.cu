@@ -1,6 +1,7 @@
 // fld_api.cu -- the C ABI of libfld.so (declared in include/fld.h): context
 // and hierarchy management, the MG-preconditioned CG driver (Table 1), the
 // mixed-precision iterative-refinement driver, and the step wrapper.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -239,6 +240,8 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
 
 }  // namespace
 
+constexpr int MAX_CHUNKS = 16;
+
 struct fld_ctx {
     fld_grid g;
     fld_params p;
@@ -298,6 +301,10 @@ struct fld_ctx {
     // copy engines, forked from and joined to the context's stream
     cudaStream_t cstream[4];
     cudaEvent_t cfork, cjoin[4];
+    // overlapped host-buffer steps: one event per plane chunk and the
+    // chunks' reduction slots (MAX_CHUNKS x NUM_SLOTS)
+    cudaEvent_t chunk_ev[MAX_CHUNKS];
+    double* chunk_sc;
 };
 
 namespace {
@@ -911,6 +918,9 @@ void free_ctx(fld_ctx* c) {
         if (c->cjoin[q]) cudaEventDestroy(c->cjoin[q]);
     }
     if (c->cfork) cudaEventDestroy(c->cfork);
+    for (int q = 0; q < MAX_CHUNKS; q++)
+        if (c->chunk_ev[q]) cudaEventDestroy(c->chunk_ev[q]);
+    if (c->chunk_sc) cudaFree(c->chunk_sc);
     if (c->h_one) cudaFreeHost(c->h_one);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
@@ -992,27 +1002,41 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
     return FLD_OK;
 }
 
-// Enqueue the assembly (Sec. 2 limiter, Sec. 3.2 system) and the multigrid
-// setup, then the scalars to the host mirror; assemble_finish reads them.
-fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
-    if (!c) return set_err(FLD_EINVAL, "null context");
-    if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
-    cudaStream_t s = c->s;
-    c->assembled = false;
-    CUDA_TRY(cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), s));
+// Assembly (Sec. 2 limiter, Sec. 3.2 system) and multigrid setup.
+//
+// Fine-level faces over the z-blocks [zb0, zb0 + nzb) of the assembly
+// decomposition (nzb < 0: all): limiter and weights, then the FP64 pass over
+// the faces the screen listed.  frac: the share of the cells, for the
+// launch statistics.
+void assemble_faces_range(fld_ctx* c, const double* E, const double* nHI, const double* eta, int zb0,
+                          int nzb, double frac) {
     Level& L0 = c->L[0];
     Op<float> op32{};
     if (c->mixed) op32 = L0.A32;
-    const double n0 = (double)L0.d.n;
+    const double n0 = (double)L0.d.n * frac;
     { KScope k(c, K_ASM_FACES, n0 * (56.0 + (c->mixed ? 16.0 : 0.0)));
-      launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, c->flist, s); }
+      launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, c->flist, c->s, zb0, nzb); }
     if (c->flist.entries) {
         KScope k(c, K_ASM_FIX, 0.0);
-        launch_assemble_fix(L0.d, c->pd, E, nHI, L0.A64, op32, c->flist, s);
+        launch_assemble_fix(L0.d, c->pd, E, nHI, L0.A64, op32, c->flist, c->s, zb0, nzb);
     }
-    { KScope k(c, K_ASM_RHS, n0 * (64.0 + (c->mixed ? 28.0 : 8.0)));
-      launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr,
-                          L0.bnd, red(c, R_STORE_SUM_MAX, S_BB, S_RMAX), s); }
+}
+
+// Right-hand side over z-blocks (it needs the faces of the z-block above).
+void assemble_rhs_range(fld_ctx* c, const double* E, const double* nHI, const double* eta, int zb0, int nzb,
+                        double frac, const RedArgs& ra) {
+    Level& L0 = c->L[0];
+    Op<float> op32{};
+    if (c->mixed) op32 = L0.A32;
+    KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * (64.0 + (c->mixed ? 28.0 : 8.0)));
+    launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr, L0.bnd, ra,
+                        c->s, zb0, nzb);
+}
+
+// The coarse levels, the coarsest-grid setup, then the scalars to the host
+// mirror (assemble_finish reads them).
+fld_status assemble_coarse(fld_ctx* c) {
+    cudaStream_t s = c->s;
     for (int l = 1; l < c->nl; l++) {
         Level& F = c->L[l - 1];
         Level& C = c->L[l];
@@ -1036,6 +1060,19 @@ fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, cons
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, s));
     return FLD_OK;
+}
+
+// Enqueue the whole assembly: fine-level faces, limiter and right-hand
+// side, coarse levels and coarsest-grid setup, then the scalars to the host
+// mirror; assemble_finish reads them.
+fld_status assemble_enqueue(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+    if (!c) return set_err(FLD_EINVAL, "null context");
+    if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
+    c->assembled = false;
+    CUDA_TRY(cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), c->s));
+    assemble_faces_range(c, E, nHI, eta, 0, -1, 1.0);
+    assemble_rhs_range(c, E, nHI, eta, 0, -1, 1.0, red(c, R_STORE_SUM_MAX, S_BB, S_RMAX));
+    return assemble_coarse(c);
 }
 
 // After the assembly's scalars arrived: input checks.
@@ -1147,10 +1184,14 @@ void finalize_info(fld_ctx* c, fld_info* inf) {
     inf->ms = ms;
 }
 
-fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
+// The step after its assembly has been enqueued (assembly status st).
+fld_status step_after_assembly(fld_ctx* c, fld_status st, double* E, const double* nHI, const double* eta,
+                               fld_info* info) {
     fld_info inf{};
-    CUDA_TRY(cudaEventRecord(c->e0, c->s));
-    fld_status st = assemble_impl(c, E, nHI, eta);
+    if (!st) {
+        if (cudaStreamSynchronize(c->s) != cudaSuccess) st = set_err(FLD_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+        else st = assemble_finish(c);
+    }
     if (st) {
         inf.status = st;
         if (info) *info = inf;
@@ -1169,6 +1210,11 @@ fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta
     inf.status = FLD_OK;
     if (info) *info = inf;
     return FLD_OK;
+}
+
+fld_status step_impl(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
+    CUDA_TRY(cudaEventRecord(c->e0, c->s));
+    return step_after_assembly(c, assemble_enqueue(c, E, nHI, eta), E, nHI, eta, info);
 }
 
 
@@ -1640,16 +1686,21 @@ fld_status fld_step(fld_ctx* c, double* E, const double* nHI, const double* eta,
 // Copies of host-buffer steps: each array in chunks spread over the side
 // streams (several copy engines share the host link), ordered after the
 // context stream's work so far and joined back into it.
-fld_status split_copies(fld_ctx* c, int narr, void* const* dst, const void* const* src, size_t bytes,
-                        cudaMemcpyKind kind) {
-    constexpr int NS = 4;
+fld_status copy_streams(fld_ctx* c) {
     if (!c->cstream[0]) {
-        for (int q = 0; q < NS; q++) {
+        for (int q = 0; q < 4; q++) {
             CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream[q], cudaStreamNonBlocking));
             CUDA_TRY(cudaEventCreateWithFlags(&c->cjoin[q], cudaEventDisableTiming));
         }
         CUDA_TRY(cudaEventCreateWithFlags(&c->cfork, cudaEventDisableTiming));
     }
+    return FLD_OK;
+}
+
+fld_status split_copies(fld_ctx* c, int narr, void* const* dst, const void* const* src, size_t bytes,
+                        cudaMemcpyKind kind) {
+    constexpr int NS = 4;
+    if (fld_status st = copy_streams(c)) return st;
     CUDA_TRY(cudaEventRecord(c->cfork, c->s));
     for (int q = 0; q < NS; q++) CUDA_TRY(cudaStreamWaitEvent(c->cstream[q], c->cfork, 0));
     const size_t chunk = ((bytes + NS - 1) / NS + 255) / 256 * 256;
@@ -1666,6 +1717,65 @@ fld_status split_copies(fld_ctx* c, int narr, void* const* dst, const void* cons
     return FLD_OK;
 }
 
+// Whether the host-buffer step overlaps its input transfer with the
+// assembly: the faces of plane 0 need plane nz - 1 on a periodic z axis
+// (the last chunk), and small grids gain nothing.
+bool overlap_host_step(const fld_ctx* c) {
+    const Dims& d = c->L[0].d;
+    return !d.pz && d.n >= (1LL << 21) && asm_shape(d).nzb >= 2;
+}
+
+// Enqueue the input transfer of a host-buffer step overlapped with the
+// fine-level assembly.  The planes travel in chunks of whole z-blocks of
+// the assembly decomposition on one side stream, in order; the faces of a
+// chunk are formed as soon as it has arrived, its right-hand side once the
+// next chunk's faces exist (it needs the z faces above it).  Each chunk's
+// right-hand-side reductions go to slots of their own, summed (||b||^2) and
+// maximised (max |b|) in chunk order afterwards.  Then the coarse levels.
+fld_status assemble_host_overlapped(fld_ctx* c, const double* E, const double* nHI, const double* eta) {
+    Level& L0 = c->L[0];
+    const Dims& d = L0.d;
+    const AsmShape a = asm_shape(d);
+    const int zbc = std::max((a.nzb + MAX_CHUNKS - 1) / MAX_CHUNKS, (a.nzb + 7) / 8);   // z-blocks per chunk
+    const int nch = (a.nzb + zbc - 1) / zbc;
+    if (fld_status st = copy_streams(c)) return st;
+    for (int q = 0; q < nch; q++)
+        if (!c->chunk_ev[q]) CUDA_TRY(cudaEventCreateWithFlags(&c->chunk_ev[q], cudaEventDisableTiming));
+    if (!c->chunk_sc) CUDA_TRY(cudaMalloc(&c->chunk_sc, MAX_CHUNKS * NUM_SLOTS * sizeof(double)));
+    cudaStream_t s = c->s, cs = c->cstream[0];
+    c->assembled = false;
+    CUDA_TRY(cudaMemsetAsync(c->sc, 0, NUM_SLOTS * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(c->chunk_sc, 0, (size_t)nch * NUM_SLOTS * sizeof(double), s));
+    // the staging buffers are free once the context's stream has reached here
+    CUDA_TRY(cudaEventRecord(c->cfork, s));
+    CUDA_TRY(cudaStreamWaitEvent(cs, c->cfork, 0));
+    const long long nxy = (long long)d.nx * d.ny;
+    const double* src[3] = {E, nHI, eta};
+    int p0[MAX_CHUNKS + 1];
+    for (int q = 0; q <= nch; q++) p0[q] = std::min(d.nz, q * zbc * a.kch);
+    for (int q = 0; q < nch; q++) {
+        const size_t off = (size_t)p0[q] * nxy, len = (size_t)(p0[q + 1] - p0[q]) * nxy * sizeof(double);
+        for (int v = 0; v < 3; v++)
+            CUDA_TRY(cudaMemcpyAsync(c->stage[v] + off, src[v] + off, len, cudaMemcpyHostToDevice, cs));
+        CUDA_TRY(cudaEventRecord(c->chunk_ev[q], cs));
+    }
+    auto chunk_red = [&](int q) {
+        RedArgs r = red(c, R_STORE_SUM_MAX, S_BB, S_RMAX);
+        r.sc = c->chunk_sc + (size_t)q * NUM_SLOTS;
+        return r;
+    };
+    auto frac = [&](int q) { return (double)(p0[q + 1] - p0[q]) / d.nz; };
+    const double *Es = c->stage[0], *ns = c->stage[1], *es = c->stage[2];
+    for (int q = 0; q < nch; q++) {
+        CUDA_TRY(cudaStreamWaitEvent(s, c->chunk_ev[q], 0));
+        assemble_faces_range(c, Es, ns, es, q * zbc, zbc, frac(q));
+        if (q > 0) assemble_rhs_range(c, Es, ns, es, (q - 1) * zbc, zbc, frac(q - 1), chunk_red(q - 1));
+    }
+    assemble_rhs_range(c, Es, ns, es, (nch - 1) * zbc, zbc, frac(nch - 1), chunk_red(nch - 1));
+    launch_combine_chunks(c->chunk_sc, nch, c->sc, S_BB, S_RMAX, s);
+    return assemble_coarse(c);
+}
+
 fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double* eta, fld_info* info) {
     if (!c) return set_err(FLD_EINVAL, "null context");
     if (!E || !nHI || !eta) return set_err(FLD_EINVAL, "null field pointer");
@@ -1678,13 +1788,19 @@ fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double*
                 return set_err(FLD_ENOMEM, "staging allocation failed");
             }
         }
-    {
+    fld_status st;
+    if (overlap_host_step(c)) {
+        CUDA_TRY(cudaEventRecord(c->e0, c->s));
+        st = assemble_host_overlapped(c, E, nHI, eta);
+        // no transfer from the caller's buffers may outlive a failed call
+        if (st && c->cstream[0]) cudaStreamSynchronize(c->cstream[0]);
+        st = step_after_assembly(c, st, c->stage[0], c->stage[1], c->stage[2], info);
+    } else {
         void* dst[3] = {c->stage[0], c->stage[1], c->stage[2]};
         const void* src[3] = {E, nHI, eta};
-        fld_status st = split_copies(c, 3, dst, src, bytes, cudaMemcpyHostToDevice);
-        if (st) return st;
+        if ((st = split_copies(c, 3, dst, src, bytes, cudaMemcpyHostToDevice))) return st;
+        st = step_impl(c, c->stage[0], c->stage[1], c->stage[2], info);
     }
-    fld_status st = step_impl(c, c->stage[0], c->stage[1], c->stage[2], info);
     if (st) return st;
     {
         void* dst[1] = {E};

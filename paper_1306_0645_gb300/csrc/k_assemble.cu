@@ -145,17 +145,19 @@ __device__ __forceinline__ bool capped32(float e1, float e2, float kL1, float kL
 __global__ void __launch_bounds__(256) k_assemble_faces(Dims d, PhysDev p, const double* __restrict__ E,
                                                        const double* __restrict__ nHI,
                                                        const double* __restrict__ eta, Op<double> op,
-                                                       Op<float> op32, double* sc, FaceList fl) {
+                                                       Op<float> op32, double* sc, FaceList fl, int zb0,
+                                                       int kch) {
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     bool bad = false;
     const bool screen = p.limiter == 0;
     __shared__ unsigned s_cnt;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    // the block's index in the whole grid's decomposition (its face list)
+    const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * (zb0 + blockIdx.z));
     if (tid == 0) s_cnt = 0u;
     __syncthreads();
     unsigned* seg = fl.entries ? fl.entries + bid * fl.cap : nullptr;
-    COL_BEGIN(d)
+    COL_BEGIN_ZB(d, zb0, kch)
         const double Ec = E[c], nc = nHI[c];
         bad |= !valid_bits(Ec) || !valid_bits(nc) || !valid_bits(eta[c]);
         const double kc = nc * p.sigma;
@@ -255,10 +257,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
                                                              const double* __restrict__ nHI,
                                                              const double* __restrict__ eta, Op<double> op,
                                                              Op<float> op32, double* __restrict__ b,
-                                                             double* __restrict__ diag64, Bnd bnd, RedArgs ra) {
+                                                             double* __restrict__ diag64, Bnd bnd, RedArgs ra,
+                                                             int zb0, int kch) {
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     double acc[2] = {0.0, 0.0};
-    COL_BEGIN(d)
+    COL_BEGIN_ZB(d, zb0, kch)
         const double Ec = E[c];
         double flux = 0.0, wsum = 0.0;
         float wsum32 = 0.0f;
@@ -331,43 +334,65 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
     grid_reduce<2>(acc, ismax, ra);
 }
 
+AsmShape asm_shape(const Dims& d) {
+    AsmShape a;
+    a.sh = col_shape(d, 256, 152 * 64);
+    a.kch = (d.nz + (int)a.sh.grid.z - 1) / (int)a.sh.grid.z;
+    a.nzb = (d.nz + a.kch - 1) / a.kch;
+    return a;
+}
+
+// z-blocks [zb0, zb0 + nzb) of the decomposition (nzb < 0: all of them)
+static dim3 zb_grid(const AsmShape& a, int zb0, int& nzb) {
+    if (nzb < 0 || zb0 + nzb > a.nzb) nzb = a.nzb - zb0;
+    return dim3(a.sh.grid.x, a.sh.grid.y, (unsigned)nzb);
+}
+
 void launch_assemble_faces(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                            const double* eta, Op<double> op, Op<float> op32, double* sc,
-                           FaceList fl, cudaStream_t s) {
-    ColShape sh = col_shape(d);
-    k_assemble_faces<<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, sc, fl);
+                           FaceList fl, cudaStream_t s, int zb0, int nzb) {
+    const AsmShape a = asm_shape(d);
+    const dim3 g = zb_grid(a, zb0, nzb);
+    if (nzb <= 0) return;
+    k_assemble_faces<<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, sc, fl, zb0, a.kch);
 }
 
 void launch_assemble_fix(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
-                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s) {
+                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s, int zb0, int nzb) {
     if (!fl.entries) return;
-    ColShape sh = col_shape(d);
-    const unsigned blocks = sh.grid.x * sh.grid.y * sh.grid.z;
-    k_assemble_fix<<<blocks, 256, 0, s>>>(d, p, E, nHI, op, op32, fl);
+    const AsmShape a = asm_shape(d);
+    zb_grid(a, zb0, nzb);
+    if (nzb <= 0) return;
+    const long long per_zb = (long long)a.sh.grid.x * a.sh.grid.y;
+    FaceList f = fl;
+    f.entries = fl.entries + per_zb * zb0 * fl.cap;
+    f.counts = fl.counts + per_zb * zb0;
+    k_assemble_fix<<<(unsigned)(per_zb * nzb), 256, 0, s>>>(d, p, E, nHI, op, op32, f);
 }
 
 void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap) {
-    ColShape sh = col_shape(d);
-    *blocks = (long long)sh.grid.x * sh.grid.y * sh.grid.z;
-    const long long kch = (d.nz + sh.grid.z - 1) / sh.grid.z;
-    const long long cells = (long long)sh.block.x * sh.block.y * kch;
+    const AsmShape a = asm_shape(d);
+    *blocks = (long long)a.sh.grid.x * a.sh.grid.y * a.nzb;
+    const long long cells = (long long)a.sh.block.x * a.sh.block.y * a.kch;
     // 40% of the block's faces; a fuller block computes the rest in place
     *cap = (limiter == 0 && d.n <= (1LL << 30)) ? (int)((3 * cells * 2 + 4) / 5) : 0;
 }
 
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
-                         Bnd bnd, const RedArgs& ra, cudaStream_t s) {
-    ColShape sh = col_shape(d);
+                         Bnd bnd, const RedArgs& ra, cudaStream_t s, int zb0, int nzb) {
+    const AsmShape a = asm_shape(d);
+    const dim3 g = zb_grid(a, zb0, nzb);
+    if (nzb <= 0) return;
     const bool be = p.theta == 1.0, dir = p.dmask != 0;
     if (be && !dir)
-        k_assemble_rhs<true, false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+        k_assemble_rhs<true, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra, zb0, a.kch);
     else if (be)
-        k_assemble_rhs<true, true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+        k_assemble_rhs<true, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra, zb0, a.kch);
     else if (!dir)
-        k_assemble_rhs<false, false><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+        k_assemble_rhs<false, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra, zb0, a.kch);
     else
-        k_assemble_rhs<false, true><<<sh.grid, sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra);
+        k_assemble_rhs<false, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, op, op32, b, diag64, bnd, ra, zb0, a.kch);
 }
 
 // Photons through the Dirichlet faces of side sd (sum, and sum of absolute

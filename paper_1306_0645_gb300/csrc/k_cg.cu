@@ -222,7 +222,27 @@ __global__ void k_cg_check(cudaGraphConditionalHandle h, cudaGraphConditionalHan
     if (both) cudaGraphSetConditional(h2, cont ? 1u : 0u);
 }
 
+// Reductions done in chunks (slots of nch consecutive NUM_SLOTS blocks):
+// slot s_sum summed and s_max maximised in chunk order, a non-finite flag
+// of any chunk kept.
+__global__ void k_combine_chunks(const double* __restrict__ csc, int nch, double* sc, int s_sum, int s_max) {
+    double sum = 0.0, mx = 0.0, nf = 0.0;
+    for (int q = 0; q < nch; q++) {
+        const double* v = csc + (long long)q * NUM_SLOTS;
+        sum += v[s_sum];
+        mx = fmax(mx, v[s_max]);
+        nf = fmax(nf, v[S_NONFINITE]);
+    }
+    sc[s_sum] = sum;
+    sc[s_max] = mx;
+    if (nf != 0.0) sc[S_NONFINITE] = nf;
+}
+
 // ---------------------------------------------------------------- launchers
+
+void launch_combine_chunks(const double* chunk_sc, int nch, double* sc, int s_sum, int s_max, cudaStream_t s) {
+    k_combine_chunks<<<1, 1, 0, s>>>(chunk_sc, nch, sc, s_sum, s_max);
+}
 
 void launch_f64_to_f32(long long n, const double* a, float* b, cudaStream_t s) {
     k_f64_to_f32<<<grid_blocks(n, 256), 256, 0, s>>>(n, a, b);

@@ -61,14 +61,26 @@ struct FaceList {
 };
 
 // ---- assembly (k_assemble.cu)
+// The assembly kernels walk the planes in nzb z-blocks of kch planes each
+// (grid sh); a launch covers the z-blocks [zb0, zb0 + nzb) (nzb < 0: all),
+// so the assembly of a grid can follow its planes as they arrive.  The
+// face lists belong to the blocks of this decomposition.
+struct AsmShape {
+    ColShape sh;
+    int kch, nzb;
+};
+AsmShape asm_shape(const Dims& d);
 // Pass 1: opacity, face limiter and weights (FP64, plus FP32 copies of the
 // weights and mass term when op32.m != nullptr); flags invalid inputs.
+// Reads E and n_HI of planes zb0 * kch - 1 .. (zb0 + nzb) * kch - 1.
 void launch_assemble_faces(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                            const double* eta, Op<double> op, Op<float> op32, double* sc,
-                           FaceList fl, cudaStream_t s);
-// FP64 limiter for the listed faces (one block per list segment).
+                           FaceList fl, cudaStream_t s, int zb0 = 0, int nzb = -1);
+// FP64 limiter for the listed faces of those z-blocks (one block per list
+// segment).
 void launch_assemble_fix(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
-                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s);
+                         Op<double> op, Op<float> op32, FaceList fl, cudaStream_t s, int zb0 = 0,
+                         int nzb = -1);
 // Size of the face lists for a level: blocks of the faces launch and
 // entries per block (0 when lists are not used).
 void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap);
@@ -76,10 +88,11 @@ void face_list_shape(const Dims& d, int limiter, long long* blocks, int* cap);
 // op32.invd), the FP64 diagonal if diag64, ||b||^2 into slot0 and max |b|
 // into slot1.  Cells on a Dirichlet face (p.dmask) also get the face's
 // limiter weight: stored in bnd, added to m (FP64 and FP32) and its flux
-// to b.
+// to b.  Needs the weights of the planes one past its z-blocks (upper
+// z faces) and E of the planes on either side.
 void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const double* nHI,
                          const double* eta, Op<double> op, Op<float> op32, double* b, double* diag64,
-                         Bnd bnd, const RedArgs& ra, cudaStream_t s);
+                         Bnd bnd, const RedArgs& ra, cudaStream_t s, int zb0 = 0, int nzb = -1);
 // Photons through the Dirichlet faces of side s over the step (before the
 // finalisation overwrites E): sum of w_b (inv_theta (E - E_b) + dE) into
 // slot S_OUT0 + s and the sum of its absolute values into S_OUTABS0 + s
@@ -134,6 +147,10 @@ void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s);
 // Device-side CG convergence test: sc[S_KITER] += 1 and the conditional h
 // set to continue while sc[S_RR] > sc[S_THRESH], S_KITER < S_MAXIT and no
 // non-finite reduction (one thread).
+// Reductions done in nch chunks, each into its own block of NUM_SLOTS
+// slots: sc[s_sum] = the chunks' s_sum summed in chunk order, sc[s_max] =
+// their s_max maximised, and the non-finite flag of any chunk.
+void launch_combine_chunks(const double* chunk_sc, int nch, double* sc, int s_sum, int s_max, cudaStream_t s);
 void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s,
                      const cudaGraphConditionalHandle* h2 = nullptr);
 // r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.  diag (may
