@@ -57,13 +57,13 @@ struct Level {
 
 // Kernel classes for launch counting and optional CUDA-event timing.
 enum KClass {
-    K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_TO_F32, K_COARSE_SETUP, K_SMOOTH_ZERO,
+    K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
     K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
-    "assemble_faces", "assemble_rhs", "coarsen", "invd", "to_f32", "coarse_setup", "smooth_zero",
+    "assemble_faces", "assemble_rhs", "coarsen", "invd", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
     "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail"};
@@ -194,9 +194,11 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     const size_t ts = mixed ? sizeof(float) : sizeof(double);
     for (int l = 0; l < nl; l++) {
         const size_t n = (size_t)dims[l][0] * dims[l][1] * dims[l][2];
-        for (int q = 0; q < 4; q++) buf(l, "A64", q, n * sizeof(double));
-        // the FP64 inverse diagonal serves the FP64 cycle only (the mixed
-        // solver's cycle is FP32 on every level)
+        // the coarse levels serve only the cycle, FP32 on every level of the
+        // mixed solver: FP64 operators there for the FP64 solver only (the
+        // fine level keeps its FP64 operator for the refinement residual)
+        if (!(mixed && l > 0))
+            for (int q = 0; q < 4; q++) buf(l, "A64", q, n * sizeof(double));
         if (!mixed) buf(l, "A64", 4, n * sizeof(double));
         if (mixed)
             for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
@@ -1037,26 +1039,35 @@ void assemble_rhs_range(fld_ctx* c, const double* E, const double* nHI, const do
 // mirror (assemble_finish reads them).
 fld_status assemble_coarse(fld_ctx* c) {
     cudaStream_t s = c->s;
+    // the mixed solver's coarse operators are formed in FP32 from the FP32
+    // operator of the level above (its FP32 cycle is their only reader)
     for (int l = 1; l < c->nl; l++) {
         Level& F = c->L[l - 1];
         Level& C = c->L[l];
         const double nf = (double)F.d.n, nc = (double)C.d.n;
-        { KScope k(c, K_COARSEN, 32.0 * (nf + nc)); launch_coarsen(F.d, C.d, F.A64, C.A64, s); }
-        for (int sd = 0; sd < 6; sd++)
-            if ((C.bnd.mask >> sd) & 1) {
-                KScope k(c, K_COARSEN, 0.0);
-                launch_coarsen_bnd(F.d, C.d, sd, F.bnd, C.bnd, C.A64, s);
-            }
-        if (!c->mixed) { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
         if (c->mixed) {
-            { KScope k(c, K_TO_F32, 48.0 * nc); launch_to_f32(C.d, C.A64, C.A32, s); }
-            { KScope k(c, K_INVD, 36.0 * nc); launch_invd<float>(C.d, C.A32, C.A64, s); }
+            { KScope k(c, K_COARSEN, 16.0 * (nf + nc)); launch_coarsen<float>(F.d, C.d, F.A32, C.A32, s); }
+            for (int sd = 0; sd < 6; sd++)
+                if ((C.bnd.mask >> sd) & 1) {
+                    KScope k(c, K_COARSEN, 0.0);
+                    launch_coarsen_bnd<float>(F.d, C.d, sd, F.bnd, C.bnd, C.A32, s);
+                }
+            { KScope k(c, K_INVD, 20.0 * nc); launch_invd<float>(C.d, C.A32, C.A32, s); }
+        } else {
+            { KScope k(c, K_COARSEN, 32.0 * (nf + nc)); launch_coarsen<double>(F.d, C.d, F.A64, C.A64, s); }
+            for (int sd = 0; sd < 6; sd++)
+                if ((C.bnd.mask >> sd) & 1) {
+                    KScope k(c, K_COARSEN, 0.0);
+                    launch_coarsen_bnd<double>(F.d, C.d, sd, F.bnd, C.bnd, C.A64, s);
+                }
+            { KScope k(c, K_INVD, 40.0 * nc); launch_invd<double>(C.d, C.A64, C.A64, s); }
         }
     }
     Level& Lc = c->L[c->nl - 1];
     { const double nc = (double)Lc.d.n;
       KScope k(c, K_COARSE_SETUP, 16.0 * nc * nc);
-      launch_coarse_setup(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, c->mixed, s); }
+      if (c->mixed && c->nl > 1) launch_coarse_setup<float>(Lc.d, Lc.A32, c->dense, c->ainv, c->sc, true, s);
+      else launch_coarse_setup<double>(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, c->mixed, s); }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, s));
     return FLD_OK;

@@ -69,19 +69,23 @@ __device__ __forceinline__ T nbr_sum_prod(const Dims& d, const Op<T>& A, long lo
 
 // ------------------------------------------------------------ operators
 
-__global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
+// Rediscretised coarse operator in precision T (FP64 for the FP64 cycle;
+// FP32 from the FP32 operator for the mixed solver's cycle, which alone
+// reads the coarse levels there).
+template <class T>
+__global__ void k_coarsen(Dims f, Dims cd, Op<T> F, Op<T> C) {
     COL_BEGIN(cd)
         const int I = i, J = j, K = k;
         const long long fx = f.nx, fxy = (long long)f.nx * f.ny;
         const long long base = 2LL * I + fx * 2LL * J + fxy * 2LL * K;
-        double ms = 0.0;
+        T ms = 0;
 #pragma unroll
         for (int dk = 0; dk < 2; dk++)
 #pragma unroll
             for (int dj = 0; dj < 2; dj++)
 #pragma unroll
                 for (int di = 0; di < 2; di++) ms += F.m[base + di + fx * dj + fxy * dk];
-        double sx = 0.0, sy = 0.0, sz = 0.0;
+        T sx = 0, sy = 0, sz = 0;
 #pragma unroll
         for (int a = 0; a < 2; a++)
 #pragma unroll
@@ -90,10 +94,10 @@ __global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
                 sy += F.wy[base + a + fxy * b];
                 sz += F.wz[base + a + fx * b];
             }
-        C.m[c] = ms * 0.125;
-        C.wx[c] = sx * 0.0625;
-        C.wy[c] = sy * 0.0625;
-        C.wz[c] = sz * 0.0625;
+        C.m[c] = ms * (T)0.125;
+        C.wx[c] = sx * (T)0.0625;
+        C.wy[c] = sy * (T)0.0625;
+        C.wz[c] = sz * (T)0.0625;
     }
 }
 
@@ -102,7 +106,8 @@ __global__ void k_coarsen(Dims f, Dims cd, Op<double> F, Op<double> C) {
 // coarse mass term to the mean of the 8 children's m, which holds their
 // boundary weights / 8 = 2 w_c; the rediscretised mass term has w_c, so
 // w_c is taken back off.
-__global__ void k_coarsen_bnd(Dims f, Dims cd, int sd, Bnd F, Bnd C, Op<double> CA) {
+template <class T>
+__global__ void k_coarsen_bnd(Dims f, Dims cd, int sd, Bnd F, Bnd C, Op<T> CA) {
     const int a = sd >> 1, hi = sd & 1;
     const long long nfc = bnd_side_size(cd, sd);
     const long long offc = bnd_offset(cd, sd), offf = bnd_offset(f, sd);
@@ -117,27 +122,21 @@ __global__ void k_coarsen_bnd(Dims f, Dims cd, int sd, Bnd F, Bnd C, Op<double> 
         if (a == 0) { i = hi ? cd.nx - 1 : 0; j = u; k = v; }
         else if (a == 1) { i = u; j = hi ? cd.ny - 1 : 0; k = v; }
         else { i = u; j = v; k = hi ? cd.nz - 1 : 0; }
-        CA.m[i + (long long)cd.nx * (j + (long long)cd.ny * k)] -= wc;
+        T& mc = CA.m[i + (long long)cd.nx * (j + (long long)cd.ny * k)];
+        mc = (T)(mc - wc);
     }
 }
 
-template <class T>
-__global__ void k_invd(Dims d, Op<T> A, Op<double> A64) {
+// Inverse diagonal of A in precision T, the diagonal summed in the
+// precision S of the operator src it is formed from.
+template <class T, class S>
+__global__ void k_invd(Dims d, Op<T> A, Op<S> src) {
     COL_BEGIN(d)
-        double swu, sw;
+        S swu, sw;
         // u unused: pass m as a harmless array for the weight sum only
-        nbr_sums<double>(d, A64, c, i, j, k, A64.m, swu, sw);
-        const double diag = A64.m[c] + sw;
-        A.invd[c] = (T)(1.0 / diag);
-    }
-}
-
-__global__ void k_to_f32(Dims d, Op<double> A, Op<float> B) {
-    GRID_LOOP(c, d.n) {
-        B.m[c] = (float)A.m[c];
-        B.wx[c] = (float)A.wx[c];
-        B.wy[c] = (float)A.wy[c];
-        B.wz[c] = (float)A.wz[c];
+        nbr_sums<S>(d, src, c, i, j, k, src.m, swu, sw);
+        const S diag = src.m[c] + sw;
+        A.invd[c] = (T)((S)1 / diag);
     }
 }
 
@@ -279,7 +278,8 @@ __global__ void k_prolong_add(Dims f, Dims cd, const T* __restrict__ ec, T* __re
 
 // ---------------------------------------------------------- coarsest grid
 
-__global__ void k_dense_build(Dims d, Op<double> A, double* __restrict__ M) {
+template <class T>
+__global__ void k_dense_build(Dims d, Op<T> A, double* __restrict__ M) {
     const long long n = d.n;
     GRID_LOOP(c, n) {
         double* row = M + c * n;
@@ -291,8 +291,12 @@ __global__ void k_dense_build(Dims d, Op<double> A, double* __restrict__ M) {
         cell_ijk(c, d, i, j, k);
         double* row = M + c * n;
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-        double diag = A.m[c];
-        auto add = [&](double w, long long nb) { diag += w; row[nb] -= w; };
+        double diag = (double)A.m[c];
+        auto add = [&](T wt, long long nb) {
+            const double w = (double)wt;
+            diag += w;
+            row[nb] -= w;
+        };
         if (i > 0) add(A.wx[c], c - 1); else if (d.px) add(A.wx[c], c + d.nx - 1);
         if (i < d.nx - 1) add(A.wx[c + 1], c + 1); else if (d.px) add(A.wx[c - (d.nx - 1)], c - (d.nx - 1));
         if (j > 0) add(A.wy[c], c - sy); else if (d.py) add(A.wy[c], c + (long long)(d.ny - 1) * sy);
@@ -470,21 +474,19 @@ __global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* 
 
 static const int TPB = 256;
 
-void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s) {
+template <class T>
+void launch_coarsen(const Dims& f, const Dims& c, Op<T> F, Op<T> C, cudaStream_t s) {
     ColShape sh = col_shape(c);
-    k_coarsen<<<sh.grid, sh.block, 0, s>>>(f, c, F, C);
-}
-void launch_coarsen_bnd(const Dims& f, const Dims& c, int sd, Bnd F, Bnd C, Op<double> CA,
-                        cudaStream_t st) {
-    k_coarsen_bnd<<<grid_blocks(bnd_side_size(c, sd), 256), 256, 0, st>>>(f, c, sd, F, C, CA);
+    k_coarsen<T><<<sh.grid, sh.block, 0, s>>>(f, c, F, C);
 }
 template <class T>
-void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s) {
-    ColShape sh = col_shape(d);
-    k_invd<T><<<sh.grid, sh.block, 0, s>>>(d, A, A64);
+void launch_coarsen_bnd(const Dims& f, const Dims& c, int sd, Bnd F, Bnd C, Op<T> CA, cudaStream_t st) {
+    k_coarsen_bnd<T><<<grid_blocks(bnd_side_size(c, sd), 256), 256, 0, st>>>(f, c, sd, F, C, CA);
 }
-void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s) {
-    k_to_f32<<<grid_blocks(d.n, TPB), TPB, 0, s>>>(d, A, B);
+template <class T>
+void launch_invd(const Dims& d, Op<T> A, const Op<T>& src, cudaStream_t s) {
+    ColShape sh = col_shape(d);
+    k_invd<T, T><<<sh.grid, sh.block, 0, s>>>(d, A, src);
 }
 template <class T>
 void launch_smooth_zero(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s) {
@@ -524,9 +526,10 @@ void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaSt
 static size_t chol_smem_bytes(long long n, size_t ts) { return 2 * (size_t)n * (size_t)n * ts; }
 static const size_t CHOL_SMEM_MAX = 200 * 1024;
 
-void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc, bool fp32,
+template <class T>
+void launch_coarse_setup(const Dims& d, Op<T> A, double* dense, double* ainv, double* sc, bool fp32,
                          cudaStream_t s) {
-    k_dense_build<<<1, TPB, 0, s>>>(d, A, dense);
+    k_dense_build<T><<<1, TPB, 0, s>>>(d, A, dense);
     const size_t ts = fp32 ? sizeof(float) : sizeof(double);
     if (d.n <= GJ_MAX) {
         const size_t gb = (size_t)d.n * (size_t)d.n * ts;
@@ -566,7 +569,10 @@ void launch_coarse_apply(int n, const double* ainv, const T* r, T* z, cudaStream
 }
 
 #define INST(T)                                                                                    \
-    template void launch_invd<T>(const Dims&, Op<T>, const Op<double>&, cudaStream_t);              \
+    template void launch_invd<T>(const Dims&, Op<T>, const Op<T>&, cudaStream_t);                   \
+    template void launch_coarsen<T>(const Dims&, const Dims&, Op<T>, Op<T>, cudaStream_t);           \
+    template void launch_coarsen_bnd<T>(const Dims&, const Dims&, int, Bnd, Bnd, Op<T>, cudaStream_t); \
+    template void launch_coarse_setup<T>(const Dims&, Op<T>, double*, double*, double*, bool, cudaStream_t); \
     template void launch_smooth_zero<T>(const Dims&, Op<T>, const T*, T*, cudaStream_t);            \
     template void launch_rb_colour<T>(const Dims&, Op<T>, const T*, T*, int, cudaStream_t);         \
     template void launch_jacobi<T>(const Dims&, Op<T>, const T*, const T*, T*, double, bool,        \

@@ -101,15 +101,16 @@ void launch_bnd_outflow(const Dims& d, const PhysDev& p, int s, Bnd bnd, const d
                         const double* dE, const RedArgs& ra, cudaStream_t st);
 
 // ---- multigrid (k_mg.cu), T = float or double
-void launch_coarsen(const Dims& f, const Dims& c, Op<double> F, Op<double> C, cudaStream_t s);
+template <class T>
+void launch_coarsen(const Dims& f, const Dims& c, Op<T> F, Op<T> C, cudaStream_t s);
 // Coarse Dirichlet face weights of side s (sum of the 4 fine ones / 16);
 // the coarse mass term, which k_coarsen took as the mean of the children's
 // full m, gives back the difference: m_c -= w_c.  After launch_coarsen.
-void launch_coarsen_bnd(const Dims& f, const Dims& c, int s, Bnd F, Bnd C, Op<double> CA,
+template <class T>
+void launch_coarsen_bnd(const Dims& f, const Dims& c, int s, Bnd F, Bnd C, Op<T> CA,
                         cudaStream_t st);
 template <class T>
-void launch_invd(const Dims& d, Op<T> A, const Op<double>& A64, cudaStream_t s);
-void launch_to_f32(const Dims& d, Op<double> A, Op<float> B, cudaStream_t s);
+void launch_invd(const Dims& d, Op<T> A, const Op<T>& src, cudaStream_t s);
 template <class T>
 void launch_smooth_zero(const Dims& d, Op<T> A, const T* r, T* z, cudaStream_t s);
 template <class T>
@@ -125,7 +126,8 @@ template <class T>
 void launch_prolong_add(const Dims& f, const Dims& c, const T* ec, T* zf, cudaStream_t s);
 // Coarsest grid: dense matrix, Cholesky, explicit inverse (one CTA; in
 // shared memory and in FP32 when fp32 and the matrix fits, else FP64).
-void launch_coarse_setup(const Dims& d, Op<double> A, double* dense, double* ainv, double* sc, bool fp32,
+template <class T>
+void launch_coarse_setup(const Dims& d, Op<T> A, double* dense, double* ainv, double* sc, bool fp32,
                          cudaStream_t s);
 template <class T>
 void launch_coarse_apply(int n, const double* ainv, const T* r, T* z, cudaStream_t s);

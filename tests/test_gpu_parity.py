@@ -322,11 +322,12 @@ def test_host_buffer_step_matches_device_step(fld):
     ctx.close()
 
 
-@pytest.mark.parametrize("n,per,prec", [((128, 128, 128), (False, False, False), synth.PREC_MIXED),
-                                        ((160, 128, 144), (True, True, False), synth.PREC_MIXED),
-                                        ((128, 128, 160), (False, False, False), synth.PREC_FP64),
-                                        ((128, 128, 128), (False, False, True), synth.PREC_MIXED)])
-def test_overlapped_host_step_matches_device_step(fld, n, per, prec):
+@pytest.mark.parametrize("n,per,prec,outflow", [((128, 128, 128), (False, False, False), synth.PREC_MIXED, False),
+                                                ((160, 128, 144), (True, True, False), synth.PREC_MIXED, False),
+                                                ((128, 128, 160), (False, False, False), synth.PREC_FP64, False),
+                                                ((128, 128, 128), (False, False, True), synth.PREC_MIXED, False),
+                                                ((128, 128, 128), (False, False, False), synth.PREC_MIXED, True)])
+def test_overlapped_host_step_matches_device_step(fld, n, per, prec, outflow):
     # from 128^3 cells on a non-periodic z axis the host-buffer step moves
     # its inputs in plane chunks and assembles each chunk as it arrives, the
     # right-hand side's reductions summed per chunk; the per-cell arithmetic
@@ -334,6 +335,8 @@ def test_overlapped_host_step_matches_device_step(fld, n, per, prec):
     # iteration counts do (a periodic z axis takes the plain transfer)
     case = synth.config4(128, sources=256)
     g = synth.Grid(n, tuple(case.grid.h[a] for a in range(3)), per)
+    if outflow:   # Dirichlet faces: the chunked right-hand side also writes their weights
+        g = g.outflow_upper()
     rng = np.random.default_rng(17)
     E0 = 10.0 ** rng.uniform(-20, -14, g.shape)
     nHI = 10.0 ** rng.uniform(-5, -2, g.shape)
