@@ -215,7 +215,13 @@ fld_status fld_step(fld_ctx* ctx, double* E, const double* n_HI,
 
 /* fld_step with HOST arrays: copies E, n_HI, eta to the context's device
  * staging buffers, steps, and copies E back.  Host arrays may be pageable
- * or pinned; pinned memory gives full copy bandwidth. */
+ * or pinned; pinned memory gives full copy bandwidth.  From 128^3 cells on
+ * a non-periodic z axis the inputs travel in chunks of planes and each
+ * chunk is assembled as soon as it has arrived, so the transfer overlaps
+ * the assembly; E comes out as from fld_step (bit for bit when the
+ * iteration counts agree; ||b||^2 is summed per chunk).  The call returns
+ * when E is back in host memory, also on failure (no transfer from the
+ * caller's buffers outlives the call). */
 fld_status fld_step_host(fld_ctx* ctx, double* E, const double* n_HI,
                          const double* eta, fld_info* info);
 
