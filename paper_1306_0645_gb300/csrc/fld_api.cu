@@ -1812,7 +1812,12 @@ fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double*
         if ((st = split_copies(c, 3, dst, src, bytes, cudaMemcpyHostToDevice))) return st;
         st = step_impl(c, c->stage[0], c->stage[1], c->stage[2], info);
     }
-    if (st) return st;
+    if (st) {
+        // no transfer from the caller's buffers may outlive a failed call
+        for (int q = 0; q < 4; q++)
+            if (c->cstream[q]) cudaStreamSynchronize(c->cstream[q]);
+        return st;
+    }
     {
         void* dst[1] = {E};
         const void* src[1] = {c->stage[0]};
