@@ -566,3 +566,25 @@ def test_results_do_not_depend_on_launch_shapes(fld):
     assert steps[0][1:] == steps[1][1:]
     e0 = case.E.ravel()
     assert rel_max(steps[0][0].ravel() - e0, steps[1][0].ravel() - e0) < 1e-6
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_host_step_failure_then_success(fld, n):
+    # an invalid input through the host-buffer step (plain transfer at 32^3,
+    # overlapped at 128^3) fails with EINVAL and leaves E as it was; the same
+    # context then steps correctly
+    case = synth.config1(n)
+    ctx = fld.fld_create(case.grid, case.params)
+    Eh = case.E.copy()
+    Eh.ravel()[5] = -1.0
+    before = Eh.copy()
+    with pytest.raises(fld.FldError) as e:
+        fld.fld_step_host(ctx, Eh, case.nHI, case.eta)
+    assert e.value.status == fld.FLD_EINVAL
+    assert np.array_equal(Eh, before)
+    Eh = case.E.copy()
+    fld.fld_step_host(ctx, Eh, case.nHI, case.eta)
+    E = dev(case.E)
+    fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
+    ctx.close()
+    assert np.array_equal(Eh.ravel(), host(E).ravel())
