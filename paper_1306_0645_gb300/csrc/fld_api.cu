@@ -707,6 +707,7 @@ cudaGraphExec_t loop_graph(fld_ctx* c) {
             pcg_iteration<T>(c, 1, false);
             launch_cg_check(h, c->sc, c->s);
             c->capturing = false;
+            c->grec = nullptr;
             cudaGraph_t out2 = nullptr;
             ok = cudaStreamEndCapture(c->s, &out2) == cudaSuccess;
         }
