@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_assemble_rhs(Dims d, PhysDev p,
 
 AsmShape asm_shape(const Dims& d) {
     AsmShape a;
-    a.sh = col_shape(d, 256, 152 * 64);
+    // many blocks pay from 256^3 on; below, fewer keep the reductions short
+    a.sh = col_shape(d, 256, d.n >= (1LL << 24) ? 152 * 64 : 152 * 8);
     a.kch = (d.nz + (int)a.sh.grid.z - 1) / (int)a.sh.grid.z;
     a.nzb = (d.nz + a.kch - 1) / a.kch;
     return a;
