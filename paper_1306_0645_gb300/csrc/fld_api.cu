@@ -1166,6 +1166,59 @@ void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* et
     cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
 }
 
+// The side streams and events of the host-buffer transfers (created on
+// first use).
+fld_status copy_streams(fld_ctx* c) {
+    if (!c->cstream[0]) {
+        for (int q = 0; q < 4; q++) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream[q], cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->cjoin[q], cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaEventCreateWithFlags(&c->cfork, cudaEventDisableTiming));
+    }
+    return FLD_OK;
+}
+
+// finalize_enqueue for a host-buffer step: the finalisation runs in plane
+// chunks and each chunk's E^{n+1} goes back to the host (E_host) on a side
+// stream as soon as it is final, so the transfer overlaps the rest of the
+// finalisation.  The chunks' balance sums are added in chunk order; the
+// context's stream waits for the last transfer.
+fld_status finalize_enqueue_host(fld_ctx* c, double* E, const double* nHI, const double* eta, double* E_host) {
+    const Dims& d = c->L[0].d;
+    const long long nxy = (long long)d.nx * d.ny;
+    for (int sd = 0; sd < 6; sd++)
+        if ((c->L[0].bnd.mask >> sd) & 1) {
+            KScope k(c, K_FINALIZE, 0.0);
+            launch_bnd_outflow(d, c->pd, sd, c->L[0].bnd, E, c->dE, red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd),
+                               c->s);
+        }
+    const int nch = std::min(8, d.nz);
+    if (fld_status st = copy_streams(c)) return st;
+    for (int q = 0; q < nch; q++)
+        if (!c->chunk_ev[q]) CUDA_TRY(cudaEventCreateWithFlags(&c->chunk_ev[q], cudaEventDisableTiming));
+    if (!c->chunk_sc) CUDA_TRY(cudaMalloc(&c->chunk_sc, MAX_CHUNKS * NUM_SLOTS * sizeof(double)));
+    cudaStream_t cs = c->cstream[0];
+    CUDA_TRY(cudaMemsetAsync(c->chunk_sc, 0, (size_t)nch * NUM_SLOTS * sizeof(double), c->s));
+    for (int q = 0; q < nch; q++) {
+        const long long c0 = (long long)d.nz * q / nch * nxy, c1 = (long long)d.nz * (q + 1) / nch * nxy;
+        RedArgs ra = red(c, R_STORE7_FIN);
+        ra.sc = c->chunk_sc + (size_t)q * NUM_SLOTS;
+        { KScope k(c, K_FINALIZE, 40.0 * (c1 - c0));
+          launch_finalize(c1 - c0, c->pd, E + c0, c->dE + c0, nHI + c0, eta + c0, E + c0, ra, c->s); }
+        CUDA_TRY(cudaEventRecord(c->chunk_ev[q], c->s));
+        CUDA_TRY(cudaStreamWaitEvent(cs, c->chunk_ev[q], 0));
+        CUDA_TRY(cudaMemcpyAsync(E_host + c0, E + c0, (size_t)(c1 - c0) * sizeof(double), cudaMemcpyDeviceToHost, cs));
+    }
+    const SlotList sl{7, {S_BAL, S_EMIT, S_ABSORB, S_FLOOR, S_DE2, S_EN2, S_ESUM, 0}};
+    launch_combine_sums(c->chunk_sc, nch, c->sc, sl, c->s);
+    CUDA_TRY(cudaEventRecord(c->e1, c->s));
+    CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CUDA_TRY(cudaEventRecord(c->cjoin[0], cs));
+    CUDA_TRY(cudaStreamWaitEvent(c->s, c->cjoin[0], 0));
+    return FLD_OK;
+}
+
 // The photon balance and relative change from the host mirror.
 void finalize_info(fld_ctx* c, fld_info* inf) {
     harvest(c);
@@ -1197,8 +1250,9 @@ void finalize_info(fld_ctx* c, fld_info* inf) {
 }
 
 // The step after its assembly has been enqueued (assembly status st).
+// E_host: a host-buffer step whose finalisation also returns E^{n+1} to it.
 fld_status step_after_assembly(fld_ctx* c, fld_status st, double* E, const double* nHI, const double* eta,
-                               fld_info* info) {
+                               fld_info* info, double* E_host = nullptr) {
     fld_info inf{};
     if (!st) {
         if (cudaStreamSynchronize(c->s) != cudaSuccess) st = set_err(FLD_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
@@ -1215,7 +1269,15 @@ fld_status step_after_assembly(fld_ctx* c, fld_status st, double* E, const doubl
         if (info) *info = inf;
         return st;
     }
-    finalize_enqueue(c, E, nHI, eta);
+    if (E_host) {
+        if ((st = finalize_enqueue_host(c, E, nHI, eta, E_host))) {
+            inf.status = st;
+            if (info) *info = inf;
+            return st;
+        }
+    } else {
+        finalize_enqueue(c, E, nHI, eta);
+    }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(c->s));
     finalize_info(c, &inf);
@@ -1698,17 +1760,6 @@ fld_status fld_step(fld_ctx* c, double* E, const double* nHI, const double* eta,
 // Copies of host-buffer steps: each array in chunks spread over the side
 // streams (several copy engines share the host link), ordered after the
 // context stream's work so far and joined back into it.
-fld_status copy_streams(fld_ctx* c) {
-    if (!c->cstream[0]) {
-        for (int q = 0; q < 4; q++) {
-            CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream[q], cudaStreamNonBlocking));
-            CUDA_TRY(cudaEventCreateWithFlags(&c->cjoin[q], cudaEventDisableTiming));
-        }
-        CUDA_TRY(cudaEventCreateWithFlags(&c->cfork, cudaEventDisableTiming));
-    }
-    return FLD_OK;
-}
-
 fld_status split_copies(fld_ctx* c, int narr, void* const* dst, const void* const* src, size_t bytes,
                         cudaMemcpyKind kind) {
     constexpr int NS = 4;
@@ -1806,7 +1857,8 @@ fld_status fld_step_host(fld_ctx* c, double* E, const double* nHI, const double*
         st = assemble_host_overlapped(c, E, nHI, eta);
         // no transfer from the caller's buffers may outlive a failed call
         if (st && c->cstream[0]) cudaStreamSynchronize(c->cstream[0]);
-        st = step_after_assembly(c, st, c->stage[0], c->stage[1], c->stage[2], info);
+        st = step_after_assembly(c, st, c->stage[0], c->stage[1], c->stage[2], info, E);
+        if (!st) return FLD_OK;   // E is back: the finalisation returned it chunk by chunk
     } else {
         void* dst[3] = {c->stage[0], c->stage[1], c->stage[2]};
         const void* src[3] = {E, nHI, eta};

@@ -238,8 +238,24 @@ __global__ void k_combine_chunks(const double* __restrict__ csc, int nch, double
     if (nf != 0.0) sc[S_NONFINITE] = nf;
 }
 
+// Reductions done in chunks: each listed slot summed over the chunks in
+// chunk order, a non-finite flag of any chunk kept.
+__global__ void k_combine_sums(const double* __restrict__ csc, int nch, double* sc, SlotList sl) {
+    double nf = 0.0;
+    for (int t = 0; t < sl.n; t++) {
+        double sum = 0.0;
+        for (int q = 0; q < nch; q++) sum += csc[(long long)q * NUM_SLOTS + sl.s[t]];
+        sc[sl.s[t]] = sum;
+    }
+    for (int q = 0; q < nch; q++) nf = fmax(nf, csc[(long long)q * NUM_SLOTS + S_NONFINITE]);
+    if (nf != 0.0) sc[S_NONFINITE] = nf;
+}
+
 // ---------------------------------------------------------------- launchers
 
+void launch_combine_sums(const double* chunk_sc, int nch, double* sc, const SlotList& sl, cudaStream_t s) {
+    k_combine_sums<<<1, 1, 0, s>>>(chunk_sc, nch, sc, sl);
+}
 void launch_combine_chunks(const double* chunk_sc, int nch, double* sc, int s_sum, int s_max, cudaStream_t s) {
     k_combine_chunks<<<1, 1, 0, s>>>(chunk_sc, nch, sc, s_sum, s_max);
 }

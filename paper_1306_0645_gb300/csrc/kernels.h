@@ -149,6 +149,14 @@ void launch_f32_to_f64(long long n, const float* a, double* b, cudaStream_t s);
 // Device-side CG convergence test: sc[S_KITER] += 1 and the conditional h
 // set to continue while sc[S_RR] > sc[S_THRESH], S_KITER < S_MAXIT and no
 // non-finite reduction (one thread).
+// Slots of a reduction done in chunks (at most 8).
+struct SlotList {
+    int n;
+    int s[8];
+};
+// sc[slot] = the chunks' slot summed in chunk order, for each listed slot,
+// and the non-finite flag of any chunk.
+void launch_combine_sums(const double* chunk_sc, int nch, double* sc, const SlotList& sl, cudaStream_t s);
 // Reductions done in nch chunks, each into its own block of NUM_SLOTS
 // slots: sc[s_sum] = the chunks' s_sum summed in chunk order, sc[s_max] =
 // their s_max maximised, and the non-finite flag of any chunk.
