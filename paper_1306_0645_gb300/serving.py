@@ -78,6 +78,9 @@ class Server:
         self._ctx: List[Dict[int, fld.Context]] = [dict() for _ in range(workers)]
         self._bctx: List[Dict[int, List[fld.Context]]] = [dict() for _ in range(workers)]
         self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
+        # resident device fields (E, n_HI, eta) per worker and size: a worker
+        # steps one request at a time, so no request allocates device memory
+        self._fbuf: List[Dict[int, tuple]] = [dict() for _ in range(workers)]
         self._fp_cache: Dict[int, int] = {}
         self._cancelled = set()
         self._cancel_lock = threading.Lock()
@@ -124,16 +127,22 @@ class Server:
             self._ctx[w][n] = ctx
         return ctx
 
-    def _fields(self, r: synth.Request):
+    def _fields(self, r: synth.Request, out=None):
         """E, n_HI and eta of a request on the current stream, built from its
-        payload (source cells and rates)."""
+        payload (source cells and rates); into the tensors out when given."""
         torch = self.torch
         n = r.n
         cells, rates = synth.request_sources(r)
         g = synth.Grid.cube(n)
-        E = torch.full((n ** 3,), synth.E0, dtype=torch.float64, device="cuda")
-        nHI = torch.full((n ** 3,), 1e-3, dtype=torch.float64, device="cuda")
-        eta = torch.zeros((n ** 3,), dtype=torch.float64, device="cuda")
+        if out is None:
+            E = torch.full((n ** 3,), synth.E0, dtype=torch.float64, device="cuda")
+            nHI = torch.full((n ** 3,), 1e-3, dtype=torch.float64, device="cuda")
+            eta = torch.zeros((n ** 3,), dtype=torch.float64, device="cuda")
+        else:
+            E, nHI, eta = out
+            E.fill_(synth.E0)
+            nHI.fill_(1e-3)
+            eta.zero_()
         idx = torch.from_numpy(cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])).cuda()
         val = torch.from_numpy(rates * synth.HNU_HI / g.volume).cuda()
         eta.index_put_((idx,), val, accumulate=True)
@@ -148,7 +157,11 @@ class Server:
         try:
             with torch.cuda.stream(self._streams[w]):
                 ctx = self._context(w, r.n)
-                E, nHI, eta = self._fields(r)
+                buf = self._fbuf[w].get(r.n)
+                if buf is None:
+                    buf = tuple(torch.empty(r.n ** 3, dtype=torch.float64, device="cuda") for _ in range(3))
+                    self._fbuf[w][r.n] = buf
+                E, nHI, eta = self._fields(r, buf)
                 info = fld.fld_step(ctx, E, nHI, eta, check=False)
                 host = self._pinned[w].get(r.n)
                 if host is None:
@@ -302,6 +315,8 @@ class Server:
         for d in self._ctx:
             for ctx in d.values():
                 ctx.close()
+            d.clear()
+        for d in self._fbuf:
             d.clear()
         for d in self._bctx:
             for pool in d.values():
