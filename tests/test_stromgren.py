@@ -15,6 +15,7 @@ The front radius is taken from the ionised volume, r = (3 * 8 V_ion / 4 pi)^(1/3
 The oracle run pins the coupled method to the closed form on the CPU; the
 GPU runs are checked against the closed form and against the oracle."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -191,6 +192,47 @@ def cosmo_setup(n):
 def cosmo_radius(g, x, x_dark):
     v = float((np.maximum(x_dark - x, 0.0) * g.volume).sum())
     return (3 * 8 * v / (4 * math.pi)) ** (1 / 3)
+
+
+def shapiro_giroux_radius(a_rel, q0=0.5, z0=4.0):
+    """The paper's closed form (Sec. 4.1.2) for the front, with a normalised
+    to 1 at z0 and the integrand's (1 - z0) read as (1 + z0): r = r_s0
+    (lambda e^-tau(a) int_1^a e^tau (1 - 2 q0 + 2 q0 (1 + z0) / s)^(-1/2)
+    ds)^(1/3), tau(a) = lambda (F(a) - F(1)) / (6 q0^2 (1 + z0)^2),
+    F(a) = (2 - 4 q0 - 2 q0 (1 + z0) / a) (1 - 2 q0 + 2 q0 (1 + z0) / a)^(1/2)."""
+    from scipy.integrate import quad
+    lam = ALPHA * NH_Z4 / H0_EDS / (1 + z0)
+    r_s0 = (3 * NDOT_COSMO / (4 * math.pi * ALPHA * NH_Z4 ** 2)) ** (1 / 3)
+    F = lambda a: (2 - 4 * q0 - 2 * q0 * (1 + z0) / a) * (1 - 2 * q0 + 2 * q0 * (1 + z0) / a) ** 0.5
+    tau = lambda a: lam * (F(a) - F(1.0)) / (6 * q0 ** 2 * (1 + z0) ** 2)
+    g = lambda s: math.exp(tau(s) - tau(a_rel)) * (1 - 2 * q0 + 2 * q0 * (1 + z0) / s) ** -0.5
+    integral, _ = quad(g, 1.0, a_rel, epsabs=0.0, epsrel=1e-12, limit=200)
+    return r_s0 * (lam * integral) ** (1 / 3)
+
+
+def test_cosmological_closed_forms_agree():
+    # the photon-counting reference the fronts are compared with equals the
+    # paper's closed form (its r is the comoving radius times a0); the
+    # golden file holds the printed parameters this test is built on
+    here = os.path.dirname(os.path.abspath(__file__))
+    gold = {}
+    with open(os.path.join(here, "golden", "test2_cosmological.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = (t.strip() for t in line.split("=", 1))
+                gold[k] = float(v)
+    z0 = gold["z_start"]
+    assert A0 == pytest.approx(1 / (1 + z0), rel=1e-15)
+    assert H0_EDS == pytest.approx(gold["H0_over_100km_s_Mpc"] * 100e5 / (1e3 * synth.KPC), rel=1e-15)
+    assert NH_Z4 == pytest.approx(gold["rho_initial_g_cm3"] / 1.6726e-24, rel=1e-15)
+    assert L_COSMO == pytest.approx(gold["box_comoving_kpc"] * synth.KPC, rel=1e-15)
+    for t_myr in COSMO_MARKS_MYR:
+        t = t_myr * MYR
+        a_rel = eds_a(eds_t(A0) + t) / A0
+        r_sg = shapiro_giroux_radius(a_rel, gold["q0"], z0)
+        r_ode = cosmo_front_closed_form(t)
+        assert r_sg / A0 == pytest.approx(r_ode, rel=1e-6), (t_myr, r_sg / A0, r_ode)
 
 
 COSMO_MARKS_MYR = (200, 1000, 2000)
