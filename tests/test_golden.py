@@ -4,6 +4,8 @@ oracle's limiter and the synthetic inputs of the tests.  CPU only."""
 import math
 import os
 
+import numpy as np
+
 import pytest
 
 import oracle
@@ -62,3 +64,23 @@ def test_test1_parameters_and_closed_forms():
     assert r_s / synth.KPC == pytest.approx(5.39, abs=0.01)
     assert t_rec / (1e6 * synth.YEAR) == pytest.approx(122.4, abs=0.1)
     assert r_s < synth.BOX
+
+
+def test_two_sources_setup():
+    # Sec. 4.1's consolidated HII region: the synthetic recipe places two
+    # sources of the printed rate the printed distance apart in the printed
+    # box and mesh
+    t = load("two_sources.txt")
+    case = synth.config_two_sources(int(t["mesh_x"]))
+    g = case.grid
+    assert tuple(g.n) == (int(t["mesh_x"]), int(t["mesh_y"]), int(t["mesh_z"]))
+    extent = [g.n[a] * g.h[a] / synth.KPC for a in range(3)]
+    assert extent == pytest.approx([float(t["width_kpc"]), float(t["height_kpc"]), float(t["depth_kpc"])], rel=1e-12)
+    assert case.nH.min() == case.nH.max() == float(t["n_H"])
+    cells = case.sources
+    assert len(cells) == 2
+    centres = [(c + 0.5) * g.h[0] / synth.KPC for c in cells[:, 0]]
+    assert abs(centres[1] - centres[0]) == pytest.approx(float(t["separation_kpc"]), abs=g.h[0] / synth.KPC)
+    rate = case.eta.max() * g.volume / synth.HNU_HI
+    assert rate == pytest.approx(float(t["ndot_each"]), rel=1e-12)
+    assert np.count_nonzero(case.eta) == 2
