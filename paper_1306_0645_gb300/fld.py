@@ -159,6 +159,7 @@ def lib():
 
 
 def fld_last_error() -> str:
+    """The message of the calling thread's last failed call."""
     return lib().fld_last_error().decode()
 
 
@@ -193,6 +194,8 @@ def make_grid(g) -> fld_grid:
 
 
 def make_params(p=None, **overrides) -> fld_params:
+    """fld_params: the library defaults, then the fields of p (a synth.Params or
+    an fld_params) and the keyword overrides."""
     out = fld_params()
     _check(lib().fld_params_default(ctypes.byref(out)), "fld_params_default")
     if p is not None:
@@ -225,11 +228,14 @@ def _hptr(a, n, what="array"):
 
 
 def fld_footprint_bytes(grid, params) -> int:
+    """Device bytes a context of this grid and these parameters allocates (0 if
+    the pair is invalid); the serving admission uses it."""
     g, p = make_grid(grid), make_params(params)
     return int(lib().fld_footprint_bytes(ctypes.byref(g), ctypes.byref(p)))
 
 
 def fld_levels(grid) -> List[tuple]:
+    """The multigrid level shapes (nx, ny, nz), finest first."""
     g = make_grid(grid)
     dims = (ctypes.c_int * 96)()
     nl = lib().fld_levels(ctypes.byref(g), dims, 32)
@@ -270,19 +276,26 @@ class Context:
 
 
 def fld_create(grid, params=None, stream=None, **overrides) -> Context:
+    """A context (hierarchy and work buffers on the device) working on stream
+    (the current torch stream if None; graphs need a non-default one)."""
     return Context(grid, params, stream, **overrides)
 
 
 def fld_destroy(ctx: Context):
+    """Free the context's device memory (same as ctx.close())."""
     ctx.close()
 
 
 def fld_assemble(ctx: Context, E, nHI, eta):
+    """Assemble the operator and right-hand side of a step from the device
+    tensors E, n_HI and eta (FP64, one value per cell)."""
     _check(lib().fld_assemble(ctx.handle, _dptr(E, ctx.n, "E"), _dptr(nHI, ctx.n, "n_HI"),
                               _dptr(eta, ctx.n, "eta")), "fld_assemble")
 
 
 def fld_solve(ctx: Context, dE, check: bool = True) -> dict:
+    """Solve the assembled system into dE; returns the info dict (status,
+    iters, outer_iters, rel_res, ...); raises on failure if check."""
     info = fld_info()
     st = lib().fld_solve(ctx.handle, _dptr(dE, ctx.n, "dE"), ctypes.byref(info))
     if check:
@@ -293,6 +306,8 @@ def fld_solve(ctx: Context, dE, check: bool = True) -> dict:
 
 
 def fld_step(ctx: Context, E, nHI, eta, check: bool = True) -> dict:
+    """One step, E <- max(E + dE, 0) in place on the device; returns the info
+    dict with the photon balance; raises on failure if check (E unchanged)."""
     info = fld_info()
     st = lib().fld_step(ctx.handle, _dptr(E, ctx.n, "E"), _dptr(nHI, ctx.n, "n_HI"),
                         _dptr(eta, ctx.n, "eta"), ctypes.byref(info))
@@ -305,6 +320,8 @@ def fld_step(ctx: Context, E, nHI, eta, check: bool = True) -> dict:
 
 def fld_step_host(ctx: Context, E: np.ndarray, nHI: np.ndarray, eta: np.ndarray,
                   check: bool = True) -> dict:
+    """fld_step on host numpy arrays (pinned memory moves fastest): the inputs
+    go to the device, E comes back updated in place."""
     info = fld_info()
     st = lib().fld_step_host(ctx.handle, _hptr(E, ctx.n, "E"), _hptr(nHI, ctx.n, "n_HI"),
                              _hptr(eta, ctx.n, "eta"), ctypes.byref(info))
@@ -316,6 +333,8 @@ def fld_step_host(ctx: Context, E: np.ndarray, nHI: np.ndarray, eta: np.ndarray,
 
 
 def fld_step_batched(ctxs: Sequence[Context], Es, nHIs, etas, check: bool = True):
+    """Step independent contexts together (lockstep rounds, one graph launch
+    per round); returns (status, [info dict per context])."""
     n = len(ctxs)
     arr = lambda xs: (_VP * n)(*xs)
     infos = (fld_info * n)()
@@ -329,19 +348,26 @@ def fld_step_batched(ctxs: Sequence[Context], Es, nHIs, etas, check: bool = True
 
 
 def fld_apply(ctx: Context, x, y):
+    """y = A x with the assembled FP64 operator (device tensors)."""
     _check(lib().fld_apply(ctx.handle, _dptr(x, ctx.n, "x"), _dptr(y, ctx.n, "y")), "fld_apply")
 
 
 def fld_vcycle(ctx: Context, r, z):
+    """z = one V-cycle applied to r (the preconditioner; FP32 on a mixed
+    context, with r and z FP64 device tensors)."""
     _check(lib().fld_vcycle(ctx.handle, _dptr(r, ctx.n, "r"), _dptr(z, ctx.n, "z")), "fld_vcycle")
 
 
 def fld_get_system(ctx: Context, m=None, wx=None, wy=None, wz=None, b=None):
+    """Copy the assembled FP64 operator (m, wx, wy, wz) and right-hand side b
+    into the given device tensors (None: skipped)."""
     ptrs = [None if t is None else _dptr(t, ctx.n) for t in (m, wx, wy, wz, b)]
     _check(lib().fld_get_system(ctx.handle, *ptrs), "fld_get_system")
 
 
 def fld_opacity_update(E, nH, nHI, out, dt, c, sigma, hnu, alpha_B, stream=None):
+    """n_HI after the hydrogen-only linearly implicit update of one step (the
+    opacity update between radiation steps), into out."""
     import torch
     n = E.numel()
     if stream is None:
@@ -353,6 +379,7 @@ def fld_opacity_update(E, nH, nHI, out, dt, c, sigma, hnu, alpha_B, stream=None)
 
 
 def fld_params_default() -> fld_params:
+    """The library's default parameters."""
     p = fld_params()
     _check(lib().fld_params_default(ctypes.byref(p)), "fld_params_default")
     return p
@@ -364,6 +391,8 @@ def fld_profile(ctx: Context, class_mask: int = 0):
 
 
 def fld_profile_read(ctx: Context) -> List[dict]:
+    """Per kernel class: launches, timed launches, ms and algorithmic bytes
+    since the last fld_profile."""
     n = lib().fld_profile_read(ctx.handle, None, 0)
     arr = (fld_kernel_stat * n)()
     lib().fld_profile_read(ctx.handle, arr, n)
@@ -375,10 +404,13 @@ def fld_profile_read(ctx: Context) -> List[dict]:
 
 
 def fld_set_dt(ctx: Context, dt: float):
+    """Change the time step of the following steps."""
     _check(lib().fld_set_dt(ctx.handle, float(dt)), "fld_set_dt")
 
 
 def fld_set_expansion(ctx: Context, scale_factor: float, adot_over_a: float):
+    """Set the scale factor and the expansion rate adot/a (s^-1) of the
+    following steps (comoving cell widths, cosmological loss term)."""
     _check(lib().fld_set_expansion(ctx.handle, float(scale_factor), float(adot_over_a)),
            "fld_set_expansion")
 
@@ -413,14 +445,19 @@ def fld_residual_noalloc(grid, m, wx, wy, wz, b, x, r, norms, stream=None):
 
 
 def fld_autotune(ctx: Context, reps: int = 3):
+    """Time the candidate launch shapes and prefetch distances of the FP32
+    sweeps on this context and keep the fastest (mixed contexts only)."""
     _check(lib().fld_autotune(ctx.handle, int(reps)), "fld_autotune")
 
 
 def fld_tuning_size(ctx: Context) -> int:
+    """Length of the tuning table (three ints per kernel and level)."""
     return int(lib().fld_tuning_size(ctx.handle))
 
 
 def fld_get_tuning(ctx: Context) -> List[int]:
+    """The tuning table: (threads, target blocks, prefetch distance) per
+    kernel and level."""
     n = fld_tuning_size(ctx)
     buf = (ctypes.c_int * n)()
     _check(lib().fld_get_tuning(ctx.handle, buf, n), "fld_get_tuning")
@@ -428,6 +465,7 @@ def fld_get_tuning(ctx: Context) -> List[int]:
 
 
 def fld_set_tuning(ctx: Context, table: Sequence[int]):
+    """Install a tuning table (e.g. from another context of the same grid)."""
     buf = (ctypes.c_int * len(table))(*[int(v) for v in table])
     _check(lib().fld_set_tuning(ctx.handle, buf, len(table)), "fld_set_tuning")
 
@@ -522,6 +560,9 @@ def fld_group_fields(coef: np.ndarray, n_HI, kappas, n_HeI=None, n_HeII=None, et
 def fld_photo_rates(coef: np.ndarray, E_groups, n_HI=None, n_HeI=None, n_HeII=None, rho_b=None,
                     c_light=2.99792458e10, gamma_HI=None, gamma_HeI=None, gamma_HeII=None, heating=None,
                     stream=None):
+    """Photoionisation rates of HI, HeI, HeII and the photoheating rate from the
+    group energies E_groups and the group integrals coef (fld_sed_integrals),
+    into the given device tensors (None: not computed)."""
     coef = np.ascontiguousarray(coef, dtype=np.float64)
     groups = coef.shape[0]
     n = E_groups[0].numel()
