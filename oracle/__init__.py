@@ -35,6 +35,8 @@ SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
 
 
 class OracleError(RuntimeError):
+    """A failed oracle call (its C status code and the call's name)."""
+
     def __init__(self, code, what):
         super().__init__(f"oracle {what} failed with status {code}")
         self.code = code
@@ -183,14 +185,18 @@ def _shape(g):
 
 
 def num_threads() -> int:
+    """OpenMP threads the oracle runs with."""
     return _lib_handle().or_num_threads()
 
 
 def lp_lambda(x: float) -> float:
+    """Levermore-Pomraning lambda(x) = (coth x - 1/x) / x (series for small x)."""
     return _lib_handle().or_lp_lambda(float(x))
 
 
 def face_D(E1, E2, k1, k2, h, phys) -> float:
+    """Limited diffusion coefficient of one face between cells with energies
+    E1, E2 and opacities k1, k2, spacing h (Sec. 2)."""
     p = _phys(phys)
     return _lib_handle().or_face_D(float(E1), float(E2), float(k1), float(k2), float(h),
                                    ctypes.byref(p))
@@ -226,6 +232,7 @@ def _bnd(grid, op):
 
 
 def apply(grid, op, x) -> np.ndarray:
+    """A x for the assembled operator op (m, wx, wy, wz)."""
     sh = _shape(grid)
     m, wx, wy, wz = _op(grid, op)
     x = _arr(x, sh)
@@ -236,6 +243,7 @@ def apply(grid, op, x) -> np.ndarray:
 
 
 def dense_matrix(grid, op) -> np.ndarray:
+    """The operator as a dense n x n matrix (small grids)."""
     m, wx, wy, wz = _op(grid, op)
     n = m.size
     A = np.empty((n, n))
@@ -245,6 +253,7 @@ def dense_matrix(grid, op) -> np.ndarray:
 
 
 def dense_solve(grid, op, rhs) -> np.ndarray:
+    """A^-1 rhs by dense Cholesky (small grids)."""
     sh = _shape(grid)
     m, wx, wy, wz = _op(grid, op)
     rhs = _arr(rhs, sh)
@@ -258,6 +267,8 @@ def dense_solve(grid, op, rhs) -> np.ndarray:
 
 
 def vcycle(grid, op, r, solver=None) -> np.ndarray:
+    """One V-cycle of the multigrid preconditioner applied to r (solver: the
+    smoother, pre/post sweeps and coarsest-grid options)."""
     sh = _shape(grid)
     m, wx, wy, wz = _op(grid, op)
     r = _arr(r, sh)
@@ -309,6 +320,7 @@ def step(grid, phys, solver, E, nHI, eta, allow_noconv=False):
 
 
 def num_levels(n):
+    """The multigrid level shapes of an nx x ny x nz grid, finest first."""
     dims = (ctypes.c_int * 96)()
     nn = (ctypes.c_int * 3)(*[int(v) for v in n])
     nl = _lib_handle().or_num_levels(nn, dims)
@@ -341,6 +353,8 @@ def coarsen(nf, periodic, op, dirichlet=None):
 
 
 def prolong_add(nf, periodic, ec, zf):
+    """zf + P ec: trilinear prolongation of the coarse array ec onto the fine
+    array zf (fine shape nf)."""
     shf = (nf[2], nf[1], nf[0])
     shc = (nf[2] // 2, nf[1] // 2, nf[0] // 2)
     ec = _arr(ec, shc)
@@ -350,6 +364,7 @@ def prolong_add(nf, periodic, ec, zf):
 
 
 def restrict(nf, periodic, rf):
+    """R rf = P^T rf / 8: full-weighting restriction of the fine array rf."""
     shf = (nf[2], nf[1], nf[0])
     shc = (nf[2] // 2, nf[1] // 2, nf[0] // 2)
     rf = _arr(rf, shf)
@@ -359,6 +374,8 @@ def restrict(nf, periodic, rf):
 
 
 def opacity_update(E, nH, nHI, dt, c, sigma, hnu, alpha_B):
+    """n_HI after one hydrogen-only linearly implicit backward-Euler update of the
+    ionised fraction (one Jacobi iteration, clamped to [1e-12, 1])."""
     E, nH, nHI = _arr(E), _arr(nH), _arr(nHI)
     out = np.empty_like(nHI)
     _lib_handle().or_opacity_update(nHI.size, _ptr(E), _ptr(nH), _ptr(nHI), _ptr(out),

@@ -21,6 +21,7 @@ SOURCES = ["k_assemble.cu", "k_mg.cu", "k_cg.cu", "k_fine4.cu", "k_tail.cu", "fl
 
 
 def nvcc() -> str:
+    """Path of nvcc ($NVCC, then PATH, then the default CUDA install)."""
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
             return cand
@@ -33,6 +34,9 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libfld.so in the package's _build directory (one nvcc process per
+    source file, in parallel) unless it is newer than every source; returns
+    its path."""
     os.makedirs(OUT, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB

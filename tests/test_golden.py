@@ -26,7 +26,8 @@ def load(name):
 
 def test_table1_solver_defaults():
     # Table 1: PCG, at most 50 iterations, tolerance 1e-8, red/black GS with
-    # one pre- and one post-sweep (the "12 MG iterations" are unused, O5)
+    # one pre- and one post-sweep (the "12 MG iterations" are unused: one
+    # V-cycle per CG iteration)
     t = load("table1_solver.txt")
     p = fld.make_params(synth.Params())
     assert t["outer_solver"] == "PCG"
@@ -53,7 +54,7 @@ def test_test1_parameters_and_closed_forms():
     assert synth.NDOT == float(t["ndot"])
     assert synth.BOX == pytest.approx(float(t["box_kpc"]) * synth.KPC, rel=1e-15)
     assert synth.HNU_HI == pytest.approx(float(t["hnu_eV"]) * synth.EV, rel=1e-15)
-    # reading O11: the printed 2.59e-12 "cm^2/s" is the case-B 2.59e-13 cm^3/s
+    # the printed 2.59e-12 "cm^2/s" has a garbled unit; case-B at 1e4 K is 2.59e-13 cm^3/s
     assert synth.ALPHA_B == pytest.approx(float(t["alpha_B_printed"]) / 10, rel=1e-15)
     n_H = float(t["n_H"])
     r_s = (3 * synth.NDOT / (4 * math.pi * synth.ALPHA_B * n_H ** 2)) ** (1 / 3)
