@@ -66,6 +66,7 @@ TRAFFIC_OVER_ALGORITHMIC = {
 
 
 def parse():
+    """Command-line options of the benchmark."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -92,6 +93,7 @@ def parse():
 
 
 def dist_env():
+    """(world size, rank, local rank) from the torchrun environment."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -99,12 +101,14 @@ def dist_env():
 
 
 def workload(n, sources, device):
+    """The benchmark input at n^3 (sources scaled with the cell count below 512^3)."""
     from paper_1306_0645_gb300 import synth
     sources = max(1, min(sources, (sources * n ** 3) // 512 ** 3 if n != 512 else sources))
     return synth.config4(n=n, sources=sources, device=device)
 
 
 def workload_desc(n, sources):
+    """One-line description of the benchmark workload for the JSON line."""
     return (f"{n}^3 zero-gradient, log-normal density sigma_ln 1.5 mean n_H 1e-3 clamped to "
             f"[1e-3,1e3]x mean (opacity contrast 1e6), neutral, {sources} sources of 5e48 /s at the "
             f"densest peaks, dt 1e5 yr, box 6.6 kpc, paper limiter; MG-PCG to 1e-8")
@@ -122,6 +126,7 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Start sampling nvidia-smi clocks in the background."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -133,6 +138,8 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        """Stop sampling; returns the median SM clock of the samples, the
+        maximum clock and the throttle reasons seen active."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
         self.proc.terminate()
@@ -171,6 +178,7 @@ def max_over_ranks(ms, dist, device="cuda"):
 
 
 def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) of MEASURED_PEAKS.json, else the fallback figure."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         d = json.load(open(path))
@@ -195,6 +203,7 @@ def time_steps(fld, torch, ctx, E, nHI, eta, steps):
 
 
 def cpu_baseline(n, sources, steps=1):
+    """Time oracle steps of the benchmark recipe at n^3 on the host cores."""
     import oracle
     from paper_1306_0645_gb300 import synth
     case = synth.config4(n=n, sources=sources)
@@ -213,6 +222,8 @@ def cpu_baseline(n, sources, steps=1):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on a bounded sample of the workload,
+    printed as the benchmark's JSON line (rank 0 only)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -247,6 +258,8 @@ def run_reference(args):
 
 
 def main():
+    """The measured run: mixed step, FP64 multigrid, variants, e2e, serving and
+    CPU baseline, printed as one JSON line on rank 0."""
     args = parse()
     if args.impl == "reference":
         run_reference(args)
@@ -404,6 +417,7 @@ def main():
         Eg = [E0 * float(coef[k, 9]) for k in range(G)]
 
         def mg_step():
+            """One multigroup step: group fields, then all groups batched."""
             fld.fld_group_fields(coef, nHI, kap, eta=eta, etas=etg)
             torch.cuda.synchronize()
             return fld.fld_step_batched(gctx, Eg, kap, etg)

@@ -36,6 +36,9 @@ CANCELLED = -1   # Result.status of a request cancelled before it was stepped
 
 @dataclasses.dataclass
 class Result:
+    """Outcome of one request: times on the stream clock, status, iteration
+    counts, relative residual and (when kept) E^{n+1}."""
+
     rid: int
     n: int
     arrival: float          # s, stream time
@@ -49,10 +52,12 @@ class Result:
 
     @property
     def latency_ms(self) -> float:
+        """Arrival to E^{n+1} on the host, ms."""
         return (self.finish - self.arrival) * 1e3
 
     @property
     def wait_ms(self) -> float:
+        """Arrival to the start of its step (queueing), ms."""
         return (self.start - self.arrival) * 1e3
 
 
@@ -100,6 +105,8 @@ class Server:
 
     # ---------------------------------------------------------- admission
     def footprint(self, n: int) -> int:
+        """Device bytes a request of grid size n holds while it runs: the
+        context (fld_footprint_bytes) and its three fields."""
         if n not in self._fp_cache:
             fp = fld.fld_footprint_bytes(synth.Grid.cube(n), self.params)
             self._fp_cache[n] = fp + 3 * n ** 3 * 8 if fp else 0
@@ -149,6 +156,8 @@ class Server:
         return E, nHI, eta
 
     def step_one(self, w: int, r: synth.Request, t0: float) -> Result:
+        """Step one request on worker w (admission, fields, fld_step, E back to
+        pinned host memory)."""
         torch = self.torch
         start = time.perf_counter() - t0
         nbytes = self.footprint(r.n)
@@ -254,6 +263,8 @@ class Server:
         t0 = time.perf_counter()
 
         def worker(w):
+            """Worker thread: take requests (or groups of them) until the stop
+            marker and record their results."""
             self.torch.cuda.set_device(self.device)
             while True:
                 item = q.get()
@@ -312,6 +323,7 @@ class Server:
         return [results[r.rid] for r in requests]
 
     def close(self):
+        """Free every resident context and field buffer."""
         for d in self._ctx:
             for ctx in d.values():
                 ctx.close()
@@ -326,6 +338,7 @@ class Server:
 
 
 def summarize(results: Sequence[Result]) -> dict:
+    """Counts, latency and waiting percentiles and throughput of a run."""
     ok = [r for r in results if r.status == fld.FLD_OK]
     cancelled = sum(1 for r in results if r.status == CANCELLED)
     lat = np.array([r.latency_ms for r in ok]) if ok else np.zeros(1)

@@ -64,18 +64,22 @@ class Grid:
 
     @property
     def shape(self):
+        """Array shape (nz, ny, nx): x is the fastest index."""
         return (self.n[2], self.n[1], self.n[0])
 
     @property
     def cells(self) -> int:
+        """Number of cells."""
         return self.n[0] * self.n[1] * self.n[2]
 
     @property
     def volume(self) -> float:
+        """Cell volume, cm^3."""
         return self.h[0] * self.h[1] * self.h[2]
 
     @staticmethod
     def cube(n: int, box: float = BOX, periodic: bool = False) -> "Grid":
+        """n^3 cubic cells filling a box of side box (cm)."""
         return Grid((n, n, n), (box / n,) * 3, (periodic,) * 3)
 
 
@@ -322,6 +326,9 @@ def config4(n: int = 512, sources: int = 65536, device: str = "cpu") -> Case:
 
 @dataclasses.dataclass
 class Request:
+    """One serving request: id, arrival time, grid size n (n^3 cells), the
+    seed of its source positions and its number of sources."""
+
     rid: int
     arrival: float   # s after the stream starts
     n: int
