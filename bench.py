@@ -59,9 +59,6 @@ TRAFFIC_OVER_ALGORITHMIC = {
     "restrict": 2.1 / 2.5,
     "prolong_add": 6.7 / 8.5,
     "cg_update": 10.5 / 12.0,
-    "assemble_faces": 72.0 / 72.0,
-    "residual64": 56.0 / 56.0,
-    "finalize": 39.4 / 40.0,
 }
 
 
@@ -76,9 +73,12 @@ def parse():
     ap.add_argument("--sources", type=int, default=65536)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-n", type=int, default=256, help="grid of the CPU-baseline sample")
-    ap.add_argument("--ref-n", type=int, default=128, help="grid of the reference-arm sample")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--one-core-n", type=int, default=128,
+                    help="grid of the one-core oracle sample of the CPU baseline (0 skips it)")
+    ap.add_argument("--ref-n", type=int, default=256, help="grid of the reference arm's per-step sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle step at the benchmark size (CPU baseline and oracle error)")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (Poisson stream, 0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0)
@@ -202,23 +202,43 @@ def time_steps(fld, torch, ctx, E, nHI, eta, steps):
     return ev[0].elapsed_time(ev[steps]), per, infos
 
 
-def cpu_baseline(n, sources, steps=1):
-    """Time oracle steps of the benchmark recipe at n^3 on the host cores."""
+def oracle_errors(E, Eo):
+    """Error of a CUDA-path E^{n+1} against the oracle's: L2 and max norm
+    relative to the field, and the largest relative error of the cells with
+    E > 1e-6 max E (not controlled by a 1e-8 residual; stated only)."""
+    mask = Eo > 1e-6 * Eo.max()
+    return {"l2": float(np.linalg.norm(E - Eo) / np.linalg.norm(Eo)),
+            "max_rel_to_max": float(np.abs(E - Eo).max() / np.abs(Eo).max()),
+            "cellwise_E_gt_1e-6max": float((np.abs(E - Eo)[mask] / Eo[mask]).max())}
+
+
+def oracle_sample(n):
+    """One oracle step of the benchmark recipe at n^3 on this process's cores;
+    prints its throughput as JSON (run by one_core_baseline in a child process
+    limited to one OpenMP thread)."""
     import oracle
     from paper_1306_0645_gb300 import synth
-    case = synth.config4(n=n, sources=sources)
+    src = max(1, 65536 * n ** 3 // 512 ** 3)
+    case = synth.config4(n=n, sources=src)
     oracle.build()
-    E = case.E.copy()
     t0 = time.perf_counter()
-    iters = []
-    for _ in range(steps):
-        E, info = oracle.step(case.grid, case.params, {}, E, case.nHI, case.eta)
-        iters.append(info["iters"])
+    _, info = oracle.step(case.grid, case.params, {}, case.E, case.nHI, case.eta)
     dt = time.perf_counter() - t0
-    return {"value": case.grid.cells * steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} FP64 oracle step(s) (MG-PCG to 1e-8, plain C + OpenMP) on the same "
-                      f"recipe at {n}^3 with {sources} sources ({dt:.1f} s, iters {iters})"}
+    print(json.dumps({"value": case.grid.cells / dt, "s": dt, "cores": oracle.num_threads(),
+                      "iters": info["iters"], "n": n, "sources": src}), flush=True)
+
+
+def one_core_baseline(n):
+    """The oracle on one host core: one step of the recipe at n^3 in a child
+    process with OMP_NUM_THREADS=1."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"],
+            "sample": f"1 oracle step at {n}^3 with {d['sources']} sources ({d['s']:.1f} s, {d['iters']} iters)"}
 
 
 def run_reference(args):
@@ -233,6 +253,8 @@ def run_reference(args):
     n = args.ref_n
     src = max(1, args.sources * n ** 3 // 512 ** 3)
     case = synth.config4(n=n, sources=src)
+    cfg_n = args.n
+    cfg_src = args.sources if cfg_n == 512 else max(1, args.sources * cfg_n ** 3 // 512 ** 3)
     E = case.E.copy()
     for _ in range(args.warmup):
         E, _ = oracle.step(case.grid, case.params, {}, E, case.nHI, case.eta)
@@ -245,13 +267,15 @@ def run_reference(args):
     total = time.perf_counter() - t0
     value = case.grid.cells * args.steps / total
     cores = oracle.num_threads()
-    sample = (f"FP64 oracle (plain C + OpenMP, {cores} threads) on the benchmark recipe at {n}^3 with "
-              f"{src} sources, one oracle step per step")
+    sample = (f"each step: one FP64 oracle step (plain C + OpenMP, {cores} threads, MG-PCG to 1e-8) of the "
+              f"workload's recipe at {n}^3 with {src} sources, a bounded sample of the {cfg_n}^3 workload "
+              f"(cell-solves/s is per cell, so the sample's rate stands for the workload's)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
            "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": workload_desc(n, src), "n": n, "sources": src},
+           "data": "synthetic", "config": {"workload": workload_desc(cfg_n, cfg_src), "n": cfg_n,
+                                           "sources": cfg_src, "sample_n": n, "sample_sources": src},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -261,6 +285,9 @@ def main():
     """The measured run: mixed step, FP64 multigrid, variants, e2e, serving and
     CPU baseline, printed as one JSON line on rank 0."""
     args = parse()
+    if args.oracle_sample:
+        oracle_sample(args.oracle_sample)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -353,8 +380,20 @@ def main():
                   "frac": float(model_cell * cells / (total_ms / args.steps * 1e-3) / (peak * 1e9)),
                   "own_bytes_per_cell": float(step_bytes / cells)}
 
+    # ---- the headline step against the FP64 oracle at full size: one more
+    # mixed step from the current E^n, the same step by the FP64 GPU
+    # multigrid below and by the oracle on the host cores (which is also the
+    # CPU baseline of this workload)
+    E_n = E.clone()
+    E_mx = E_n.clone()
+    info_mx = fld.fld_step(ctx, E_mx, nHI, eta)
+    torch.cuda.synchronize()
+    E_mx_h = E_mx.cpu().numpy()
+    del E_mx
+
     # ---- plain FP64 multigrid on the same input
     fp64 = None
+    E_64_h = None
     if args.fp64_steps > 0:
         import dataclasses
         p64 = dataclasses.replace(pm, precision=synth.PREC_FP64)
@@ -366,6 +405,10 @@ def main():
         fp64 = {"value": cells * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps, "iters": [i["iters"] for i in inf64],
                 "rel_res": [i["rel_res"] for i in inf64]}
+        E64.copy_(E_n)
+        fld.fld_step(ctx64, E64, nHI, eta)
+        torch.cuda.synchronize()
+        E_64_h = E64.cpu().numpy()
         ctx64.close()
         del E64
 
@@ -475,9 +518,28 @@ def main():
                             "precision": "mixed", "latency": "arrival to E^{n+1} on the host"})
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.cpu_n > 0:
-        src = max(1, args.sources * args.cpu_n ** 3 // 512 ** 3)
-        cpu = cpu_baseline(args.cpu_n, src)
+    oracle_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        E_in = E_n.cpu().numpy().reshape(case.grid.shape)
+        t0 = time.perf_counter()
+        Eo, io = oracle.step(case.grid, case.params, {}, E_in, case.nHI, case.eta)
+        t_or = time.perf_counter() - t0
+        cpu = {"value": cells / t_or, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"1 FP64 oracle step (plain C + OpenMP, MG-PCG to 1e-8) of the benchmark workload "
+                         f"itself, {n}^3 with {sources} sources, from the E^n of the timed steps "
+                         f"({t_or:.1f} s, {io['iters']} iters)"}
+        if args.one_core_n > 0:
+            cpu["one_core"] = one_core_baseline(args.one_core_n)
+        oracle_err = {"reference": f"FP64 oracle step to ||r||/||b|| <= 1e-8 from the same E^n "
+                                   f"({io['iters']} iterations)",
+                      "mixed": dict(oracle_errors(E_mx_h.reshape(case.grid.shape), Eo),
+                                    rel_res=info_mx["rel_res"], iters=info_mx["iters"],
+                                    outer_iters=info_mx["outer_iters"])}
+        if E_64_h is not None:
+            oracle_err["fp64_mg"] = oracle_errors(E_64_h.reshape(case.grid.shape), Eo)
+        del Eo, E_in
 
     if rank == 0:
         out = {
@@ -496,6 +558,7 @@ def main():
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
             "roofline": roofline, "step_roofline_frac": step_frac, "step_roofline_model": step_model,
             "kernel_breakdown_one_step": breakdown,
+            "oracle_err": oracle_err,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "serving": serving_out, "variants": variants,
         }

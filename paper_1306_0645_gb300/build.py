@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfld.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_assemble.cu", "k_mg.cu", "k_cg.cu", "k_fine4.cu", "k_tail.cu", "fld_api.cu", "fld_noalloc.cu", "fld_sed.cu"]
+SOURCES = ["k_assemble.cu", "k_mixed.cu", "k_mg.cu", "k_cg.cu", "k_fine4.cu", "k_tail.cu", "fld_api.cu", "fld_noalloc.cu", "fld_sed.cu"]
 
 
 def nvcc() -> str:

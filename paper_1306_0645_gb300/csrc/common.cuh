@@ -44,6 +44,9 @@ enum Slot {
     S_THRESH,     // device-side CG loop: stop when ||r||^2 <= this,
     S_MAXIT,      //   or after this many iterations;
     S_KITER,      //   iterations done
+    S_EMAX,       // mixed assembly: max E, max n_HI, max eta (bit patterns of
+    S_NMAX,       //   non-negative doubles, so they are maximised as integers;
+    S_ETAMAX,     //   the low word is cleared), the scales of the df arithmetic
     NUM_SLOTS = 40
 };
 
@@ -55,7 +58,9 @@ enum RedOp {
     R_STORE2,       // sc[slot0] = v0, sc[slot1] = v1
     R_STORE3,       // sc[slot0..2] = v0..v2 (slots consecutive from slot0)
     R_STORE7_FIN,   // sc[S_BAL], [S_EMIT], [S_ABSORB], [S_FLOOR], [S_DE2], [S_EN2], [S_ESUM] = v0..v6
-    R_STORE_SUM_MAX // sc[slot0] = v0 (sum), sc[slot1] = v1 (max)
+    R_STORE_SUM_MAX, // sc[slot0] = v0 (sum), sc[slot1] = v1 (max)
+    R_IRRES         // scaled refinement residual: sc[S_R0] = sc[S_RR] = v0,
+                    // sc[S_RMAX] = v1 (max), sc[S_SCALE] = aux
 };
 
 struct RedArgs {
@@ -65,6 +70,7 @@ struct RedArgs {
     int op;
     int slot0, slot1;
     int first;            // R_RHO: first iteration
+    double aux;           // R_IRRES: the scale stored in S_SCALE
 };
 
 constexpr int RED_THREADS = 256;
@@ -144,6 +150,13 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
         sc[S_EN2] = v[5];
         sc[S_ESUM] = v[6];
         for (int q = 0; q < 7; q++) bad = bad || !isfinite(v[q]);
+        break;
+    case R_IRRES:
+        sc[S_R0] = v[0];
+        sc[S_RR] = v[0];
+        sc[S_RMAX] = v[1];
+        sc[S_SCALE] = ra.aux;
+        bad = !isfinite(v[0]) || !isfinite(v[1]);
         break;
     case R_STORE3:
         sc[ra.slot0] = v[0];

@@ -50,6 +50,7 @@ struct Level {
     Dims d;
     Op<double> A64;
     Op<float> A32;
+    Op<float> Alo;     // mixed fine level: low parts of m and w (df with A32)
     Bnd bnd;           // Dirichlet face weights (FP64)
     void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
     Tune tune[NTUNE];
@@ -60,13 +61,13 @@ enum KClass {
     K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
-    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_NUM
+    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_IR_RESID, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
     "assemble_faces", "assemble_rhs", "coarsen", "invd", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
-    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail"};
+    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail", "ir_residual"};
 
 struct KStat {
     long long launches, timed;
@@ -197,11 +198,14 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
         // the coarse levels serve only the cycle, FP32 on every level of the
         // mixed solver: FP64 operators there for the FP64 solver only (the
         // fine level keeps its FP64 operator for the refinement residual)
-        if (!(mixed && l > 0))
-            for (int q = 0; q < 4; q++) buf(l, "A64", q, n * sizeof(double));
-        if (!mixed) buf(l, "A64", 4, n * sizeof(double));
+        // the fine operator of the mixed solver is double-float: the FP32
+        // operator of its V-cycles plus low parts (k_mixed.cu)
+        if (!mixed)
+            for (int q = 0; q < 5; q++) buf(l, "A64", q, n * sizeof(double));
         if (mixed)
             for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
+        if (mixed && l == 0)
+            for (int q = 0; q < 4; q++) buf(l, "Alo", q, n * sizeof(float));
         if (l > 0) {
             buf(l, "vec", 0, n * ts);
             buf(l, "vec", 1, n * ts);
@@ -216,8 +220,6 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
     const size_t n0 = (size_t)g->nx * g->ny * g->nz;
     buf(0, "b", 0, n0 * sizeof(double));
     buf(0, "dE", 0, n0 * sizeof(double));
-    if (mixed) buf(0, "r64", 0, n0 * sizeof(double));
-    if (mixed) buf(0, "diag64", 0, n0 * sizeof(double));
     {
         Dims d0;
         d0.nx = g->nx; d0.ny = g->ny; d0.nz = g->nz;
@@ -251,8 +253,11 @@ struct fld_ctx {
     bool mixed;
     int nl;
     Level L[MAX_LEVELS];
-    double *b, *dE, *r64;
-    double* diag64;   // mixed mode: FP64 diagonal of the fine operator
+    double* b;
+    // refinement unknown: FP64, or (mixed mode) a double-float pair per cell
+    // scaled by the step's power of two (k_mixed.cu)
+    double* dE;
+    int ks;           // mixed mode: the inner solve's scale 2^ks
     FaceList flist;   // faces left by the FP32 limiter screen
     void* cg[6];   // r, z, p0, p1, q, x
     int nc;
@@ -883,14 +888,16 @@ fld_status alloc_ctx(fld_ctx* c) {
             float* f = (float*)ptr;
             if (q == 0) L.A32.m = f; else if (q == 1) L.A32.wx = f; else if (q == 2) L.A32.wy = f;
             else if (q == 3) L.A32.wz = f; else L.A32.invd = f;
+        } else if (!strcmp(kind, "Alo")) {
+            float* f = (float*)ptr;
+            if (q == 0) L.Alo.m = f; else if (q == 1) L.Alo.wx = f; else if (q == 2) L.Alo.wy = f;
+            else L.Alo.wz = f;
         } else if (!strcmp(kind, "vec")) {
             if (q == 0) L.r = ptr; else if (q == 1) L.z = ptr; else L.t = ptr;
         } else if (!strcmp(kind, "bnd")) {
             L.bnd.w = (double*)ptr;
         } else if (!strcmp(kind, "b")) c->b = (double*)ptr;
         else if (!strcmp(kind, "dE")) c->dE = (double*)ptr;
-        else if (!strcmp(kind, "r64")) c->r64 = (double*)ptr;
-        else if (!strcmp(kind, "diag64")) c->diag64 = (double*)ptr;
         else if (!strcmp(kind, "flist")) {
             if (q == 0) c->flist.entries = (unsigned*)ptr;
             else c->flist.counts = (unsigned*)ptr;
@@ -930,6 +937,65 @@ void free_ctx(fld_ctx* c) {
     delete c;
 }
 
+// ---- mixed-precision refinement (kernels in k_mixed.cu)
+
+RedArgs red_irres(fld_ctx* c, int ks) {
+    RedArgs r = red(c, R_IRRES);
+    r.aux = std::ldexp(1.0, ks);
+    return r;
+}
+
+// The first refinement's right-hand side: r32 = b / 2^ks with 2^ks the
+// power of two above max |b| (in the host mirror after the assembly).
+void scale_rhs_enqueue(fld_ctx* c) {
+    const long long n = c->L[0].d.n;
+    c->ks = exp_above(c->h_sc[S_RMAX]);
+    KScope k(c, K_IR_SCALE, 16.0 * n);
+    launch_ir_scale_b(n, c->b, c->ks, (float*)c->cg[0], (float*)c->cg[5], red_irres(c, c->ks), c->s);
+}
+
+// x64 += 2^ks (x32 + alpha p_last) after an inner solve (x64 = ... after
+// the first one).
+void update_enqueue(fld_ctx* c, bool assign) {
+    const long long n = c->L[0].d.n;
+    const bool defer = defers_x<float>(c);
+    KScope k(c, K_IR_UPDATE, ((assign ? 12.0 : 20.0) + (defer ? 4.0 : 0.0)) * n);
+    launch_ir_update_mx(n, c->dE, (const float*)c->cg[5], c->sc, assign, c->ks,
+                        defer ? (const float*)c->cg[2 + c->run.cur] : nullptr, c->sc, c->pd.dt_exp, c->s);
+}
+
+// The scale of the next inner solve, predicted from the one just done: its
+// residual fell from ||r32_0|| to ||r32|| (S_RR), so the new residual's
+// largest entry is about 2^ks ||r32||.
+int next_scale(fld_ctx* c) {
+    const double rr = c->h_sc[S_RR];
+    return rr > 0.0 && std::isfinite(rr) ? c->ks + exp_above(std::sqrt(rr)) : c->ks - 30;
+}
+
+void residual_enqueue(fld_ctx* c, int ks) {
+    Level& L0 = c->L[0];
+    KScope k(c, K_IR_RESID, 56.0 * L0.d.n);
+    launch_ir_residual(L0.d, L0.A32, L0.Alo, c->b, c->dE, ks, (float*)c->cg[0], (float*)c->cg[5],
+                       red_irres(c, ks), c->sc, c->pd.dt_exp, c->s);
+}
+
+// After a residual launched with scale 2^ks has reported its largest entry:
+// 0 if it stays well inside the FP32 range (or is 0), 1 with ks corrected
+// for a relaunch, -1 if it stays non-finite after a few corrections.
+int scale_fix(fld_ctx* c, int& ks, int attempt) {
+    const double mx = c->h_sc[S_RMAX];
+    const bool nonfinite = c->h_sc[S_NONFINITE] != 0.0 || !std::isfinite(mx);
+    if (!nonfinite && (mx == 0.0 || (mx >= 0x1p-40 && mx <= 0x1p40))) return 0;
+    if (attempt >= 3) return nonfinite ? -1 : 0;
+    ks += nonfinite ? 100 : exp_above(mx);
+    return 1;
+}
+
+// ||b - A x|| / ||b|| from the scaled residual's norm.
+double scaled_rel_res(fld_ctx* c, double bb) {
+    return std::ldexp(std::sqrt(c->h_sc[S_R0]), c->ks) / std::sqrt(bb);
+}
+
 fld_status solve_impl(fld_ctx* c, fld_info* info) {
     const long long n = c->L[0].d.n;
     const double bb = c->h_sc[S_BB];
@@ -956,29 +1022,16 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
         if ((st = read_scalars(c))) return st;
         inf.rel_res = std::sqrt(c->h_sc[S_TRUE_RR] / bb);
     } else {
-        // Iterative refinement: FP64 residual, FP32 inner MG-PCG on the
-        // scaled residual, FP64 update.  The first residual is b itself
-        // (x = 0), whose norm and max |b| the assembly already reduced.
+        // Iterative refinement: the residual in double-float arithmetic, the
+        // FP32 inner MG-PCG on it scaled by a power of two 2^ks, the FP64
+        // update.  The first residual is b itself (x = 0), scaled by the
+        // power of two above max |b|, which the assembly reduced.
         int inner_total = 0, outer = 0;
-        double r64sq = bb;
-        const double* rsrc = c->b;
+        inf.rel_res = 1.0;
+        scale_rhs_enqueue(c);
+        if ((st = read_scalars(c))) return st;
+        if (c->h_sc[S_NONFINITE] != 0.0) return set_err(FLD_ENONFINITE, "non-finite scaled right-hand side");
         for (;;) {
-            if (outer > 0) {
-                { KScope k(c, K_RESIDUAL64, 56.0 * n);
-                  launch_residual64(c->L[0].d, c->L[0].A64, c->diag64, c->b, c->dE, c->r64,
-                                    red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
-                if ((st = read_scalars(c))) return st;
-                if (c->h_sc[S_NONFINITE] != 0.0)
-                    return set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", outer);
-                r64sq = c->h_sc[S_R64];
-                rsrc = c->r64;
-            }
-            inf.rel_res = std::sqrt(r64sq / bb);
-            if (inf.rel_res <= rtol) { conv = true; break; }
-            if (inner_total >= c->p.max_iter) break;
-            { KScope k(c, K_IR_SCALE, 16.0 * n);
-              launch_ir_scale(n, rsrc, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
-            if ((st = read_scalars(c))) return st;
             int it = 0;
             bool iconv = false;
             // the inner solve need not reduce its residual further than the
@@ -989,10 +1042,21 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
             st = pcg<float>(c, c->h_sc[S_R0], irtol, c->p.max_iter - inner_total, &it, &iconv);
             if (st) return st;
             inner_total += it;
-            { KScope k(c, K_IR_UPDATE, ((outer == 0 ? 12.0 : 20.0) + (defers_x<float>(c) ? 4.0 : 0.0)) * n);
-              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, outer == 0, c->s,
-                               defers_x<float>(c) ? (const float*)c->cg[2 + c->run.cur] : nullptr); }
+            update_enqueue(c, outer == 0);
             outer++;
+            int ks = next_scale(c);
+            for (int attempt = 0;; attempt++) {
+                residual_enqueue(c, ks);
+                if ((st = read_scalars(c))) return st;
+                const int fix = scale_fix(c, ks, attempt);
+                if (fix == 0) break;
+                if (fix < 0) return set_err(FLD_ENONFINITE, "non-finite refinement residual after %d refinements", outer);
+                CUDA_TRY(cudaMemsetAsync(c->sc + S_NONFINITE, 0, sizeof(double), c->s));
+            }
+            c->ks = ks;
+            inf.rel_res = scaled_rel_res(c, bb);
+            if (inf.rel_res <= rtol) { conv = true; break; }
+            if (inner_total >= c->p.max_iter) break;
         }
         inf.iters = inner_total;
         inf.outer_iters = outer;
@@ -1014,10 +1078,20 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
 void assemble_faces_range(fld_ctx* c, const double* E, const double* nHI, const double* eta, int zb0,
                           int nzb, double frac) {
     Level& L0 = c->L[0];
-    Op<float> op32{};
-    if (c->mixed) op32 = L0.A32;
     const double n0 = (double)L0.d.n * frac;
-    { KScope k(c, K_ASM_FACES, n0 * (56.0 + (c->mixed ? 16.0 : 0.0)));
+    if (c->mixed) {
+        // double-float limiter in place (k_mixed.cu): reads E, n_HI, eta,
+        // writes m and the three weights as float pairs
+        { KScope k(c, K_ASM_FACES, n0 * 56.0);
+          launch_asm_faces_mx(L0.d, c->pd, E, nHI, eta, L0.A32, L0.Alo, c->sc, c->flist, c->s, zb0, nzb); }
+        if (c->flist.entries) {
+            KScope k(c, K_ASM_FIX, 0.0);
+            launch_asm_fix_mx(L0.d, c->pd, E, nHI, L0.A32, L0.Alo, c->flist, c->s, zb0, nzb);
+        }
+        return;
+    }
+    Op<float> op32{};
+    { KScope k(c, K_ASM_FACES, n0 * 56.0);
       launch_assemble_faces(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->sc, c->flist, c->s, zb0, nzb); }
     if (c->flist.entries) {
         KScope k(c, K_ASM_FIX, 0.0);
@@ -1029,11 +1103,15 @@ void assemble_faces_range(fld_ctx* c, const double* E, const double* nHI, const 
 void assemble_rhs_range(fld_ctx* c, const double* E, const double* nHI, const double* eta, int zb0, int nzb,
                         double frac, const RedArgs& ra) {
     Level& L0 = c->L[0];
-    Op<float> op32{};
-    if (c->mixed) op32 = L0.A32;
-    KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * (64.0 + (c->mixed ? 28.0 : 8.0)));
-    launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, op32, c->b, c->mixed ? c->diag64 : nullptr, L0.bnd, ra,
-                        c->s, zb0, nzb);
+    if (c->mixed) {
+        // reads E, n_HI, eta, the df weights and the FP32 mass term; writes
+        // b and the FP32 inverse diagonal
+        KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * 64.0);
+        launch_asm_rhs_mx(L0.d, c->pd, E, nHI, eta, L0.A32, L0.Alo, c->b, L0.bnd, ra, c->sc, c->s, zb0, nzb);
+        return;
+    }
+    KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * 72.0);
+    launch_assemble_rhs(L0.d, c->pd, E, nHI, eta, L0.A64, Op<float>{}, c->b, nullptr, L0.bnd, ra, c->s, zb0, nzb);
 }
 
 // The coarse levels, the coarsest-grid setup, then the scalars to the host
@@ -1067,8 +1145,9 @@ fld_status assemble_coarse(fld_ctx* c) {
     Level& Lc = c->L[c->nl - 1];
     { const double nc = (double)Lc.d.n;
       KScope k(c, K_COARSE_SETUP, 16.0 * nc * nc);
-      if (c->mixed && c->nl > 1) launch_coarse_setup<float>(Lc.d, Lc.A32, c->dense, c->ainv, c->sc, true, s);
-      else launch_coarse_setup<double>(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, c->mixed, s); }
+      // the mixed solver's cycle is FP32 throughout, also on a one-level grid
+      if (c->mixed) launch_coarse_setup<float>(Lc.d, Lc.A32, c->dense, c->ainv, c->sc, true, s);
+      else launch_coarse_setup<double>(Lc.d, Lc.A64, c->dense, c->ainv, c->sc, false, s); }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, s));
     return FLD_OK;
@@ -1150,6 +1229,54 @@ void fill_physdev(fld_ctx* c, double dt) {
     for (int a = 0; a < 3; a++)
         if (!(pd.twoL_h32[a] < 2e5f)) pd.thr32 = -1.0f;
     pd.limiter = p->limiter;
+    // double-float constants of the mixed kernels (high part the nearest
+    // float, low part the nearest float to the rest)
+    auto to_df = [](double v) {
+        df r;
+        r.h = (float)v;
+        r.l = (float)(v - (double)r.h);
+        return r;
+    };
+    auto in_range = [](double v) {
+        const double a = std::fabs(v);
+        return std::isfinite(v) && (a == 0.0 || (a > 1e-36 && a < 1e36));
+    };
+    bool lim_ok = true;
+    for (int a = 0; a < 3; a++) {
+        const double sh = p->sigma * pd.h[a], cw = p->theta * dt * p->c / pd.h[a], rm = pd.Rmin * pd.h[a];
+        pd.sigh[a] = to_df(sh);
+        pd.cw[a] = to_df(cw);
+        pd.rminh[a] = to_df(rm);
+        pd.wmaxd[a].h = pd.wmax32[a];
+        pd.wmaxd[a].l = (float)(pd.wmax[a] - (double)pd.wmax32[a]);
+        lim_ok = lim_ok && in_range(sh) && in_range(cw) && in_range(rm) && in_range(pd.wmax[a]);
+    }
+    pd.df_limiter = lim_ok ? 1 : 0;
+    pd.one_dta_d = to_df(pd.one_dta);
+    pd.mdtcs_d = to_df(pd.mdtcs);
+    pd.dtcs_d = to_df(pd.dtcs);
+    pd.dta_d = to_df(pd.dta);
+    int e2 = 0;
+    const double fr = std::frexp(dt, &e2);   // dt = fr 2^e2, fr in [1/2, 1)
+    pd.dt_exp = e2 - 1;
+    pd.dtm_d = to_df(2.0 * fr);
+    pd.ith_d = to_df(pd.inv_theta);
+}
+
+// E = max(E + dE, 0) over n cells from E with the photon-balance sums:
+// FP64 sums (FP64 solver), or df sums on the FP32 pipe (mixed solver,
+// k_mixed.cu; its scales come from the assembly's maxima in c->sc).
+void finalize_any(fld_ctx* c, long long n, double* E, const double* dE, const double* nHI, const double* eta,
+                  const RedArgs& ra) {
+    if (c->mixed) launch_finalize_mx(n, c->pd, E, dE, nHI, eta, E, ra, c->sc, c->s);
+    else launch_finalize(n, c->pd, E, dE, nHI, eta, E, ra, c->s);
+}
+
+// Photons through the Dirichlet faces of side sd (before E is overwritten).
+void bnd_outflow_any(fld_ctx* c, int sd, const double* E) {
+    const RedArgs ra = red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd);
+    if (c->mixed) launch_bnd_outflow_mx(c->L[0].d, c->pd, sd, c->L[0].bnd, E, c->dE, ra, c->sc, c->s);
+    else launch_bnd_outflow(c->L[0].d, c->pd, sd, c->L[0].bnd, E, c->dE, ra, c->s);
 }
 
 void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* eta) {
@@ -1158,10 +1285,9 @@ void finalize_enqueue(fld_ctx* c, double* E, const double* nHI, const double* et
     for (int sd = 0; sd < 6; sd++)
         if ((c->L[0].bnd.mask >> sd) & 1) {
             KScope k(c, K_FINALIZE, 0.0);
-            launch_bnd_outflow(c->L[0].d, c->pd, sd, c->L[0].bnd, E, c->dE,
-                               red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd), c->s);
+            bnd_outflow_any(c, sd, E);
         }
-    { KScope k(c, K_FINALIZE, 40.0 * n); launch_finalize(n, c->pd, E, c->dE, nHI, eta, E, red(c, R_STORE7_FIN), c->s); }
+    { KScope k(c, K_FINALIZE, 40.0 * n); finalize_any(c, n, E, c->dE, nHI, eta, red(c, R_STORE7_FIN)); }
     cudaEventRecord(c->e1, c->s);
     cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
 }
@@ -1190,8 +1316,7 @@ fld_status finalize_enqueue_host(fld_ctx* c, double* E, const double* nHI, const
     for (int sd = 0; sd < 6; sd++)
         if ((c->L[0].bnd.mask >> sd) & 1) {
             KScope k(c, K_FINALIZE, 0.0);
-            launch_bnd_outflow(d, c->pd, sd, c->L[0].bnd, E, c->dE, red(c, R_STORE2, S_OUT0 + sd, S_OUTABS0 + sd),
-                               c->s);
+            bnd_outflow_any(c, sd, E);
         }
     const int nch = std::min(8, d.nz);
     if (fld_status st = copy_streams(c)) return st;
@@ -1205,7 +1330,7 @@ fld_status finalize_enqueue_host(fld_ctx* c, double* E, const double* nHI, const
         RedArgs ra = red(c, R_STORE7_FIN);
         ra.sc = c->chunk_sc + (size_t)q * NUM_SLOTS;
         { KScope k(c, K_FINALIZE, 40.0 * (c1 - c0));
-          launch_finalize(c1 - c0, c->pd, E + c0, c->dE + c0, nHI + c0, eta + c0, E + c0, ra, c->s); }
+          finalize_any(c, c1 - c0, E + c0, c->dE + c0, nHI + c0, eta + c0, ra); }
         CUDA_TRY(cudaEventRecord(c->chunk_ev[q], c->s));
         CUDA_TRY(cudaStreamWaitEvent(cs, c->chunk_ev[q], 0));
         CUDA_TRY(cudaMemcpyAsync(E_host + c0, E + c0, (size_t)(c1 - c0) * sizeof(double), cudaMemcpyDeviceToHost, cs));
@@ -1316,6 +1441,7 @@ struct BItem {
     int prec;            // CG precision in progress (0 FP64, 1 FP32)
     double bb;
     int inner_total, outer;
+    int ks, attempt;     // mixed: scale of the residual in flight, relaunches
     bool conv;
     std::string err;
 };
@@ -1418,8 +1544,7 @@ void batch_after(BItem& b) {
         } else {
             // the first refinement residual is b itself (x = 0)
             b.inf.rel_res = 1.0;
-            { KScope k(c, K_IR_SCALE, 16.0 * n);
-              launch_ir_scale(n, c->b, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
+            scale_rhs_enqueue(c);
             cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
             b.state = BS_SCALE;
         }
@@ -1427,6 +1552,10 @@ void batch_after(BItem& b) {
     }
     case BS_SCALE: {
         harvest(c);
+        if (c->h_sc[S_NONFINITE] != 0.0) {
+            set_err(FLD_ENONFINITE, "non-finite scaled right-hand side");
+            return bfail(b, FLD_ENONFINITE);
+        }
         double irtol = 0.5 * rtol / b.inf.rel_res;
         if (irtol < c->p.inner_rtol) irtol = c->p.inner_rtol;
         if (irtol > 0.5) irtol = 0.5;
@@ -1449,13 +1578,11 @@ void batch_after(BItem& b) {
             b.state = BS_TRUE_RES;
         } else {
             b.inner_total += c->run.k;
-            { KScope k(c, K_IR_UPDATE, ((b.outer == 0 ? 12.0 : 20.0) + (defers_x<float>(c) ? 4.0 : 0.0)) * n);
-              launch_ir_update(n, c->dE, (const float*)c->cg[5], c->sc, b.outer == 0, c->s,
-                               defers_x<float>(c) ? (const float*)c->cg[2 + c->run.cur] : nullptr); }
+            update_enqueue(c, b.outer == 0);
             b.outer++;
-            { KScope k(c, K_RESIDUAL64, 56.0 * n);
-              launch_residual64(c->L[0].d, c->L[0].A64, c->diag64, c->b, c->dE, c->r64,
-                                red(c, R_STORE_SUM_MAX, S_R64, S_RMAX), c->s); }
+            b.ks = next_scale(c);
+            b.attempt = 0;
+            residual_enqueue(c, b.ks);
             cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
             b.state = BS_RESID;
         }
@@ -1463,11 +1590,22 @@ void batch_after(BItem& b) {
     }
     case BS_RESID: {
         harvest(c);
-        if (c->h_sc[S_NONFINITE] != 0.0) {
-            set_err(FLD_ENONFINITE, "non-finite FP64 residual after %d refinements", b.outer);
+        const int fix = scale_fix(c, b.ks, b.attempt);
+        if (fix < 0) {
+            set_err(FLD_ENONFINITE, "non-finite refinement residual after %d refinements", b.outer);
             return bfail(b, FLD_ENONFINITE);
         }
-        b.inf.rel_res = std::sqrt(c->h_sc[S_R64] / b.bb);
+        if (fix > 0) {
+            // the predicted scale left the FP32 range: again with the scale the
+            // residual reported
+            b.attempt++;
+            cudaMemsetAsync(c->sc + S_NONFINITE, 0, sizeof(double), c->s);
+            residual_enqueue(c, b.ks);
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+            return;
+        }
+        c->ks = b.ks;
+        b.inf.rel_res = scaled_rel_res(c, b.bb);
         b.inf.iters = b.inner_total;
         b.inf.outer_iters = b.outer;
         if (b.inf.rel_res <= rtol) {
@@ -1479,10 +1617,14 @@ void batch_after(BItem& b) {
                     b.inf.rel_res, rtol, b.inner_total);
             return bfail(b, FLD_ENOCONV);
         } else {
-            { KScope k(c, K_IR_SCALE, 16.0 * n);
-              launch_ir_scale(n, c->r64, (float*)c->cg[0], (float*)c->cg[5], red(c, R_STORE2, S_R0, S_RR), c->s); }
-            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
-            b.state = BS_SCALE;
+            // the residual kernel left the next inner solve's scaled
+            // right-hand side and its norm: straight to the inner solve
+            double irtol = 0.5 * rtol / b.inf.rel_res;
+            if (irtol < c->p.inner_rtol) irtol = c->p.inner_rtol;
+            if (irtol > 0.5) irtol = 0.5;
+            b.prec = 1;
+            if ((st = pcg_begin<float>(c, c->h_sc[S_R0], irtol, c->p.max_iter - b.inner_total))) return bfail(b, st);
+            b.state = BS_ITER;
         }
         return;
     }
@@ -1739,7 +1881,10 @@ fld_status fld_solve(fld_ctx* c, double* dE, fld_info* info) {
     fld_info inf{};
     fld_status st = solve_impl(c, &inf);
     if (st == FLD_OK || st == FLD_ENOCONV) {
-        CUDA_TRY(cudaMemcpyAsync(dE, c->dE, c->L[0].d.n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        // the mixed solver keeps dE as a double-float pair scaled by the
+        // step's power of two
+        if (c->mixed) launch_dE_to_f64(c->L[0].d.n, c->dE, dE, c->sc, c->pd.dt_exp, c->s);
+        else CUDA_TRY(cudaMemcpyAsync(dE, c->dE, c->L[0].d.n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
         CUDA_TRY(cudaEventRecord(c->e1, c->s));
         CUDA_TRY(cudaStreamSynchronize(c->s));
         harvest(c);
@@ -1964,7 +2109,11 @@ fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E, const double** nH
 fld_status fld_apply(fld_ctx* c, const double* x, double* y) {
     if (!c || !x || !y) return set_err(FLD_EINVAL, "null argument");
     if (!c->assembled) return set_err(FLD_EINVAL, "fld_apply before fld_assemble");
-    { KScope k(c, K_APPLY, 48.0 * c->L[0].d.n); launch_apply<double>(c->L[0].d, c->L[0].A64, x, y, c->s); }
+    {
+        KScope k(c, K_APPLY, 48.0 * c->L[0].d.n);
+        if (c->mixed) launch_apply_mx(c->L[0].d, c->L[0].A32, c->L[0].Alo, x, y, c->s);
+        else launch_apply<double>(c->L[0].d, c->L[0].A64, x, y, c->s);
+    }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(c->s));
     harvest(c);
@@ -1995,11 +2144,23 @@ fld_status fld_vcycle(fld_ctx* c, const double* r, double* z) {
 fld_status fld_get_system(fld_ctx* c, double* m, double* wx, double* wy, double* wz, double* b) {
     if (!c) return set_err(FLD_EINVAL, "null context");
     if (!c->assembled) return set_err(FLD_EINVAL, "fld_get_system before fld_assemble");
-    const size_t bytes = c->L[0].d.n * sizeof(double);
-    const double* src[5] = {c->L[0].A64.m, c->L[0].A64.wx, c->L[0].A64.wy, c->L[0].A64.wz, c->b};
+    const long long n = c->L[0].d.n;
+    const size_t bytes = n * sizeof(double);
     double* dst[5] = {m, wx, wy, wz, b};
-    for (int q = 0; q < 5; q++)
-        if (dst[q]) CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, c->s));
+    if (c->mixed) {
+        // the double-float operator as FP64 values
+        const Level& L = c->L[0];
+        const float* hi[4] = {L.A32.m, L.A32.wx, L.A32.wy, L.A32.wz};
+        const float* lo[4] = {L.Alo.m, L.Alo.wx, L.Alo.wy, L.Alo.wz};
+        for (int q = 0; q < 4; q++)
+            if (dst[q]) launch_df_to_f64(n, hi[q], lo[q], dst[q], c->s);
+        if (b) CUDA_TRY(cudaMemcpyAsync(b, c->b, bytes, cudaMemcpyDeviceToDevice, c->s));
+        CUDA_TRY(cudaGetLastError());
+    } else {
+        const double* src[5] = {c->L[0].A64.m, c->L[0].A64.wx, c->L[0].A64.wy, c->L[0].A64.wz, c->b};
+        for (int q = 0; q < 5; q++)
+            if (dst[q]) CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, c->s));
+    }
     CUDA_TRY(cudaStreamSynchronize(c->s));
     return FLD_OK;
 }

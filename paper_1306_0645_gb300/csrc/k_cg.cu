@@ -137,38 +137,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual64(Dims d, Op<double> A
     grid_reduce<2>(acc, mx, ra);
 }
 
-// r32 = r64 / s with s = max |r64|; x32 = 0; ||r32||^2 -> S_R0 and S_RR.
-__global__ void __launch_bounds__(RED_THREADS) k_ir_scale(long long n, const double* __restrict__ r64,
-                                                          float* __restrict__ r32, float* __restrict__ x32,
-                                                          RedArgs ra) {
-    const double s = ra.sc[S_RMAX];
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    DotAcc<float> da;
-    GRID_LOOP(c, n) {
-        const float v = (float)(r64[c] * inv);
-        r32[c] = v;
-        x32[c] = 0.0f;
-        da.add(v, v);
-    }
-    double acc[2] = {da.value(), 0.0};
-    acc[1] = acc[0];
-    const bool mx[2] = {false, false};
-    grid_reduce<2>(acc, mx, ra);
-}
-
-// x64 += s x32 (assign: x64 = s x32, the first refinement from x64 = 0).
-// p_last: the inner solve deferred its last update of x, x32 + alpha p_last
-// (the FP32 operation the update kernel would have done) takes its place.
-__global__ void k_ir_update(long long n, double* __restrict__ x64, const float* __restrict__ x32,
-                            const double* __restrict__ sc, int assign, const float* __restrict__ p_last) {
-    const double s = sc[S_RMAX];
-    const float alpha = (float)sc[S_ALPHA];
-    GRID_LOOP(c, n) {
-        const float xf = p_last ? fmaf(alpha, p_last[c], x32[c]) : x32[c];
-        x64[c] = assign ? s * (double)xf : fma(s, (double)xf, x64[c]);
-    }
-}
-
 // E_out = max(E + dE, 0) and the sums of the photon balance of the
 // unfloored update (energy density units; the host applies dt, dt c sigma,
 // dt adot/a and V / h nu): sum dE, sum eta, sum n_HI E^theta, sum E^theta
@@ -297,14 +265,6 @@ void launch_residual64(const Dims& d, Op<double> A, const double* diag, const do
                        double* r, const RedArgs& ra, cudaStream_t s) {
     ColShape sh = col_shape(d);
     k_residual64<<<sh.grid, sh.block, 0, s>>>(d, A, diag, b, x, r, ra);
-}
-void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
-                     cudaStream_t s) {
-    k_ir_scale<<<red_blocks(n), RED_THREADS, 0, s>>>(n, r64, r32, x32, ra);
-}
-void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
-                      cudaStream_t s, const float* p_last) {
-    k_ir_update<<<grid_blocks(n, 256), 256, 0, s>>>(n, x64, x32, sc, assign ? 1 : 0, p_last);
 }
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,
                      const double* nHI, const double* eta, double* E_out, const RedArgs& ra,

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "df.cuh"
 
 namespace fld {
 
@@ -25,6 +26,17 @@ struct PhysDev {
     float twoL_h32[3];  // 2 L_unit / h
     float thr32;        // screen threshold on 9 (kappa_f L)^2 + (R L)^2
     int limiter;        // 0 paper, 1 Levermore-Pomraning
+    // double-float constants of the mixed-precision kernels (k_mixed.cu)
+    df sigh[3];         // sigma h: optical depth of a cell per unit n_HI
+    df cw[3];           // theta dt c / h: a face weight is cw K S / sqrt(X)
+    df rminh[3];        // R_min h
+    df wmaxd[3];        // wmax (hi = wmax32)
+    df one_dta_d, mdtcs_d;   // mass term m = one_dta + mdtcs n_HI
+    df dtcs_d, dta_d;        // loss rate dt (c sigma n_HI + adot/a)
+    df dtm_d;                // dt = dtm 2^dt_exp, dtm in [1, 2)
+    df ith_d;                // 1 / theta
+    int dt_exp;
+    int df_limiter;     // the df limiter's constants lie in the FP32 range
 };
 
 // Operator of one level: mass term m, lower-face weights, inverse diagonal.
@@ -100,6 +112,56 @@ void launch_assemble_rhs(const Dims& d, const PhysDev& p, const double* E, const
 void launch_bnd_outflow(const Dims& d, const PhysDev& p, int s, Bnd bnd, const double* E,
                         const double* dE, const RedArgs& ra, cudaStream_t st);
 
+// ---- mixed-precision step on the FP32 pipe in double-float arithmetic
+// (k_mixed.cu).  The fine operator is (A, L): the FP32 operator of the
+// V-cycles and the low parts of m and the weights.
+// Pass 1: m and the face weights (df), input validation into sc[S_BAD], the
+// maxima of E, n_HI and eta into sc[S_EMAX], sc[S_NMAX], sc[S_ETAMAX] (the
+// caller zeroes them with the other slots before the assembly).
+// Faces the FP32 screen does not settle go to the per-block lists fl (when
+// fl.entries is set), finished by launch_asm_fix_mx.
+void launch_asm_faces_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, const double* eta,
+                         Op<float> A, Op<float> L, double* sc, FaceList fl, cudaStream_t s, int zb0 = 0,
+                         int nzb = -1);
+// The df limiter for the listed faces of those z-blocks.
+void launch_asm_fix_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, Op<float> A,
+                       Op<float> L, FaceList fl, cudaStream_t s, int zb0 = 0, int nzb = -1);
+// Pass 2: b (FP64), ||b||^2 and max |b| (reduction ra, R_STORE_SUM_MAX), the
+// FP32 inverse diagonal A.invd, Dirichlet face weights into bnd and m; scg:
+// the slots of pass 1's maxima.  Needs pass 1 of its z-blocks and the one
+// above.
+void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, const double* eta,
+                       Op<float> A, Op<float> L, double* b, Bnd bnd, const RedArgs& ra, const double* scg,
+                       cudaStream_t s, int zb0 = 0, int nzb = -1);
+// r32 = b 2^-ks (nearest float), x32 = 0; ||r32||^2, max |r32| (R_IRRES).
+void launch_ir_scale_b(long long n, const double* b, int ks, float* r32, float* x32, const RedArgs& ra,
+                       cudaStream_t s);
+// The refinement unknown x (dE) of the mixed solver is a df pair per cell
+// (float2), scaled by 2^-K with K the step's scale exponent (from the
+// maxima in scg, the context's slots).
+// x += 2^ks x32 (assign: x = 2^ks x32); p_last (optional): x32 still lacks
+// the last CG iteration's update, x32 + sc[S_ALPHA] p_last in FP32 is used
+void launch_ir_update_mx(long long n, void* x, const float* x32, const double* sc, bool assign, int ks,
+                         const float* p_last, const double* scg, int dt_exp, cudaStream_t s);
+// r = b - m x - sum_f w_f (x - x_nbr) in df; r32 = r 2^-ks (nearest float),
+// x32 = 0; ||r32||^2, max |r32| (R_IRRES).
+void launch_ir_residual(const Dims& d, Op<float> A, Op<float> L, const double* b, const void* x, int ks,
+                        float* r32, float* x32, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s);
+ColShape ir_residual_shape(const Dims& d);
+// E_out = max(E + dE, 0) and the photon-balance sums as launch_finalize,
+// summed in df relative to the scales of the maxima in scg; dE the df x.
+void launch_finalize_mx(long long n, const PhysDev& p, const double* E, const void* dE, const double* nHI,
+                        const double* eta, double* E_out, const RedArgs& ra, const double* scg, cudaStream_t s);
+// launch_bnd_outflow with dE the df x
+void launch_bnd_outflow_mx(const Dims& d, const PhysDev& p, int s, Bnd bnd, const double* E, const void* dE,
+                           const RedArgs& ra, const double* scg, cudaStream_t st);
+// the df x as FP64 values (fld_solve's output)
+void launch_dE_to_f64(long long n, const void* x, double* out, const double* scg, int dt_exp, cudaStream_t s);
+// out = h + l in FP64 (inspection hooks)
+void launch_df_to_f64(long long n, const float* h, const float* l, double* out, cudaStream_t s);
+// y = A x with the df operator, in FP64 (test hook)
+void launch_apply_mx(const Dims& d, Op<float> A, Op<float> L, const double* x, double* y, cudaStream_t s);
+
 // ---- multigrid (k_mg.cu), T = float or double
 template <class T>
 void launch_coarsen(const Dims& f, const Dims& c, Op<T> F, Op<T> C, cudaStream_t s);
@@ -167,14 +229,6 @@ void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s,
 // be null) is the stored FP64 diagonal.
 void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
                        double* r, const RedArgs& ra, cudaStream_t s);
-// r32 = r64 / sc[S_RMAX]; x32 = 0; ||r32||^2 -> S_R0 (and S_RR).
-void launch_ir_scale(long long n, const double* r64, float* r32, float* x32, const RedArgs& ra,
-                     cudaStream_t s);
-// x64 += sc[S_RMAX] * x32 (assign: x64 = sc[S_RMAX] * x32); p_last (optional):
-// x32 still lacks the last CG iteration's update, x32 + sc[S_ALPHA] p_last
-// in FP32 is used
-void launch_ir_update(long long n, double* x64, const float* x32, const double* sc, bool assign,
-                      cudaStream_t s, const float* p_last = nullptr);
 // E_out = max(E + dE, 0); sums for the photon balance into S_BAL (dE),
 // S_EMIT (eta), S_ABSORB (n_HI E^theta), S_ESUM (E^theta), the floor's
 // energy into S_FLOOR, sum dE^2 into S_DE2, sum E_out^2 into S_EN2

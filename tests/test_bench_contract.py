@@ -21,9 +21,20 @@ def test_reference_arm_json_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
-    assert d["config"]["n"] == 16 and "workload" in d["config"]
+    # the line names the benchmark's workload; each step times a bounded sample of it
+    assert d["config"]["n"] == 512 and d["config"]["sample_n"] == 16 and "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_one_core_oracle_sample():
+    # the child run that times the oracle on one core for the CPU baseline
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "bench.py", "--oracle-sample", "16"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["cores"] == 1 and d["value"] > 0 and d["n"] == 16

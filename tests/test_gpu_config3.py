@@ -7,7 +7,15 @@ CUDA path at the paper's tolerance 1e-8 in mixed precision, the oracle in FP64
 solved to 1e-12.  Each step's error is asserted at 1e-6 in the L2 norm and in
 the max norm relative to max E (the accuracy a 1e-8 residual controls), and
 the per-step table is written to $FLD_REPORT_DIR/config3_errors.json when
-that variable is set."""
+that variable is set.  A 1e-8 residual does not control the relative error
+of each cell; so after the 20 steps one more step, from the oracle's state on
+both sides, runs the CUDA path to 1e-11 (the oracle to 1e-13) and holds it
+to 1e-6 relative in every cell with E > 1e-6 max E.  After 20 steps E is
+large and nearly steady, the face fluxes are some 10^3 times |b|, and no
+solver reaches 1e-12 here: the plain FP64 residual stalls near 2e-12, the
+double-float one of the mixed solver near 6e-12 (both measured on this
+state); 1e-11 lies above both."""
+import dataclasses
 import json
 import os
 
@@ -55,12 +63,25 @@ def test_config3_twenty_steps(fld, oracle):
                      "err_max_rel_to_max": einf, "err_cellwise_E_gt_1e-6max": ecell,
                      "nHI_err_max_rel": exhi, "balance_rel": info["balance_rel"],
                      "floor_added_photons": info["floor_added"]})
+    # the cell-wise check at a tolerance that controls it, from the oracle's state
+    p12 = dataclasses.replace(p, rtol=1e-11, max_iter=200)
+    ctx12 = fld.fld_create(case.grid, p12)
+    Eg = dev(Eo)
+    info12 = fld.fld_step(ctx12, Eg, dev(nHIo), etag)
+    Eo12, _ = oracle.step(case.grid, p, {"rtol": 1e-13, "max_iter": 200}, Eo, nHIo, case.eta)
+    E12 = Eg.cpu().numpy().reshape(case.grid.shape)
+    mask = Eo12 > 1e-6 * Eo12.max()
+    cell12 = float((np.abs(E12 - Eo12)[mask] / Eo12[mask]).max())
+    rows.append({"step": "21 (from the oracle's state, CUDA path to 1e-11)", "rel_res": info12["rel_res"],
+                 "err_cellwise_E_gt_1e-6max": cell12})
+    ctx12.close()
     ctx.close()
     out = os.environ.get("FLD_REPORT_DIR")
     if out:
         os.makedirs(out, exist_ok=True)
         with open(os.path.join(out, "config3_errors.json"), "w") as f:
             json.dump(rows, f, indent=1)
-    for r in rows:
+    for r in rows[:-1]:
         assert r["rel_res"] <= 1e-8
         assert r["err_l2"] < 1e-6 and r["err_max_rel_to_max"] < 1e-6, r
+    assert info12["rel_res"] <= 1e-11 and cell12 < 1e-6, rows[-1]

@@ -94,6 +94,46 @@ def test_assembly_paper_limiter_regimes(fld, oracle):
     assert np.isclose(D, Dmax, rtol=1e-12).any() and (D < 0.5 * Dmax).any()
 
 
+@pytest.mark.parametrize("n,per,lim", SMALL)
+def test_mixed_assembly_parity(fld, oracle, n, per, lim):
+    """The mixed solver's double-float operator (an FP32 high part plus a low
+    part, both returned as FP64 by fld_get_system) and its FP64 right-hand
+    side, assembled on the FP32 pipe, against the oracle's FP64 assembly."""
+    case = synth.random_case(n, seed=100 + sum(n), periodic=per, limiter=lim, zero_frac=0.05)
+    case.params.adot_over_a = 2e-17
+    case.params.precision = synth.PREC_MIXED
+    ref = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
+    ctx = fld.fld_create(case.grid, case.params)
+    E, nHI, eta = dev(case.E), dev(case.nHI), dev(case.eta)
+    fld.fld_assemble(ctx, E, nHI, eta)
+    out = {k: torch.empty_like(E) for k in ("m", "wx", "wy", "wz", "b")}
+    fld.fld_get_system(ctx, **out)
+    for k in ("m", "wx", "wy", "wz"):
+        np.testing.assert_allclose(host(out[k]).reshape(ref[k].shape), ref[k], rtol=1e-12, atol=0)
+    assert rel_max(host(out["b"]).reshape(ref["b"].shape), ref["b"]) < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
+def test_mixed_limiter_regimes(fld, oracle, prec):
+    """Capped, thick and streaming faces along one axis, with face energies
+    over 43 decades: the FP64 and the double-float limiter against the
+    oracle's."""
+    g = synth.Grid((64, 4, 4), (1e19, 2e20, 2e20))
+    p = synth.Params(limiter=synth.LIMITER_PAPER, precision=prec)
+    x = np.arange(64)
+    E = np.broadcast_to(10.0 ** (-30 + 1.4 * np.maximum(x - 32, 0)), g.shape).copy()
+    nHI = np.broadcast_to(10.0 ** (-8 + 0.15 * x), g.shape).copy()
+    eta = np.zeros(g.shape)
+    ref = oracle.assemble(g, p, E, nHI, eta)
+    ctx = fld.fld_create(g, p)
+    fld.fld_assemble(ctx, dev(E), dev(nHI), dev(eta))
+    wx = torch.empty(g.cells, dtype=torch.float64, device="cuda")
+    fld.fld_get_system(ctx, wx=wx)
+    np.testing.assert_allclose(host(wx).reshape(g.shape), ref["wx"], rtol=1e-12, atol=0)
+    ctx.close()
+
+
 @pytest.mark.parametrize("n,per,lim", SMALL[:6])
 def test_apply_and_vcycle_parity(fld, oracle, n, per, lim):
     case = synth.random_case(n, seed=200 + sum(n), periodic=per, limiter=lim)
