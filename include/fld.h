@@ -145,6 +145,11 @@ typedef struct {
                                   (default 32768, at most 2^24; 0 = one
                                   launch per sweep);
                                   same arithmetic as the per-level kernels */
+    int paper_order;           /* red/black Gauss-Seidel: 0 (default) post-
+                                  sweeps black then red, so the V-cycle is a
+                                  symmetric preconditioner; 1 red then black
+                                  in the post-sweeps as in the pre-sweeps,
+                                  Table 1's "nonsymmetric" relaxation */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -174,7 +179,8 @@ typedef struct fld_ctx fld_ctx;
 /* Fill *p with defaults: c = 2.99792458e10, dmax_coef 0.006, rmin_coef 1e-20,
  * sigma 1.6e-18, hnu 13.6 eV, PAPER limiter, FP64, RB-GS, omega 0.8,
  * rtol 1e-8, max_iter 50, pre = post = 1, inner_rtol 1e-4, coarse_cap 1024,
- * graphs -1, fused_post 0, theta 1, scale_factor 1, tail_cells 32768.
+ * graphs -1, fused_post 0, theta 1, scale_factor 1, tail_cells 32768,
+ * paper_order 0.
  * dt and L_unit are set to 1e5 yr and 6.6 kpc and should be overwritten. */
 fld_status fld_params_default(fld_params* p);
 

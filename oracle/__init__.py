@@ -74,7 +74,7 @@ class _Solver(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("omega", ctypes.c_double),
                 ("pre", ctypes.c_int), ("post", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("coarse_cap", ctypes.c_int)]
+                ("coarse_cap", ctypes.c_int), ("paper_order", ctypes.c_int)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -156,7 +156,7 @@ def _solver(s) -> _Solver:
     return _Solver(int(_get(s, "smoother", SMOOTH_RBGS)), float(_get(s, "jacobi_omega", 0.8)),
                    int(_get(s, "pre", 1)), int(_get(s, "post", 1)),
                    float(_get(s, "rtol", 1e-8)), int(_get(s, "max_iter", 50)),
-                   int(_get(s, "coarse_cap", 1024)))
+                   int(_get(s, "coarse_cap", 1024)), int(_get(s, "paper_order", 0)))
 
 
 def _arr(a, shape=None):

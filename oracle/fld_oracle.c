@@ -57,7 +57,9 @@
  *     Dirichlet boundary faces; coarse mass term = mean of the 8 children's
  *     mass terms, the boundary weights apart); dense Cholesky on the coarsest
  *     grid; one V(pre,post) cycle per PCG iteration, red = (i+j+k) even,
- *     pre-sweeps red then black, post-sweeps black then red (symmetric);
+ *     pre-sweeps red then black, post-sweeps black then red (symmetric;
+ *     or red then black, the order of Table 1's "nonsymmetric" relaxation,
+ *     with paper_order);
  *     weighted Jacobi as the alternative smoother;
  *   - PCG from x0 = 0, stop when ||r||_2 / ||b||_2 <= rtol on the
  *     recursively updated residual; b = 0 gives dE = 0 in 0 iterations;
@@ -120,6 +122,8 @@ typedef struct {
     double rtol;
     int max_iter;
     int coarse_cap;    /* largest coarsest-grid size accepted */
+    int paper_order;   /* RB-GS post-sweeps red then black (Table 1's
+                          "nonsymmetric" relaxation); 0: black then red */
 } or_solver;
 
 typedef struct {
@@ -730,7 +734,8 @@ static void vcycle(or_hier* H, int l, const double* r, double* z,
     vcycle(H, l + 1, H->rc[l + 1], H->zc[l + 1], s);
     prolong_add(L, C, H->zc[l + 1], z);
     for (int it = 0; it < s->post; it++) {
-        if (s->smoother == OR_SMOOTH_RBGS) { gs_colour(L, r, z, 1); gs_colour(L, r, z, 0); }
+        if (s->smoother == OR_SMOOTH_RBGS && s->paper_order) { gs_colour(L, r, z, 0); gs_colour(L, r, z, 1); }
+        else if (s->smoother == OR_SMOOTH_RBGS) { gs_colour(L, r, z, 1); gs_colour(L, r, z, 0); }
         else jacobi_sweep(L, r, z, s->omega, H->tmp[l]);
     }
 }

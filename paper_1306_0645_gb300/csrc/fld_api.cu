@@ -117,18 +117,9 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     }
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz))
         return set_err(FLD_EINVAL, "cell widths must be finite and > 0");
-    for (int a = 0; a < 3; a++) {
-        const int lo = g->bc[a], hi = g->bc_hi[a];
-        if (lo < FLD_BC_ZERO_GRADIENT || lo > FLD_BC_OUTFLOW || hi < FLD_BC_ZERO_GRADIENT || hi > FLD_BC_OUTFLOW)
-            return set_err(FLD_EINVAL, "unknown boundary condition (%d, %d) on axis %d", lo, hi, a);
-        if (lo == FLD_BC_PERIODIC && hi != FLD_BC_PERIODIC && hi != FLD_BC_ZERO_GRADIENT)
-            return set_err(FLD_EINVAL, "axis %d is periodic but its upper face is %d", a, hi);
-        if (lo != FLD_BC_PERIODIC && hi == FLD_BC_PERIODIC)
-            return set_err(FLD_EINVAL, "axis %d: periodic upper face needs a periodic lower face", a);
-        for (int u = 0; u < 2; u++)
-            if ((u ? hi : lo) == FLD_BC_DIRICHLET && lo != FLD_BC_PERIODIC &&
-                !(std::isfinite(g->bc_value[2 * a + u]) && g->bc_value[2 * a + u] >= 0.0))
-                return set_err(FLD_EINVAL, "Dirichlet value of face %d must be finite and >= 0", 2 * a + u);
+    {
+        char msg[160];
+        if (!fld::bc_valid(g, msg, sizeof msg)) return set_err(FLD_EINVAL, "%s", msg);
     }
     if (!finite_pos(p->dt)) return set_err(FLD_EINVAL, "dt must be finite and > 0");
     if (!finite_pos(p->c)) return set_err(FLD_EINVAL, "c must be finite and > 0");
@@ -163,6 +154,7 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
         return set_err(FLD_EINVAL, "coarse_cap must lie in [1, %d]", COARSE_CAP_MAX);
     if (p->tail_cells < 0 || p->tail_cells > (1 << 24))
         return set_err(FLD_EINVAL, "tail_cells must lie in [0, 2^24]");
+    if (p->paper_order != 0 && p->paper_order != 1) return set_err(FLD_EINVAL, "paper_order must be 0 or 1");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
@@ -173,6 +165,41 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
                        dims[nl - 1][0], dims[nl - 1][1], dims[nl - 1][2], nc, p->coarse_cap);
     return FLD_OK;
 }
+
+}  // namespace
+
+namespace fld {
+// The per-face boundary conditions of a grid: known kinds, a periodic axis
+// periodic at both faces (an upper face left at 0, zero gradient, counts as
+// periodic too), and finite non-negative Dirichlet values.  On failure msg
+// says why.
+bool bc_valid(const fld_grid* g, char* msg, size_t len) {
+    for (int a = 0; a < 3; a++) {
+        const int lo = g->bc[a], hi = g->bc_hi[a];
+        if (lo < FLD_BC_ZERO_GRADIENT || lo > FLD_BC_OUTFLOW || hi < FLD_BC_ZERO_GRADIENT || hi > FLD_BC_OUTFLOW) {
+            snprintf(msg, len, "unknown boundary condition (%d, %d) on axis %d", lo, hi, a);
+            return false;
+        }
+        if (lo == FLD_BC_PERIODIC && hi != FLD_BC_PERIODIC && hi != FLD_BC_ZERO_GRADIENT) {
+            snprintf(msg, len, "axis %d is periodic but its upper face is %d", a, hi);
+            return false;
+        }
+        if (lo != FLD_BC_PERIODIC && hi == FLD_BC_PERIODIC) {
+            snprintf(msg, len, "axis %d: periodic upper face needs a periodic lower face", a);
+            return false;
+        }
+        for (int u = 0; u < 2; u++)
+            if ((u ? hi : lo) == FLD_BC_DIRICHLET && lo != FLD_BC_PERIODIC &&
+                !(std::isfinite(g->bc_value[2 * a + u]) && g->bc_value[2 * a + u] >= 0.0)) {
+                snprintf(msg, len, "Dirichlet value of face %d must be finite and >= 0", 2 * a + u);
+                return false;
+            }
+    }
+    return true;
+}
+}  // namespace fld
+
+namespace {
 
 // Sides (bit 2 axis + upper) held at a fixed E: Dirichlet and outflow faces.
 int dirichlet_mask(const fld_grid* g) {
@@ -463,6 +490,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
         ta.nlev = c->nl - l;
         ta.pre = c->p.pre;
         ta.post = c->p.post;
+        ta.paper_order = c->p.paper_order;
         ta.ainv = c->ainv;
         double bytes = 0.0;
         for (int q = 0; q < ta.nlev; q++) {
@@ -529,7 +557,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
     if constexpr (std::is_same<T, float>::value) {
         // one fused post-sweep: t = z + P e_c, then black and red from t into z
-        if (p.fused_post && p.smoother == FLD_SMOOTH_RBGS && p.post == 1 && post4_ok(L.d)) {
+        if (p.fused_post && !p.paper_order && p.smoother == FLD_SMOOTH_RBGS && p.post == 1 && post4_ok(L.d)) {
             { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts);
               launch_prolong_to4(L.d, C.d, (const float*)C.z, z, t, s); }
             KScope k(c, kc(K_POST_FUSED), 7.0 * n * ts);
@@ -539,10 +567,14 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
         }
     }
     { KScope k(c, kc(K_PROLONG), (2.0 * n + nc) * ts); prolong_any<T>(L.d, C.d, (const T*)C.z, z, s, L.tune[TN_PROLONG]); }
+    // post-sweeps black then red (symmetric cycle), or red then black as
+    // the pre-sweeps (Table 1's order, paper_order)
+    const int first = p.paper_order ? 0 : 1;
     for (int it = 0; it < p.post; it++) {
         if (p.smoother == FLD_SMOOTH_RBGS) {
-            for (int colour = 1; colour >= 0; colour--) {
-                const bool last = it == p.post - 1 && colour == 0;
+            for (int q = 0; q < 2; q++) {
+                const int colour = q == 0 ? first : 1 - first;
+                const bool last = it == p.post - 1 && q == 1;
                 if constexpr (std::is_same<T, float>::value) {
                     if (last && dot && use4<T>(L.d)) {
                         KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
@@ -1763,6 +1795,7 @@ fld_status fld_params_default(fld_params* p) {
     p->coarse_cap = 1024;
     p->graphs = -1;
     p->fused_post = 0;
+    p->paper_order = 0;
     p->theta = 1.0;
     p->scale_factor = 1.0;
     p->tail_cells = 32768;

@@ -75,6 +75,10 @@ fld_status fld_residual_noalloc(const fld_grid* g, const double* m, const double
         return fail(FLD_EINVAL, "fld_residual_noalloc: null argument");
     if (g->nx < 1 || g->ny < 1 || g->nz < 1)
         return fail(FLD_EINVAL, "fld_residual_noalloc: grid dimensions must be >= 1");
+    {
+        char msg[160];
+        if (!bc_valid(g, msg, sizeof msg)) return fail(FLD_EINVAL, std::string("fld_residual_noalloc: ") + msg);
+    }
     Dims d;
     d.nx = g->nx;
     d.ny = g->ny;
@@ -85,7 +89,7 @@ fld_status fld_residual_noalloc(const fld_grid* g, const double* m, const double
     d.n = (long long)d.nx * d.ny * d.nz;
     // the fixed scratch holds the partial sums of at most RED_MAX_BLOCKS
     // blocks, the most the launch of an x-y plane of about 2^22 cells needs
-    const ColShape sh = col_shape(d);
+    const ColShape sh = residual64_shape(d);
     if ((long long)sh.grid.x * sh.grid.y * sh.grid.z > RED_MAX_BLOCKS || d.n > (1LL << 33))
         return fail(FLD_EINVAL,
                     "fld_residual_noalloc: grid too large for the fixed scratch (an x-y plane may need "

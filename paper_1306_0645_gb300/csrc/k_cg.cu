@@ -261,9 +261,11 @@ void launch_apply(const Dims& d, Op<T> A, const T* x, T* y, cudaStream_t s) {
     ColShape sh = col_shape(d);
     k_apply<T><<<sh.grid, sh.block, 0, s>>>(d, A, x, y);
 }
+ColShape residual64_shape(const Dims& d) { return col_shape(d); }
+
 void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
                        double* r, const RedArgs& ra, cudaStream_t s) {
-    ColShape sh = col_shape(d);
+    const ColShape sh = residual64_shape(d);
     k_residual64<<<sh.grid, sh.block, 0, s>>>(d, A, diag, b, x, r, ra);
 }
 void launch_finalize(long long n, const PhysDev& p, const double* E, const double* dE,

@@ -204,7 +204,8 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
 
 // Up-leg phases of level L: z += P zc, then the post-sweeps.
 template <bool CG, class T, class Sync>
-__device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T* zc, int post, long long tid,
+__device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T* zc, int post, int first,
+                        long long tid,
                         long long nth, Sync sync) {
     const Dims& d = L.d;
     const Op<T>& A = L.A;
@@ -231,8 +232,10 @@ __device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T
         z[c] = ldw<CG>((const T*)z, c) + acc;
     }
     sync();
+    // first: the colour the post-sweep starts with (1 black: symmetric cycle)
     for (int it = 0; it < post; it++)
-        for (int colour = 1; colour >= 0; colour--) {
+        for (int q = 0; q < 2; q++) {
+            const int colour = q == 0 ? first : 1 - first;
             TAIL_LOOP(c, d.n) {
                 int i, j, k;
                 tail_ijk(c, d, i, j, k);
@@ -289,7 +292,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
                 tail_down<false, T>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].r, a.pre, tid, nth, bsync);
             tail_coarsest<false, T>((int)a.L[nl - 1].d.n, a.ainv, sv[nl - 1], tid, nth, bsync);
             for (int l = nl - 2; l >= ls; l--)
-                tail_up<false, T>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].z, a.post, tid, nth, bsync);
+                tail_up<false, T>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].z, a.post, a.paper_order ? 0 : 1, tid, nth,
+                                  bsync);
             for (long long c = tid; c < a.L[ls].d.n; c += nth) a.L[ls].z[c] = sv[ls].z[c];
         }
         cl.sync();
@@ -300,7 +304,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
     // ---- up, cluster mode: levels ls-1 .. 0
     for (int l = (ls < nl ? ls : nl - 1) - 1; l >= 0; l--) {
         const TailLevel<T>& L = a.L[l];
-        tail_up<true, T>(L, Vec<T>{L.r, L.z, L.t}, a.L[l + 1].d, a.L[l + 1].z, a.post, gtid, gthreads, csync);
+        tail_up<true, T>(L, Vec<T>{L.r, L.z, L.t}, a.L[l + 1].d, a.L[l + 1].z, a.post, a.paper_order ? 0 : 1, gtid,
+                         gthreads, csync);
     }
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "df.cuh"
+#include "fld.h"
 
 namespace fld {
 
@@ -225,6 +226,9 @@ void launch_combine_sums(const double* chunk_sc, int nch, double* sc, const Slot
 void launch_combine_chunks(const double* chunk_sc, int nch, double* sc, int s_sum, int s_max, cudaStream_t s);
 void launch_cg_check(cudaGraphConditionalHandle h, double* sc, cudaStream_t s,
                      const cudaGraphConditionalHandle* h2 = nullptr);
+// The launch shape of launch_residual64 (callers that size reduction
+// scratch for it check its block count).
+ColShape residual64_shape(const Dims& d);
 // r64 = b - A x (FP64); ||r64||^2 -> slot0, max|r64| -> slot1.  diag (may
 // be null) is the stored FP64 diagonal.
 void launch_residual64(const Dims& d, Op<double> A, const double* diag, const double* b, const double* x,
@@ -259,6 +263,7 @@ struct TailLevel {
 template <class T>
 struct TailArgs {
     int nlev, pre, post;
+    int paper_order;  // post-sweeps red then black (else black then red)
     int small_from;   // first level run by one CTA in shared memory (nlev: none)
     const double* ainv;
     TailLevel<T> L[TAIL_MAX_LEVELS];
@@ -272,6 +277,9 @@ int vtail_cluster();
 
 // Sets the calling thread's fld_last_error message (fld_api.cu).
 void record_error(const char* msg);
+// The per-face boundary conditions of g are consistent (fld_create's rule);
+// otherwise false with the reason in msg (fld_api.cu).
+bool bc_valid(const fld_grid* g, char* msg, size_t len);
 
 // Launch shape of a four-cells-per-thread sweep: threads per block (a
 // power of two up to 256, x lanes first) and the total blocks aimed at (the

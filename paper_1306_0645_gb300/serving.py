@@ -6,10 +6,14 @@ resident contexts (multigrid hierarchies and work buffers, one per grid size
 they have served), so a request's step runs through the C ABI on that
 worker's stream while other requests run on the others: work from requests
 that arrived while others were on the GPU overlaps on the device.
-Admission is by HBM budget: a request is admitted once the device bytes of
-the requests in flight plus its own (context footprint from
-fld_footprint_bytes, plus its fields) fit the budget; a request that can
-never fit is rejected.
+Admission is by HBM budget over everything the server keeps on the device:
+each resident context (its footprint from fld_footprint_bytes, plus its
+field buffers) is charged from its creation until it is evicted.  A request
+whose worker already holds a context of its size runs at no new charge;
+otherwise the context is created once the charged bytes plus its footprint
+fit the budget, evicting least recently used idle contexts to make room and
+waiting for running ones to finish when that is not enough.  A request
+that can never fit is rejected.
 
 Every kernel launch shape depends only on the grid size and parameters and
 every reduction adds in a fixed order, so a request's result is the same,
@@ -32,6 +36,18 @@ import numpy as np
 from . import fld, synth
 
 CANCELLED = -1   # Result.status of a request cancelled before it was stepped
+
+
+@dataclasses.dataclass
+class _Resident:
+    """A context kept on the device with its field buffers (E, n_HI, eta),
+    the bytes charged for it, and whether a step is using it."""
+
+    nbytes: float
+    ctx: Optional[object] = None
+    buf: Optional[tuple] = None
+    busy: bool = True
+    last: float = 0.0
 
 
 @dataclasses.dataclass
@@ -77,15 +93,16 @@ class Server:
         # CG iterations run as one graph launch for all of them
         self.batch = max(1, int(batch))
         self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED)
-        self._used = 0.0
+        self._used = 0.0          # bytes charged for resident contexts
+        self.peak_bytes = 0.0     # the most ever charged (never above the budget)
         self._cv = threading.Condition()
         self._streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
-        self._ctx: List[Dict[int, fld.Context]] = [dict() for _ in range(workers)]
-        self._bctx: List[Dict[int, List[fld.Context]]] = [dict() for _ in range(workers)]
+        # resident contexts with their device fields, keyed (worker, kind,
+        # size, index): kind "s" one per worker and size, kind "b" the k-th
+        # context of a batch group; no request allocates device memory of its
+        # own while its context stays resident
+        self._res: Dict[tuple, _Resident] = {}
         self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
-        # resident device fields (E, n_HI, eta) per worker and size: a worker
-        # steps one request at a time, so no request allocates device memory
-        self._fbuf: List[Dict[int, tuple]] = [dict() for _ in range(workers)]
         self._fp_cache: Dict[int, int] = {}
         self._cancelled = set()
         self._cancel_lock = threading.Lock()
@@ -112,28 +129,88 @@ class Server:
             self._fp_cache[n] = fp + 3 * n ** 3 * 8 if fp else 0
         return self._fp_cache[n]
 
-    def _admit(self, nbytes: float) -> bool:
-        if nbytes <= 0 or nbytes > self.budget:
-            return False
+    def resident_bytes(self) -> float:
+        """Bytes charged for the contexts the server keeps on the device."""
         with self._cv:
-            while self._used + nbytes > self.budget:
-                self._cv.wait()
-            self._used += nbytes
-        return True
+            return self._used
 
-    def _release(self, nbytes: float):
+    def resident_sizes(self, w: int, batch: bool = False) -> List[int]:
+        """Grid sizes of worker w's resident contexts (of its batch groups
+        when batch), sorted, with repeats for several contexts of one size."""
+        kind = "b" if batch else "s"
         with self._cv:
-            self._used -= nbytes
+            return sorted(k[2] for k in self._res if k[0] == w and k[1] == kind)
+
+    def _evict_idle(self, need: float, keep) -> None:
+        """Free least recently used idle contexts (not in keep) until need
+        more bytes fit the budget or none is left; under the lock."""
+        while self._used + need > self.budget:
+            idle = [(e.last, k) for k, e in self._res.items() if not e.busy and k not in keep]
+            if not idle:
+                return
+            _, k = min(idle)
+            e = self._res.pop(k)
+            if e.ctx is not None:
+                e.ctx.close()
+            e.buf = None
+            self._used -= e.nbytes
+
+    def _acquire(self, wanted) -> Optional[List[_Resident]]:
+        """Mark the resident contexts of wanted [(key, n), ...] busy, charging
+        the budget for those not yet resident, all at once: evicts idle
+        contexts to make room and waits for busy ones when that is not
+        enough.  None if the new ones together can never fit."""
+        keys = {k for k, _ in wanted}
+        new_bytes = sum(self.footprint(n) for k, n in wanted if k not in self._res)
+        if any(self.footprint(n) <= 0 for _, n in wanted) or new_bytes > self.budget:
+            return None
+        with self._cv:
+            while True:
+                if any(k in self._res and self._res[k].busy for k in keys):
+                    self._cv.wait()
+                    continue
+                need = sum(self.footprint(n) for k, n in wanted if k not in self._res)
+                if self._used + need > self.budget:
+                    self._evict_idle(need, keys)
+                if self._used + need <= self.budget:
+                    break
+                self._cv.wait()
+            out = []
+            for k, n in wanted:
+                e = self._res.get(k)
+                if e is None:
+                    e = _Resident(self.footprint(n))
+                    self._res[k] = e
+                    self._used += e.nbytes
+                e.busy = True
+                out.append(e)
+            self.peak_bytes = max(self.peak_bytes, self._used)
+            return out
+
+    def _release(self, entries, failed=()):
+        """Mark entries idle; drop (and uncharge) the keys in failed."""
+        with self._cv:
+            now = time.perf_counter()
+            for e in entries:
+                e.busy = False
+                e.last = now
+            for k in failed:
+                e = self._res.pop(k, None)
+                if e is not None:
+                    if e.ctx is not None:
+                        e.ctx.close()
+                    self._used -= e.nbytes
             self._cv.notify_all()
 
-    # ----------------------------------------------------------- one step
-    def _context(self, w: int, n: int) -> fld.Context:
-        ctx = self._ctx[w].get(n)
-        if ctx is None:
-            ctx = fld.fld_create(synth.Grid.cube(n), self.params, self._streams[w])
-            self._ctx[w][n] = ctx
-        return ctx
+    def _build(self, e: _Resident, w: int, n: int) -> None:
+        """Create a resident entry's context and field buffers (first use)."""
+        torch = self.torch
+        if e.ctx is None:
+            e.ctx = fld.fld_create(synth.Grid.cube(n), self.params, self._streams[w])
+        if e.buf is None:
+            e.buf = tuple(torch.empty(n ** 3, dtype=torch.float64, device="cuda") for _ in range(3))
 
+    # ----------------------------------------------------------- one step
     def _fields(self, r: synth.Request, out=None):
         """E, n_HI and eta of a request on the current stream, built from its
         payload (source cells and rates); into the tensors out when given."""
@@ -160,18 +237,17 @@ class Server:
         pinned host memory)."""
         torch = self.torch
         start = time.perf_counter() - t0
-        nbytes = self.footprint(r.n)
-        if not self._admit(nbytes):
+        key = (w, "s", r.n, 0)
+        got = self._acquire([(key, r.n)])
+        if got is None:
             return Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, fld.FLD_ENOMEM)
+        e = got[0]
+        failed = ()
         try:
             with torch.cuda.stream(self._streams[w]):
-                ctx = self._context(w, r.n)
-                buf = self._fbuf[w].get(r.n)
-                if buf is None:
-                    buf = tuple(torch.empty(r.n ** 3, dtype=torch.float64, device="cuda") for _ in range(3))
-                    self._fbuf[w][r.n] = buf
-                E, nHI, eta = self._fields(r, buf)
-                info = fld.fld_step(ctx, E, nHI, eta, check=False)
+                self._build(e, w, r.n)
+                E, nHI, eta = self._fields(r, e.buf)
+                info = fld.fld_step(e.ctx, E, nHI, eta, check=False)
                 host = self._pinned[w].get(r.n)
                 if host is None:
                     host = torch.empty(r.n ** 3, dtype=torch.float64, pin_memory=True)
@@ -179,8 +255,11 @@ class Server:
                 host.copy_(E, non_blocking=True)
                 self._streams[w].synchronize()
                 out = host.numpy().copy() if self.keep else None
+        except Exception:
+            failed = (key,)
+            raise
         finally:
-            self._release(nbytes)
+            self._release(got, failed)
         return Result(r.rid, r.n, r.arrival, start, time.perf_counter() - t0, info["status"],
                       info["iters"], info["outer_iters"], info["rel_res"], out)
 
@@ -198,23 +277,26 @@ class Server:
                 admitted.append(r)
         if not admitted:
             return out
-        # the group is admitted as a whole (the worker loop keeps it within
-        # the budget), so workers never hold part of the budget while waiting
-        total = float(sum(self.footprint(r.n) for r in admitted))
-        self._admit(total)
-        nbytes = [total]
+        # the group's contexts are acquired as a whole, so a worker never
+        # holds part of the budget while waiting for the rest
+        used: Dict[int, int] = {}
+        wanted = []
+        for r in admitted:
+            k = used.get(r.n, 0)
+            used[r.n] = k + 1
+            wanted.append(((w, "b", r.n, k), r.n))
+        got = self._acquire(wanted)
+        if got is None:
+            now = time.perf_counter() - t0
+            return out + [Result(r.rid, r.n, r.arrival, start, now, fld.FLD_ENOMEM) for r in admitted]
+        failed = ()
         try:
             with torch.cuda.stream(self._streams[w]):
-                used: Dict[int, int] = {}
                 ctxs, fields = [], []
-                for r in admitted:
-                    pool = self._bctx[w].setdefault(r.n, [])
-                    k = used.get(r.n, 0)
-                    used[r.n] = k + 1
-                    if k == len(pool):
-                        pool.append(fld.fld_create(synth.Grid.cube(r.n), self.params, self._streams[w]))
-                    ctxs.append(pool[k])
-                    fields.append(self._fields(r))
+                for r, e in zip(admitted, got):
+                    self._build(e, w, r.n)
+                    ctxs.append(e.ctx)
+                    fields.append(self._fields(r, e.buf))
                 st, infos = fld.fld_step_batched(ctxs, [f[0] for f in fields], [f[1] for f in fields],
                                                  [f[2] for f in fields], check=False)
                 hosts = []
@@ -229,9 +311,11 @@ class Server:
                     out.append(Result(r.rid, r.n, r.arrival, start, now, info["status"], info["iters"],
                                       info["outer_iters"], info["rel_res"],
                                       h.numpy().copy() if h is not None else None))
+        except Exception:
+            failed = tuple(k for k, _ in wanted)
+            raise
         finally:
-            for nb in nbytes:
-                self._release(nb)
+            self._release(got, failed)
         return out
 
     # ------------------------------------------------------------ the loop
@@ -324,17 +408,13 @@ class Server:
 
     def close(self):
         """Free every resident context and field buffer."""
-        for d in self._ctx:
-            for ctx in d.values():
-                ctx.close()
-            d.clear()
-        for d in self._fbuf:
-            d.clear()
-        for d in self._bctx:
-            for pool in d.values():
-                for ctx in pool:
-                    ctx.close()
-            d.clear()
+        with self._cv:
+            for e in self._res.values():
+                if e.ctx is not None:
+                    e.ctx.close()
+                e.buf = None
+            self._res.clear()
+            self._used = 0.0
 
 
 def summarize(results: Sequence[Result]) -> dict:

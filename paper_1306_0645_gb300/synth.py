@@ -109,6 +109,7 @@ class Params:
     theta: float = 1.0
     scale_factor: float = 1.0
     tail_cells: int = 32768
+    paper_order: int = 0
 
 
 @dataclasses.dataclass

@@ -58,3 +58,15 @@ def test_host_only_calls(libfld):
     assert fld.fld_footprint_bytes(synth.Grid.cube(101), synth.Params()) == 0
     bad = synth.Params(dt=-1.0)
     assert fld.fld_footprint_bytes(g, bad) == 0
+
+
+def test_noalloc_rejects_inconsistent_faces():
+    # the same boundary rule as fld_create: a periodic axis cannot have an
+    # outflow upper face; refused before any device pointer is read
+    from paper_1306_0645_gb300 import fld, synth
+    g = fld.make_grid(synth.Grid((4, 4, 4), (1.0, 1.0, 1.0), (True, False, False)))
+    g.bc_hi[0] = fld.FLD_BC_OUTFLOW
+    p = ctypes.c_void_p(16)
+    st = fld.lib().fld_residual_noalloc(ctypes.byref(g), p, p, p, p, p, p, None, p, None)
+    assert st == fld.FLD_EINVAL
+    assert "periodic" in fld.fld_last_error()

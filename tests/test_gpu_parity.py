@@ -628,3 +628,48 @@ def test_host_step_failure_then_success(fld, n):
     fld.fld_step(ctx, E, dev(case.nHI), dev(case.eta))
     ctx.close()
     assert np.array_equal(Eh.ravel(), host(E).ravel())
+
+
+# ------------------------------------------------------------------
+# Table 1's "nonsymmetric" red/black relaxation (paper_order): post-sweeps
+# red then black like the pre-sweeps
+
+@pytest.mark.parametrize("tail", [32768, 0])
+@pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
+def test_paper_order_vcycle_parity(fld, oracle, prec, tail):
+    case = synth.random_case((64, 32, 48), seed=77, periodic=(True, False, False), E_decades=(-20, -14))
+    op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
+    p = case.params
+    p.precision, p.tail_cells, p.paper_order = prec, tail, 1
+    ctx = fld.fld_create(case.grid, p)
+    fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
+    x = np.random.default_rng(12).standard_normal(case.grid.shape)
+    z = torch.empty(case.grid.cells, dtype=torch.float64, device="cuda")
+    fld.fld_vcycle(ctx, dev(x), z)
+    ctx.close()
+    zg = host(z).reshape(x.shape)
+    zref = oracle.vcycle(case.grid, op, x, {"paper_order": 1})
+    tol = 1e-12 if prec == synth.PREC_FP64 else 1e-5
+    assert rel_max(zg, zref) < tol
+    # the symmetric cycle is measurably different
+    zsym = oracle.vcycle(case.grid, op, x)
+    assert rel_max(zsym, zref) > 1e-3
+
+
+def test_paper_order_steps(fld, oracle):
+    # FP64 to 1e-13 against the oracle with the same relaxation, and mixed at
+    # the paper's 1e-8
+    case = synth.config2(32)
+    case.params.paper_order = 1
+    E, Eref, info, iref = fp64_step_pair(fld, oracle, case)
+    Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200, "paper_order": 1},
+                          case.E, case.nHI, case.eta)
+    assert info["rel_res"] <= 1e-13
+    assert rel_max(E - case.E, Eref - case.E) < 1e-10
+    m = synth.config4(64, sources=512)
+    m.params.paper_order = 1
+    Em, im = mixed_step(fld, m, 1e-8)
+    Emref, _ = oracle.step(m.grid, m.params, {"rtol": 1e-12, "max_iter": 200, "paper_order": 1}, m.E, m.nHI, m.eta)
+    assert im["rel_res"] <= 1e-8
+    assert np.linalg.norm(Em - Emref) / np.linalg.norm(Emref) < 1e-6
+    assert np.abs(Em - Emref).max() / np.abs(Emref).max() < 1e-6

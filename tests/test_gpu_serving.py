@@ -2,7 +2,8 @@
 
 A request's result is the same bit for bit alone and in the mix; results
 match the FP64 oracle; admission by HBM budget rejects what can never fit
-and holds back what does not fit yet."""
+and holds back what does not fit yet, counting every context it keeps
+resident."""
 import numpy as np
 import pytest
 
@@ -58,11 +59,23 @@ def test_admission_by_budget(serving):
     probe = serving.Server(workers=1)
     need = max(probe.footprint(r.n) for r in reqs)
     probe.close()
-    # a budget that holds one request at a time still serves every request
+    # a budget that holds one resident context at a time still serves every
+    # request (idle contexts are evicted to make room), and the bytes charged
+    # for resident contexts never exceed it
     srv = serving.Server(budget_bytes=1.2 * need, workers=4)
     res = srv.run(reqs, realtime=False)
+    assert srv.peak_bytes <= srv.budget and srv.resident_bytes() <= srv.budget
+    assert 0 < srv.resident_bytes()
     srv.close()
     assert all(r.status == 0 for r in res)
+    # with room for all, contexts stay resident: a second run of the same
+    # requests on the same worker charges nothing new
+    srv = serving.Server(budget_bytes=1e12, workers=1)
+    srv.run(reqs, realtime=False)
+    held = srv.resident_bytes()
+    srv.run(reqs, realtime=False)
+    assert srv.resident_bytes() == held and srv.peak_bytes == held
+    srv.close()
     # a request larger than the whole budget is rejected, the others served
     big = synth.Request(999, 0.0, 128, 5, 8)
     srv = serving.Server(budget_bytes=0.5 * serving.Server.footprint(srv, 128), workers=2)
@@ -181,7 +194,9 @@ def test_warm_builds_every_resident_context(serving, batch):
     assert len(warm) == 2 * len(sizes) * (2 if batch > 1 else 1)
     assert all(r.status == 0 and r.iters > 0 for r in warm)
     for w in range(2):
-        assert sorted(srv._ctx[w]) == list(sizes)
+        assert srv.resident_sizes(w) == list(sizes)
+        if batch > 1:
+            assert srv.resident_sizes(w, batch=True) == list(sizes)
     rw = srv.run(reqs, realtime=False)
     srv.close()
     for a, b in zip(rc, rw):

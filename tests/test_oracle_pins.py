@@ -386,6 +386,62 @@ def test_vcycle_is_symmetric(oracle):
     assert (Bu * u).sum() > 0
 
 
+@pytest.mark.parametrize("paper_order", [0, 1])
+def test_vcycle_two_levels_by_dense_matrices(oracle, paper_order):
+    # Table 1's cycle on 8^3 (two levels) written out with dense matrices: the
+    # pre-sweep red then black from z = 0, each colour c as
+    # z <- z + P_c D^-1 (r - A z) (cells of one colour do not couple), the
+    # residual restricted by R, the coarse system solved exactly, P of the
+    # correction added, then the post-sweep black then red (symmetric cycle)
+    # or red then black (paper_order, the paper's "nonsymmetric" relaxation)
+    case = synth.random_case((8, 8, 8), seed=6)
+    g = case.grid
+    op = oracle.assemble(g, case.params, case.E, case.nHI, case.eta)
+    A = oracle.dense_matrix(g, op)
+    n = A.shape[0]
+    d = np.diag(A)
+    idx = np.arange(n)
+    red = (idx % 8 + (idx // 8) % 8 + idx // 64) % 2 == 0
+
+    def sweep(z, r, colour):
+        z = z.copy()
+        z[colour] += ((r - A @ z) / d)[colour]
+        return z
+
+    # the transfer operators as matrices, from the pinned restriction and
+    # prolongation; the coarse operator from the pinned coarsening
+    R = np.stack([oracle.restrict(g.n, g.periodic, e.reshape(g.shape)).ravel() for e in np.eye(n)], axis=1)
+    P = np.stack([oracle.prolong_add(g.n, g.periodic, e.reshape((4, 4, 4)), np.zeros(g.shape)).ravel()
+                  for e in np.eye(64)], axis=1)
+    gc = synth.Grid((4, 4, 4), tuple(2 * h for h in g.h), g.periodic)
+    Ac = oracle.dense_matrix(gc, oracle.coarsen(g.n, g.periodic, op))
+    r = np.random.default_rng(2).standard_normal(n)
+    z = sweep(sweep(np.zeros(n), r, red), r, ~red)
+    z = z + P @ np.linalg.solve(Ac, R @ (r - A @ z))
+    for colour in ((red, ~red) if paper_order else (~red, red)):
+        z = sweep(z, r, colour)
+    zo = oracle.vcycle(g, op, r.reshape(g.shape), {"paper_order": paper_order}).ravel()
+    np.testing.assert_allclose(zo, z, rtol=0, atol=1e-12 * np.abs(z).max())
+
+
+def test_paper_order_cycle_is_nonsymmetric_and_pcg_converges(oracle):
+    # red then black in both sweeps makes the cycle nonsymmetric; CG
+    # preconditioned by it still reaches the dense solution
+    case = synth.random_case((16, 16, 16), seed=4, periodic=(True, False, True))
+    op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(case.grid.shape)
+    v = rng.standard_normal(case.grid.shape)
+    s = {"paper_order": 1}
+    Bu, Bv = oracle.vcycle(case.grid, op, u, s), oracle.vcycle(case.grid, op, v, s)
+    assert abs((Bu * v).sum() - (u * Bv).sum()) > 1e-6 * abs((Bu * v).sum())
+    small = synth.random_case((6, 6, 6), seed=8, periodic=(False, True, False))
+    ops = oracle.assemble(small.grid, small.params, small.E, small.nHI, small.eta)
+    x, it, rel, _ = oracle.pcg(small.grid, ops, ops["b"], {"paper_order": 1, "rtol": 1e-14, "max_iter": 100})
+    xd = oracle.dense_solve(small.grid, ops, ops["b"])
+    np.testing.assert_allclose(x, xd, rtol=0, atol=1e-12 * np.abs(xd).max())
+
+
 def test_pcg_iteration_counts_config1(oracle):
     case = synth.config1(32)
     E1, info = oracle.step(case.grid, case.params, {}, case.E, case.nHI, case.eta)

@@ -5,8 +5,11 @@ device synchronisation would stall them).
 
 Its result must equal what the library's ordinary entry points give for the
 same system: b - fld_apply(x) from an assembled context.  Two calls in a row
-check that the shared fixed scratch is reset between calls.  This file is
-collected last so that a failure here leaves every other test already run."""
+check that the shared fixed scratch is reset between calls; a grid with
+outflow faces takes its operator (boundary weights in m) from fld_get_system;
+the norms-only form (r = None) and a call on a second stream after the first
+call reuse the per-device scratch address.  This file is collected last so
+that a failure here leaves every other test already run."""
 import numpy as np
 import pytest
 
@@ -25,8 +28,15 @@ def fld():
     return f
 
 
+def _outflow_case():
+    c = synth.random_case((20, 12, 16), seed=5)
+    c.grid = c.grid.outflow_upper()
+    return c
+
+
 @pytest.mark.parametrize("make", [lambda: synth.config2(32),
-                                  lambda: synth.random_case((24, 16, 40), seed=3, periodic=(False, True, False))])
+                                  lambda: synth.random_case((24, 16, 40), seed=3, periodic=(False, True, False)),
+                                  _outflow_case])
 def test_noalloc_residual_matches_apply_twice(fld, make):
     case = make()
     n = case.grid.cells
@@ -50,6 +60,14 @@ def test_noalloc_residual_matches_apply_twice(fld, make):
         nr = norms.cpu().numpy()
         assert nr[0] == pytest.approx(float((want * want).sum()), rel=1e-12)
         assert nr[1] == pytest.approx(float(want.abs().max()), rel=1e-13)
+        # norms only (r = None), on a stream of its own after the first call
+        side = torch.cuda.Stream()
+        norms2 = torch.zeros(2, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        fld.fld_residual_noalloc(case.grid, sys_["m"], sys_["wx"], sys_["wy"], sys_["wz"], sys_["b"], x, None,
+                                 norms2, stream=side)
+        side.synchronize()
+        assert np.array_equal(norms2.cpu().numpy(), nr), call
     ctx.close()
 
 
