@@ -539,8 +539,14 @@ def main():
         # every worker's resident context and solve graphs for every size
         srv.warm([16, 32, 48, 64, 96, 128])
         res = srv.run(reqs, realtime=True)
+        # saturation: the same requests all arriving at once
+        sat = serving.summarize(srv.run(reqs, realtime=False))
         srv.close()
         serving_out = serving.summarize(res)
+        serving_out["saturation"] = {"solves_per_s": sat["solves_per_s"],
+                                     "cell_solves_per_s": sat["cell_solves_per_s"], "span_s": sat["span_s"],
+                                     "what": "the same requests all arriving at time 0 (the server's throughput "
+                                             "limit; latencies then measure the queue)"}
         serving_out.update({"rate_per_s": args.serve_rate, "workers": args.serve_workers,
                             "budget_GB": 40, "sizes": [16, 32, 48, 64, 96, 128],
                             "precision": "mixed", "latency": "arrival to E^{n+1} on the host"})
