@@ -150,6 +150,17 @@ typedef struct {
                                   symmetric preconditioner; 1 red then black
                                   in the post-sweeps as in the pre-sweeps,
                                   Table 1's "nonsymmetric" relaxation */
+    int persistent_cells;      /* mixed precision, red/black Gauss-Seidel: a
+                                  fine grid of at most persistent_cells cells
+                                  (and at most 12 levels) runs each inner
+                                  FP32 MG-PCG solve as one persistent
+                                  thread-block-cluster kernel (all V-cycle
+                                  levels and the CG vector operations, same
+                                  algorithm and stopping rule as Table 1's
+                                  solver); fld_step_batched puts the inner
+                                  solves of all such contexts in flight into
+                                  one launch over a work list.  0 = never
+                                  (default 0) */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */
@@ -269,9 +280,14 @@ fld_status fld_advance(fld_ctx* ctx, double* E, const double* n_HI, const double
                        fld_advance_info* info);
 
 /* Step n independent contexts whose work may overlap on the device.  Each
- * context runs on its own stream; infos[i] receives context i's result.
- * Returns FLD_OK if every step succeeded, else the first failing status
- * (the other steps still complete). */
+ * context's work runs on a private stream of the context (created on first
+ * use), after the work already enqueued on the context's stream and before
+ * any work enqueued there later, so contexts sharing one stream still
+ * overlap; the call returns once every step has finished.  The inner solves
+ * of contexts with persistent_cells set go to the device as one launch per
+ * round (a work list), the others as device-side CG loops.  infos[i]
+ * receives context i's result.  Returns FLD_OK if every step succeeded,
+ * else the first failing status (the other steps still complete). */
 fld_status fld_step_batched(int n, fld_ctx** ctxs, double** E,
                             const double** n_HI, const double** eta,
                             fld_info* infos);

@@ -61,13 +61,14 @@ enum KClass {
     K_ASM_FACES = 0, K_ASM_RHS, K_COARSEN, K_INVD, K_COARSE_SETUP, K_SMOOTH_ZERO,
     K_RB_COLOUR, K_JACOBI, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_COARSE_APPLY, K_DOT,
     K_CG_PMATVEC, K_CG_UPDATE, K_RESIDUAL64, K_IR_SCALE, K_IR_UPDATE, K_FINALIZE, K_APPLY,
-    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_IR_RESID, K_NUM
+    K_OPACITY, K_COARSE_LEVELS, K_ASM_FIX, K_POST_FUSED, K_VTAIL, K_IR_RESID, K_PSOLVE, K_NUM
 };
 const char* const KNAMES[K_NUM] = {
     "assemble_faces", "assemble_rhs", "coarsen", "invd", "coarse_setup", "smooth_zero",
     "rb_colour", "jacobi", "residual", "restrict", "prolong_add", "coarse_apply", "dot",
     "cg_p_matvec", "cg_update", "residual64", "ir_scale", "ir_update", "finalize", "apply",
-    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail", "ir_residual"};
+    "opacity_update", "coarse_levels", "assemble_fix", "post_smooth", "vtail", "ir_residual",
+    "psolve"};
 
 struct KStat {
     long long launches, timed;
@@ -155,6 +156,7 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     if (p->tail_cells < 0 || p->tail_cells > (1 << 24))
         return set_err(FLD_EINVAL, "tail_cells must lie in [0, 2^24]");
     if (p->paper_order != 0 && p->paper_order != 1) return set_err(FLD_EINVAL, "paper_order must be 0 or 1");
+    if (p->persistent_cells < 0) return set_err(FLD_EINVAL, "persistent_cells must be >= 0");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
@@ -212,6 +214,14 @@ int dirichlet_mask(const fld_grid* g) {
     return m;
 }
 
+// Whether a context runs its inner solves as persistent cluster kernels
+// (fld_params.persistent_cells): mixed precision, red/black Gauss-Seidel, a
+// small enough fine grid and at most TAIL_MAX_LEVELS levels.
+bool ps_wanted(const fld_params* p, size_t n0, int nl) {
+    return p->precision == FLD_PREC_MIXED && p->smoother == FLD_SMOOTH_RBGS && p->persistent_cells > 0 &&
+           n0 <= (size_t)p->persistent_cells && nl >= 2 && nl <= TAIL_MAX_LEVELS;
+}
+
 // Enumerates every device buffer a context needs, in a fixed order; the
 // same walk sizes the footprint and performs the allocation.
 template <class F>
@@ -261,6 +271,7 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
         }
     }
     for (int q = 0; q < 6; q++) buf(0, "cg", q, n0 * ts);
+    if (ps_wanted(p, n0, nl)) buf(0, "ps", 0, sizeof(PsReq));
     const size_t nc = (size_t)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
     buf(0, "dense", 0, nc * nc * sizeof(double));
     buf(0, "dense", 1, nc * nc * sizeof(double));
@@ -315,6 +326,11 @@ struct fld_ctx {
     unsigned long long id;         // unique per context, keys batch graphs
     unsigned graph_gen;            // bumped whenever the iteration graphs change
     cudaEvent_t ev_join;           // orders this stream with a batch stream
+    // fld_step_batched: the context's work runs on a private stream (so the
+    // contexts of a batch overlap even when they share one caller stream),
+    // ordered after earlier and before later work on the caller's stream
+    cudaStream_t bstream;
+    cudaStream_t user_s;
     // state of the CG run in progress (see pcg_begin / pcg_after)
     struct Run {
         double thresh;
@@ -324,6 +340,11 @@ struct fld_ctx {
     std::vector<std::pair<int, double>> glaunch[2][2];
     std::vector<std::pair<int, double>>* grec;   // launch list being captured
     double* h_one;   // pinned: [0] = 1.0 to raise S_FIRST, [1..3] loop slots
+    // persistent inner solves (k_psolve): the device descriptor, its host
+    // copy and whether this context uses them
+    PsReq* ps_req;
+    PsReq ps_host;
+    bool ps;
     int tail_from;   // first level of the persistent coarse tail (-1: none)
     int tail_cluster;   // CTAs of the tail's cluster
     // device-side CG loop per solver precision: a while-node graph whose
@@ -371,7 +392,9 @@ struct KScope {
     int cls;
     double bytes;
     cudaEvent_t a = nullptr, b = nullptr;
-    KScope(fld_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+    cudaStream_t st;   // the stream of the launch (the context's by default)
+    KScope(fld_ctx* c_, int cls_, double bytes_, cudaStream_t s_ = nullptr)
+        : c(c_), cls(cls_), bytes(bytes_), st(s_ ? s_ : c_->s) {
         if (c->capturing) {   // counted each time the graph is launched
             c->grec->push_back({cls, bytes});
             return;
@@ -381,12 +404,12 @@ struct KScope {
         if ((c->tmask >> cls) & 1ULL) {
             a = pool_event(c);
             b = pool_event(c);
-            if (a && b) cudaEventRecord(a, c->s); else a = b = nullptr;
+            if (a && b) cudaEventRecord(a, st); else a = b = nullptr;
         }
     }
     ~KScope() {
         if (a) {
-            cudaEventRecord(b, c->s);
+            cudaEventRecord(b, st);
             c->pend.push_back({cls, bytes, a, b});
         }
     }
@@ -601,7 +624,7 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
 // launch_ir_update with the p of the last iteration, p[run.cur].
 template <class T>
 bool defers_x(fld_ctx* c) {
-    return std::is_same<T, float>::value && use4<T>(c->L[0].d);
+    return std::is_same<T, float>::value && use4<T>(c->L[0].d) && !c->ps;
 }
 
 template <class T>
@@ -806,12 +829,15 @@ void count_graph_launches(fld_ctx* c, int prec, int cur) {
 // (x = 0), r0sq = ||r||^2; it stops when ||r||^2 <= rtol^2 r0sq.
 template <class T>
 fld_status pcg_begin(fld_ctx* c, double r0sq, double rtol, int max_iter) {
-    CUDA_TRY(cudaMemsetAsync(c->cg[2], 0, c->L[0].d.n * sizeof(T), c->s));
-    // beta = 0 in the first iteration, signalled on the device so that
-    // every iteration launches the same work; alpha = 0 before it, so that
-    // a deferred update of x adds nothing there
-    CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
-    CUDA_TRY(cudaMemsetAsync(c->sc + S_ALPHA, 0, sizeof(double), c->s));
+    if (!(std::is_same<T, float>::value && c->ps)) {
+        CUDA_TRY(cudaMemsetAsync(c->cg[2], 0, c->L[0].d.n * sizeof(T), c->s));
+        // beta = 0 in the first iteration, signalled on the device so that
+        // every iteration launches the same work; alpha = 0 before it, so
+        // that a deferred update of x adds nothing there (the persistent
+        // solve keeps these in registers)
+        CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
+        CUDA_TRY(cudaMemsetAsync(c->sc + S_ALPHA, 0, sizeof(double), c->s));
+    }
     c->run.thresh = rtol * rtol * r0sq;
     c->run.max_iter = max_iter;
     c->run.k = 0;
@@ -855,35 +881,89 @@ fld_status pcg_after(fld_ctx* c) {
     return FLD_OK;
 }
 
-template <class T>
-fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
-    fld_status st = pcg_begin<T>(c, r0sq, rtol, max_iter);
-    if (st) return st;
-    cudaGraphExec_t le = c->run.done ? nullptr : loop_graph<T>(c);
-    if (le) {
-        // the whole loop on the device: threshold, iteration cap and counter
-        // to their slots, one graph launch, one synchronisation
-        const int prec = std::is_same<T, float>::value ? 1 : 0;
-        c->h_one[1] = c->run.thresh;
-        c->h_one[2] = (double)max_iter;
-        c->h_one[3] = 0.0;
-        CUDA_TRY(cudaMemcpyAsync(c->sc + S_THRESH, c->h_one + 1, 3 * sizeof(double), cudaMemcpyHostToDevice, c->s));
-        CUDA_TRY(cudaGraphLaunch(le, c->s));
-        CUDA_TRY(cudaGetLastError());
-        if ((st = read_scalars(c))) return st;
-        const int k = (int)c->h_sc[S_KITER];
+// The threshold, iteration cap and iteration counter of a whole inner solve
+// run on the device (loop graph or persistent kernel) to their slots.
+fld_status whole_slots(fld_ctx* c) {
+    c->h_one[1] = c->run.thresh;
+    c->h_one[2] = (double)c->run.max_iter;
+    c->h_one[3] = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(c->sc + S_THRESH, c->h_one + 1, 3 * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    return FLD_OK;
+}
+
+// One launch of the persistent inner solves of contexts cs (all with ps
+// set and their slots written) on stream s: the work list in decreasing
+// grid size, so the largest solves start first.
+fld_status ps_enqueue(std::vector<fld_ctx*> cs, cudaStream_t s) {
+    if (cs.empty()) return FLD_OK;
+    if ((int)cs.size() > PS_MAX_BATCH) return set_err(FLD_EINVAL, "more than %d persistent solves in one launch", PS_MAX_BATCH);
+    // cluster requests first, then the single-CTA ones, each largest first
+    std::stable_sort(cs.begin(), cs.end(), [](fld_ctx* a, fld_ctx* b) {
+        if (a->ps_host.cta != b->ps_host.cta) return a->ps_host.cta < b->ps_host.cta;
+        return a->L[0].d.n > b->L[0].d.n;
+    });
+    PsBatch pb{};
+    pb.n = (int)cs.size();
+    pb.ncl = 0;
+    while (pb.ncl < pb.n && !cs[pb.ncl]->ps_host.cta) pb.ncl++;
+    pb.ticket = cs[0]->counter + 32;
+    size_t smem = 0;
+    for (int i = 0; i < pb.n; i++) {
+        pb.req[i] = cs[i]->ps_req;
+        const size_t b = psolve_smem_bytes(cs[i]->ps_host);
+        if (b > smem) smem = b;
+    }
+    {
+        KScope k(cs[0], K_PSOLVE, 0.0, s);
+        CUDA_TRY(launch_psolve(pb, smem, s));
+    }
+    return FLD_OK;
+}
+
+// After a whole inner solve has completed and its scalars are in the host
+// mirror: the run state as after its last iteration.
+fld_status whole_after(fld_ctx* c, int prec, bool graph) {
+    const int k = (int)c->h_sc[S_KITER];
+    if (graph)
         for (int q = 0; q < k; q++)
             for (auto& e : c->loop_launch[prec]) {
                 c->kstat[e.first].launches++;
                 c->kstat[e.first].bytes += e.second;
             }
-        c->run.k = k;
-        c->run.cur = k & 1;   // as after k single iterations: the last p is p[cur]
-        c->run.done = true;
-        if (c->h_sc[S_NONFINITE] != 0.0)
-            return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
-        c->run.conv = c->h_sc[S_RR] <= c->run.thresh;
-        *iters = k;
+    c->run.k = k;
+    c->run.cur = k & 1;   // as after k single iterations: the last p is p[cur]
+    c->run.done = true;
+    if (c->h_sc[S_NONFINITE] != 0.0)
+        return set_err(FLD_ENONFINITE, "non-finite value in a CG reduction at iteration %d", k);
+    c->run.conv = c->h_sc[S_RR] <= c->run.thresh;
+    return FLD_OK;
+}
+
+template <class T>
+fld_status pcg(fld_ctx* c, double r0sq, double rtol, int max_iter, int* iters, bool* converged) {
+    fld_status st = pcg_begin<T>(c, r0sq, rtol, max_iter);
+    if (st) return st;
+    if (std::is_same<T, float>::value && c->ps && !c->run.done) {
+        // the whole solve in one persistent launch
+        if ((st = whole_slots(c))) return st;
+        if ((st = ps_enqueue({c}, c->s))) return st;
+        if ((st = read_scalars(c))) return st;
+        if ((st = whole_after(c, 1, false))) return st;
+        *iters = c->run.k;
+        *converged = c->run.conv;
+        return FLD_OK;
+    }
+    cudaGraphExec_t le = c->run.done ? nullptr : loop_graph<T>(c);
+    if (le) {
+        // the whole loop on the device: threshold, iteration cap and counter
+        // to their slots, one graph launch, one synchronisation
+        const int prec = std::is_same<T, float>::value ? 1 : 0;
+        if ((st = whole_slots(c))) return st;
+        CUDA_TRY(cudaGraphLaunch(le, c->s));
+        CUDA_TRY(cudaGetLastError());
+        if ((st = read_scalars(c))) return st;
+        if ((st = whole_after(c, prec, true))) return st;
+        *iters = c->run.k;
         *converged = c->run.conv;
         return FLD_OK;
     }
@@ -935,6 +1015,7 @@ fld_status alloc_ctx(fld_ctx* c) {
             else c->flist.counts = (unsigned*)ptr;
         }
         else if (!strcmp(kind, "cg")) c->cg[q] = ptr;
+        else if (!strcmp(kind, "ps")) c->ps_req = (PsReq*)ptr;
         else if (!strcmp(kind, "dense")) { if (q == 0) c->dense = (double*)ptr; else c->ainv = (double*)ptr; }
         else if (!strcmp(kind, "red")) {
             if (q == 0) c->partials = (double*)ptr;
@@ -955,6 +1036,7 @@ void free_ctx(fld_ctx* c) {
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     drop_graphs(c);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->bstream) cudaStreamDestroy(c->bstream);
     for (int q = 0; q < 4; q++) {
         if (c->cstream[q]) cudaStreamDestroy(c->cstream[q]);
         if (c->cjoin[q]) cudaEventDestroy(c->cjoin[q]);
@@ -1474,6 +1556,9 @@ struct BItem {
     double bb;
     int inner_total, outer;
     int ks, attempt;     // mixed: scale of the residual in flight, relaunches
+    int whole;           // the inner solve in flight runs whole on the device:
+                         // 0 no (one round per iteration), 1 persistent
+                         // kernel, 2 device-side loop graph
     bool conv;
     std::string err;
 };
@@ -1597,7 +1682,14 @@ void batch_after(BItem& b) {
         return;
     }
     case BS_ITER: {
-        if ((st = pcg_after(c))) return bfail(b, st);
+        if (b.whole) {
+            harvest(c);
+            st = whole_after(c, b.prec, b.whole == 2);
+            b.whole = 0;
+            if (st) return bfail(b, st);
+        } else if ((st = pcg_after(c))) {
+            return bfail(b, st);
+        }
         if (!c->run.done) return;
         if (!c->mixed) {
             b.inf.iters = c->run.k;
@@ -1690,6 +1782,20 @@ fld_status step_batched_impl(int n, fld_ctx** cs, double** E, const double** nHI
     cudaEvent_t bev = nullptr;
     fld_status st = batch_stream(&bs, &bev);
     if (st) return st;
+    // each context onto its private stream, after the caller's work
+    for (int i = 0; i < n; i++) {
+        fld_ctx* c = cs[i];
+        if (!c->bstream && cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            c->bstream = nullptr;
+            for (int q = 0; q < i; q++) cs[q]->s = cs[q]->user_s;
+            return set_err(FLD_ECUDA, "stream creation for batch item %d failed", i);
+        }
+        c->user_s = c->s;
+        cudaEventRecord(c->ev_join, c->s);
+        cudaStreamWaitEvent(c->bstream, c->ev_join, 0);
+        c->s = c->bstream;
+    }
     std::vector<BItem> items(n);
     for (int i = 0; i < n; i++) {
         BItem& b = items[i];
@@ -1702,16 +1808,55 @@ fld_status step_batched_impl(int n, fld_ctx** cs, double** E, const double** nHI
         b.prec = 0;
         b.bb = 0.0;
         b.inner_total = b.outer = 0;
+        b.whole = 0;
         b.conv = false;
         b.state = BS_ASM;
         cudaEventRecord(b.c->e0, b.c->s);
         if ((st = assemble_enqueue(b.c, b.E, b.nHI, b.eta))) bfail(b, st);
     }
     for (;;) {
-        // contexts inside CG: their iterations as one batch-graph launch
+        // contexts entering an inner solve: the persistent ones all in one
+        // launch over a work list, the others with a device-side loop graph
+        // on their own streams; both run the whole solve in this round
+        std::vector<fld_ctx*> psc;
         std::vector<BItem*> iter, direct;
+        for (BItem& b : items) {
+            if (b.state != BS_ITER || b.c->run.k != 0 || b.c->run.done) continue;
+            fld_ctx* c = b.c;
+            if (b.prec == 1 && c->ps) {
+                if ((st = whole_slots(c))) { bfail(b, st); continue; }
+                cudaEventRecord(c->ev_join, c->s);
+                cudaStreamWaitEvent(bs, c->ev_join, 0);
+                psc.push_back(c);
+                b.whole = 1;
+                continue;
+            }
+            cudaGraphExec_t le = b.prec ? loop_graph<float>(c) : loop_graph<double>(c);
+            if (le) {
+                if ((st = whole_slots(c))) { bfail(b, st); continue; }
+                if (cudaGraphLaunch(le, c->s) != cudaSuccess) {
+                    cudaGetLastError();
+                    bfail(b, set_err(FLD_ECUDA, "launch of the device-side CG loop failed"));
+                    continue;
+                }
+                cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+                b.whole = 2;
+            }
+        }
+        if (!psc.empty()) {
+            st = ps_enqueue(psc, bs);
+            cudaEventRecord(bev, bs);
+            for (BItem& b : items)
+                if (b.whole == 1) {
+                    cudaStreamWaitEvent(b.c->s, bev, 0);
+                    cudaMemcpyAsync(b.c->h_sc, b.c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, b.c->s);
+                    if (st) bfail(b, st);
+                }
+        }
+        // the other contexts inside CG: their iterations as one batch-graph
+        // launch per round
         for (BItem& b : items)
-            if (b.state == BS_ITER) {
+            if (b.state == BS_ITER && !b.whole) {
                 const bool g = b.prec ? pcg_graph<float>(b.c, b.c->run.cur) != nullptr
                                       : pcg_graph<double>(b.c, b.c->run.cur) != nullptr;
                 (g ? iter : direct).push_back(&b);
@@ -1748,6 +1893,13 @@ fld_status step_batched_impl(int n, fld_ctx** cs, double** E, const double** nHI
         if (!any) break;
         for (BItem& b : items)
             if (b.state != BS_DONE) batch_after(b);
+    }
+    // back to the caller's streams, which wait for the private ones
+    for (int i = 0; i < n; i++) {
+        fld_ctx* c = cs[i];
+        cudaEventRecord(c->ev_join, c->bstream);
+        c->s = c->user_s;
+        cudaStreamWaitEvent(c->s, c->ev_join, 0);
     }
     fld_status first = FLD_OK;
     std::string msg;
@@ -1796,6 +1948,7 @@ fld_status fld_params_default(fld_params* p) {
     p->graphs = -1;
     p->fused_post = 0;
     p->paper_order = 0;
+    p->persistent_cells = 0;
     p->theta = 1.0;
     p->scale_factor = 1.0;
     p->tail_cells = 32768;
@@ -1854,6 +2007,47 @@ fld_status fld_create(fld_ctx** out, const fld_grid* g, const fld_params* p, voi
         while (l0 < c->nl - 1 && c->L[l0].d.n > p->tail_cells) l0++;
         c->tail_cluster = c->mixed ? vtail_cluster<float>() : vtail_cluster<double>();
         if (l0 < c->nl - 1 && c->nl - l0 <= TAIL_MAX_LEVELS && c->tail_cluster > 0) c->tail_from = l0;
+    }
+    // persistent inner solves: the V-cycle over every level with the fine
+    // level's CG vectors, written once to the context's device descriptor
+    c->ps = false;
+    if (c->ps_req && psolve_shape().cluster > 0) {
+        PsReq& R = c->ps_host;
+        memset(&R, 0, sizeof(R));
+        TailArgs<float>& ta = R.v;
+        ta.nlev = c->nl;
+        ta.pre = p->pre;
+        ta.post = p->post;
+        ta.paper_order = p->paper_order;
+        for (int q = 0; q < c->nl; q++) {
+            Level& Q = c->L[q];
+            TailLevel<float>& t = ta.L[q];
+            t.d = Q.d;
+            t.A = Q.A32;
+            t.r = (float*)(q == 0 ? c->cg[0] : Q.r);
+            t.z = (float*)(q == 0 ? c->cg[1] : Q.z);
+            t.t = (float*)Q.t;
+        }
+        ta.small_from = ta.nlev;
+        for (int q = 0; q < ta.nlev; q++)
+            if (ta.L[q].d.n <= TAIL_SMALL_CELLS) {
+                size_t cells = 0;
+                for (int u = q; u < ta.nlev; u++) cells += (size_t)ta.L[u].d.n;
+                if (3 * cells * sizeof(float) <= TAIL_SMEM_MAX) ta.small_from = q;
+                break;
+            }
+        ta.ainv = c->ainv;   // filled by every assembly
+        R.cta = psolve_cta_bytes(ta) <= PS_SMEM_MAX ? 1 : 0;
+        R.x = (float*)c->cg[5];
+        R.p = (float*)c->cg[2];
+        R.q = (float*)c->cg[4];
+        R.sc = c->sc;
+        if (cudaMemcpy(c->ps_req, &R, sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return set_err(FLD_ECUDA, "copy of the persistent-solve descriptor failed");
+        }
+        c->ps = true;
     }
     {
         long long blocks = 0;

@@ -105,6 +105,33 @@ __device__ __forceinline__ void tail_ijk(long long c, const Dims& d, int& i, int
     i = (int)(rem - jj * nx);
 }
 
+// A thread's strided walk c = c0, c0 + s, ... over a level's cells with the
+// coordinates kept incrementally: the stride is split once into (di, dj, dk)
+// in the level's mixed radix, so a step costs a few adds and compares
+// instead of two divisions (i + di < 2 nx and j + dj + 1 < 2 ny, so one
+// carry each suffices).
+struct Walk {
+    long long c, s;
+    int i, j, k, di, dj, dk, nx, ny;
+    __device__ __forceinline__ Walk(const Dims& d, long long c0, long long stride)
+        : c(c0), s(stride), nx(d.nx), ny(d.ny) {
+        tail_ijk(c0 < d.n ? c0 : 0, d, i, j, k);
+        const unsigned su = (unsigned)stride, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
+        const unsigned t = su / nxu;
+        di = (int)(su - t * nxu);
+        dk = (int)(t / nyu);
+        dj = (int)(t - (unsigned)dk * nyu);
+    }
+    __device__ __forceinline__ void next() {
+        c += s;
+        i += di;
+        if (i >= nx) { i -= nx; j++; }
+        j += dj;
+        if (j >= ny) { j -= ny; k++; }
+        k += dk;
+    }
+};
+
 __device__ __forceinline__ int tail_fine_tap(int I, int t, int nf, int periodic) {
     int f = 2 * I - 1 + t;
     if (f < 0) f = periodic ? f + nf : 0;
@@ -139,9 +166,9 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
     const T* r = v.r;
     T* z = v.z;
     if (pre >= 1) {
-        TAIL_LOOP(c, d.n) {
-            int i, j, k;
-            tail_ijk(c, d, i, j, k);
+        for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+            const long long c = w.c;
+            const int i = w.i, j = w.j, k = w.k;
             const T rcv = ldw<CG>(r, c);
             if (((i + j + k) & 1) == 0) z[c] = rcv * A.invd[c];
             else z[c] = A.invd[c] * (rcv + tail_nbr_sum_prod<CG, T>(d, A, c, i, j, k, r, A.invd));
@@ -149,9 +176,9 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
         sync();
         for (int it = 1; it < pre; it++)
             for (int colour = 0; colour < 2; colour++) {
-                TAIL_LOOP(c, d.n) {
-                    int i, j, k;
-                    tail_ijk(c, d, i, j, k);
+                for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+                    const long long c = w.c;
+                    const int i = w.i, j = w.j, k = w.k;
                     if (((i + j + k) & 1) != colour) continue;
                     T swu, sw;
                     tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
@@ -163,9 +190,9 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
         TAIL_LOOP(c, d.n) z[c] = T(0);
         sync();
     }
-    TAIL_LOOP(c, d.n) {
-        int i, j, k;
-        tail_ijk(c, d, i, j, k);
+    for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+        const long long c = w.c;
+        const int i = w.i, j = w.j, k = w.k;
         T swu, sw;
         tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
         const T zc = ldw<CG>((const T*)z, c);
@@ -173,9 +200,9 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
     }
     sync();
     const T wt[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
-    TAIL_LOOP(cc, cd.n) {
-        int I, J, K;
-        tail_ijk(cc, cd, I, J, K);
+    for (Walk w(cd, tid, nth); w.c < cd.n; w.next()) {
+        const long long cc = w.c;
+        const int I = w.i, J = w.j, K = w.k;
         int fi[4], fj[4], fk[4];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
@@ -211,9 +238,9 @@ __device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T
     const Op<T>& A = L.A;
     T* z = v.z;
     const T w2[2] = {T(0.75), T(0.25)};
-    TAIL_LOOP(c, d.n) {
-        int i, j, k;
-        tail_ijk(c, d, i, j, k);
+    for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+        const long long c = w.c;
+        const int i = w.i, j = w.j, k = w.k;
         int Ix[2], Iy[2], Iz[2];
         tail_coarse_pair(i, cd.nx, cd.px, Ix[0], Ix[1]);
         tail_coarse_pair(j, cd.ny, cd.py, Iy[0], Iy[1]);
@@ -236,9 +263,9 @@ __device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T
     for (int it = 0; it < post; it++)
         for (int q = 0; q < 2; q++) {
             const int colour = q == 0 ? first : 1 - first;
-            TAIL_LOOP(c, d.n) {
-                int i, j, k;
-                tail_ijk(c, d, i, j, k);
+            for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+                const long long c = w.c;
+                const int i = w.i, j = w.j, k = w.k;
                 if (((i + j + k) & 1) != colour) continue;
                 T swu, sw;
                 tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
@@ -261,10 +288,12 @@ __device__ void tail_coarsest(int n, const double* ainv, Vec<T> v, long long tid
 
 #undef TAIL_LOOP
 
+// One V-cycle from the tail's first level down and back up, run by every
+// thread of the calling cluster (smem: the dynamic shared memory of the
+// small levels); it ends with a cluster barrier, so L[0].z is complete and
+// visible to the whole cluster on return.
 template <class T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char tail_smem[];
-    cg::cluster_group cl = cg::this_cluster();
+__device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, cg::cluster_group& cl, unsigned char* smem) {
     const long long gthreads = (long long)TAIL_THREADS * cl.num_blocks();
     const long long gtid = (long long)cl.block_rank() * TAIL_THREADS + threadIdx.x;
     const int nl = a.nlev, ls = a.small_from;
@@ -280,7 +309,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
         if (cl.block_rank() == 0) {
             const long long tid = threadIdx.x, nth = TAIL_THREADS;
             Vec<T> sv[TAIL_MAX_LEVELS];
-            T* base = reinterpret_cast<T*>(tail_smem);
+            T* base = reinterpret_cast<T*>(smem);
             for (int l = ls; l < nl; l++) {
                 const long long n = a.L[l].d.n;
                 sv[l] = Vec<T>{base, base + n, base + 2 * n};
@@ -306,6 +335,280 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
         const TailLevel<T>& L = a.L[l];
         tail_up<true, T>(L, Vec<T>{L.r, L.z, L.t}, a.L[l + 1].d, a.L[l + 1].z, a.post, a.paper_order ? 0 : 1, gtid,
                          gthreads, csync);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vtail(TailArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    tail_cycle<T>(a, cl, tail_smem);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent inner solves over a work list (mixed precision).
+//
+// Each cluster takes a ticket, solves that request's FP32 system A x = r by
+// MG-preconditioned CG (Table 1's solver: the V-cycle over all of the
+// request's levels, then the CG vector operations) to its threshold or
+// iteration cap, and takes the next ticket; the requests may have any grid
+// sizes.  Phases are separated by the hardware cluster barrier and the dot
+// products are summed in a fixed order (per thread in its cell order with
+// error-free FP32 products, per CTA by warps, then the CTAs' partials in
+// rank order, read by every CTA from distributed shared memory), so every
+// CTA computes the same scalars and a request's result depends only on the
+// cluster shape, never on the other requests or on which cluster took it.
+
+// Sum of v over the cluster, the same in every thread of every CTA.  part:
+// a __shared__ slot of this CTA, not written again before the next cluster
+// barrier that follows this call.
+__device__ __forceinline__ double ps_cluster_sum(double v, double* part, cg::cluster_group& cl) {
+    __shared__ double wsum[TAIL_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = wsum[lane];
+        t = warp_sum(t);
+        if (lane == 0) *part = t;
+    }
+    cl.sync();
+    double tot = 0.0;
+    const unsigned nb = cl.num_blocks();
+    for (unsigned b = 0; b < nb; b++) tot += *cl.map_shared_rank(part, b);
+    return tot;
+}
+
+// The inner solve of one request: r holds the scaled residual, x = 0.
+__device__ void ps_solve(const PsReq& R, cg::cluster_group& cl, unsigned char* smem, double* part) {
+    const TailArgs<float>& a = R.v;
+    const Dims& d = a.L[0].d;
+    const Op<float>& A = a.L[0].A;
+    float* r = a.L[0].r;
+    float* z = a.L[0].z;
+    float* p = R.p;
+    float* q = R.q;
+    float* x = R.x;
+    const long long nth = (long long)TAIL_THREADS * cl.num_blocks();
+    const long long tid = (long long)cl.block_rank() * TAIL_THREADS + threadIdx.x;
+    const double thresh = __ldcg(R.sc + S_THRESH);
+    const int maxit = (int)__ldcg(R.sc + S_MAXIT);
+    double rho = 0.0, rho_old = 0.0, beta = 0.0, pq = 0.0, alpha = 0.0, rr = __ldcg(R.sc + S_RR);
+    int k = 0, slot = 0;
+    bool bad = false;
+    while (k < maxit) {
+        tail_cycle<float>(a, cl, smem);   // z = M r
+        DotAcc<float> arz;
+        for (long long c = tid; c < d.n; c += nth) arz.add(__ldcg(r + c), __ldcg(z + c));
+        rho = ps_cluster_sum(arz.value(), part + slot, cl);
+        slot = (slot + 1) & 3;
+        beta = k == 0 ? 0.0 : rho / rho_old;
+        rho_old = rho;
+        const float bf = (float)beta;
+        if (k == 0)
+            for (long long c = tid; c < d.n; c += nth) p[c] = __ldcg(z + c);
+        else
+            for (long long c = tid; c < d.n; c += nth) p[c] = fmaf(bf, __ldcg(p + c), __ldcg(z + c));
+        cl.sync();
+        // q = A p and <p, q>
+        DotAcc<float> apq;
+        for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
+            const long long c = w.c;
+            float swu, sw;
+            tail_nbr_sums<true, float>(d, A, c, w.i, w.j, w.k, p, swu, sw);
+            const float pc = __ldcg(p + c);
+            const float qc = A.m[c] * pc + sw * pc - swu;
+            q[c] = qc;
+            apq.add(pc, qc);
+        }
+        pq = ps_cluster_sum(apq.value(), part + slot, cl);
+        slot = (slot + 1) & 3;
+        alpha = rho / pq;
+        const float af = (float)alpha;
+        // x += alpha p, r -= alpha q, ||r||^2
+        DotAcc<float> arr;
+        for (long long c = tid; c < d.n; c += nth) {
+            x[c] = fmaf(af, __ldcg(p + c), __ldcg(x + c));
+            const float rn = fmaf(-af, __ldcg(q + c), __ldcg(r + c));
+            r[c] = rn;
+            arr.add(rn, rn);
+        }
+        rr = ps_cluster_sum(arr.value(), part + slot, cl);
+        slot = (slot + 1) & 3;
+        k++;
+        if (!isfinite(rho) || !isfinite(alpha) || !isfinite(rr)) {
+            bad = true;
+            break;
+        }
+        if (rr <= thresh) break;
+    }
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
+        double* sc = R.sc;
+        sc[S_RHO] = rho;
+        sc[S_RHO_OLD] = rho_old;
+        sc[S_BETA] = beta;
+        sc[S_PQ] = pq;
+        sc[S_ALPHA] = alpha;
+        sc[S_RR] = rr;
+        sc[S_KITER] = (double)k;
+        sc[S_FIRST] = 0.0;
+        if (bad) sc[S_NONFINITE] = 1.0;
+    }
+}
+
+// Sum of v over the CTA, the same in every thread (fixed order).
+__device__ __forceinline__ double ps_block_sum(double v) {
+    __shared__ double wsum[TAIL_THREADS / 32];
+    __shared__ double tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = wsum[lane];
+        t = warp_sum(t);
+        if (lane == 0) tot = t;
+    }
+    __syncthreads();
+    const double out = tot;
+    __syncthreads();
+    return out;
+}
+
+// The inner solve of a small request by one CTA: the vectors of every
+// level and the CG vectors live in shared memory (block barriers between
+// the phases, no L2 round trip); the operator comes from global memory
+// (read-only here, so cached in L1).  r is read from and x written back to
+// the request's global vectors.
+__device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
+    const TailArgs<float>& a = R.v;
+    const int nl = a.nlev;
+    const long long tid = threadIdx.x, nth = TAIL_THREADS;
+    auto bsync = []() { __syncthreads(); };
+    Vec<float> sv[TAIL_MAX_LEVELS];
+    float* base = reinterpret_cast<float*>(smem);
+    for (int l = 0; l < nl; l++) {
+        const long long n = a.L[l].d.n;
+        sv[l] = Vec<float>{base, base + n, base + 2 * n};
+        base += 3 * n;
+    }
+    const Dims& d = a.L[0].d;
+    const Op<float>& A = a.L[0].A;
+    const long long n0 = d.n;
+    float* r = sv[0].r;
+    float* z = sv[0].z;
+    float* p = base;
+    float* q = base + n0;
+    float* x = base + 2 * n0;
+    for (long long c = tid; c < n0; c += nth) {
+        r[c] = __ldcg(a.L[0].r + c);
+        x[c] = 0.0f;
+    }
+    __syncthreads();
+    const double thresh = __ldcg(R.sc + S_THRESH);
+    const int maxit = (int)__ldcg(R.sc + S_MAXIT);
+    double rho = 0.0, rho_old = 0.0, beta = 0.0, pq = 0.0, alpha = 0.0, rr = __ldcg(R.sc + S_RR);
+    int k = 0;
+    bool bad = false;
+    while (k < maxit) {
+        // z = M r: the V-cycle over every level in shared memory
+        for (int l = 0; l < nl - 1; l++)
+            tail_down<false, float>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].r, a.pre, tid, nth, bsync);
+        tail_coarsest<false, float>((int)a.L[nl - 1].d.n, a.ainv, sv[nl - 1], tid, nth, bsync);
+        for (int l = nl - 2; l >= 0; l--)
+            tail_up<false, float>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].z, a.post, a.paper_order ? 0 : 1, tid, nth,
+                                  bsync);
+        DotAcc<float> arz;
+        for (long long c = tid; c < n0; c += nth) arz.add(r[c], z[c]);
+        rho = ps_block_sum(arz.value());
+        beta = k == 0 ? 0.0 : rho / rho_old;
+        rho_old = rho;
+        const float bf = (float)beta;
+        if (k == 0)
+            for (long long c = tid; c < n0; c += nth) p[c] = z[c];
+        else
+            for (long long c = tid; c < n0; c += nth) p[c] = fmaf(bf, p[c], z[c]);
+        __syncthreads();
+        DotAcc<float> apq;
+        for (Walk w(d, tid, nth); w.c < n0; w.next()) {
+            const long long c = w.c;
+            float swu, sw;
+            tail_nbr_sums<false, float>(d, A, c, w.i, w.j, w.k, p, swu, sw);
+            const float pc = p[c];
+            const float qc = A.m[c] * pc + sw * pc - swu;
+            q[c] = qc;
+            apq.add(pc, qc);
+        }
+        pq = ps_block_sum(apq.value());
+        alpha = rho / pq;
+        const float af = (float)alpha;
+        DotAcc<float> arr;
+        for (long long c = tid; c < n0; c += nth) {
+            x[c] = fmaf(af, p[c], x[c]);
+            const float rn = fmaf(-af, q[c], r[c]);
+            r[c] = rn;
+            arr.add(rn, rn);
+        }
+        rr = ps_block_sum(arr.value());
+        k++;
+        if (!isfinite(rho) || !isfinite(alpha) || !isfinite(rr)) {
+            bad = true;
+            break;
+        }
+        if (rr <= thresh) break;
+    }
+    for (long long c = tid; c < n0; c += nth) R.x[c] = x[c];
+    if (threadIdx.x == 0) {
+        double* sc = R.sc;
+        sc[S_RHO] = rho;
+        sc[S_RHO_OLD] = rho_old;
+        sc[S_BETA] = beta;
+        sc[S_PQ] = pq;
+        sc[S_ALPHA] = alpha;
+        sc[S_RR] = rr;
+        sc[S_KITER] = (double)k;
+        sc[S_FIRST] = 0.0;
+        if (bad) sc[S_NONFINITE] = 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS) k_psolve(const __grid_constant__ PsBatch b) {
+    extern __shared__ __align__(16) unsigned char ps_smem[];
+    __shared__ __align__(16) PsReq R;
+    __shared__ double part[4];
+    __shared__ int item;
+    cg::cluster_group cl = cg::this_cluster();
+    for (;;) {
+        if (cl.block_rank() == 0 && threadIdx.x == 0) item = (int)atomicAdd(b.ticket, 1u);
+        cl.sync();
+        const int it = *cl.map_shared_rank(&item, 0);
+        // every CTA has read the ticket before CTA 0 may draw the next one
+        // or exit (its shared memory must outlive the remote reads)
+        cl.sync();
+        if (it >= b.ncl) break;
+        const unsigned* src = reinterpret_cast<const unsigned*>(b.req[it]);
+        unsigned* dst = reinterpret_cast<unsigned*>(&R);
+        for (int w = threadIdx.x; w < (int)(sizeof(PsReq) / 4); w += TAIL_THREADS) dst[w] = __ldcg(src + w);
+        __syncthreads();
+        ps_solve(R, cl, ps_smem, part);
+        // the last reduction's remote reads are done before the next request
+        cl.sync();
+    }
+    // then the small requests, each CTA on its own (no remote accesses
+    // follow, so the CTAs may finish independently)
+    for (;;) {
+        if (threadIdx.x == 0) item = b.ncl + (int)atomicAdd(b.ticket + 1, 1u);
+        __syncthreads();
+        const int it = item;
+        __syncthreads();
+        if (it >= b.n) break;
+        const unsigned* src = reinterpret_cast<const unsigned*>(b.req[it]);
+        unsigned* dst = reinterpret_cast<unsigned*>(&R);
+        for (int w = threadIdx.x; w < (int)(sizeof(PsReq) / 4); w += TAIL_THREADS) dst[w] = __ldcg(src + w);
+        __syncthreads();
+        ps_solve_cta(R, ps_smem);
+        __syncthreads();
     }
 }
 
@@ -367,6 +670,60 @@ int vtail_cluster() {
         if (n > 0) return cluster;
     }
     return 0;
+}
+
+size_t psolve_cta_bytes(const TailArgs<float>& v) {
+    size_t cells = 0;
+    for (int l = 0; l < v.nlev; l++) cells += (size_t)v.L[l].d.n;
+    return (3 * cells + 3 * (size_t)v.L[0].d.n) * sizeof(float);
+}
+
+size_t psolve_smem_bytes(const PsReq& r) { return r.cta ? psolve_cta_bytes(r.v) : vtail_smem_bytes(r.v); }
+
+// Cluster size of the persistent solves (fixed per device, so a request's
+// arithmetic never depends on the launch that carries it) and how many such
+// clusters can be resident at once; {0, 0} if none fits.
+PsShape psolve_shape() {
+    static thread_local int dev = -1;
+    static thread_local PsShape shape{0, 0};
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return PsShape{0, 0};
+    }
+    if (d == dev) return shape;
+    dev = d;
+    shape = PsShape{0, 0};
+    if (cudaFuncSetAttribute(k_psolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS_SMEM_MAX) !=
+        cudaSuccess)
+        cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config(PS_CLUSTER, nullptr, attr);
+    cfg.dynamicSmemBytes = PS_SMEM_MAX;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_psolve, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    if (n > 0) shape = PsShape{PS_CLUSTER, n};
+    return shape;
+}
+
+cudaError_t launch_psolve(const PsBatch& b, size_t smem, cudaStream_t s) {
+    const PsShape sh = psolve_shape();
+    if (sh.cluster == 0) return cudaErrorNotSupported;
+    if (b.n < 1) return cudaSuccess;
+    // enough clusters for the cluster requests and for one CTA per small one
+    const int ncta = b.n - b.ncl;
+    int clusters = b.ncl > (ncta + sh.cluster - 1) / sh.cluster ? b.ncl : (ncta + sh.cluster - 1) / sh.cluster;
+    if (clusters > sh.clusters) clusters = sh.clusters;
+    cudaError_t e = cudaMemsetAsync(b.ticket, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config(sh.cluster, s, attr);
+    cfg.gridDim = dim3(sh.cluster * clusters, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    return cudaLaunchKernelEx(&cfg, k_psolve, b);
 }
 
 template cudaError_t launch_vtail<float>(const TailArgs<float>&, int, cudaStream_t);

@@ -275,6 +275,42 @@ cudaError_t launch_vtail(const TailArgs<T>& a, int cluster, cudaStream_t s);
 template <class T>
 int vtail_cluster();
 
+// ---- persistent inner solves over a work list (k_tail.cu, mixed
+// precision): each cluster takes requests by ticket and runs a request's
+// whole FP32 MG-PCG solve (V-cycles over all its levels and the CG vector
+// operations) to ||r||^2 <= sc[S_THRESH] or sc[S_MAXIT] iterations.
+struct PsReq {
+    TailArgs<float> v;   // all levels; L[0].r is the CG residual (in: the
+                         // right-hand side, x = 0), L[0].z the preconditioned one
+    float *x, *p, *q;    // fine-level CG vectors
+    double* sc;          // the request's scalar slots: S_THRESH, S_MAXIT in;
+                         // S_KITER, S_RR, S_RHO.., S_NONFINITE out
+    int cta;             // 1: solved by one CTA with every vector in its
+                         // shared memory (psolve_cta_bytes fits), else by a cluster
+    int pad_;
+};
+constexpr int PS_MAX_BATCH = 256;
+constexpr int PS_CLUSTER = 8;
+// the most dynamic shared memory of a persistent launch
+constexpr size_t PS_SMEM_MAX = 200 * 1024;
+struct PsBatch {
+    int n;          // requests: [0, ncl) by clusters, [ncl, n) by single CTAs
+    int ncl;
+    unsigned* ticket;                 // two counters, set to 0 by launch_psolve
+    const PsReq* req[PS_MAX_BATCH];   // device descriptors, in work-list order
+};
+struct PsShape {
+    int cluster;    // CTAs per cluster
+    int clusters;   // clusters resident at once
+};
+PsShape psolve_shape();
+// shared memory of a single-CTA solve: r, z, t of every level and p, q, x
+size_t psolve_cta_bytes(const TailArgs<float>& v);
+size_t psolve_smem_bytes(const PsReq& r);
+// one launch: min(n, resident clusters) clusters drain the work list; smem
+// is the largest psolve_smem_bytes of the batch
+cudaError_t launch_psolve(const PsBatch& b, size_t smem, cudaStream_t s);
+
 // Sets the calling thread's fld_last_error message (fld_api.cu).
 void record_error(const char* msg);
 // The per-face boundary conditions of g are consistent (fld_create's rule);

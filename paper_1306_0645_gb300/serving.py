@@ -36,6 +36,7 @@ import numpy as np
 from . import fld, synth
 
 CANCELLED = -1   # Result.status of a request cancelled before it was stepped
+_MAX_SOURCES = 64  # sources a request may carry
 
 
 @dataclasses.dataclass
@@ -104,6 +105,8 @@ class Server:
         self._res: Dict[tuple, _Resident] = {}
         self._pinned: List[Dict[int, object]] = [dict() for _ in range(workers)]
         self._fp_cache: Dict[int, int] = {}
+        self._staging: List[Optional[object]] = [None] * workers
+        self._init = None
         self._cancelled = set()
         self._cancel_lock = threading.Lock()
 
@@ -203,34 +206,49 @@ class Server:
             self._cv.notify_all()
 
     def _build(self, e: _Resident, w: int, n: int) -> None:
-        """Create a resident entry's context and field buffers (first use)."""
+        """Create a resident entry's context (on worker w's stream) and field
+        buffers (first use): E, n_HI and eta as rows of one (3, n^3)
+        tensor."""
         torch = self.torch
         if e.ctx is None:
             e.ctx = fld.fld_create(synth.Grid.cube(n), self.params, self._streams[w])
         if e.buf is None:
-            e.buf = tuple(torch.empty(n ** 3, dtype=torch.float64, device="cuda") for _ in range(3))
+            e.buf = torch.empty((3, n ** 3), dtype=torch.float64, device="cuda")
 
     # ----------------------------------------------------------- one step
-    def _fields(self, r: synth.Request, out=None):
+    def _stage(self, w: int, slots: int):
+        """Worker w's pinned staging words for `slots` requests' sources
+        (reused once the worker's stream has been synchronised)."""
+        torch = self.torch
+        st = self._staging[w]
+        if st is None or st.shape[0] < slots:
+            st = torch.empty((slots, 2 * _MAX_SOURCES), dtype=torch.int64, pin_memory=True)
+            self._staging[w] = st
+        return st
+
+    def _fields(self, r: synth.Request, out=None, stage=None):
         """E, n_HI and eta of a request on the current stream, built from its
-        payload (source cells and rates); into the tensors out when given."""
+        payload (distinct source cells and rates): one broadcast fill of the
+        three rows of out (a (3, n^3) tensor, allocated when None), one copy
+        of the payload from the pinned row stage (when given) and one
+        scatter."""
         torch = self.torch
         n = r.n
         cells, rates = synth.request_sources(r)
+        ns = len(cells)
         g = synth.Grid.cube(n)
         if out is None:
-            E = torch.full((n ** 3,), synth.E0, dtype=torch.float64, device="cuda")
-            nHI = torch.full((n ** 3,), 1e-3, dtype=torch.float64, device="cuda")
-            eta = torch.zeros((n ** 3,), dtype=torch.float64, device="cuda")
-        else:
-            E, nHI, eta = out
-            E.fill_(synth.E0)
-            nHI.fill_(1e-3)
-            eta.zero_()
-        idx = torch.from_numpy(cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])).cuda()
-        val = torch.from_numpy(rates * synth.HNU_HI / g.volume).cuda()
-        eta.index_put_((idx,), val, accumulate=True)
-        return E, nHI, eta
+            out = torch.empty((3, n ** 3), dtype=torch.float64, device="cuda")
+        if self._init is None:
+            self._init = torch.tensor([synth.E0, 1e-3, 0.0], dtype=torch.float64, device="cuda").view(3, 1)
+        out.copy_(self._init.expand(3, n ** 3))
+        if stage is None:
+            stage = torch.empty(2 * max(ns, 1), dtype=torch.int64, pin_memory=True)
+        stage[:ns] = torch.from_numpy(cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2]))
+        stage[ns:2 * ns] = torch.from_numpy(rates * synth.HNU_HI / g.volume).view(torch.int64)
+        dv = stage[:2 * ns].to("cuda", non_blocking=True)
+        out[2].index_put_((dv[:ns],), dv[ns:].view(torch.float64))
+        return out[0], out[1], out[2]
 
     def step_one(self, w: int, r: synth.Request, t0: float) -> Result:
         """Step one request on worker w (admission, fields, fld_step, E back to
@@ -246,7 +264,7 @@ class Server:
         try:
             with torch.cuda.stream(self._streams[w]):
                 self._build(e, w, r.n)
-                E, nHI, eta = self._fields(r, e.buf)
+                E, nHI, eta = self._fields(r, e.buf, self._stage(w, 1)[0])
                 info = fld.fld_step(e.ctx, E, nHI, eta, check=False)
                 host = self._pinned[w].get(r.n)
                 if host is None:
@@ -293,24 +311,31 @@ class Server:
         try:
             with torch.cuda.stream(self._streams[w]):
                 ctxs, fields = [], []
-                for r, e in zip(admitted, got):
+                stage = self._stage(w, len(admitted))
+                for q, (r, e) in enumerate(zip(admitted, got)):
                     self._build(e, w, r.n)
                     ctxs.append(e.ctx)
-                    fields.append(self._fields(r, e.buf))
+                    fields.append(self._fields(r, e.buf, stage[q]))
+                # the contexts overlap on private streams forked from and
+                # joined to the worker's
                 st, infos = fld.fld_step_batched(ctxs, [f[0] for f in fields], [f[1] for f in fields],
                                                  [f[2] for f in fields], check=False)
+                # E^{n+1} of every request back to pinned host memory, as a
+                # single step does
                 hosts = []
-                for r, f in zip(admitted, fields):
-                    h = torch.empty(r.n ** 3, dtype=torch.float64, pin_memory=True) if self.keep else None
-                    if h is not None:
-                        h.copy_(f[0], non_blocking=True)
+                for r, f, e in zip(admitted, fields, got):
+                    h = self._pinned[w].get(("b", r.n, len(hosts)))
+                    if h is None:
+                        h = torch.empty(r.n ** 3, dtype=torch.float64, pin_memory=True)
+                        self._pinned[w][("b", r.n, len(hosts))] = h
+                    h.copy_(f[0], non_blocking=True)
                     hosts.append(h)
                 self._streams[w].synchronize()
                 now = time.perf_counter() - t0
                 for r, info, h in zip(admitted, infos, hosts):
                     out.append(Result(r.rid, r.n, r.arrival, start, now, info["status"], info["iters"],
                                       info["outer_iters"], info["rel_res"],
-                                      h.numpy().copy() if h is not None else None))
+                                      h.numpy().copy() if self.keep else None))
         except Exception:
             failed = tuple(k for k, _ in wanted)
             raise

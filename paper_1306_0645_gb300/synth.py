@@ -110,6 +110,7 @@ class Params:
     scale_factor: float = 1.0
     tail_cells: int = 32768
     paper_order: int = 0
+    persistent_cells: int = 0
 
 
 @dataclasses.dataclass

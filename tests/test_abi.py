@@ -58,6 +58,15 @@ def test_host_only_calls(libfld):
     assert fld.fld_footprint_bytes(synth.Grid.cube(101), synth.Params()) == 0
     bad = synth.Params(dt=-1.0)
     assert fld.fld_footprint_bytes(g, bad) == 0
+    # persistent inner solves: off by default; a mixed grid within the limit
+    # holds one more buffer (its device descriptor); negative is invalid
+    assert fld.fld_params_default().persistent_cells == 0
+    base = fld.fld_footprint_bytes(g, mixed)
+    ps = fld.fld_footprint_bytes(g, synth.Params(precision=synth.PREC_MIXED, persistent_cells=1 << 20))
+    assert 0 < ps - base <= 4096
+    assert fld.fld_footprint_bytes(g, synth.Params(precision=synth.PREC_MIXED, persistent_cells=1000)) == base
+    assert fld.fld_footprint_bytes(g, synth.Params(persistent_cells=1 << 20)) == fp
+    assert fld.fld_footprint_bytes(g, synth.Params(persistent_cells=-1)) == 0
 
 
 def test_noalloc_rejects_inconsistent_faces():
