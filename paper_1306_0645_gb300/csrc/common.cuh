@@ -193,14 +193,29 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], const bool (&ismax)
     __threadfence();
     double w[NV];
 #pragma unroll
-    for (int k = 0; k < NV; k++) {
-        double acc = ismax[k] ? -INFINITY : 0.0;
-        for (int b = tid; b < G; b += nthr) {
-            double p = __ldcg(&ra.partials[k * RED_MAX_BLOCKS + b]);
-            acc = ismax[k] ? fmax(acc, p) : acc + p;
-        }
-        w[k] = acc;
+    for (int k = 0; k < NV; k++) w[k] = ismax[k] ? -INFINITY : 0.0;
+    // the partials b = tid, tid + nthr, ... of every value, U of them per
+    // step with their loads issued together (the same order of additions
+    // as one at a time)
+    constexpr int U = NV <= 2 ? 8 : (NV <= 4 ? 4 : 2);
+    int b = tid;
+    for (; b + (U - 1) * nthr < G; b += U * nthr) {
+        double p[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int k = 0; k < NV; k++) p[u][k] = __ldcg(&ra.partials[k * RED_MAX_BLOCKS + b + u * nthr]);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int k = 0; k < NV; k++) w[k] = ismax[k] ? fmax(w[k], p[u][k]) : w[k] + p[u][k];
     }
+    for (; b < G; b += nthr)
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const double p = __ldcg(&ra.partials[k * RED_MAX_BLOCKS + b]);
+            w[k] = ismax[k] ? fmax(w[k], p) : w[k] + p;
+        }
     block_reduce<NV>(w, ismax);
     if (tid == 0) {
         red_finalize(ra, w);
@@ -244,8 +259,15 @@ constexpr int FLAT_MAX_BLOCKS = 152 * 16;
 #define GRID_LOOP(c, n) \
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < (n); c += (long long)gridDim.x * blockDim.x)
 
+// Blocks of a flat reduction over n items: 16 items per thread (fewer
+// partial sums for the last block to add on small grids), but two blocks
+// per SM while the items allow one per thread, and at most FLAT_MAX_BLOCKS.
 inline int red_blocks(long long n, int threads = RED_THREADS) {
-    long long b = (n + threads - 1) / threads;
+    long long b = (n + 16LL * threads - 1) / (16LL * threads);
+    if (b < 152 * 2) {
+        const long long one = (n + threads - 1) / threads;
+        b = one < 152 * 2 ? one : 152 * 2;
+    }
     if (b > FLAT_MAX_BLOCKS) b = FLAT_MAX_BLOCKS;
     if (b < 1) b = 1;
     return (int)b;

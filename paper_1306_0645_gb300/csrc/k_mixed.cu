@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_asm_faces_mx(Dims d, PhysDev p, const d
     __syncthreads();
     unsigned* seg = fl.entries ? fl.entries + bid * fl.cap : nullptr;
     COL_BEGIN_ZB(d, zb0, kch)
-        if (k + PF_PLANES < k1_) {
+        if (PF_PLANES > 0 && k + PF_PLANES < k1_) {
             const long long cp = c + PF_PLANES * sz;
             pfl2(E + cp);
             pfl2(nHI + cp);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) k_asm_rhs_mx(Dims d, PhysDev p, const dou
     bool have_z = false;
     for (int k = k0; k < k1; k++) {
         const long long c = (long long)k * nxy + (long long)j * d.nx + i;
-        if (inb && k + PF_PLANES < k1) {
+        if (PF_PLANES > 0 && inb && k + PF_PLANES < k1) {
             const long long cp = c + PF_PLANES * nxy;
             pfl2(E + cp);
             pfl2(nHI + cp);
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Dims d, Op<float> A, Op<flo
     bool have_z = false;
     for (int k = k0; k < k1; k++) {
         const long long c = (long long)k * nxy + (long long)j * d.nx + i;
-        if (inb && k + PF_PLANES < k1) {
+        if (PF_PLANES > 0 && inb && k + PF_PLANES < k1) {
             const long long cp = c + PF_PLANES * nxy;
             pfl2(b + cp);
             pfl2(x + cp);
@@ -764,7 +764,14 @@ void launch_ir_update_mx(long long n, void* x, const float* x32, const double* s
 
 // many short z-chunks: at 512^3 about 16 blocks per SM in several full
 // waves (measured: 2.6 ms with 152 x 8 target blocks, 1.9 ms with 152 x 64)
-ColShape ir_residual_shape(const Dims& d) { return col_shape(d, 256, 152 * 64); }
+// About 2048 cells per block (each thread walks eight planes or more), from
+// 152 * 4 to 152 * 64 blocks.
+ColShape ir_residual_shape(const Dims& d) {
+    long long t = d.n / 2048;
+    if (t < 152 * 4) t = 152 * 4;
+    if (t > 152 * 64) t = 152 * 64;
+    return col_shape(d, 256, (int)t);
+}
 
 void launch_ir_residual(const Dims& d, Op<float> A, Op<float> L, const double* b, const void* x, int Ks,
                         float* r32, float* x32, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s) {

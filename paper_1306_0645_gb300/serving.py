@@ -82,17 +82,22 @@ class Server:
     """A pool of worker threads stepping requests under an HBM budget."""
 
     def __init__(self, budget_bytes: float = 40e9, workers: int = 8, keep_results: bool = False,
-                 params: Optional[synth.Params] = None, device: int = 0, batch: int = 1):
+                 params: Optional[synth.Params] = None, device: int = 0, batch: int = 1,
+                 batch_max_n: int = 64):
         import torch
         self.torch = torch
         self.device = device
         self.budget = float(budget_bytes)
         self.workers = workers
         self.keep = keep_results
-        # batch > 1: a free worker takes every request that has arrived (up
-        # to batch) and steps them together through fld_step_batched, whose
-        # CG iterations run as one graph launch for all of them
+        # batch > 1: a free worker takes every request of at most
+        # batch_max_n^3 cells that has arrived (up to batch) and steps them
+        # together through fld_step_batched (their inner solves one
+        # persistent launch over a work list, or device-side CG loops on
+        # private streams); larger requests are stepped alone, so a batch
+        # never waits for a large grid
         self.batch = max(1, int(batch))
+        self.batch_max_n = int(batch_max_n)
         self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED)
         self._used = 0.0          # bytes charged for resident contexts
         self.peak_bytes = 0.0     # the most ever charged (never above the budget)
@@ -358,7 +363,7 @@ class Server:
                 if self.footprint(r.n) <= 0 or self.footprint(r.n) > self.budget:
                     continue
                 out.append(self.step_one(w, r, t0))
-                if self.batch > 1:
+                if self.batch > 1 and r.n <= self.batch_max_n:
                     out.extend(self.step_batch(w, [r], t0))
         return out
 
@@ -369,7 +374,21 @@ class Server:
         q: "queue.Queue" = queue.Queue()
         results: Dict[int, Result] = {}
         lock = threading.Lock()
+        # the stop markers go in only once every request has its result, so
+        # requests put back into the queue (large grids a batching worker
+        # left for the next free worker) never sit behind them
+        all_done = threading.Event()
+        total = len({r.rid for r in requests})
+        if total == 0:
+            all_done.set()
         t0 = time.perf_counter()
+
+        def record(res):
+            with lock:
+                for r in res:
+                    results[r.rid] = r
+                if len(results) >= total:
+                    all_done.set()
 
         def worker(w):
             """Worker thread: take requests (or groups of them) until the stop
@@ -379,39 +398,51 @@ class Server:
                 item = q.get()
                 if item is None:
                     return
-                if not self._take(item):
+                group = [item]
+                try:
+                    res = serve(w, item, group)
+                except Exception:
+                    # a failed call (recorded, so run() still finishes)
                     now = time.perf_counter() - t0
-                    res = [Result(item.rid, item.n, item.arrival, now, now, CANCELLED)]
-                elif self.batch == 1:
-                    res = [self.step_one(w, item, t0)]
-                else:
-                    group, stop = [item], False
-                    total = self.footprint(item.n)
-                    while len(group) < self.batch:
-                        try:
-                            nxt = q.get_nowait()
-                        except queue.Empty:
-                            break
-                        if nxt is None:
-                            stop = True
-                            break
-                        fp = self.footprint(nxt.n)
-                        if not self._take(nxt):
-                            now = time.perf_counter() - t0
-                            with lock:
-                                results[nxt.rid] = Result(nxt.rid, nxt.n, nxt.arrival, now, now, CANCELLED)
-                            continue
-                        if total + fp > self.budget:
-                            q.put(nxt)       # waits for a later group
-                            break
-                        group.append(nxt)
-                        total += fp
-                    res = self.step_batch(w, group, t0)
-                    if stop:
-                        q.put(None)
-                with lock:
-                    for r in res:
-                        results[r.rid] = r
+                    res = [Result(r.rid, r.n, r.arrival, now, now, fld.FLD_ECUDA) for r in group]
+                record(res)
+
+        def serve(w, item, group):
+            """Step item (alone, or with the other small arrived requests it
+            collects into group) on worker w; returns their results."""
+            if not self._take(item):
+                now = time.perf_counter() - t0
+                return [Result(item.rid, item.n, item.arrival, now, now, CANCELLED)]
+            if self.batch == 1 or item.n > self.batch_max_n:
+                return [self.step_one(w, item, t0)]
+            stop, later = False, []
+            used = self.footprint(item.n)
+            while len(group) < self.batch:
+                try:
+                    nxt = q.get_nowait()
+                except queue.Empty:
+                    break
+                if nxt is None:
+                    stop = True
+                    break
+                if nxt.n > self.batch_max_n:
+                    later.append(nxt)    # stepped alone, by the next free worker
+                    continue
+                fp = self.footprint(nxt.n)
+                if not self._take(nxt):
+                    now = time.perf_counter() - t0
+                    record([Result(nxt.rid, nxt.n, nxt.arrival, now, now, CANCELLED)])
+                    continue
+                if used + fp > self.budget:
+                    later.append(nxt)    # waits for a later group
+                    break
+                group.append(nxt)
+                used += fp
+            for r in later:
+                q.put(r)
+            if stop:
+                q.put(None)
+            return self.step_batch(w, group, t0)
 
         threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
         for t in threads:
@@ -425,6 +456,7 @@ class Server:
             else:
                 r = dataclasses.replace(r, arrival=time.perf_counter() - t0)
             q.put(r)
+        all_done.wait()
         for _ in threads:
             q.put(None)
         for t in threads:
