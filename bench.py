@@ -86,6 +86,8 @@ def parse():
                     help="timed steps of each method variant (trapezoidal rule, outflow faces, "
                          "comoving units) on the same workload; 0 skips them")
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-batch", type=int, default=8,
+                    help="requests a worker of the batched serving leg steps together")
     ap.add_argument("--graphs", type=int, default=-1, choices=[-1, 0, 1],
                     help="fld_params.graphs of the measured contexts (0: every launch eager, e.g. for a "
                          "profiler's launch list)")
@@ -535,21 +537,33 @@ def main():
     if args.serve_requests > 0:
         from paper_1306_0645_gb300 import serving
         reqs = synth.request_stream(count=args.serve_requests, rate=args.serve_rate, seed=5 + rank)
-        srv = serving.Server(budget_bytes=40e9, workers=args.serve_workers)
-        # every worker's resident context and solve graphs for every size
-        srv.warm([16, 32, 48, 64, 96, 128])
-        res = srv.run(reqs, realtime=True)
-        # saturation: the same requests all arriving at once
-        sat = serving.summarize(srv.run(reqs, realtime=False))
-        srv.close()
-        serving_out = serving.summarize(res)
-        serving_out["saturation"] = {"solves_per_s": sat["solves_per_s"],
-                                     "cell_solves_per_s": sat["cell_solves_per_s"], "span_s": sat["span_s"],
-                                     "what": "the same requests all arriving at time 0 (the server's throughput "
-                                             "limit; latencies then measure the queue)"}
+        sizes = [16, 32, 48, 64, 96, 128]
+
+        def serve_leg(batch):
+            """Realtime latency and saturation throughput of one serving mode."""
+            srv = serving.Server(budget_bytes=40e9, workers=args.serve_workers, batch=batch)
+            # every worker's resident contexts and solve graphs for every size
+            srv.warm(sizes)
+            res = srv.run(reqs, realtime=True)
+            # saturation: the same requests all arriving at once
+            sat = serving.summarize(srv.run(reqs, realtime=False))
+            srv.close()
+            out = serving.summarize(res)
+            out["mode"] = ("threads: one request per worker" if batch == 1 else
+                           f"a free worker steps up to {batch} arrived requests of at most {srv.batch_max_n}^3 "
+                           f"cells in one fld_step_batched (persistent inner solves over a work list); larger "
+                           f"ones alone")
+            out["saturation"] = {"solves_per_s": sat["solves_per_s"],
+                                 "cell_solves_per_s": sat["cell_solves_per_s"], "span_s": sat["span_s"],
+                                 "what": "the same requests all arriving at time 0 (the server's throughput "
+                                         "limit; latencies then measure the queue)"}
+            return out
+
+        serving_out = serve_leg(1)
         serving_out.update({"rate_per_s": args.serve_rate, "workers": args.serve_workers,
-                            "budget_GB": 40, "sizes": [16, 32, 48, 64, 96, 128],
+                            "budget_GB": 40, "sizes": sizes,
                             "precision": "mixed", "latency": "arrival to E^{n+1} on the host"})
+        serving_out["batched"] = serve_leg(args.serve_batch)
 
     cpu = None
     oracle_err = None

@@ -37,6 +37,7 @@ from . import fld, synth
 
 CANCELLED = -1   # Result.status of a request cancelled before it was stepped
 _MAX_SOURCES = 64  # sources a request may carry
+PERSISTENT_CELLS = 8192   # grids up to this size solve in one persistent CTA each
 
 
 @dataclasses.dataclass
@@ -98,7 +99,10 @@ class Server:
         # never waits for a large grid
         self.batch = max(1, int(batch))
         self.batch_max_n = int(batch_max_n)
-        self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED)
+        # default: mixed precision, and the inner solves of grids up to 16^3
+        # as single-CTA persistent kernels (all their vectors in shared memory)
+        self.params = params or synth.Params(limiter=synth.LIMITER_PAPER, precision=synth.PREC_MIXED,
+                                             persistent_cells=PERSISTENT_CELLS)
         self._used = 0.0          # bytes charged for resident contexts
         self.peak_bytes = 0.0     # the most ever charged (never above the budget)
         self._cv = threading.Condition()
