@@ -160,7 +160,7 @@ typedef struct {
                                   solver); fld_step_batched puts the inner
                                   solves of all such contexts in flight into
                                   one launch over a work list.  0 = never
-                                  (default 0) */
+                                  (default 0), at most 2^24 */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */

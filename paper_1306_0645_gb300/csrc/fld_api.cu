@@ -156,7 +156,8 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     if (p->tail_cells < 0 || p->tail_cells > (1 << 24))
         return set_err(FLD_EINVAL, "tail_cells must lie in [0, 2^24]");
     if (p->paper_order != 0 && p->paper_order != 1) return set_err(FLD_EINVAL, "paper_order must be 0 or 1");
-    if (p->persistent_cells < 0) return set_err(FLD_EINVAL, "persistent_cells must be >= 0");
+    if (p->persistent_cells < 0 || p->persistent_cells > (1 << 24))
+        return set_err(FLD_EINVAL, "persistent_cells must lie in [0, 2^24]");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];

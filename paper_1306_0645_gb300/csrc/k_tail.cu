@@ -36,37 +36,40 @@ constexpr int TAIL_THREADS = 1024;
 // memory and are read through L2 (.cg); in single-CTA mode they live in
 // shared memory and are read directly.
 template <bool CG, class T>
-__device__ __forceinline__ T ldw(const T* p, long long i) {
+__device__ __forceinline__ T ldw(const T* p, int i) {
     if constexpr (CG) return __ldcg(p + i);
     else return p[i];
 }
 
+// Cell offsets within a level are 32-bit: tail and persistent-solve levels
+// hold fewer than 2^31 cells (the size limits of fld_params bound them).
+
 // sum_f w_f u_nbr and sum_f w_f of cell c
 template <bool CG, class T>
-__device__ __forceinline__ void tail_nbr_sums(const Dims& d, const Op<T>& A, long long c, int i, int j,
-                                              int k, const T* u, T& swu, T& sw) {
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+__device__ __forceinline__ void tail_nbr_sums(const Dims& d, const Op<T>& A, int c, int i, int j, int k,
+                                              const T* u, T& swu, T& sw) {
+    const int sy = d.nx, sz = d.nx * d.ny;
     T a = T(0), s = T(0);
     {
         const T wl = A.wx[c];
         if (i > 0) { a += wl * ldw<CG>(u, c - 1); s += wl; }
         else if (d.px) { a += wl * ldw<CG>(u, c + d.nx - 1); s += wl; }
         if (i < d.nx - 1) { const T wu = A.wx[c + 1]; a += wu * ldw<CG>(u, c + 1); s += wu; }
-        else if (d.px) { const long long up = c - (d.nx - 1); const T wu = A.wx[up]; a += wu * ldw<CG>(u, up); s += wu; }
+        else if (d.px) { const int up = c - (d.nx - 1); const T wu = A.wx[up]; a += wu * ldw<CG>(u, up); s += wu; }
     }
     {
         const T wl = A.wy[c];
         if (j > 0) { a += wl * ldw<CG>(u, c - sy); s += wl; }
-        else if (d.py) { a += wl * ldw<CG>(u, c + (long long)(d.ny - 1) * sy); s += wl; }
+        else if (d.py) { a += wl * ldw<CG>(u, c + (d.ny - 1) * sy); s += wl; }
         if (j < d.ny - 1) { const T wu = A.wy[c + sy]; a += wu * ldw<CG>(u, c + sy); s += wu; }
-        else if (d.py) { const long long up = c - (long long)(d.ny - 1) * sy; const T wu = A.wy[up]; a += wu * ldw<CG>(u, up); s += wu; }
+        else if (d.py) { const int up = c - (d.ny - 1) * sy; const T wu = A.wy[up]; a += wu * ldw<CG>(u, up); s += wu; }
     }
     {
         const T wl = A.wz[c];
         if (k > 0) { a += wl * ldw<CG>(u, c - sz); s += wl; }
-        else if (d.pz) { a += wl * ldw<CG>(u, c + (long long)(d.nz - 1) * sz); s += wl; }
+        else if (d.pz) { a += wl * ldw<CG>(u, c + (d.nz - 1) * sz); s += wl; }
         if (k < d.nz - 1) { const T wu = A.wz[c + sz]; a += wu * ldw<CG>(u, c + sz); s += wu; }
-        else if (d.pz) { const long long up = c - (long long)(d.nz - 1) * sz; const T wu = A.wz[up]; a += wu * ldw<CG>(u, up); s += wu; }
+        else if (d.pz) { const int up = c - (d.nz - 1) * sz; const T wu = A.wz[up]; a += wu * ldw<CG>(u, up); s += wu; }
     }
     swu = a;
     sw = s;
@@ -74,28 +77,27 @@ __device__ __forceinline__ void tail_nbr_sums(const Dims& d, const Op<T>& A, lon
 
 // sum_f w_f u_nbr v_nbr (the red neighbours r * invd of a zero-guess sweep)
 template <bool CG, class T>
-__device__ __forceinline__ T tail_nbr_sum_prod(const Dims& d, const Op<T>& A, long long c, int i, int j,
-                                               int k, const T* u, const T* v) {
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+__device__ __forceinline__ T tail_nbr_sum_prod(const Dims& d, const Op<T>& A, int c, int i, int j, int k,
+                                               const T* u, const T* v) {
+    const int sy = d.nx, sz = d.nx * d.ny;
     T a = T(0);
     if (i > 0) a += A.wx[c] * ldw<CG>(u, c - 1) * v[c - 1];
     else if (d.px) a += A.wx[c] * ldw<CG>(u, c + d.nx - 1) * v[c + d.nx - 1];
     if (i < d.nx - 1) a += A.wx[c + 1] * ldw<CG>(u, c + 1) * v[c + 1];
-    else if (d.px) { const long long up = c - (d.nx - 1); a += A.wx[up] * ldw<CG>(u, up) * v[up]; }
+    else if (d.px) { const int up = c - (d.nx - 1); a += A.wx[up] * ldw<CG>(u, up) * v[up]; }
     if (j > 0) a += A.wy[c] * ldw<CG>(u, c - sy) * v[c - sy];
-    else if (d.py) { const long long lo = c + (long long)(d.ny - 1) * sy; a += A.wy[c] * ldw<CG>(u, lo) * v[lo]; }
+    else if (d.py) { const int lo = c + (d.ny - 1) * sy; a += A.wy[c] * ldw<CG>(u, lo) * v[lo]; }
     if (j < d.ny - 1) a += A.wy[c + sy] * ldw<CG>(u, c + sy) * v[c + sy];
-    else if (d.py) { const long long up = c - (long long)(d.ny - 1) * sy; a += A.wy[up] * ldw<CG>(u, up) * v[up]; }
+    else if (d.py) { const int up = c - (d.ny - 1) * sy; a += A.wy[up] * ldw<CG>(u, up) * v[up]; }
     if (k > 0) a += A.wz[c] * ldw<CG>(u, c - sz) * v[c - sz];
-    else if (d.pz) { const long long lo = c + (long long)(d.nz - 1) * sz; a += A.wz[c] * ldw<CG>(u, lo) * v[lo]; }
+    else if (d.pz) { const int lo = c + (d.nz - 1) * sz; a += A.wz[c] * ldw<CG>(u, lo) * v[lo]; }
     if (k < d.nz - 1) a += A.wz[c + sz] * ldw<CG>(u, c + sz) * v[c + sz];
-    else if (d.pz) { const long long up = c - (long long)(d.nz - 1) * sz; a += A.wz[up] * ldw<CG>(u, up) * v[up]; }
+    else if (d.pz) { const int up = c - (d.nz - 1) * sz; a += A.wz[up] * ldw<CG>(u, up) * v[up]; }
     return a;
 }
 
-// Cell coordinates by 32-bit unsigned division (tail levels hold fewer
-// than 2^24 cells; 64-bit division would cost far more than the sweep).
-__device__ __forceinline__ void tail_ijk(long long c, const Dims& d, int& i, int& j, int& k) {
+// Cell coordinates by 32-bit unsigned division.
+__device__ __forceinline__ void tail_ijk(int c, const Dims& d, int& i, int& j, int& k) {
     const unsigned cu = (unsigned)c, nx = (unsigned)d.nx, nxy = (unsigned)d.nx * (unsigned)d.ny;
     const unsigned kk = cu / nxy;
     const unsigned rem = cu - kk * nxy;
@@ -111,17 +113,18 @@ __device__ __forceinline__ void tail_ijk(long long c, const Dims& d, int& i, int
 // instead of two divisions (i + di < 2 nx and j + dj + 1 < 2 ny, so one
 // carry each suffices).
 struct Walk {
-    long long c, s;
+    int c, s, n;
     int i, j, k, di, dj, dk, nx, ny;
-    __device__ __forceinline__ Walk(const Dims& d, long long c0, long long stride)
-        : c(c0), s(stride), nx(d.nx), ny(d.ny) {
-        tail_ijk(c0 < d.n ? c0 : 0, d, i, j, k);
+    __device__ __forceinline__ Walk(const Dims& d, int c0, int stride)
+        : c(c0), s(stride), n((int)d.n), nx(d.nx), ny(d.ny) {
+        tail_ijk(c0 < n ? c0 : 0, d, i, j, k);
         const unsigned su = (unsigned)stride, nxu = (unsigned)d.nx, nyu = (unsigned)d.ny;
         const unsigned t = su / nxu;
         di = (int)(su - t * nxu);
         dk = (int)(t / nyu);
         dj = (int)(t - (unsigned)dk * nyu);
     }
+    __device__ __forceinline__ bool more() const { return c < n; }
     __device__ __forceinline__ void next() {
         c += s;
         i += di;
@@ -131,6 +134,52 @@ struct Walk {
         k += dk;
     }
 };
+
+// The same walk over the cells of one colour, (i + j + k) % 2 == col, of a
+// level with an even x extent: half-index h over the n / 2 cells of that
+// colour, x position 2 t + ((col + j + k) & 1), so no lane of a warp idles
+// on a cell of the other colour.
+struct WalkC {
+    int h, s, n2;
+    int t, j, k, dt, dj, dk, nx2, ny, nx, col;
+    __device__ __forceinline__ WalkC(const Dims& d, int colour, int h0, int stride)
+        : h(h0), s(stride), n2((int)(d.n >> 1)), nx2(d.nx >> 1), ny(d.ny), nx(d.nx), col(colour) {
+        const unsigned hu = (unsigned)(h0 < n2 ? h0 : 0), n2x = (unsigned)nx2, nyu = (unsigned)d.ny;
+        const unsigned r = hu / n2x;
+        t = (int)(hu - r * n2x);
+        k = (int)(r / nyu);
+        j = (int)(r - (unsigned)k * nyu);
+        const unsigned su = (unsigned)stride;
+        const unsigned q = su / n2x;
+        dt = (int)(su - q * n2x);
+        dk = (int)(q / nyu);
+        dj = (int)(q - (unsigned)dk * nyu);
+    }
+    __device__ __forceinline__ bool more() const { return h < n2; }
+    __device__ __forceinline__ int i() const { return 2 * t + ((col + j + k) & 1); }
+    __device__ __forceinline__ int c() const { return i() + nx * (j + ny * k); }
+    __device__ __forceinline__ void next() {
+        h += s;
+        t += dt;
+        if (t >= nx2) { t -= nx2; j++; }
+        j += dj;
+        if (j >= ny) { j -= ny; k++; }
+        k += dk;
+    }
+};
+
+// f(c, i, j, k) for every cell of colour col in this thread's share: the
+// colour walk where nx is even, else the plain walk with the other colour
+// skipped.  The cells are independent, so the order does not matter.
+template <class F>
+__device__ __forceinline__ void for_colour(const Dims& d, int col, int tid, int nth, F f) {
+    if ((d.nx & 1) == 0) {
+        for (WalkC w(d, col, tid, nth); w.more(); w.next()) f(w.c(), w.i(), w.j, w.k);
+    } else {
+        for (Walk w(d, tid, nth); w.more(); w.next())
+            if (((w.i + w.j + w.k) & 1) == col) f(w.c, w.i, w.j, w.k);
+    }
+}
 
 __device__ __forceinline__ int tail_fine_tap(int I, int t, int nf, int periodic) {
     int f = 2 * I - 1 + t;
@@ -154,61 +203,54 @@ struct Vec {
 };
 
 // Phase loops: the participating threads stride over the level's cells.
-#define TAIL_LOOP(c, n) for (long long c = tid; c < (n); c += nth)
+#define TAIL_LOOP(c, n) for (int c = tid; c < (int)(n); c += nth)
 
 // Down-leg phases of level L into the coarse right-hand side rc:
 // smoothing from zero (and further pre-sweeps), t = r - A z, rc = R t.
 template <bool CG, class T, class Sync>
-__device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc, int pre, long long tid,
-                          long long nth, Sync sync) {
+__device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc, int pre, int tid, int nth,
+                          Sync sync) {
     const Dims& d = L.d;
     const Op<T>& A = L.A;
     const T* r = v.r;
     T* z = v.z;
     if (pre >= 1) {
-        for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-            const long long c = w.c;
-            const int i = w.i, j = w.j, k = w.k;
-            const T rcv = ldw<CG>(r, c);
-            if (((i + j + k) & 1) == 0) z[c] = rcv * A.invd[c];
-            else z[c] = A.invd[c] * (rcv + tail_nbr_sum_prod<CG, T>(d, A, c, i, j, k, r, A.invd));
-        }
+        // red cells r / diag, black cells from the red ones' r / diag (the
+        // two colours independent, so in one phase)
+        for_colour(d, 0, tid, nth, [&](int c, int, int, int) { z[c] = ldw<CG>(r, c) * A.invd[c]; });
+        for_colour(d, 1, tid, nth, [&](int c, int i, int j, int k) {
+            z[c] = A.invd[c] * (ldw<CG>(r, c) + tail_nbr_sum_prod<CG, T>(d, A, c, i, j, k, r, A.invd));
+        });
         sync();
         for (int it = 1; it < pre; it++)
             for (int colour = 0; colour < 2; colour++) {
-                for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-                    const long long c = w.c;
-                    const int i = w.i, j = w.j, k = w.k;
-                    if (((i + j + k) & 1) != colour) continue;
+                for_colour(d, colour, tid, nth, [&](int c, int i, int j, int k) {
                     T swu, sw;
                     tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
                     z[c] = A.invd[c] * (ldw<CG>(r, c) + swu);
-                }
+                });
                 sync();
             }
     } else {
         TAIL_LOOP(c, d.n) z[c] = T(0);
         sync();
     }
-    for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-        const long long c = w.c;
-        const int i = w.i, j = w.j, k = w.k;
+    for (Walk w(d, tid, nth); w.more(); w.next()) {
+        const int c = w.c;
         T swu, sw;
-        tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
+        tail_nbr_sums<CG, T>(d, A, c, w.i, w.j, w.k, z, swu, sw);
         const T zc = ldw<CG>((const T*)z, c);
         v.t[c] = ldw<CG>(r, c) - (A.m[c] * zc + sw * zc - swu);
     }
     sync();
     const T wt[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
-    for (Walk w(cd, tid, nth); w.c < cd.n; w.next()) {
-        const long long cc = w.c;
-        const int I = w.i, J = w.j, K = w.k;
+    for (Walk w(cd, tid, nth); w.more(); w.next()) {
         int fi[4], fj[4], fk[4];
 #pragma unroll
         for (int t = 0; t < 4; t++) {
-            fi[t] = tail_fine_tap(I, t, d.nx, d.px);
-            fj[t] = tail_fine_tap(J, t, d.ny, d.py);
-            fk[t] = tail_fine_tap(K, t, d.nz, d.pz);
+            fi[t] = tail_fine_tap(w.i, t, d.nx, d.px);
+            fj[t] = tail_fine_tap(w.j, t, d.ny, d.py);
+            fk[t] = tail_fine_tap(w.k, t, d.nz, d.pz);
         }
         T acc = T(0);
 #pragma unroll
@@ -216,7 +258,7 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
             T acc_j = T(0);
 #pragma unroll
             for (int tj = 0; tj < 4; tj++) {
-                const long long row = (long long)d.nx * (fj[tj] + (long long)d.ny * fk[tk]);
+                const int row = d.nx * (fj[tj] + d.ny * fk[tk]);
                 T acc_i = T(0);
 #pragma unroll
                 for (int ti = 0; ti < 4; ti++) acc_i += wt[ti] * ldw<CG>((const T*)v.t, row + fi[ti]);
@@ -224,34 +266,32 @@ __device__ void tail_down(const TailLevel<T>& L, Vec<T> v, const Dims& cd, T* rc
             }
             acc += wt[tk] * acc_j;
         }
-        rc[cc] = acc * T(0.125);
+        rc[w.c] = acc * T(0.125);
     }
     sync();
 }
 
 // Up-leg phases of level L: z += P zc, then the post-sweeps.
 template <bool CG, class T, class Sync>
-__device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T* zc, int post, int first,
-                        long long tid,
-                        long long nth, Sync sync) {
+__device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T* zc, int post, int first, int tid,
+                        int nth, Sync sync) {
     const Dims& d = L.d;
     const Op<T>& A = L.A;
     T* z = v.z;
     const T w2[2] = {T(0.75), T(0.25)};
-    for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-        const long long c = w.c;
-        const int i = w.i, j = w.j, k = w.k;
+    for (Walk w(d, tid, nth); w.more(); w.next()) {
+        const int c = w.c;
         int Ix[2], Iy[2], Iz[2];
-        tail_coarse_pair(i, cd.nx, cd.px, Ix[0], Ix[1]);
-        tail_coarse_pair(j, cd.ny, cd.py, Iy[0], Iy[1]);
-        tail_coarse_pair(k, cd.nz, cd.pz, Iz[0], Iz[1]);
+        tail_coarse_pair(w.i, cd.nx, cd.px, Ix[0], Ix[1]);
+        tail_coarse_pair(w.j, cd.ny, cd.py, Iy[0], Iy[1]);
+        tail_coarse_pair(w.k, cd.nz, cd.pz, Iz[0], Iz[1]);
         T acc = T(0);
 #pragma unroll
         for (int b = 0; b < 2; b++) {
             T acc_j = T(0);
 #pragma unroll
             for (int q = 0; q < 2; q++) {
-                const long long row = (long long)cd.nx * (Iy[q] + (long long)cd.ny * Iz[b]);
+                const int row = cd.nx * (Iy[q] + cd.ny * Iz[b]);
                 acc_j += w2[q] * (w2[0] * ldw<CG>(zc, row + Ix[0]) + w2[1] * ldw<CG>(zc, row + Ix[1]));
             }
             acc += w2[b] * acc_j;
@@ -263,24 +303,21 @@ __device__ void tail_up(const TailLevel<T>& L, Vec<T> v, const Dims& cd, const T
     for (int it = 0; it < post; it++)
         for (int q = 0; q < 2; q++) {
             const int colour = q == 0 ? first : 1 - first;
-            for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-                const long long c = w.c;
-                const int i = w.i, j = w.j, k = w.k;
-                if (((i + j + k) & 1) != colour) continue;
+            for_colour(d, colour, tid, nth, [&](int c, int i, int j, int k) {
                 T swu, sw;
                 tail_nbr_sums<CG, T>(d, A, c, i, j, k, z, swu, sw);
                 z[c] = A.invd[c] * (ldw<CG>((const T*)v.r, c) + swu);
-            }
+            });
             sync();
         }
 }
 
 // z = A^-1 r on the coarsest grid with the stored explicit inverse.
 template <bool CG, class T, class Sync>
-__device__ void tail_coarsest(int n, const double* ainv, Vec<T> v, long long tid, long long nth, Sync sync) {
+__device__ void tail_coarsest(int n, const double* ainv, Vec<T> v, int tid, int nth, Sync sync) {
     TAIL_LOOP(row, n) {
         double acc = 0.0;
-        for (int q = 0; q < n; q++) acc += ainv[(long long)q * n + row] * (double)ldw<CG>((const T*)v.r, q);
+        for (int q = 0; q < n; q++) acc += ainv[q * n + row] * (double)ldw<CG>((const T*)v.r, q);
         v.z[row] = (T)acc;
     }
     sync();
@@ -294,8 +331,8 @@ __device__ void tail_coarsest(int n, const double* ainv, Vec<T> v, long long tid
 // visible to the whole cluster on return.
 template <class T>
 __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, cg::cluster_group& cl, unsigned char* smem) {
-    const long long gthreads = (long long)TAIL_THREADS * cl.num_blocks();
-    const long long gtid = (long long)cl.block_rank() * TAIL_THREADS + threadIdx.x;
+    const int gthreads = TAIL_THREADS * (int)cl.num_blocks();
+    const int gtid = (int)cl.block_rank() * TAIL_THREADS + (int)threadIdx.x;
     const int nl = a.nlev, ls = a.small_from;
     auto csync = [&]() { cl.sync(); };
     auto bsync = []() { __syncthreads(); };
@@ -307,7 +344,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, cg::cluster_gro
     if (ls < nl) {
         // ---- the small levels in CTA 0 alone, vectors in shared memory
         if (cl.block_rank() == 0) {
-            const long long tid = threadIdx.x, nth = TAIL_THREADS;
+            const int tid = threadIdx.x, nth = TAIL_THREADS;
             Vec<T> sv[TAIL_MAX_LEVELS];
             T* base = reinterpret_cast<T*>(smem);
             for (int l = ls; l < nl; l++) {
@@ -315,7 +352,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, cg::cluster_gro
                 sv[l] = Vec<T>{base, base + n, base + 2 * n};
                 base += 3 * n;
             }
-            for (long long c = tid; c < a.L[ls].d.n; c += nth) sv[ls].r[c] = __ldcg(a.L[ls].r + c);
+            for (int c = tid; c < (int)a.L[ls].d.n; c += nth) sv[ls].r[c] = __ldcg(a.L[ls].r + c);
             __syncthreads();
             for (int l = ls; l < nl - 1; l++)
                 tail_down<false, T>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].r, a.pre, tid, nth, bsync);
@@ -323,7 +360,7 @@ __device__ __forceinline__ void tail_cycle(const TailArgs<T>& a, cg::cluster_gro
             for (int l = nl - 2; l >= ls; l--)
                 tail_up<false, T>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].z, a.post, a.paper_order ? 0 : 1, tid, nth,
                                   bsync);
-            for (long long c = tid; c < a.L[ls].d.n; c += nth) a.L[ls].z[c] = sv[ls].z[c];
+            for (int c = tid; c < (int)a.L[ls].d.n; c += nth) a.L[ls].z[c] = sv[ls].z[c];
         }
         cl.sync();
     } else {
@@ -390,8 +427,9 @@ __device__ void ps_solve(const PsReq& R, cg::cluster_group& cl, unsigned char* s
     float* p = R.p;
     float* q = R.q;
     float* x = R.x;
-    const long long nth = (long long)TAIL_THREADS * cl.num_blocks();
-    const long long tid = (long long)cl.block_rank() * TAIL_THREADS + threadIdx.x;
+    const int nth = TAIL_THREADS * (int)cl.num_blocks();
+    const int tid = (int)cl.block_rank() * TAIL_THREADS + (int)threadIdx.x;
+    const int n = (int)d.n;
     const double thresh = __ldcg(R.sc + S_THRESH);
     const int maxit = (int)__ldcg(R.sc + S_MAXIT);
     double rho = 0.0, rho_old = 0.0, beta = 0.0, pq = 0.0, alpha = 0.0, rr = __ldcg(R.sc + S_RR);
@@ -400,21 +438,21 @@ __device__ void ps_solve(const PsReq& R, cg::cluster_group& cl, unsigned char* s
     while (k < maxit) {
         tail_cycle<float>(a, cl, smem);   // z = M r
         DotAcc<float> arz;
-        for (long long c = tid; c < d.n; c += nth) arz.add(__ldcg(r + c), __ldcg(z + c));
+        for (int c = tid; c < n; c += nth) arz.add(__ldcg(r + c), __ldcg(z + c));
         rho = ps_cluster_sum(arz.value(), part + slot, cl);
         slot = (slot + 1) & 3;
         beta = k == 0 ? 0.0 : rho / rho_old;
         rho_old = rho;
         const float bf = (float)beta;
         if (k == 0)
-            for (long long c = tid; c < d.n; c += nth) p[c] = __ldcg(z + c);
+            for (int c = tid; c < n; c += nth) p[c] = __ldcg(z + c);
         else
-            for (long long c = tid; c < d.n; c += nth) p[c] = fmaf(bf, __ldcg(p + c), __ldcg(z + c));
+            for (int c = tid; c < n; c += nth) p[c] = fmaf(bf, __ldcg(p + c), __ldcg(z + c));
         cl.sync();
         // q = A p and <p, q>
         DotAcc<float> apq;
-        for (Walk w(d, tid, nth); w.c < d.n; w.next()) {
-            const long long c = w.c;
+        for (Walk w(d, tid, nth); w.more(); w.next()) {
+            const int c = w.c;
             float swu, sw;
             tail_nbr_sums<true, float>(d, A, c, w.i, w.j, w.k, p, swu, sw);
             const float pc = __ldcg(p + c);
@@ -428,7 +466,7 @@ __device__ void ps_solve(const PsReq& R, cg::cluster_group& cl, unsigned char* s
         const float af = (float)alpha;
         // x += alpha p, r -= alpha q, ||r||^2
         DotAcc<float> arr;
-        for (long long c = tid; c < d.n; c += nth) {
+        for (int c = tid; c < n; c += nth) {
             x[c] = fmaf(af, __ldcg(p + c), __ldcg(x + c));
             const float rn = fmaf(-af, __ldcg(q + c), __ldcg(r + c));
             r[c] = rn;
@@ -484,7 +522,7 @@ __device__ __forceinline__ double ps_block_sum(double v) {
 __device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
     const TailArgs<float>& a = R.v;
     const int nl = a.nlev;
-    const long long tid = threadIdx.x, nth = TAIL_THREADS;
+    const int tid = threadIdx.x, nth = TAIL_THREADS;
     auto bsync = []() { __syncthreads(); };
     Vec<float> sv[TAIL_MAX_LEVELS];
     float* base = reinterpret_cast<float*>(smem);
@@ -495,13 +533,13 @@ __device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
     }
     const Dims& d = a.L[0].d;
     const Op<float>& A = a.L[0].A;
-    const long long n0 = d.n;
+    const int n0 = (int)d.n;
     float* r = sv[0].r;
     float* z = sv[0].z;
     float* p = base;
     float* q = base + n0;
     float* x = base + 2 * n0;
-    for (long long c = tid; c < n0; c += nth) {
+    for (int c = tid; c < n0; c += nth) {
         r[c] = __ldcg(a.L[0].r + c);
         x[c] = 0.0f;
     }
@@ -520,19 +558,19 @@ __device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
             tail_up<false, float>(a.L[l], sv[l], a.L[l + 1].d, sv[l + 1].z, a.post, a.paper_order ? 0 : 1, tid, nth,
                                   bsync);
         DotAcc<float> arz;
-        for (long long c = tid; c < n0; c += nth) arz.add(r[c], z[c]);
+        for (int c = tid; c < n0; c += nth) arz.add(r[c], z[c]);
         rho = ps_block_sum(arz.value());
         beta = k == 0 ? 0.0 : rho / rho_old;
         rho_old = rho;
         const float bf = (float)beta;
         if (k == 0)
-            for (long long c = tid; c < n0; c += nth) p[c] = z[c];
+            for (int c = tid; c < n0; c += nth) p[c] = z[c];
         else
-            for (long long c = tid; c < n0; c += nth) p[c] = fmaf(bf, p[c], z[c]);
+            for (int c = tid; c < n0; c += nth) p[c] = fmaf(bf, p[c], z[c]);
         __syncthreads();
         DotAcc<float> apq;
-        for (Walk w(d, tid, nth); w.c < n0; w.next()) {
-            const long long c = w.c;
+        for (Walk w(d, tid, nth); w.more(); w.next()) {
+            const int c = w.c;
             float swu, sw;
             tail_nbr_sums<false, float>(d, A, c, w.i, w.j, w.k, p, swu, sw);
             const float pc = p[c];
@@ -544,7 +582,7 @@ __device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
         alpha = rho / pq;
         const float af = (float)alpha;
         DotAcc<float> arr;
-        for (long long c = tid; c < n0; c += nth) {
+        for (int c = tid; c < n0; c += nth) {
             x[c] = fmaf(af, p[c], x[c]);
             const float rn = fmaf(-af, q[c], r[c]);
             r[c] = rn;
@@ -558,7 +596,7 @@ __device__ void ps_solve_cta(const PsReq& R, unsigned char* smem) {
         }
         if (rr <= thresh) break;
     }
-    for (long long c = tid; c < n0; c += nth) R.x[c] = x[c];
+    for (int c = tid; c < n0; c += nth) R.x[c] = x[c];
     if (threadIdx.x == 0) {
         double* sc = R.sc;
         sc[S_RHO] = rho;
