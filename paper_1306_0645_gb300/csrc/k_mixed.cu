@@ -261,7 +261,7 @@ struct FluxWalk {
 // A face the screen does not settle goes to the block's list for the
 // compacted pass k_asm_fix_mx (whole warps on the df limiter); a block whose
 // list is full computes the rest in place.
-__global__ void __launch_bounds__(256) k_asm_faces_mx(Dims d, PhysDev p, const double* __restrict__ E,
+__global__ void __launch_bounds__(256, 4) k_asm_faces_mx(Dims d, PhysDev p, const double* __restrict__ E,
                                                      const double* __restrict__ nHI,
                                                      const double* __restrict__ eta, Op<float> A, Op<float> L,
                                                      double* sc, FaceList fl, int zb0, int kch) {
