@@ -695,36 +695,33 @@ __device__ __forceinline__ float red_res(const float* __restrict__ rf, long long
     return ((x + fy + fz) & 1) == 0 ? rf[(row + x) >> 1] : 0.0f;
 }
 
-// x-y weighted sums of fine plane fz for coarse cells 4t .. 4t+3 of row J
-// from a red-compressed residual: one float4 per fine row holds the red
-// values of fine cells 8t .. 8t+7.
-__device__ __forceinline__ float4 xy_sum_red(const Dims& f, const float* __restrict__ rf, int t, int J,
-                                             int fz, bool load_l, bool load_r) {
+// x-y weighted sums of fine plane fz (offset pbase = fz nx ny) for coarse
+// cells 4t .. 4t+3 of a coarse row, from a red-compressed residual: one
+// float4 per fine row holds the red values of fine cells x0 .. x0+7 (x0 =
+// 8t).  The four fine rows fy[q] (offsets ry[q] = fy[q] nx, folded at the
+// boundary once per thread) are weighted 1/4, 3/4, 3/4, 1/4.  In a row
+// whose even cells are red, coarse cell i takes 3/4 of its own red value
+// and 1/4 of the next one (the one after the last from the next lane); with
+// odd red cells, 1/4 of the previous one.  xl, xr: the folded fine cells
+// x0 - 1 and x0 + 8, read directly by the lanes at a block or grid edge.
+__device__ __forceinline__ float4 xy_sum_red(const float* __restrict__ rf, long long pbase, const int (&fy)[4],
+                                             const int (&ry)[4], int fz, int x0, int xl, int xr, bool load_l,
+                                             bool load_r) {
     const float wv[4] = {0.25f, 0.75f, 0.75f, 0.25f};
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const long long plane = (long long)fz * f.nx * f.ny;
-    const int x0 = 8 * t;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        const int fy = fold(2 * J - 1 + q, f.ny, f.py);
-        const long long row = plane + (long long)fy * f.nx;
+        const long long row = pbase + ry[q];
         const float4 h = ld4(rf, (row + x0) >> 1);
-        // fine cell x0 is red when x0 + fy + fz is even (x0 is)
-        const bool even_red = ((fy + fz) & 1) == 0;
-        float v[8];
-        v[0] = even_red ? h.x : 0.f; v[1] = even_red ? 0.f : h.x;
-        v[2] = even_red ? h.y : 0.f; v[3] = even_red ? 0.f : h.y;
-        v[4] = even_red ? h.z : 0.f; v[5] = even_red ? 0.f : h.z;
-        v[6] = even_red ? h.w : 0.f; v[7] = even_red ? 0.f : h.w;
-        // fine cell x0 - 1 is red when the odd cells are, x0 + 8 when the even ones are
+        const bool e = ((fy[q] + fz) & 1) == 0;   // the even cells of the row are red
         const float lsh = __shfl_up_sync(FULL, h.w, 1);
         const float rsh = __shfl_down_sync(FULL, h.x, 1);
-        const float L = load_l ? red_res(rf, row, fold(x0 - 1, f.nx, f.px), fy, fz) : (even_red ? 0.f : lsh);
-        const float R = load_r ? red_res(rf, row, fold(x0 + 8, f.nx, f.px), fy, fz) : (even_red ? rsh : 0.f);
-        const float c0 = 0.25f * L + 0.75f * v[0] + 0.75f * v[1] + 0.25f * v[2];
-        const float c1 = 0.25f * v[1] + 0.75f * v[2] + 0.75f * v[3] + 0.25f * v[4];
-        const float c2 = 0.25f * v[3] + 0.75f * v[4] + 0.75f * v[5] + 0.25f * v[6];
-        const float c3 = 0.25f * v[5] + 0.75f * v[6] + 0.75f * v[7] + 0.25f * R;
+        const float L = load_l ? red_res(rf, row, xl, fy[q], fz) : (e ? 0.f : lsh);
+        const float R = load_r ? red_res(rf, row, xr, fy[q], fz) : (e ? rsh : 0.f);
+        const float c0 = fmaf(0.75f, h.x, 0.25f * ((e ? h.y : 0.f) + L));
+        const float c1 = fmaf(0.75f, h.y, 0.25f * (e ? h.z : h.x));
+        const float c2 = fmaf(0.75f, h.z, 0.25f * (e ? h.w : h.y));
+        const float c3 = fmaf(0.75f, h.w, 0.25f * ((e ? 0.f : h.z) + R));
         acc.x = fmaf(wv[q], c0, acc.x);
         acc.y = fmaf(wv[q], c1, acc.y);
         acc.z = fmaf(wv[q], c2, acc.z);
@@ -788,8 +785,17 @@ __global__ void __launch_bounds__(256) k_restrict_red4(Dims f, Dims cd, const fl
     if (K0 >= K1) return;
     const bool load_l = threadIdx.x == 0 || t == 0;
     const bool load_r = threadIdx.x == blockDim.x - 1 || t == qt - 1;
-    float4 s0 = xy_sum_red(f, rf, t, J, fold(2 * K0 - 1, f.nz, f.pz), load_l, load_r);
-    float4 s1 = xy_sum_red(f, rf, t, J, 2 * K0, load_l, load_r);
+    int fy[4], ry[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        fy[q] = fold(2 * J - 1 + q, f.ny, f.py);
+        ry[q] = fy[q] * f.nx;
+    }
+    const int x0 = 8 * t, xl = fold(x0 - 1, f.nx, f.px), xr = fold(x0 + 8, f.nx, f.px);
+    const long long nxy = (long long)f.nx * f.ny;
+    auto sum = [&](int fz) { return xy_sum_red(rf, fz * nxy, fy, ry, fz, x0, xl, xr, load_l, load_r); };
+    float4 s0 = sum(fold(2 * K0 - 1, f.nz, f.pz));
+    float4 s1 = sum(2 * K0);
     for (int K = K0; K < K1; K++) {
         if (pf > 0 && K + pf < K1) {
             const long long o = (long long)(2 * (K + pf) + 1) * f.nx * f.ny + (long long)(2 * J) * f.nx + 8 * t;
@@ -800,8 +806,8 @@ __global__ void __launch_bounds__(256) k_restrict_red4(Dims f, Dims cd, const fl
                 pf2(rf, (o + (long long)f.nx * f.ny + f.nx) >> 1);
             }
         }
-        const float4 s2 = xy_sum_red(f, rf, t, J, 2 * K + 1, load_l, load_r);
-        const float4 s3 = xy_sum_red(f, rf, t, J, fold(2 * K + 2, f.nz, f.pz), load_l, load_r);
+        const float4 s2 = sum(2 * K + 1);
+        const float4 s3 = sum(fold(2 * K + 2, f.nz, f.pz));
         float4 o;
         o.x = 0.125f * (0.25f * s0.x + 0.75f * s1.x + 0.75f * s2.x + 0.25f * s3.x);
         o.y = 0.125f * (0.25f * s0.y + 0.75f * s1.y + 0.75f * s2.y + 0.25f * s3.y);
