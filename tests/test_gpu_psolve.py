@@ -96,6 +96,51 @@ def test_persistent_solve_takes_the_iterations_of_the_launch_path(fld, make):
     assert abs(a["iters"] - b["iters"]) <= a["outer_iters"], (a, b)
 
 
+def with_faces(case, dirichlet, ebc=(0.0,) * 6, theta=1.0):
+    g = case.grid
+    case.grid = synth.Grid(g.n, g.h, g.periodic, dirichlet=dirichlet, ebc=ebc)
+    case.params.theta = theta
+    return case
+
+
+def solver_variant(case, **kw):
+    for k, v in kw.items():
+        setattr(case.params, k, v)
+    return case
+
+
+VARIANTS = [
+    # Table 1's red-then-black post-sweeps, both modes
+    ("paper_order_cta", lambda: solver_variant(synth.config3(16, sources=4), paper_order=1)),
+    ("paper_order_cluster", lambda: solver_variant(synth.config3(32, sources=16), paper_order=1)),
+    # two pre- and post-sweeps (the colour sweeps after the zero-guess one)
+    ("pre2_post2_cta", lambda: solver_variant(synth.random_case((16, 16, 16), seed=31), pre=2, post=2)),
+    ("pre2_post2_cluster", lambda: solver_variant(
+        synth.random_case((32, 24, 16), seed=32, periodic=(True, False, True)), pre=2, post=2)),
+    # Sec. 4.1 faces (outflow above) with the trapezoidal rule, and Dirichlet
+    # faces on a grid with a periodic axis
+    ("outflow_trapezoidal", lambda: with_faces(synth.random_case((16, 12, 20), seed=33), (False, True) * 3,
+                                               theta=0.5)),
+    ("dirichlet_mixed", lambda: with_faces(synth.random_case((24, 16, 8), seed=34, periodic=(False, False, True)),
+                                           (True, False, True, True, False, False),
+                                           (1e-19, 0.0, 3e-20, 0.0, 0.0, 0.0), theta=0.75)),
+]
+
+
+@pytest.mark.parametrize("name,make", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_persistent_solver_variants_match_oracle(fld, oracle, name, make):
+    # the same V-cycle options and face types as the launch-per-kernel path,
+    # against the oracle's step solved to 1e-13
+    case = make()
+    E, info, prof = ps_step(fld, case, 1e-8, PS_ALL)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    assert prof["psolve"] == info["outer_iters"] >= 1
+    Eref, _ = oracle.step(case.grid, case.params, {"rtol": 1e-13, "max_iter": 200}, case.E, case.nHI, case.eta)
+    el2 = np.linalg.norm(E - Eref) / np.linalg.norm(Eref)
+    einf = np.abs(E - Eref).max() / np.abs(Eref).max()
+    assert el2 < 1e-6 and einf < 1e-6, (el2, einf)
+
+
 def test_persistent_noconv_leaves_E_unchanged(fld):
     case = synth.config3(32, sources=16)
     case.params.max_iter = 2
