@@ -20,6 +20,10 @@
 // k_mg.cu (red/black Gauss-Seidel from a zero guess, colour sweeps, r - A z,
 // full-weighting restriction, trilinear prolongation, dense inverse on the
 // coarsest grid), so the tail gives the V-cycle those kernels give.
+//
+// The same phases also serve k_psolve, which runs whole inner MG-PCG solves
+// of small grids (every level, then the CG vector operations) for a work
+// list of requests in one launch (see the section below).
 #include <cooperative_groups.h>
 
 #include "kernels.h"
