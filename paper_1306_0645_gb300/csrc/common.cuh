@@ -23,7 +23,7 @@ enum Slot {
     S_ALPHA,
     S_RR,         // ||r||^2 of the current (inner) solve
     S_R0,         // ||r_0||^2 of the current inner solve
-    S_R64,        // ||r64||^2 (outer FP64 residual)
+    S_XZERO,      // != 0: the next CG p/q kernel starts x at 0 (its reduction clears it)
     S_RMAX,       // max |r64|
     S_SCALE,      // inner-solve scale s (mixed mode)
     S_BAL,        // photon balance partial sums
@@ -133,6 +133,7 @@ __device__ __forceinline__ void red_finalize(const RedArgs& ra, const double* v)
     case R_ALPHA:
         sc[S_PQ] = v[0];
         sc[S_ALPHA] = sc[S_RHO] / v[0];
+        sc[S_XZERO] = 0.0;   // every block has read it (the last block runs this)
         bad = !isfinite(sc[S_ALPHA]);
         break;
     case R_STORE2:

@@ -838,6 +838,15 @@ fld_status pcg_begin(fld_ctx* c, double r0sq, double rtol, int max_iter) {
         // solve keeps these in registers)
         CUDA_TRY(cudaMemcpyAsync(c->sc + S_FIRST, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
         CUDA_TRY(cudaMemsetAsync(c->sc + S_ALPHA, 0, sizeof(double), c->s));
+        if (std::is_same<T, float>::value) {
+            // the FP32 solve starts from x = 0: the first p/q kernel writes
+            // it where the update of x is deferred to that kernel, else here
+            // (the FP64 solve's caller clears its x)
+            if (defers_x<T>(c))
+                CUDA_TRY(cudaMemcpyAsync(c->sc + S_XZERO, c->h_one, sizeof(double), cudaMemcpyHostToDevice, c->s));
+            else
+                CUDA_TRY(cudaMemsetAsync(c->cg[5], 0, c->L[0].d.n * sizeof(T), c->s));
+        }
     }
     c->run.thresh = rtol * rtol * r0sq;
     c->run.max_iter = max_iter;
@@ -1065,8 +1074,8 @@ RedArgs red_irres(fld_ctx* c, int ks) {
 void scale_rhs_enqueue(fld_ctx* c) {
     const long long n = c->L[0].d.n;
     c->ks = exp_above(c->h_sc[S_RMAX]);
-    KScope k(c, K_IR_SCALE, 16.0 * n);
-    launch_ir_scale_b(n, c->b, c->ks, (float*)c->cg[0], (float*)c->cg[5], red_irres(c, c->ks), c->s);
+    KScope k(c, K_IR_SCALE, 12.0 * n);
+    launch_ir_scale_b(n, c->b, c->ks, (float*)c->cg[0], red_irres(c, c->ks), c->s);
 }
 
 // x64 += 2^ks (x32 + alpha p_last) after an inner solve (x64 = ... after
@@ -1087,11 +1096,14 @@ int next_scale(fld_ctx* c) {
     return rr > 0.0 && std::isfinite(rr) ? c->ks + exp_above(std::sqrt(rr)) : c->ks - 30;
 }
 
-void residual_enqueue(fld_ctx* c, int ks) {
+// The refinement residual with the scale 2^ks; write: also the next inner
+// solve's right-hand side r32 (else only its norms, for a residual that is
+// expected to meet the tolerance).
+void residual_enqueue(fld_ctx* c, int ks, bool write) {
     Level& L0 = c->L[0];
-    KScope k(c, K_IR_RESID, 56.0 * L0.d.n);
-    launch_ir_residual(L0.d, L0.A32, L0.Alo, c->b, c->dE, ks, (float*)c->cg[0], (float*)c->cg[5],
-                       red_irres(c, ks), c->sc, c->pd.dt_exp, c->s);
+    KScope k(c, K_IR_RESID, (write ? 52.0 : 48.0) * L0.d.n);
+    launch_ir_residual(L0.d, L0.A32, L0.Alo, c->b, c->dE, ks, (float*)c->cg[0], write, red_irres(c, ks), c->sc,
+                       c->pd.dt_exp, c->s);
 }
 
 // After a residual launched with scale 2^ks has reported its largest entry:
@@ -1104,6 +1116,15 @@ int scale_fix(fld_ctx* c, int& ks, int attempt) {
     if (attempt >= 3) return nonfinite ? -1 : 0;
     ks += nonfinite ? 100 : exp_above(mx);
     return 1;
+}
+
+// Whether the refinement residual after the inner solve just done is
+// expected to meet the tolerance (with a factor 2 of margin): the inner
+// solve's final ||r32|| scaled by 2^ks against ||b||.  Its residual is then
+// launched for its norms only.
+bool expect_converged(fld_ctx* c, double bb, double rtol) {
+    const double rr = c->h_sc[S_RR];
+    return rr >= 0.0 && std::isfinite(rr) && bb > 0.0 && std::ldexp(std::sqrt(rr), c->ks) <= 0.5 * rtol * std::sqrt(bb);
 }
 
 // ||b - A x|| / ||b|| from the scaled residual's norm.
@@ -1159,9 +1180,10 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
             inner_total += it;
             update_enqueue(c, outer == 0);
             outer++;
+            const bool write = !expect_converged(c, bb, rtol);
             int ks = next_scale(c);
             for (int attempt = 0;; attempt++) {
-                residual_enqueue(c, ks);
+                residual_enqueue(c, ks, write);
                 if ((st = read_scalars(c))) return st;
                 const int fix = scale_fix(c, ks, attempt);
                 if (fix == 0) break;
@@ -1172,6 +1194,12 @@ fld_status solve_impl(fld_ctx* c, fld_info* info) {
             inf.rel_res = scaled_rel_res(c, bb);
             if (inf.rel_res <= rtol) { conv = true; break; }
             if (inner_total >= c->p.max_iter) break;
+            if (!write) {
+                // expected to converge and did not: the right-hand side of
+                // the next inner solve (same scale, same norms)
+                residual_enqueue(c, ks, true);
+                if ((st = read_scalars(c))) return st;
+            }
         }
         inf.iters = inner_total;
         inf.outer_iters = outer;
@@ -1557,6 +1585,7 @@ struct BItem {
     double bb;
     int inner_total, outer;
     int ks, attempt;     // mixed: scale of the residual in flight, relaunches
+    bool write;          // mixed: the residual in flight writes the next right-hand side
     int whole;           // the inner solve in flight runs whole on the device:
                          // 0 no (one round per iteration), 1 persistent
                          // kernel, 2 device-side loop graph
@@ -1705,9 +1734,10 @@ void batch_after(BItem& b) {
             b.inner_total += c->run.k;
             update_enqueue(c, b.outer == 0);
             b.outer++;
+            b.write = !expect_converged(c, b.bb, rtol);
             b.ks = next_scale(c);
             b.attempt = 0;
-            residual_enqueue(c, b.ks);
+            residual_enqueue(c, b.ks, b.write);
             cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
             b.state = BS_RESID;
         }
@@ -1725,7 +1755,7 @@ void batch_after(BItem& b) {
             // residual reported
             b.attempt++;
             cudaMemsetAsync(c->sc + S_NONFINITE, 0, sizeof(double), c->s);
-            residual_enqueue(c, b.ks);
+            residual_enqueue(c, b.ks, b.write);
             cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
             return;
         }
@@ -1741,6 +1771,12 @@ void batch_after(BItem& b) {
             set_err(FLD_ENOCONV, "no convergence: relative residual %.3e > rtol %.3e after %d iterations",
                     b.inf.rel_res, rtol, b.inner_total);
             return bfail(b, FLD_ENOCONV);
+        } else if (!b.write) {
+            // expected to converge and did not: the same residual again,
+            // now writing the next inner solve's right-hand side
+            b.write = true;
+            residual_enqueue(c, b.ks, true);
+            cudaMemcpyAsync(c->h_sc, c->sc, NUM_SLOTS * sizeof(double), cudaMemcpyDeviceToHost, c->s);
         } else {
             // the residual kernel left the next inner solve's scaled
             // right-hand side and its norm: straight to the inner solve
@@ -1810,6 +1846,7 @@ fld_status step_batched_impl(int n, fld_ctx** cs, double** E, const double** nHI
         b.bb = 0.0;
         b.inner_total = b.outer = 0;
         b.whole = 0;
+        b.write = true;
         b.conv = false;
         b.state = BS_ASM;
         cudaEventRecord(b.c->e0, b.c->s);

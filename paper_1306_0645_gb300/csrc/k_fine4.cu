@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
                                                       float* __restrict__ x, RedArgs ra, int pf) {
     const float beta = (float)ra.sc[S_BETA];
     const float alpha_prev = x ? (float)ra.sc[S_ALPHA] : 0.0f;
+    // the first iteration of a solve starts x at 0 instead of updating it
+    const bool x_zero = x && ra.sc[S_XZERO] != 0.0;
     const Walk w = walk_of(d);
     DotAcc<float> da;
     auto P = [&](long long i) {
@@ -190,7 +192,9 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
             if (w.valid) {
                 st4(p_out, g.c, pc);
                 st4(q, g.c, qv);
-                if (x) {
+                if (x_zero) {
+                    st4(x, g.c, make_float4(0.f, 0.f, 0.f, 0.f));
+                } else if (x) {
                     // p_in of this plane was read one plane ago (L1)
                     const float4 pv = ld4(p_in, g.c);
                     float4 xv = ld4(x, g.c);

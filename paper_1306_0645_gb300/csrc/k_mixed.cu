@@ -478,17 +478,15 @@ __global__ void __launch_bounds__(256) k_asm_rhs_mx(Dims d, PhysDev p, const dou
 // -------------------------------------------------------------- refinement
 
 // The first refinement's right-hand side, r = b (x = 0): r32 = b * 2^-Ks
-// rounded to FP32, x32 = 0, ||r32||^2 and max |r32| (reduction R_IRRES with
-// aux = 2^Ks).
+// rounded to FP32, ||r32||^2 and max |r32| (reduction R_IRRES with aux =
+// 2^Ks).  The inner solve starts its x32 at 0 itself.
 __global__ void __launch_bounds__(RED_THREADS) k_ir_scale_b(long long n, const double* __restrict__ b, int Ks,
-                                                           float* __restrict__ r32, float* __restrict__ x32,
-                                                           RedArgs ra) {
+                                                           float* __restrict__ r32, RedArgs ra) {
     DotAcc<float> da;
     float mx = 0.0f;
     GRID_LOOP(c, n) {
         const float v = round64(b[c], Ks);
         r32[c] = v;
-        x32[c] = 0.0f;
         da.add(v, v);
         mx = fmaxf(mx, fabsf(v));
     }
@@ -522,12 +520,14 @@ __global__ void k_ir_update_mx(long long n, float2* __restrict__ x, const float*
 }
 
 // Refinement residual r = b - m x - sum_f w_f (x - x_nbr) of the df iterate
-// x: r32 = r * 2^-Ks rounded to FP32 (the next inner solve's right-hand
-// side), x32 = 0, ||r32||^2 and max |r32| (reduction R_IRRES).
+// x: ||r32||^2 and max |r32| of r32 = r * 2^-Ks rounded to FP32 (reduction
+// R_IRRES) and, with WRITE, r32 itself (the next inner solve's right-hand
+// side; without it the launch only measures the residual).
+template <bool WRITE>
 __global__ void __launch_bounds__(256) k_ir_residual(Dims d, Op<float> A, Op<float> L,
                                                     const double* __restrict__ b, const float2* __restrict__ x,
-                                                    int Ks, float* __restrict__ r32, float* __restrict__ x32,
-                                                    RedArgs ra, const double* scg, int dt_exp) {
+                                                    int Ks, float* __restrict__ r32, RedArgs ra, const double* scg,
+                                                    int dt_exp) {
     const int K = step_scale(scg, dt_exp);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -570,8 +570,7 @@ __global__ void __launch_bounds__(256) k_ir_residual(Dims d, Op<float> A, Op<flo
         R.add(split64(b[c], K));
         R.addmul({-A.m[c], -L.m[c]}, xc);
         const float v = ldexp2(R.value().h, K - Ks);
-        r32[c] = v;
-        x32[c] = 0.0f;
+        if (WRITE) r32[c] = v;
         da.add(v, v);
         mx = fmaxf(mx, fabsf(v));
     }
@@ -751,9 +750,9 @@ void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const d
         k_asm_rhs_mx<false, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
 }
 
-void launch_ir_scale_b(long long n, const double* b, int Ks, float* r32, float* x32, const RedArgs& ra,
+void launch_ir_scale_b(long long n, const double* b, int Ks, float* r32, const RedArgs& ra,
                        cudaStream_t s) {
-    k_ir_scale_b<<<red_blocks(n), RED_THREADS, 0, s>>>(n, b, Ks, r32, x32, ra);
+    k_ir_scale_b<<<red_blocks(n), RED_THREADS, 0, s>>>(n, b, Ks, r32, ra);
 }
 
 void launch_ir_update_mx(long long n, void* x, const float* x32, const double* sc, bool assign, int ks,
@@ -774,9 +773,12 @@ ColShape ir_residual_shape(const Dims& d) {
 }
 
 void launch_ir_residual(const Dims& d, Op<float> A, Op<float> L, const double* b, const void* x, int Ks,
-                        float* r32, float* x32, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s) {
+                        float* r32, bool write, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s) {
     const ColShape sh = ir_residual_shape(d);
-    k_ir_residual<<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, x32, ra, scg, dt_exp);
+    if (write)
+        k_ir_residual<true><<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, ra, scg, dt_exp);
+    else
+        k_ir_residual<false><<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, ra, scg, dt_exp);
 }
 
 void launch_finalize_mx(long long n, const PhysDev& p, const double* E, const void* dE, const double* nHI,

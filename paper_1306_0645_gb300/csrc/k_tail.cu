@@ -471,7 +471,8 @@ __device__ void ps_solve(const PsReq& R, cg::cluster_group& cl, unsigned char* s
         // x += alpha p, r -= alpha q, ||r||^2
         DotAcc<float> arr;
         for (int c = tid; c < n; c += nth) {
-            x[c] = fmaf(af, __ldcg(p + c), __ldcg(x + c));
+            // x starts at 0 (the caller's x32 is not cleared)
+            x[c] = k == 0 ? af * __ldcg(p + c) : fmaf(af, __ldcg(p + c), __ldcg(x + c));
             const float rn = fmaf(-af, __ldcg(q + c), __ldcg(r + c));
             r[c] = rn;
             arr.add(rn, rn);

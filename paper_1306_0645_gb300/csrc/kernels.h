@@ -134,9 +134,8 @@ void launch_asm_fix_mx(const Dims& d, const PhysDev& p, const double* E, const d
 void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, const double* eta,
                        Op<float> A, Op<float> L, double* b, Bnd bnd, const RedArgs& ra, const double* scg,
                        cudaStream_t s, int zb0 = 0, int nzb = -1);
-// r32 = b 2^-ks (nearest float), x32 = 0; ||r32||^2, max |r32| (R_IRRES).
-void launch_ir_scale_b(long long n, const double* b, int ks, float* r32, float* x32, const RedArgs& ra,
-                       cudaStream_t s);
+// r32 = b 2^-ks (nearest float); ||r32||^2, max |r32| (R_IRRES).
+void launch_ir_scale_b(long long n, const double* b, int ks, float* r32, const RedArgs& ra, cudaStream_t s);
 // The refinement unknown x (dE) of the mixed solver is a df pair per cell
 // (float2), scaled by 2^-K with K the step's scale exponent (from the
 // maxima in scg, the context's slots).
@@ -144,10 +143,10 @@ void launch_ir_scale_b(long long n, const double* b, int ks, float* r32, float* 
 // the last CG iteration's update, x32 + sc[S_ALPHA] p_last in FP32 is used
 void launch_ir_update_mx(long long n, void* x, const float* x32, const double* sc, bool assign, int ks,
                          const float* p_last, const double* scg, int dt_exp, cudaStream_t s);
-// r = b - m x - sum_f w_f (x - x_nbr) in df; r32 = r 2^-ks (nearest float),
-// x32 = 0; ||r32||^2, max |r32| (R_IRRES).
+// r = b - m x - sum_f w_f (x - x_nbr) in df; ||r32||^2, max |r32| of r32 =
+// r 2^-ks (nearest float) (R_IRRES), r32 itself only with write.
 void launch_ir_residual(const Dims& d, Op<float> A, Op<float> L, const double* b, const void* x, int ks,
-                        float* r32, float* x32, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s);
+                        float* r32, bool write, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s);
 ColShape ir_residual_shape(const Dims& d);
 // E_out = max(E + dE, 0) and the photon-balance sums as launch_finalize,
 // summed in df relative to the scales of the maxima in scg; dE the df x.
