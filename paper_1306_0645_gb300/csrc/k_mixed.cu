@@ -599,8 +599,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize_mx(long long n, PhysDe
     Acc2 sd, sq, sn, st;
     DotAcc<float> s2d, s2e;
     double floor_e = 0.0;
-    // four cells per thread and pass, their loads issued together
-    constexpr int U = 4;
+    // two cells per thread and pass, their loads issued together (four
+    // needed 78 registers and three blocks per SM: 1.04 against 1.00 ms per
+    // 512^3 step)
+    constexpr int U = 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long c0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; c0 < n; c0 += U * stride) {
         float2 dv[U];
