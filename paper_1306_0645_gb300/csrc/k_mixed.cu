@@ -23,6 +23,7 @@
 // of order 2^-47 (|b| + m |x| + sum_f w_f |x - x_nbr|), and the refinement
 // converges as an FP64 one would.
 #include "limiter.cuh"
+#include "walk4.cuh"
 
 namespace fld {
 
@@ -579,6 +580,166 @@ __global__ void __launch_bounds__(256) k_ir_residual(Dims d, Op<float> A, Op<flo
     grid_reduce<2>(acc, ismax, ra);
 }
 
+// Four consecutive cells of a df array (c a multiple of 4: 32-byte aligned).
+__device__ __forceinline__ void ld_df4(const float2* __restrict__ u, long long c, df v[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(u + c);
+    const float4 e = *reinterpret_cast<const float4*>(u + c + 2);
+    v[0] = {a.x, a.y};
+    v[1] = {a.z, a.w};
+    v[2] = {e.x, e.y};
+    v[3] = {e.z, e.w};
+}
+// Four consecutive df weights from their high and low arrays.
+__device__ __forceinline__ void ld_w4(const float* __restrict__ h, const float* __restrict__ l, long long c,
+                                      df w[4]) {
+    const float4 a = ld4(h, c), e = ld4(l, c);
+    w[0] = {a.x, e.x};
+    w[1] = {a.y, e.y};
+    w[2] = {a.z, e.z};
+    w[3] = {a.w, e.w};
+}
+
+// k_ir_residual for levels whose x extent is a multiple of 4 (at least 16):
+// a thread owns four consecutive cells of a row (walk4.cuh) and walks its
+// chunk of planes.  Every flux is the same df operation as in FluxWalk and
+// every cell sums its terms in the same order (x lo, x hi, y lo, y hi,
+// z lo, z hi, b, -m x), so r32 equals k_ir_residual's bit for bit: the
+// x-lower flux of a cell, negated, is its left neighbour's x-upper flux
+// (within the thread, or from the next lane for the last cell), the
+// z-upper flux of a plane is the next plane's z-lower one, and a missing
+// face (a zero-gradient boundary) is the flux of a cell with itself, 0.
+// Vector loads and one address computation per four cells take about half
+// the instructions of the one-cell form, whose issue rate bounds it.
+template <bool WRITE>
+__global__ void __launch_bounds__(256, 2) k_ir_residual4(Dims d, Op<float> A, Op<float> L,
+                                                      const double* __restrict__ b,
+                                                      const float2* __restrict__ x, int Ks,
+                                                      float* __restrict__ r32, RedArgs ra, const double* scg,
+                                                      int dt_exp) {
+    const int K = step_scale(scg, dt_exp);
+    // the lanes of this warp (a block of fewer than 32 threads has fewer)
+    const unsigned wm = __activemask();
+    const Walk w = walk_of(d);
+    DotAcc<float> da;
+    float mx = 0.0f;
+    if (w.k0 < w.k1) {
+        Geo g = geo_of(d, w, w.k0);
+        df xc[4], fz[4];
+        ld_df4(x, g.c, xc);
+        {
+            // the z-lower fluxes of the chunk's first plane
+            df xd[4], wd[4];
+            ld_df4(x, g.c + zdn(d, w.k0, w.nxy), xd);
+            ld_w4(A.wz, L.wz, g.c, wd);
+#pragma unroll
+            for (int e = 0; e < 4; e++) fz[e] = df_mul_raw(wd[e], df_sub(xd[e], xc[e]));
+        }
+        for (int k = w.k0; k < w.k1; k++) {
+            if (k > w.k0) g = geo_of(d, w, k);
+            if (PF_PLANES > 0 && k + PF_PLANES < w.k1) {
+                const long long cp = g.c + PF_PLANES * w.nxy;
+                pfl2(b + cp);
+                pfl2(x + cp);
+                pfl2(A.m + cp);
+                pfl2(L.m + cp);
+                pfl2(A.wx + cp);
+                pfl2(L.wx + cp);
+                pfl2(A.wy + cp);
+                pfl2(L.wy + cp);
+                pfl2(A.wz + cp);
+                pfl2(L.wz + cp);
+            }
+            Acc2 R[4];
+            // x faces: lower fluxes of the four cells, the last cell's upper
+            {
+                df wx[4];
+                ld_w4(A.wx, L.wx, g.c, wx);
+                const float lh = __shfl_up_sync(wm, xc[3].h, 1);
+                const float ll = __shfl_up_sync(wm, xc[3].l, 1);
+                df xl = {lh, ll};
+                if (g.load_l) {
+                    const float2 v = x[g.xl];
+                    xl = {v.x, v.y};
+                }
+                df fl[4];
+                fl[0] = df_mul_raw(wx[0], df_sub(xl, xc[0]));
+#pragma unroll
+                for (int e = 1; e < 4; e++) fl[e] = df_mul_raw(wx[e], df_sub(xc[e - 1], xc[e]));
+                const float nh = __shfl_down_sync(wm, fl[0].h, 1);
+                const float nl = __shfl_down_sync(wm, fl[0].l, 1);
+                df fu3 = {-nh, -nl};
+                if (g.load_r) {
+                    const float2 v = x[g.xr];
+                    fu3 = df_mul_raw({A.wx[g.xr_w], L.wx[g.xr_w]}, df_sub({v.x, v.y}, xc[3]));
+                }
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    R[e].add(fl[e]);
+                    R[e].add(e < 3 ? df_neg(fl[e + 1]) : fu3);
+                }
+            }
+            // y faces (the upper face's weight is the lower weight of the row above)
+            {
+                df xm[4], wl[4];
+                ld_df4(x, g.ym, xm);
+                ld_w4(A.wy, L.wy, g.c, wl);
+#pragma unroll
+                for (int e = 0; e < 4; e++) R[e].add(df_mul_raw(wl[e], df_sub(xm[e], xc[e])));
+            }
+            {
+                df xp[4], wu[4];
+                ld_df4(x, g.yp, xp);
+                ld_w4(A.wy, L.wy, g.yp, wu);
+#pragma unroll
+                for (int e = 0; e < 4; e++) R[e].add(df_mul_raw(wu[e], df_sub(xp[e], xc[e])));
+            }
+            // z faces: the carried lower flux, the upper one formed here
+            df xu[4];
+            {
+                df wu[4];
+                const long long up = zup(d, k, w.nxy);
+                ld_df4(x, g.c + up, xu);
+                ld_w4(A.wz, L.wz, g.c + up, wu);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    R[e].add(fz[e]);
+                    const df f = df_mul_raw(wu[e], df_sub(xu[e], xc[e]));
+                    R[e].add(f);
+                    fz[e] = df_neg(f);
+                }
+            }
+            // b - m x
+            {
+                const double2 b01 = *reinterpret_cast<const double2*>(b + g.c);
+                const double2 b23 = *reinterpret_cast<const double2*>(b + g.c + 2);
+                const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+                const float4 mh = ld4(A.m, g.c), ml = ld4(L.m, g.c);
+                const float mhv[4] = {mh.x, mh.y, mh.z, mh.w}, mlv[4] = {ml.x, ml.y, ml.z, ml.w};
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    R[e].add(split64(bv[e], K));
+                    R[e].addmul({-mhv[e], -mlv[e]}, xc[e]);
+                    v[e] = ldexp2(R[e].value().h, K - Ks);
+                }
+                if (w.valid) {
+                    if (WRITE) st4(r32, g.c, make_float4(v[0], v[1], v[2], v[3]));
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        da.add(v[e], v[e]);
+                        mx = fmaxf(mx, fabsf(v[e]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) xc[e] = xu[e];
+        }
+    }
+    double acc[2] = {da.value(), (double)mx};
+    const bool ismax[2] = {false, true};
+    grid_reduce<2>(acc, ismax, ra);
+}
+
 // ------------------------------------------------------------ finalisation
 
 // E_out = max(E + dE, 0) (FP64; dE the df iterate scaled by 2^-K) and the
@@ -774,8 +935,30 @@ ColShape ir_residual_shape(const Dims& d) {
     return col_shape(d, 256, (int)t);
 }
 
+// The four-cell form: 256 threads of four cells and about IR4_CELLS cells
+// per block (each thread walks IR4_CELLS / 1024 planes or more).
+constexpr long long IR4_CELLS = 16384;
+
+ColShape ir_residual4_shape(const Dims& d) {
+    Dims h = d;
+    h.nx = d.nx / 4;
+    long long t = d.n / IR4_CELLS;
+    if (t < 152 * 4) t = 152 * 4;
+    if (t > 152 * 64) t = 152 * 64;
+    return col_shape(h, 256, (int)t);
+}
+
 void launch_ir_residual(const Dims& d, Op<float> A, Op<float> L, const double* b, const void* x, int Ks,
                         float* r32, bool write, const RedArgs& ra, const double* scg, int dt_exp, cudaStream_t s) {
+    if (fine4_ok(d)) {
+        const ColShape sh = ir_residual4_shape(d);
+        if (write)
+            k_ir_residual4<true><<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, ra, scg, dt_exp);
+        else
+            k_ir_residual4<false><<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, ra, scg,
+                                                               dt_exp);
+        return;
+    }
     const ColShape sh = ir_residual_shape(d);
     if (write)
         k_ir_residual<true><<<sh.grid, sh.block, 0, s>>>(d, A, L, b, (const float2*)x, Ks, r32, ra, scg, dt_exp);
