@@ -476,6 +476,202 @@ __global__ void __launch_bounds__(256) k_asm_rhs_mx(Dims d, PhysDev p, const dou
     grid_reduce<2>(acc, ismax, ra);
 }
 
+// Four consecutive doubles (c a multiple of 4: 32-byte aligned).
+__device__ __forceinline__ void ld_d4(const double* __restrict__ u, long long c, double v[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(u + c);
+    const double2 e = *reinterpret_cast<const double2*>(u + c + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = e.x;
+    v[3] = e.y;
+}
+// Four consecutive df weights from their high and low arrays.
+__device__ __forceinline__ void ld_w4(const float* __restrict__ h, const float* __restrict__ l, long long c,
+                                      df w[4]) {
+    const float4 a = ld4(h, c), e = ld4(l, c);
+    w[0] = {a.x, e.x};
+    w[1] = {a.y, e.y};
+    w[2] = {a.z, e.z};
+    w[3] = {a.w, e.w};
+}
+
+// k_asm_rhs_mx without Dirichlet faces, for levels whose x extent is a
+// multiple of 4 (at least 16): a thread owns four consecutive cells of a row
+// (walk4.cuh) and walks a part of one z-block of the assembly decomposition
+// (blockIdx.z = z-block * zs + part).  Every flux is FluxWalk's df operation
+// and every cell adds its terms in FluxWalk's order, as do the FP32
+// diagonal's weights, so b and invd equal k_asm_rhs_mx's bit for bit (only
+// the order of the sums of ||b||^2 differs).  The x-lower flux of a cell,
+// negated, is its left neighbour's x-upper flux; a missing face (a
+// zero-gradient boundary) is the flux of a cell with itself, 0, and adds a
+// zero weight.
+template <bool BE>
+__global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const double* __restrict__ E,
+                                                     const double* __restrict__ nHI,
+                                                     const double* __restrict__ eta, Op<float> A, Op<float> L,
+                                                     double* __restrict__ b, RedArgs ra, const double* scg,
+                                                     int zb0, int kch, int zs) {
+    const int K = step_scale(scg, p.dt_exp);
+    const unsigned wm = __activemask();
+    Walk w = walk_of(d);
+    {
+        const int zb = zb0 + (int)blockIdx.z / zs;
+        const int part = (kch + zs - 1) / zs;
+        w.k0 = zb * kch + ((int)blockIdx.z % zs) * part;
+        w.k1 = min(min(d.nz, (zb + 1) * kch), w.k0 + part);
+    }
+    double bb = 0.0;
+    float bmax = 0.0f;
+    if (w.k0 < w.k1) {
+        Geo g = geo_of(d, w, w.k0);
+        double ec[4];
+        ld_d4(E, g.c, ec);
+        df fz[4];
+        float wzc[4];
+        {
+            // the z-lower fluxes and weights of the part's first plane
+            double ed[4];
+            df wd[4];
+            ld_d4(E, g.c + zdn(d, w.k0, w.nxy), ed);
+            ld_w4(A.wz, L.wz, g.c, wd);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                fz[e] = df_mul_raw(wd[e], split64(ed[e] - ec[e], K));
+                wzc[e] = wd[e].h;
+            }
+        }
+        for (int k = w.k0; k < w.k1; k++) {
+            if (k > w.k0) g = geo_of(d, w, k);
+            if (PF_PLANES > 0 && k + PF_PLANES < w.k1) {
+                const long long cp = g.c + PF_PLANES * w.nxy;
+                pfl2(E + cp);
+                pfl2(nHI + cp);
+                pfl2(eta + cp);
+                pfl2(A.wx + cp);
+                pfl2(L.wx + cp);
+                pfl2(A.wy + cp);
+                pfl2(L.wy + cp);
+                pfl2(A.wz + cp);
+                pfl2(L.wz + cp);
+                pfl2(A.m + cp);
+            }
+            Acc2 F[4];
+            float ws[4];
+            // x faces
+            {
+                df wx[4];
+                ld_w4(A.wx, L.wx, g.c, wx);
+                const double el_sh = __shfl_up_sync(wm, ec[3], 1);
+                const double el = g.load_l ? E[g.xl] : el_sh;
+                df fl[4];
+                fl[0] = df_mul_raw(wx[0], split64(el - ec[0], K));
+#pragma unroll
+                for (int e = 1; e < 4; e++) fl[e] = df_mul_raw(wx[e], split64(ec[e - 1] - ec[e], K));
+                const float nh = __shfl_down_sync(wm, fl[0].h, 1);
+                const float nl = __shfl_down_sync(wm, fl[0].l, 1);
+                const float nw = __shfl_down_sync(wm, wx[0].h, 1);
+                df fu3 = {-nh, -nl};
+                float wu3 = nw;
+                if (g.load_r) {
+                    const float wh = A.wx[g.xr_w];
+                    fu3 = df_mul_raw({wh, L.wx[g.xr_w]}, split64(E[g.xr] - ec[3], K));
+                    wu3 = wh;
+                }
+                if (!g.has_xr) wu3 = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    F[e].add(fl[e]);
+                    F[e].add(e < 3 ? df_neg(fl[e + 1]) : fu3);
+                    ws[e] = wx[e].h;
+                    ws[e] += e < 3 ? wx[e + 1].h : wu3;
+                }
+            }
+            // y faces (the upper face's weight is the lower weight of the row above)
+            {
+                double em[4];
+                df wl[4];
+                ld_d4(E, g.ym, em);
+                ld_w4(A.wy, L.wy, g.c, wl);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    F[e].add(df_mul_raw(wl[e], split64(em[e] - ec[e], K)));
+                    ws[e] += wl[e].h;
+                }
+            }
+            {
+                double ep[4];
+                df wu[4];
+                ld_d4(E, g.yp, ep);
+                ld_w4(A.wy, L.wy, g.yp, wu);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    F[e].add(df_mul_raw(wu[e], split64(ep[e] - ec[e], K)));
+                    ws[e] += g.has_yp ? wu[e].h : 0.0f;
+                }
+            }
+            // z faces: the carried lower flux, the upper one formed here
+            double eu[4];
+            {
+                const long long up = zup(d, k, w.nxy);
+                const bool has_zu = k < d.nz - 1 || d.pz;
+                df wu[4];
+                ld_d4(E, g.c + up, eu);
+                ld_w4(A.wz, L.wz, g.c + up, wu);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    F[e].add(fz[e]);
+                    const df f = df_mul_raw(wu[e], split64(eu[e] - ec[e], K));
+                    F[e].add(f);
+                    fz[e] = df_neg(f);
+                    ws[e] += wzc[e];
+                    ws[e] += has_zu ? wu[e].h : 0.0f;
+                    wzc[e] = wu[e].h;
+                }
+            }
+            // b = dt eta - dt (c sigma n_HI + adot/a) E + flux / theta
+            {
+                double nc[4], qc[4];
+                ld_d4(nHI, g.c, nc);
+                ld_d4(eta, g.c, qc);
+                const float4 m4 = ld4(A.m, g.c);
+                const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+                double bo[4];
+                float iv[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    Acc2 B;
+                    B.add(df_mul_raw(split64(qc[e], K - p.dt_exp), p.dtm_d));
+                    const df loss = df_add(df_mul(p.dtcs_d, split64(nc[e], 0)), p.dta_d);
+                    B.submul(loss, split64(ec[e], K));
+                    if (BE) {
+                        B.add(F[e].s);
+                        B.c = __fadd_rn(B.c, F[e].c);
+                    } else {
+                        B.add(df_mul_raw(F[e].value(), p.ith_d));
+                    }
+                    const df bd = B.value();
+                    bo[e] = df2d(bd, K);
+                    iv[e] = 1.0f / (mv[e] + ws[e]);
+                    if (w.valid) {
+                        bb = fma(bo[e], bo[e], bb);
+                        bmax = fmaxf(bmax, fabsf(bd.h));
+                    }
+                }
+                if (w.valid) {
+                    *reinterpret_cast<double2*>(b + g.c) = make_double2(bo[0], bo[1]);
+                    *reinterpret_cast<double2*>(b + g.c + 2) = make_double2(bo[2], bo[3]);
+                    st4(A.invd, g.c, make_float4(iv[0], iv[1], iv[2], iv[3]));
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) ec[e] = eu[e];
+        }
+    }
+    double acc[2] = {bb, f2d(bmax, K)};
+    const bool ismax[2] = {false, true};
+    grid_reduce<2>(acc, ismax, ra);
+}
+
 // -------------------------------------------------------------- refinement
 
 // The first refinement's right-hand side, r = b (x = 0): r32 = b * 2^-Ks
@@ -588,15 +784,6 @@ __device__ __forceinline__ void ld_df4(const float2* __restrict__ u, long long c
     v[1] = {a.z, a.w};
     v[2] = {e.x, e.y};
     v[3] = {e.z, e.w};
-}
-// Four consecutive df weights from their high and low arrays.
-__device__ __forceinline__ void ld_w4(const float* __restrict__ h, const float* __restrict__ l, long long c,
-                                      df w[4]) {
-    const float4 a = ld4(h, c), e = ld4(l, c);
-    w[0] = {a.x, e.x};
-    w[1] = {a.y, e.y};
-    w[2] = {a.z, e.z};
-    w[3] = {a.w, e.w};
 }
 
 // k_ir_residual for levels whose x extent is a multiple of 4 (at least 16):
@@ -901,8 +1088,23 @@ void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const d
     const AsmShape a = asm_shape(d);
     if (nzb < 0 || zb0 + nzb > a.nzb) nzb = a.nzb - zb0;
     if (nzb <= 0) return;
-    const dim3 g(a.sh.grid.x, a.sh.grid.y, (unsigned)nzb);
     const bool be = p.theta == 1.0, dir = p.dmask != 0;
+    if (!dir && fine4_ok(d)) {
+        // four cells per thread; each z-block in parts of about 32 planes
+        Dims h = d;
+        h.nx = d.nx / 4;
+        const ColShape sh = col_shape(h, 256, 1);
+        const long long xy = (long long)sh.grid.x * sh.grid.y;
+        int zs = (a.kch + 31) / 32;
+        while (zs > 1 && xy * nzb * zs > RED_MAX_BLOCKS) zs--;
+        const dim3 g4(sh.grid.x, sh.grid.y, (unsigned)(nzb * zs));
+        if (be)
+            k_asm_rhs4_mx<true><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs);
+        else
+            k_asm_rhs4_mx<false><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs);
+        return;
+    }
+    const dim3 g(a.sh.grid.x, a.sh.grid.y, (unsigned)nzb);
     if (be && !dir)
         k_asm_rhs_mx<true, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
     else if (be)
