@@ -161,6 +161,19 @@ typedef struct {
                                   solves of all such contexts in flight into
                                   one launch over a work list.  0 = never
                                   (default 0), at most 2^24 */
+    int precond_bf16;          /* mixed precision, red/black Gauss-Seidel with
+                                  one pre-sweep: 1 (default) the V-cycle
+                                  smooths the fine level with its
+                                  coefficients (face weights and inverse
+                                  diagonal) stored as bfloat16, rounded from
+                                  the FP32 operator, which halves their bytes
+                                  in the smoothing and residual sweeps; the
+                                  cycle stays symmetric, and the CG operator,
+                                  the FP64 refinement residual and the
+                                  stopping rule are unchanged, so only the
+                                  preconditioner differs (by relative
+                                  perturbations of its coefficients below
+                                  2^-8).  0: FP32 coefficients */
 } fld_params;
 
 /* Result of one solve or step (host memory, filled on return). */

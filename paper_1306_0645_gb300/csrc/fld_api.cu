@@ -51,6 +51,8 @@ struct Level {
     Op<double> A64;
     Op<float> A32;
     Op<float> Alo;     // mixed fine level: low parts of m and w (df with A32)
+    Op<unsigned short> Abf;   // mixed fine level: bfloat16 copies of wx, wy, wz, invd for
+                              // the V-cycle's sweeps (fld_params.precond_bf16), else null
     Bnd bnd;           // Dirichlet face weights (FP64)
     void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
     Tune tune[NTUNE];
@@ -158,6 +160,7 @@ fld_status validate(const fld_grid* g, const fld_params* p) {
     if (p->paper_order != 0 && p->paper_order != 1) return set_err(FLD_EINVAL, "paper_order must be 0 or 1");
     if (p->persistent_cells < 0 || p->persistent_cells > (1 << 24))
         return set_err(FLD_EINVAL, "persistent_cells must lie in [0, 2^24]");
+    if (p->precond_bf16 != 0 && p->precond_bf16 != 1) return set_err(FLD_EINVAL, "precond_bf16 must be 0 or 1");
     int dims[MAX_LEVELS][3];
     int nl = level_shapes(g, dims);
     long long nc = (long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2];
@@ -223,6 +226,18 @@ bool ps_wanted(const fld_params* p, size_t n0, int nl) {
            n0 <= (size_t)p->persistent_cells && nl >= 2 && nl <= TAIL_MAX_LEVELS;
 }
 
+// Whether the fine level's V-cycle sweeps read bfloat16 copies of its
+// coefficients (fld_params.precond_bf16): mixed precision, red/black
+// Gauss-Seidel with one pre-sweep (the zero-guess residual, which needs no
+// m) and separate colour sweeps, four-cell sweeps on a fine level that
+// lies above the coarsest level and outside the persistent coarse tail, and
+// inner solves launched kernel by kernel.
+bool bf16_wanted(const fld_params* p, int nx, size_t n0, int nl) {
+    return p->precision == FLD_PREC_MIXED && p->precond_bf16 == 1 && p->smoother == FLD_SMOOTH_RBGS &&
+           p->pre == 1 && p->fused_post == 0 && nl >= 2 && nx % 4 == 0 && nx >= 16 &&
+           !(p->tail_cells > 0 && n0 <= (size_t)p->tail_cells) && !ps_wanted(p, n0, nl);
+}
+
 // Enumerates every device buffer a context needs, in a fixed order; the
 // same walk sizes the footprint and performs the allocation.
 template <class F>
@@ -244,6 +259,8 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
             for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
         if (mixed && l == 0)
             for (int q = 0; q < 4; q++) buf(l, "Alo", q, n * sizeof(float));
+        if (l == 0 && bf16_wanted(p, g->nx, n, nl))
+            for (int q = 0; q < 4; q++) buf(l, "Abf", q, n * sizeof(unsigned short));
         if (l > 0) {
             buf(l, "vec", 0, n * ts);
             buf(l, "vec", 1, n * ts);
@@ -544,15 +561,27 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     Op<T> A = op_of<T>(L);
     T* t = (T*)L.t;
     const fld_params& p = c->p;
+    // the fine level of a mixed context may sweep with bfloat16 copies of
+    // its coefficients (allocated only where bf16_wanted holds): half the
+    // bytes of the face weights and the inverse diagonal
+    const bool bf = std::is_same<T, float>::value && L.Abf.wx != nullptr;
+    const double cw = bf ? 0.5 : 1.0;
     if (p.smoother == FLD_SMOOTH_RBGS) {
         if (p.pre >= 1) {
-            { KScope k(c, kc(K_SMOOTH_ZERO), 6.0 * n * ts); smooth_zero_any<T>(L.d, A, r, z, s, L.tune[TN_SMOOTH0]); }
-            for (int it = 1; it < p.pre; it++)
-                for (int colour = 0; colour < 2; colour++) {
-                    KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
-                    rb_colour_any<T>(L.d, A, r, z, colour, s, L.tune[TN_RB]);
-                }
-        } else {
+            KScope k(c, kc(K_SMOOTH_ZERO), (2.0 + 4.0 * cw) * n * ts);
+            if constexpr (std::is_same<T, float>::value) {
+                if (bf) launch_smooth_zero4(L.d, L.Abf, r, z, s, L.tune[TN_SMOOTH0]);
+                else smooth_zero_any<T>(L.d, A, r, z, s, L.tune[TN_SMOOTH0]);
+            } else {
+                smooth_zero_any<T>(L.d, A, r, z, s, L.tune[TN_SMOOTH0]);
+            }
+        }
+        for (int it = 1; it < p.pre; it++)
+            for (int colour = 0; colour < 2; colour++) {
+                KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
+                rb_colour_any<T>(L.d, A, r, z, colour, s, L.tune[TN_RB]);
+            }
+        if (p.pre < 1) {
             cudaMemsetAsync(z, 0, L.d.n * sizeof(T), s);
         }
     } else {
@@ -574,8 +603,15 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     const bool zg = p.smoother == FLD_SMOOTH_RBGS && p.pre == 1 && std::is_same<T, float>::value &&
                     fine4_ok(L.d);
     const bool cmp = zg && red_compress_ok(L.d);
-    { KScope k(c, kc(K_RESIDUAL), (cmp ? 4.5 : (zg ? 5.0 : 7.0)) * n * ts);
-      residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg, cmp); }
+    {
+        KScope k(c, kc(K_RESIDUAL), (cmp ? 1.5 + 3.0 * cw : (zg ? 2.0 + 3.0 * cw : 7.0)) * n * ts);
+        if constexpr (std::is_same<T, float>::value) {
+            if (bf) launch_residual4(L.d, L.Abf, z, t, s, L.tune[TN_RES], cmp);
+            else residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg, cmp);
+        } else {
+            residual_any<T>(L.d, A, r, z, t, s, L.tune[TN_RES], zg, cmp);
+        }
+    }
     { KScope k(c, kc(K_RESTRICT), ((cmp ? 0.5 : 1.0) * n + nc) * ts);
       restrict_any<T>(L.d, C.d, t, (T*)C.r, s, L.tune[TN_RESTRICT], cmp); }
     vcycle<T>(c, l + 1, (const T*)C.r, (T*)C.z);
@@ -599,15 +635,19 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
             for (int q = 0; q < 2; q++) {
                 const int colour = q == 0 ? first : 1 - first;
                 const bool last = it == p.post - 1 && q == 1;
+                KScope k(c, kc(K_RB_COLOUR), (2.5 + 4.0 * cw) * n * ts);
                 if constexpr (std::is_same<T, float>::value) {
                     if (last && dot && use4<T>(L.d)) {
-                        KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
-                        launch_rb_colour4_dot(L.d, A, r, z, colour, *dot, s, L.tune[TN_RB]);
+                        if (bf) launch_rb_colour4_dot(L.d, L.Abf, r, z, colour, *dot, s, L.tune[TN_RB]);
+                        else launch_rb_colour4_dot(L.d, A, r, z, colour, *dot, s, L.tune[TN_RB]);
                         *dot_done = true;
                         continue;
                     }
+                    if (bf) {
+                        launch_rb_colour4(L.d, L.Abf, r, z, colour, s, L.tune[TN_RB]);
+                        continue;
+                    }
                 }
-                KScope k(c, kc(K_RB_COLOUR), 6.5 * n * ts);
                 rb_colour_any<T>(L.d, A, r, z, colour, s, L.tune[TN_RB]);
             }
         } else {
@@ -1010,6 +1050,10 @@ fld_status alloc_ctx(fld_ctx* c) {
             float* f = (float*)ptr;
             if (q == 0) L.A32.m = f; else if (q == 1) L.A32.wx = f; else if (q == 2) L.A32.wy = f;
             else if (q == 3) L.A32.wz = f; else L.A32.invd = f;
+        } else if (!strcmp(kind, "Abf")) {
+            unsigned short* h = (unsigned short*)ptr;
+            if (q == 0) L.Abf.wx = h; else if (q == 1) L.Abf.wy = h; else if (q == 2) L.Abf.wz = h;
+            else L.Abf.invd = h;
         } else if (!strcmp(kind, "Alo")) {
             float* f = (float*)ptr;
             if (q == 0) L.Alo.m = f; else if (q == 1) L.Alo.wx = f; else if (q == 2) L.Alo.wy = f;
@@ -1250,7 +1294,8 @@ void assemble_rhs_range(fld_ctx* c, const double* E, const double* nHI, const do
         // reads E, n_HI, eta, the df weights and the FP32 mass term; writes
         // b and the FP32 inverse diagonal
         KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * 64.0);
-        launch_asm_rhs_mx(L0.d, c->pd, E, nHI, eta, L0.A32, L0.Alo, c->b, L0.bnd, ra, c->sc, c->s, zb0, nzb);
+        launch_asm_rhs_mx(L0.d, c->pd, E, nHI, eta, L0.A32, L0.Alo, c->b, L0.bnd, ra, c->sc, c->s, zb0, nzb,
+                          L0.Abf);
         return;
     }
     KScope k(c, K_ASM_RHS, (double)L0.d.n * frac * 72.0);
@@ -1987,6 +2032,7 @@ fld_status fld_params_default(fld_params* p) {
     p->fused_post = 0;
     p->paper_order = 0;
     p->persistent_cells = 0;
+    p->precond_bf16 = 1;
     p->theta = 1.0;
     p->scale_factor = 1.0;
     p->tail_cells = 32768;
@@ -2481,6 +2527,12 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
             cudaMemsetAsync(L.A32.wy, 0, nb, s);
             cudaMemsetAsync(L.A32.wz, 0, nb, s);
             cudaMemsetAsync(L.A32.invd, 0, nb, s);
+            if (L.Abf.wx) {
+                cudaMemsetAsync(L.Abf.wx, 0, nb / 2, s);
+                cudaMemsetAsync(L.Abf.wy, 0, nb / 2, s);
+                cudaMemsetAsync(L.Abf.wz, 0, nb / 2, s);
+                cudaMemsetAsync(L.Abf.invd, 0, nb / 2, s);
+            }
         }
         if (l == 0) {
             cudaMemsetAsync(c->cg[2], 0, nb, s);
@@ -2491,10 +2543,19 @@ fld_status fld_autotune(fld_ctx* c, int reps) {
             if (k == TN_POST && !(c->p.fused_post && post4_ok(L.d))) continue;
             auto run = [&](const Tune& tn) {
                 switch (k) {
-                case TN_SMOOTH0: launch_smooth_zero4(L.d, L.A32, r, t, s, tn); break;
-                case TN_RB: launch_rb_colour4(L.d, L.A32, r, t, 0, s, tn); break;
+                // the sweeps the V-cycle launches: bfloat16 coefficients where
+                // the level has them
+                case TN_SMOOTH0:
+                    if (L.Abf.wx) launch_smooth_zero4(L.d, L.Abf, r, t, s, tn);
+                    else launch_smooth_zero4(L.d, L.A32, r, t, s, tn);
+                    break;
+                case TN_RB:
+                    if (L.Abf.wx) launch_rb_colour4(L.d, L.Abf, r, t, 0, s, tn);
+                    else launch_rb_colour4(L.d, L.A32, r, t, 0, s, tn);
+                    break;
                 case TN_RES:
-                    launch_residual4(L.d, L.A32, r, z, t, s, tn, zg_cfg, zg_cfg && red_compress_ok(L.d));
+                    if (L.Abf.wx) launch_residual4(L.d, L.Abf, z, t, s, tn, red_compress_ok(L.d));
+                    else launch_residual4(L.d, L.A32, r, z, t, s, tn, zg_cfg, zg_cfg && red_compress_ok(L.d));
                     break;
                 case TN_RESTRICT:
                     launch_restrict4(L.d, C.d, t, (float*)C.t, s, tn, zg_cfg && red_compress_ok(L.d));

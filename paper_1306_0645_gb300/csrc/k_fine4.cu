@@ -23,25 +23,41 @@ __device__ __forceinline__ void xnb(const float* __restrict__ u, const Geo& g, f
     R = g.load_r ? u[g.xr] : r;
 }
 
+// Coefficients of the smoothing operator as FP32 values, from FP32 storage
+// or from bfloat16 storage (the upper half of an FP32 number, so the
+// conversion is exact): four consecutive ones (i a multiple of 4) or one.
+__device__ __forceinline__ float4 ldw4(const float* __restrict__ p, long long i) { return ld4(p, i); }
+__device__ __forceinline__ float4 ldw4(const unsigned short* __restrict__ p, long long i) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p + i);
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
+                       __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+}
+__device__ __forceinline__ float ldw(const float* __restrict__ p, long long i) { return p[i]; }
+__device__ __forceinline__ float ldw(const unsigned short* __restrict__ p, long long i) {
+    return __uint_as_float((unsigned)p[i] << 16);
+}
+
 // Weight of the upper x face of element 3 (0 on a zero-gradient boundary).
-__device__ __forceinline__ float wx_up(const float* __restrict__ wx, const Geo& g, float4 wv) {
+template <class T>
+__device__ __forceinline__ float wx_up(const T* __restrict__ wx, const Geo& g, float4 wv) {
     const float r = __shfl_down_sync(FULL, wv.x, 1);
     if (!g.has_xr) return 0.0f;
-    return g.load_r ? wx[g.xr_w] : r;
+    return g.load_r ? ldw(wx, g.xr_w) : r;
 }
 
 struct Faces4 {      // the six face weights of each of the four cells
     float4 xl, xu, yl, yu, zl, zu;
 };
 
-__device__ __forceinline__ Faces4 faces_of(const Op<float>& A, const Geo& g, float4 wxc, float4 wzc,
+template <class T>
+__device__ __forceinline__ Faces4 faces_of(const Op<T>& A, const Geo& g, float4 wxc, float4 wzc,
                                            float4 wzu, bool has_zu) {
     Faces4 f;
     f.xl = wxc;
     const float xu3 = wx_up(A.wx, g, wxc);
     f.xu = make_float4(wxc.y, wxc.z, wxc.w, xu3);
-    f.yl = ld4(A.wy, g.c);
-    f.yu = g.has_yp ? ld4(A.wy, g.yp) : make_float4(0.f, 0.f, 0.f, 0.f);
+    f.yl = ldw4(A.wy, g.c);
+    f.yu = g.has_yp ? ldw4(A.wy, g.yp) : make_float4(0.f, 0.f, 0.f, 0.f);
     f.zl = wzc;
     f.zu = has_zu ? wzu : make_float4(0.f, 0.f, 0.f, 0.f);
     return f;
@@ -150,15 +166,15 @@ __global__ void __launch_bounds__(256, 4) k_cg_p_matvec4(Dims d, Op<float> A, co
 // (2m, 2m + 1) along x holds one red cell, whose residual goes to res[m],
 // so cell l has residual res[l >> 1] if it is red and 0 if it is black
 // (18 bytes per cell; k_restrict_red4 reads this form).
-template <bool ZG, bool CMP>
-__global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const float* __restrict__ r,
+template <class T, bool ZG, bool CMP>
+__global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<T> A, const float* __restrict__ r,
                                                    const float* __restrict__ z, float* __restrict__ res, int pf) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
     Geo g = geo_of(d, w, w.k0);
     float4 zc = ld4(z, g.c);
     float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
-    float4 wzc = ld4(A.wz, g.c);
+    float4 wzc = ldw4(A.wz, g.c);
     for (int k = w.k0; k < w.k1; k++) {
         if (k > w.k0) g = geo_of(d, w, k);
         if (pf > 0 && k + pf < w.k1) {
@@ -174,8 +190,8 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
         }
         const bool has_zu = k < d.nz - 1 || d.pz;
         const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
-        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
-        const float4 wxc = ld4(A.wx, g.c);
+        const float4 wzu = ldw4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+        const float4 wxc = ldw4(A.wx, g.c);
         const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
         float L, R;
         xnb(z, g, zc, L, R);
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
                 else st4(res, g.c, e0_red ? make_float4(h.x, 0.f, h.y, 0.f) : make_float4(0.f, h.x, 0.f, h.y));
             }
         } else {
-            const float4 m = ld4(A.m, g.c), rc = ld4(r, g.c);
+            const float4 m = ldw4(A.m, g.c), rc = ld4(r, g.c);
             float4 o;
 #define R1(X, LX, RX)                                                                   \
             o.X = rc.X - (m.X * zc.X + f.xl.X * (zc.X - (LX)) + f.xu.X * (zc.X - (RX)) +    \
@@ -223,19 +239,20 @@ __global__ void __launch_bounds__(256, 4) k_residual4(Dims d, Op<float> A, const
 
 // First red/black Gauss-Seidel sweep from z = 0 (see k_smooth_zero): red
 // cells r / diag; black cells (r + sum_f w_f r_nbr / diag_nbr) / diag.
-__global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, const float* __restrict__ r,
+template <class T>
+__global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<T> A, const float* __restrict__ r,
                                                       float* __restrict__ z, int pf) {
     const Walk w = walk_of(d);
     if (w.k0 >= w.k1) return;
     auto U = [&](long long i) {
-        const float4 a = ld4(r, i), b = ld4(A.invd, i);
+        const float4 a = ld4(r, i), b = ldw4(A.invd, i);
         return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
     };
-    auto Us = [&](long long i) { return r[i] * A.invd[i]; };
+    auto Us = [&](long long i) { return r[i] * ldw(A.invd, i); };
     Geo g = geo_of(d, w, w.k0);
     float4 uc = U(g.c);
     float4 ud = U(g.c + zdn(d, w.k0, w.nxy));
-    float4 wzc = ld4(A.wz, g.c);
+    float4 wzc = ldw4(A.wz, g.c);
     for (int k = w.k0; k < w.k1; k++) {
         if (k > w.k0) g = geo_of(d, w, k);
         if (pf > 0 && k + pf < w.k1) {
@@ -248,15 +265,15 @@ __global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, co
         }
         const bool has_zu = k < d.nz - 1 || d.pz;
         const float4 uu = U(g.c + zup(d, k, w.nxy));
-        const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
-        const float4 wxc = ld4(A.wx, g.c);
+        const float4 wzu = ldw4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+        const float4 wxc = ldw4(A.wx, g.c);
         const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
         const float lsh = __shfl_up_sync(FULL, uc.w, 1);
         const float rsh = __shfl_down_sync(FULL, uc.x, 1);
         const float L = g.load_l ? Us(g.xl) : lsh;
         const float R = g.load_r ? Us(g.xr) : rsh;
         const float4 uym = U(g.ym), uyp = U(g.yp);
-        const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
+        const float4 rc = ld4(r, g.c), iv = ldw4(A.invd, g.c);
         // parity of element 0: red = (i + j + k) even, i0 = 4 i4 is even
         const bool e0_red = ((w.j + k) & 1) == 0;
         float4 o;
@@ -286,8 +303,8 @@ __global__ void __launch_bounds__(256, 4) k_smooth_zero4(Dims d, Op<float> A, co
 // other colour are read, never written, so the in-place update is exact.
 // With dot (the last sweep of a V-cycle's post-smoothing on the finest
 // level) it also forms <r, z> of the finished z for CG.
-template <bool DOT>
-__global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, const float* __restrict__ r,
+template <class T, bool DOT>
+__global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<T> A, const float* __restrict__ r,
                                                     float* z, int colour, RedArgs ra, int pf) {
     const Walk w = walk_of(d);
     DotAcc<float> da;
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, cons
         Geo g = geo_of(d, w, w.k0);
         float4 zc = ld4(z, g.c);
         float4 zd = ld4(z, g.c + zdn(d, w.k0, w.nxy));
-        float4 wzc = ld4(A.wz, g.c);
+        float4 wzc = ldw4(A.wz, g.c);
         for (int k = w.k0; k < w.k1; k++) {
             if (k > w.k0) g = geo_of(d, w, k);
             if (pf > 0 && k + pf < w.k1) {
@@ -309,13 +326,13 @@ __global__ void __launch_bounds__(256, 4) k_rb_colour4(Dims d, Op<float> A, cons
             }
             const bool has_zu = k < d.nz - 1 || d.pz;
             const float4 zu = ld4(z, g.c + zup(d, k, w.nxy));
-            const float4 wzu = ld4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
-            const float4 wxc = ld4(A.wx, g.c);
+            const float4 wzu = ldw4(A.wz, g.c + (k < d.nz - 1 ? w.nxy : (d.pz ? -(long long)(d.nz - 1) * w.nxy : 0)));
+            const float4 wxc = ldw4(A.wx, g.c);
             const Faces4 f = faces_of(A, g, wxc, wzc, wzu, has_zu);
             float L, R;
             xnb(z, g, zc, L, R);
             const float4 zym = ld4(z, g.ym), zyp = ld4(z, g.yp);
-            const float4 rc = ld4(r, g.c), iv = ld4(A.invd, g.c);
+            const float4 rc = ld4(r, g.c), iv = ldw4(A.invd, g.c);
             const bool e0_mine = ((w.j + k + colour) & 1) == 0;
             float4 o = zc;
 #define U1(X, LX, RX)                                                                       \
@@ -913,11 +930,19 @@ void launch_residual4(const Dims& d, Op<float> A, const float* r, const float* z
                       cudaStream_t s, const Tune& tn, bool after_zero_sweep, bool red_compressed) {
     ColShape sh = shape4(d, tn);
     if (after_zero_sweep && red_compressed)
-        k_residual4<true, true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+        k_residual4<float, true, true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
     else if (after_zero_sweep)
-        k_residual4<true, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+        k_residual4<float, true, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
     else
-        k_residual4<false, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+        k_residual4<float, false, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, res, tn.pf);
+}
+void launch_residual4(const Dims& d, Op<unsigned short> A, const float* z, float* res, cudaStream_t s,
+                      const Tune& tn, bool red_compressed) {
+    ColShape sh = shape4(d, tn);
+    if (red_compressed)
+        k_residual4<unsigned short, true, true><<<sh.grid, sh.block, 0, s>>>(d, A, nullptr, z, res, tn.pf);
+    else
+        k_residual4<unsigned short, true, false><<<sh.grid, sh.block, 0, s>>>(d, A, nullptr, z, res, tn.pf);
 }
 bool red_compress_ok(const Dims& f) { return fine4_ok(f) && f.nx % 8 == 0; }
 
@@ -939,20 +964,41 @@ void launch_prolong_add4(const Dims& f, const Dims& c, const float* ec, float* z
     ColShape sh = shape4(f, tn);
     k_prolong_add4<<<sh.grid, sh.block, 0, s>>>(f, c, ec, zf, tn.pf);
 }
+template <class T>
+static void smooth_zero4_t(const Dims& d, Op<T> A, const float* r, float* z, cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
+    k_smooth_zero4<T><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, tn.pf);
+}
+template <class T>
+static void rb_colour4_t(const Dims& d, Op<T> A, const float* r, float* z, int colour, const RedArgs* ra,
+                         cudaStream_t s, const Tune& tn) {
+    ColShape sh = shape4(d, tn);
+    if (ra) k_rb_colour4<T, true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, *ra, tn.pf);
+    else k_rb_colour4<T, false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{}, tn.pf);
+}
 void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, cudaStream_t s,
                          const Tune& tn) {
-    ColShape sh = shape4(d, tn);
-    k_smooth_zero4<<<sh.grid, sh.block, 0, s>>>(d, A, r, z, tn.pf);
+    smooth_zero4_t(d, A, r, z, s, tn);
+}
+void launch_smooth_zero4(const Dims& d, Op<unsigned short> A, const float* r, float* z, cudaStream_t s,
+                         const Tune& tn) {
+    smooth_zero4_t(d, A, r, z, s, tn);
 }
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                        cudaStream_t s, const Tune& tn) {
-    ColShape sh = shape4(d, tn);
-    k_rb_colour4<false><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, RedArgs{}, tn.pf);
+    rb_colour4_t(d, A, r, z, colour, nullptr, s, tn);
+}
+void launch_rb_colour4(const Dims& d, Op<unsigned short> A, const float* r, float* z, int colour,
+                       cudaStream_t s, const Tune& tn) {
+    rb_colour4_t(d, A, r, z, colour, nullptr, s, tn);
 }
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                            const RedArgs& ra, cudaStream_t s, const Tune& tn) {
-    ColShape sh = shape4(d, tn);
-    k_rb_colour4<true><<<sh.grid, sh.block, 0, s>>>(d, A, r, z, colour, ra, tn.pf);
+    rb_colour4_t(d, A, r, z, colour, &ra, s, tn);
+}
+void launch_rb_colour4_dot(const Dims& d, Op<unsigned short> A, const float* r, float* z, int colour,
+                           const RedArgs& ra, cudaStream_t s, const Tune& tn) {
+    rb_colour4_t(d, A, r, z, colour, &ra, s, tn);
 }
 
 }  // namespace fld

@@ -24,6 +24,7 @@
 // converges as an FP64 one would.
 #include "limiter.cuh"
 #include "walk4.cuh"
+#include <cuda_bf16.h>
 
 namespace fld {
 
@@ -33,6 +34,14 @@ namespace {
 // clearing the sign of the 64-bit pattern is compiled as an FP64 absolute
 // value, an instruction of the FP64 pipe.
 __device__ __forceinline__ unsigned hiword(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
+
+// The bfloat16 nearest to v, as its 16 bits.
+__device__ __forceinline__ unsigned short bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+// Four of them packed in storage order.
+__device__ __forceinline__ uint2 bf16_pack4(float a, float b, float c, float d) {
+    return make_uint2((unsigned)bf16_bits(a) | ((unsigned)bf16_bits(b) << 16),
+                      (unsigned)bf16_bits(c) | ((unsigned)bf16_bits(d) << 16));
+}
 
 // L2 prefetch of the line holding p (a streamed array's element one or more
 // planes ahead): its bytes are requested from HBM without holding a
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(256) k_asm_rhs_mx(Dims d, PhysDev p, const dou
                                                    const double* __restrict__ nHI,
                                                    const double* __restrict__ eta, Op<float> A, Op<float> L,
                                                    double* __restrict__ b, Bnd bnd, RedArgs ra, const double* scg,
-                                                   int zb0, int kch) {
+                                                   int zb0, int kch, Op<unsigned short> Bf) {
     const int K = step_scale(scg, p.dt_exp);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -469,7 +478,14 @@ __global__ void __launch_bounds__(256) k_asm_rhs_mx(Dims d, PhysDev p, const dou
         b[c] = b64;
         bb = fma(b64, b64, bb);
         bmax = fmaxf(bmax, fabsf(bd.h));
-        A.invd[c] = 1.0f / (A.m[c] + wsum32);
+        const float iv = 1.0f / (A.m[c] + wsum32);
+        A.invd[c] = iv;
+        if (Bf.invd) {
+            Bf.wx[c] = bf16_bits(A.wx[c]);
+            Bf.wy[c] = bf16_bits(A.wy[c]);
+            Bf.wz[c] = bf16_bits(A.wz[c]);
+            Bf.invd[c] = bf16_bits(iv);
+        }
     }
     double acc[2] = {bb, f2d(bmax, K)};
     const bool ismax[2] = {false, true};
@@ -510,7 +526,7 @@ __global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const
                                                      const double* __restrict__ nHI,
                                                      const double* __restrict__ eta, Op<float> A, Op<float> L,
                                                      double* __restrict__ b, RedArgs ra, const double* scg,
-                                                     int zb0, int kch, int zs) {
+                                                     int zb0, int kch, int zs, Op<unsigned short> Bf) {
     const int K = step_scale(scg, p.dt_exp);
     const unsigned wm = __activemask();
     Walk w = walk_of(d);
@@ -557,10 +573,13 @@ __global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const
             }
             Acc2 F[4];
             float ws[4];
+            float wxl[4], wyl[4], wzl[4];   // the lower faces' FP32 weights
             // x faces
             {
                 df wx[4];
                 ld_w4(A.wx, L.wx, g.c, wx);
+#pragma unroll
+                for (int e = 0; e < 4; e++) wxl[e] = wx[e].h;
                 const double el_sh = __shfl_up_sync(wm, ec[3], 1);
                 const double el = g.load_l ? E[g.xl] : el_sh;
                 df fl[4];
@@ -596,6 +615,7 @@ __global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const
                 for (int e = 0; e < 4; e++) {
                     F[e].add(df_mul_raw(wl[e], split64(em[e] - ec[e], K)));
                     ws[e] += wl[e].h;
+                    wyl[e] = wl[e].h;
                 }
             }
             {
@@ -625,6 +645,7 @@ __global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const
                     fz[e] = df_neg(f);
                     ws[e] += wzc[e];
                     ws[e] += has_zu ? wu[e].h : 0.0f;
+                    wzl[e] = wzc[e];
                     wzc[e] = wu[e].h;
                 }
             }
@@ -661,6 +682,12 @@ __global__ void __launch_bounds__(256, 2) k_asm_rhs4_mx(Dims d, PhysDev p, const
                     *reinterpret_cast<double2*>(b + g.c) = make_double2(bo[0], bo[1]);
                     *reinterpret_cast<double2*>(b + g.c + 2) = make_double2(bo[2], bo[3]);
                     st4(A.invd, g.c, make_float4(iv[0], iv[1], iv[2], iv[3]));
+                    if (Bf.invd) {
+                        *reinterpret_cast<uint2*>(Bf.wx + g.c) = bf16_pack4(wxl[0], wxl[1], wxl[2], wxl[3]);
+                        *reinterpret_cast<uint2*>(Bf.wy + g.c) = bf16_pack4(wyl[0], wyl[1], wyl[2], wyl[3]);
+                        *reinterpret_cast<uint2*>(Bf.wz + g.c) = bf16_pack4(wzl[0], wzl[1], wzl[2], wzl[3]);
+                        *reinterpret_cast<uint2*>(Bf.invd + g.c) = bf16_pack4(iv[0], iv[1], iv[2], iv[3]);
+                    }
                 }
             }
 #pragma unroll
@@ -1084,7 +1111,7 @@ void launch_asm_fix_mx(const Dims& d, const PhysDev& p, const double* E, const d
 
 void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, const double* eta,
                        Op<float> A, Op<float> L, double* b, Bnd bnd, const RedArgs& ra, const double* scg,
-                       cudaStream_t s, int zb0, int nzb) {
+                       cudaStream_t s, int zb0, int nzb, Op<unsigned short> Bf) {
     const AsmShape a = asm_shape(d);
     if (nzb < 0 || zb0 + nzb > a.nzb) nzb = a.nzb - zb0;
     if (nzb <= 0) return;
@@ -1099,20 +1126,24 @@ void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const d
         while (zs > 1 && xy * nzb * zs > RED_MAX_BLOCKS) zs--;
         const dim3 g4(sh.grid.x, sh.grid.y, (unsigned)(nzb * zs));
         if (be)
-            k_asm_rhs4_mx<true><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs);
+            k_asm_rhs4_mx<true><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs, Bf);
         else
-            k_asm_rhs4_mx<false><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs);
+            k_asm_rhs4_mx<false><<<g4, sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, ra, scg, zb0, a.kch, zs, Bf);
         return;
     }
     const dim3 g(a.sh.grid.x, a.sh.grid.y, (unsigned)nzb);
     if (be && !dir)
-        k_asm_rhs_mx<true, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
+        k_asm_rhs_mx<true, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch,
+                                                             Bf);
     else if (be)
-        k_asm_rhs_mx<true, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
+        k_asm_rhs_mx<true, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch,
+                                                             Bf);
     else if (!dir)
-        k_asm_rhs_mx<false, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
+        k_asm_rhs_mx<false, false><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch,
+                                                             Bf);
     else
-        k_asm_rhs_mx<false, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch);
+        k_asm_rhs_mx<false, true><<<g, a.sh.block, 0, s>>>(d, p, E, nHI, eta, A, L, b, bnd, ra, scg, zb0, a.kch,
+                                                             Bf);
 }
 
 void launch_ir_scale_b(long long n, const double* b, int Ks, float* r32, const RedArgs& ra,

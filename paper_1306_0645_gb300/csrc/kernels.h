@@ -131,9 +131,11 @@ void launch_asm_fix_mx(const Dims& d, const PhysDev& p, const double* E, const d
 // FP32 inverse diagonal A.invd, Dirichlet face weights into bnd and m; scg:
 // the slots of pass 1's maxima.  Needs pass 1 of its z-blocks and the one
 // above.
+// Bf: where its pointers are set, also the bfloat16 copies (nearest) of the
+// FP32 weights wx, wy, wz and of the FP32 inverse diagonal.
 void launch_asm_rhs_mx(const Dims& d, const PhysDev& p, const double* E, const double* nHI, const double* eta,
                        Op<float> A, Op<float> L, double* b, Bnd bnd, const RedArgs& ra, const double* scg,
-                       cudaStream_t s, int zb0 = 0, int nzb = -1);
+                       cudaStream_t s, int zb0 = 0, int nzb = -1, Op<unsigned short> Bf = {});
 // r32 = b 2^-ks (nearest float); ||r32||^2, max |r32| (R_IRRES).
 void launch_ir_scale_b(long long n, const double* b, int ks, float* r32, const RedArgs& ra, cudaStream_t s);
 // The refinement unknown x (dE) of the mixed solver is a df pair per cell
@@ -346,6 +348,17 @@ void launch_smooth_zero4(const Dims& d, Op<float> A, const float* r, float* z, c
                          const Tune& tn = Tune{});
 void launch_rb_colour4(const Dims& d, Op<float> A, const float* r, float* z, int colour,
                        cudaStream_t s, const Tune& tn = Tune{});
+// The same sweeps with the smoothing operator's coefficients (wx, wy, wz,
+// invd; m unused) stored as bfloat16 (the upper 16 bits of the FP32
+// values, rounded to nearest); the residual only in its zero-guess form.
+void launch_smooth_zero4(const Dims& d, Op<unsigned short> A, const float* r, float* z, cudaStream_t s,
+                         const Tune& tn = Tune{});
+void launch_rb_colour4(const Dims& d, Op<unsigned short> A, const float* r, float* z, int colour,
+                       cudaStream_t s, const Tune& tn = Tune{});
+void launch_rb_colour4_dot(const Dims& d, Op<unsigned short> A, const float* r, float* z, int colour,
+                           const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
+void launch_residual4(const Dims& d, Op<unsigned short> A, const float* z, float* res, cudaStream_t s,
+                      const Tune& tn, bool red_compressed);
 void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s);
 // one colour of a sweep followed by <r, z> of the result (reduction ra)
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,

@@ -17,11 +17,12 @@ __device__ __forceinline__ float4 ld4(const float* __restrict__ p, long long i) 
 __device__ __forceinline__ void st4(float* p, long long i, float4 v) {
     *reinterpret_cast<float4*>(p + i) = v;
 }
-// Prefetch of the 16 bytes at p + i into L2.  The sweeps issue it for the
+// Prefetch of the line holding p + i into L2.  The sweeps issue it for the
 // plane pf ahead of the one they compute, so that plane's loads hit L2:
 // bytes are requested from HBM without holding registers or scoreboard
 // entries while the current plane waits on its own loads.
-__device__ __forceinline__ void pf2(const float* p, long long i) {
+template <class T>
+__device__ __forceinline__ void pf2(const T* p, long long i) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p + i)));
 }
 

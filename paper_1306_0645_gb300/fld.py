@@ -48,7 +48,8 @@ class fld_params(ctypes.Structure):
                 ("post", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("coarse_cap", ctypes.c_int), ("graphs", ctypes.c_int), ("fused_post", ctypes.c_int),
                 ("theta", ctypes.c_double), ("scale_factor", ctypes.c_double), ("tail_cells", ctypes.c_int),
-                ("paper_order", ctypes.c_int), ("persistent_cells", ctypes.c_int)]
+                ("paper_order", ctypes.c_int), ("persistent_cells", ctypes.c_int),
+                ("precond_bf16", ctypes.c_int)]
 
 
 class fld_info(ctypes.Structure):

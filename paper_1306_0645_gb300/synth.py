@@ -111,6 +111,7 @@ class Params:
     tail_cells: int = 32768
     paper_order: int = 0
     persistent_cells: int = 0
+    precond_bf16: int = 1
 
 
 @dataclasses.dataclass

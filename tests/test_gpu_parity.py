@@ -183,11 +183,13 @@ def test_mixed_vcycle_parity(fld, oracle, n, per, tail, pre):
     # one pre-sweep the residual takes the zero-guess form (the weighted sum
     # of the black neighbours at red cells, 0 at black cells), which equals
     # r - A z in exact arithmetic; with two pre-sweeps it is r - A z itself.
-    # Both agree with the oracle to FP32 rounding of the cycle.
+    # Both agree with the oracle to FP32 rounding of the cycle (the FP32
+    # coefficients: precond_bf16 = 0; the bfloat16 ones in test_gpu_bf16.py).
     case = synth.random_case(n, seed=400 + sum(n), periodic=per, E_decades=(-20, -14))
     op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
     p = case.params
     p.precision, p.pre, p.post, p.tail_cells = synth.PREC_MIXED, pre, 1, tail
+    p.precond_bf16 = 0
     ctx = fld.fld_create(case.grid, p)
     fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
     x = np.random.default_rng(11).standard_normal(case.grid.shape)
@@ -478,9 +480,11 @@ def test_fused_post_sweep_equals_colour_sweeps(fld, make):
     # the fused black+red post-sweep does the arithmetic of the two colour
     # sweeps, so the whole mixed step is bit-identical (rows of 128 cells
     # and more take the fused kernel: periodic and reflecting axes, a
-    # partial last block of lanes, rows that are not a multiple of PBY)
+    # partial last block of lanes, rows that are not a multiple of PBY); the
+    # fused kernel reads FP32 coefficients, so the colour sweeps do too
     case = make()
     case.params.precision = synth.PREC_MIXED
+    case.params.precond_bf16 = 0
     out = []
     for fused in (0, 1):
         case.params.fused_post = fused
@@ -640,7 +644,7 @@ def test_paper_order_vcycle_parity(fld, oracle, prec, tail):
     case = synth.random_case((64, 32, 48), seed=77, periodic=(True, False, False), E_decades=(-20, -14))
     op = oracle.assemble(case.grid, case.params, case.E, case.nHI, case.eta)
     p = case.params
-    p.precision, p.tail_cells, p.paper_order = prec, tail, 1
+    p.precision, p.tail_cells, p.paper_order, p.precond_bf16 = prec, tail, 1, 0
     ctx = fld.fld_create(case.grid, p)
     fld.fld_assemble(ctx, dev(case.E), dev(case.nHI), dev(case.eta))
     x = np.random.default_rng(12).standard_normal(case.grid.shape)
