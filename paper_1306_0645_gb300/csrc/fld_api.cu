@@ -51,7 +51,7 @@ struct Level {
     Op<double> A64;
     Op<float> A32;
     Op<float> Alo;     // mixed fine level: low parts of m and w (df with A32)
-    Op<unsigned short> Abf;   // mixed fine level: bfloat16 copies of wx, wy, wz, invd for
+    Op<unsigned short> Abf;   // mixed levels: bfloat16 copies of wx, wy, wz, invd for
                               // the V-cycle's sweeps (fld_params.precond_bf16), else null
     Bnd bnd;           // Dirichlet face weights (FP64)
     void *r, *z, *t;   // level vectors in the solver precision (level 0: t only)
@@ -226,16 +226,16 @@ bool ps_wanted(const fld_params* p, size_t n0, int nl) {
            n0 <= (size_t)p->persistent_cells && nl >= 2 && nl <= TAIL_MAX_LEVELS;
 }
 
-// Whether the fine level's V-cycle sweeps read bfloat16 copies of its
-// coefficients (fld_params.precond_bf16): mixed precision, red/black
-// Gauss-Seidel with one pre-sweep (the zero-guess residual, which needs no
-// m) and separate colour sweeps, four-cell sweeps on a fine level that
-// lies above the coarsest level and outside the persistent coarse tail, and
-// inner solves launched kernel by kernel.
-bool bf16_wanted(const fld_params* p, int nx, size_t n0, int nl) {
+// Whether the V-cycle sweeps of level l (nx by n cells; the fine level has
+// n0) read bfloat16 copies of its coefficients (fld_params.precond_bf16):
+// mixed precision, red/black Gauss-Seidel with one pre-sweep (the
+// zero-guess residual, which needs no m) and separate colour sweeps,
+// four-cell sweeps on a level above the coarsest one and outside the
+// persistent coarse tail, and inner solves launched kernel by kernel.
+bool bf16_wanted(const fld_params* p, int l, int nx, size_t n, size_t n0, int nl) {
     return p->precision == FLD_PREC_MIXED && p->precond_bf16 == 1 && p->smoother == FLD_SMOOTH_RBGS &&
-           p->pre == 1 && p->fused_post == 0 && nl >= 2 && nx % 4 == 0 && nx >= 16 &&
-           !(p->tail_cells > 0 && n0 <= (size_t)p->tail_cells) && !ps_wanted(p, n0, nl);
+           p->pre == 1 && p->fused_post == 0 && l < nl - 1 && nx % 4 == 0 && nx >= 16 &&
+           !(p->tail_cells > 0 && n <= (size_t)p->tail_cells) && !ps_wanted(p, n0, nl);
 }
 
 // Enumerates every device buffer a context needs, in a fixed order; the
@@ -259,7 +259,7 @@ void plan(const fld_grid* g, const fld_params* p, F&& buf) {
             for (int q = 0; q < 5; q++) buf(l, "A32", q, n * sizeof(float));
         if (mixed && l == 0)
             for (int q = 0; q < 4; q++) buf(l, "Alo", q, n * sizeof(float));
-        if (l == 0 && bf16_wanted(p, g->nx, n, nl))
+        if (bf16_wanted(p, l, dims[l][0], n, (size_t)g->nx * g->ny * g->nz, nl))
             for (int q = 0; q < 4; q++) buf(l, "Abf", q, n * sizeof(unsigned short));
         if (l > 0) {
             buf(l, "vec", 0, n * ts);
@@ -561,9 +561,9 @@ void vcycle(fld_ctx* c, int l, const T* r, T* z, const RedArgs* dot = nullptr, b
     Op<T> A = op_of<T>(L);
     T* t = (T*)L.t;
     const fld_params& p = c->p;
-    // the fine level of a mixed context may sweep with bfloat16 copies of
-    // its coefficients (allocated only where bf16_wanted holds): half the
-    // bytes of the face weights and the inverse diagonal
+    // the levels of a mixed context may sweep with bfloat16 copies of their
+    // coefficients (allocated only where bf16_wanted holds): half the bytes
+    // of the face weights and the inverse diagonal
     const bool bf = std::is_same<T, float>::value && L.Abf.wx != nullptr;
     const double cw = bf ? 0.5 : 1.0;
     if (p.smoother == FLD_SMOOTH_RBGS) {
@@ -1320,6 +1320,10 @@ fld_status assemble_coarse(fld_ctx* c) {
                     launch_coarsen_bnd<float>(F.d, C.d, sd, F.bnd, C.bnd, C.A32, s);
                 }
             { KScope k(c, K_INVD, 20.0 * nc); launch_invd<float>(C.d, C.A32, C.A32, s); }
+            if (C.Abf.wx) {
+                KScope k(c, K_INVD, 24.0 * nc);
+                launch_op_to_bf16(C.d.n, C.A32, C.Abf, s);
+            }
         } else {
             { KScope k(c, K_COARSEN, 32.0 * (nf + nc)); launch_coarsen<double>(F.d, C.d, F.A64, C.A64, s); }
             for (int sd = 0; sd < 6; sd++)

@@ -9,6 +9,7 @@
 // same operations as the scalar kernels of k_mg.cu / k_cg.cu, restricted to
 // levels whose x extent is a multiple of 4.
 #include "walk4.cuh"
+#include <cuda_bf16.h>
 
 namespace fld {
 
@@ -815,6 +816,26 @@ __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const flo
 
 // ------------------------------------------------------------ flat vectors
 
+// The bfloat16 copies of a level's smoothing coefficients (nearest, as the
+// assembly writes the fine level's).
+__global__ void __launch_bounds__(256) k_op_to_bf16(long long n4, Op<float> A, Op<unsigned short> B) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long i = 4 * q;
+        const float* src[4] = {A.wx, A.wy, A.wz, A.invd};
+        unsigned short* dst[4] = {B.wx, B.wy, B.wz, B.invd};
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const float4 v = ld4(src[a], i);
+            const unsigned lo = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v.x)) |
+                                ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v.y)) << 16);
+            const unsigned hi = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v.z)) |
+                                ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v.w)) << 16);
+            *reinterpret_cast<uint2*>(dst[a] + i) = make_uint2(lo, hi);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(RED_THREADS) k_dot4(long long n4, const float* __restrict__ a,
                                                       const float* __restrict__ b, RedArgs ra) {
     DotAcc<float> da;
@@ -865,6 +886,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_update4(long long n4, float*
 }
 
 // ---------------------------------------------------------------- launchers
+
+void launch_op_to_bf16(long long n, Op<float> A, Op<unsigned short> B, cudaStream_t s) {
+    k_op_to_bf16<<<grid_blocks(n / 4, 256), 256, 0, s>>>(n / 4, A, B);
+}
 
 void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s) {
     k_dot4<<<red_blocks(n / 4), RED_THREADS, 0, s>>>(n / 4, a, b, ra);

@@ -359,6 +359,8 @@ void launch_rb_colour4_dot(const Dims& d, Op<unsigned short> A, const float* r, 
                            const RedArgs& ra, cudaStream_t s, const Tune& tn = Tune{});
 void launch_residual4(const Dims& d, Op<unsigned short> A, const float* z, float* res, cudaStream_t s,
                       const Tune& tn, bool red_compressed);
+// B.wx, wy, wz, invd = the bfloat16 values nearest to A's (n a multiple of 4).
+void launch_op_to_bf16(long long n, Op<float> A, Op<unsigned short> B, cudaStream_t s);
 void launch_dot4(long long n, const float* a, const float* b, const RedArgs& ra, cudaStream_t s);
 // one colour of a sweep followed by <r, z> of the result (reduction ra)
 void launch_rb_colour4_dot(const Dims& d, Op<float> A, const float* r, float* z, int colour,
