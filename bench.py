@@ -52,7 +52,10 @@ UNIT = "cell-solves/s"
 MODEL_ASM, MODEL_ITER, MODEL_IR, MODEL_FIN = 80.0, 144.0, 52.0, 24.0
 
 TRAFFIC_OVER_ALGORITHMIC = {
+    "rb_colour": 19.9 / 18.0,
     "cg_p_matvec": 40.5 / 40.0,
+    "smooth_zero": 16.1 / 16.0,
+    "residual": 12.0 / 12.0,
     "restrict": 2.1 / 2.5,
     "prolong_add": 6.7 / 8.5,
     "cg_update": 10.5 / 12.0,
