@@ -79,3 +79,35 @@ def test_noalloc_rejects_inconsistent_faces():
     st = fld.lib().fld_residual_noalloc(ctypes.byref(g), p, p, p, p, p, p, None, p, None)
     assert st == fld.FLD_EINVAL
     assert "periodic" in fld.fld_last_error()
+
+
+def test_bf16_coefficient_footprint(libfld):
+    # fld_params.precond_bf16 (on by default): the levels whose V-cycle sweeps
+    # run four cells per thread outside the persistent coarse tail (and
+    # above the coarsest level) hold bfloat16 copies of wx, wy, wz and invd,
+    # two bytes per cell each, in mixed contexts with red/black Gauss-Seidel,
+    # one pre-sweep and separate colour sweeps; nothing otherwise
+    from paper_1306_0645_gb300 import fld, synth
+    g = synth.Grid((128, 64, 96), (1.0,) * 3, (False,) * 3)
+    levels = fld.fld_levels(g)
+    tail = synth.Params().tail_cells
+
+    def fp(**kw):
+        return fld.fld_footprint_bytes(g, synth.Params(precision=synth.PREC_MIXED, **kw))
+
+    assert fld.fld_params_default().precond_bf16 == 1
+    want = sum(4 * ((2 * nx * ny * nz + 511) // 512 * 512) for (nx, ny, nz) in levels[:-1]
+               if nx % 4 == 0 and nx >= 16 and nx * ny * nz > tail)
+    assert want > 0 and fp() - fp(precond_bf16=0) == want
+    # no copies where the sweeps keep FP32 coefficients
+    for kw in ({"pre": 2}, {"smoother": synth.SMOOTH_JACOBI}, {"fused_post": 1}, {"persistent_cells": 1 << 24},
+               {"tail_cells": 1 << 24}):
+        assert fp(precond_bf16=1, **kw) == fp(precond_bf16=0, **kw), kw
+    assert fld.fld_footprint_bytes(g, synth.Params(precond_bf16=1)) == \
+        fld.fld_footprint_bytes(g, synth.Params(precond_bf16=0))
+    # an x extent that is not a multiple of 4 keeps the one-cell sweeps
+    g2 = synth.Grid((130, 64, 96), (1.0,) * 3, (False,) * 3)
+    assert fld.fld_footprint_bytes(g2, synth.Params(precision=synth.PREC_MIXED)) == \
+        fld.fld_footprint_bytes(g2, synth.Params(precision=synth.PREC_MIXED, precond_bf16=0))
+    # only 0 and 1
+    assert fp(precond_bf16=2) == 0 and fp(precond_bf16=-1) == 0
