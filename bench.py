@@ -378,6 +378,9 @@ def main():
     traffic = ratio * bytes_per if ratio else None
     roofline = {"kernel": d["name"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                # the DRAM bytes the launch moves (ncu ratio x algorithmic) over its time: a colour
+                # sweep changes half of z but writes every 16-byte group of it back
+                "traffic_frac": (traffic / (avg_ms * 1e-3) / 1e9 / peak) if traffic else None,
                 "launches_timed": d["timed"], "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per,
                 "share_of_step": d["ms"] / cal_ms,
                 "timing": "CUDA events around each launch of the class on the context's stream, over "
