@@ -310,7 +310,8 @@ fld_status fld_apply(fld_ctx* ctx, const double* x, double* y);
 
 /* One multigrid V-cycle with zero initial guess, z = B r, on the assembled
  * hierarchy in the context's solver precision (device, FP64 arguments; a
- * mixed-precision context runs its FP32 cycle on r rounded to FP32 and uses
+ * mixed-precision context runs its FP32 cycle on r rounded to FP32, with the
+ * bfloat16 smoothing coefficients where precond_bf16 gives them, and uses
  * its CG work vectors).  For tests. */
 fld_status fld_vcycle(fld_ctx* ctx, const double* r, double* z);
 
