@@ -36,10 +36,19 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
 
 
+def no_tail(case):
+    case.params.tail_cells = 0
+    return case
+
+
 CASES = [
     ("config4_96", lambda: synth.config4(96, sources=256)),
     ("periodic_xz", lambda: synth.random_case((128, 40, 24), seed=41, periodic=(True, False, True))),
     ("periodic_y", lambda: synth.random_case((64, 48, 40), seed=42, periodic=(False, True, False))),
+    # nx = 36 without the persistent tail: the fine level's residual in the
+    # full layout (nx not a multiple of 8) with bfloat16 coefficients, above a
+    # level of nx = 18 that keeps the one-cell FP32 sweeps
+    ("mixed_levels", lambda: no_tail(synth.random_case((36, 32, 32), seed=43, periodic=(False, False, True)))),
 ]
 
 
