@@ -548,6 +548,26 @@ __global__ void __launch_bounds__(256, 3) k_post_smooth4(Dims d, Op<float> A, co
     }
 }
 
+// The trilinear interpolation's x step for a thread's four fine cells from
+// coarse cells I (c0), I + 1 (c1) and their outer neighbours I - 1 (cm) and
+// I + 2 (cp): weights 3/4 for the nearer coarse cell, 1/4 for the farther.
+__device__ __forceinline__ float4 xinterp(float c0, float c1, float cm, float cp) {
+    return make_float4(fmaf(0.75f, c0, 0.25f * cm), fmaf(0.75f, c0, 0.25f * c1), fmaf(0.75f, c1, 0.25f * c0),
+                       fmaf(0.75f, c1, 0.25f * cp));
+}
+
+// The y and z steps: rows a (nearer, 3/4) and b (farther, 1/4) of the nearer
+// coarse plane (0, 3/4) and of the farther one (1, 1/4), summed in that order.
+__device__ __forceinline__ float4 pcomb(float4 a0, float4 b0, float4 a1, float4 b1) {
+    const float w0 = 0.75f * 0.75f, w1 = 0.25f * 0.75f, w2 = 0.75f * 0.25f, w3 = 0.25f * 0.25f;
+    float4 r;
+    r.x = fmaf(w3, b1.x, fmaf(w2, a1.x, fmaf(w1, b0.x, w0 * a0.x)));
+    r.y = fmaf(w3, b1.y, fmaf(w2, a1.y, fmaf(w1, b0.y, w0 * a0.y)));
+    r.z = fmaf(w3, b1.z, fmaf(w2, a1.z, fmaf(w1, b0.z, w0 * a0.z)));
+    r.w = fmaf(w3, b1.w, fmaf(w2, a1.w, fmaf(w1, b0.w, w0 * a0.w)));
+    return r;
+}
+
 // Out-of-place prolongation: zo = z + P ec (see k_prolong_add4).
 __global__ void __launch_bounds__(256) k_prolong_to4(Dims f, Dims cd, const float* __restrict__ ec,
                                                      const float* __restrict__ z, float* __restrict__ zo) {
@@ -565,24 +585,20 @@ __global__ void __launch_bounds__(256) k_prolong_to4(Dims f, Dims cd, const floa
     for (int k = w.k0; k < w.k1; k++) {
         const int K0 = k >> 1;
         const int K1 = wrapc((k & 1) ? K0 + 1 : K0 - 1, cd.nz, cd.pz);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 X[4];   // rows (J0, K0), (J1, K0), (J0, K1), (J1, K1), x-interpolated
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int Jq = (q & 1) ? J1 : J0;
             const int Kq = (q & 2) ? K1 : K0;
-            const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
             const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
             const float2 cc = *reinterpret_cast<const float2*>(ec + row + I);
-            const float c0 = cc.x, c1 = cc.y;
-            const float lsh = __shfl_up_sync(FULL, c1, 1);
-            const float rsh = __shfl_down_sync(FULL, c0, 1);
+            const float lsh = __shfl_up_sync(FULL, cc.y, 1);
+            const float rsh = __shfl_down_sync(FULL, cc.x, 1);
             const float cm = load_l ? ec[row + xm] : lsh;
             const float cp = load_r ? ec[row + xp] : rsh;
-            acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
-            acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
-            acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
-            acc.w = fmaf(wq, 0.75f * c1 + 0.25f * cp, acc.w);
+            X[q] = xinterp(cc.x, cc.y, cm, cp);
         }
+        const float4 acc = pcomb(X[0], X[1], X[2], X[3]);
         const long long c = (long long)k * w.nxy + (long long)w.j * f.nx + 4 * w.i4;
         if (w.valid) {
             float4 v = ld4(z, c);
@@ -764,7 +780,12 @@ __global__ void __launch_bounds__(256) k_restrict_red4(Dims f, Dims cd, const fl
 
 // Trilinear prolongation and correction zf += P ec (see k_prolong_add): a
 // thread owns four fine cells along x, which interpolate from coarse cells
-// 2 i4 - 1 .. 2 i4 + 2 of two coarse rows in two coarse planes.
+// 2 i4 - 1 .. 2 i4 + 2 of two coarse rows (J0 = j / 2 and its neighbour
+// towards j) in two coarse planes (K0 = k / 2 and its neighbour towards k).
+// Fine planes 2K - 1 .. 2K + 2 all read coarse plane K, so the thread keeps
+// the x-interpolated rows of the window of coarse planes K - 1, K, K + 1
+// around K = k / 2 in registers and interpolates one new coarse plane every
+// second fine plane (one coarse row per fine plane, against four).
 __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const float* __restrict__ ec,
                                                       float* __restrict__ zf, int pf) {
     const Walk w = walk_of(f);
@@ -779,29 +800,41 @@ __global__ void __launch_bounds__(256) k_prolong_add4(Dims f, Dims cd, const flo
     const int J0 = w.j >> 1;
     const int J1 = fold((w.j & 1) ? J0 + 1 : J0 - 1, cd.ny, cd.py);
     const long long cxy = (long long)cd.nx * cd.ny;
-    for (int k = w.k0; k < w.k1; k++) {
-        if (pf > 0 && k + pf < w.k1)
-            pf2(zf, (long long)(k + pf) * w.nxy + (long long)w.j * f.nx + 4 * w.i4);
-        const int K0 = k >> 1;
-        const int K1 = fold((k & 1) ? K0 + 1 : K0 - 1, cd.nz, cd.pz);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // rows J0 (a) and J1 (b) of coarse plane K, x-interpolated
+    auto rows = [&](int K, float4& a, float4& b) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int Jq = (q & 1) ? J1 : J0;
-            const int Kq = (q & 2) ? K1 : K0;
-            const float wq = ((q & 1) ? 0.25f : 0.75f) * ((q & 2) ? 0.25f : 0.75f);
-            const long long row = (long long)Kq * cxy + (long long)Jq * cd.nx;
+        for (int q = 0; q < 2; q++) {
+            const long long row = (long long)K * cxy + (long long)(q ? J1 : J0) * cd.nx;
             const float2 cc = *reinterpret_cast<const float2*>(ec + row + I);
-            const float c0 = cc.x, c1 = cc.y;
-            const float lsh = __shfl_up_sync(FULL, c1, 1);
-            const float rsh = __shfl_down_sync(FULL, c0, 1);
+            const float lsh = __shfl_up_sync(FULL, cc.y, 1);
+            const float rsh = __shfl_down_sync(FULL, cc.x, 1);
             const float cm = load_l ? ec[row + xm] : lsh;
             const float cp = load_r ? ec[row + xp] : rsh;
-            acc.x = fmaf(wq, 0.75f * c0 + 0.25f * cm, acc.x);
-            acc.y = fmaf(wq, 0.75f * c0 + 0.25f * c1, acc.y);
-            acc.z = fmaf(wq, 0.75f * c1 + 0.25f * c0, acc.z);
-            acc.w = fmaf(wq, 0.75f * c1 + 0.25f * cp, acc.w);
+            const float4 v = xinterp(cc.x, cc.y, cm, cp);
+            if (q) b = v;
+            else a = v;
         }
+    };
+    int K = w.k0 >> 1;
+    float4 am, bm, a0, b0, ap, bp;
+    rows(fold(K - 1, cd.nz, cd.pz), am, bm);
+    rows(K, a0, b0);
+    rows(fold(K + 1, cd.nz, cd.pz), ap, bp);
+    for (int k = w.k0; k < w.k1; k++) {
+        if (k > w.k0 && (k & 1) == 0) {
+            // the window moves up one coarse plane
+            K = k >> 1;
+            am = a0;
+            bm = b0;
+            a0 = ap;
+            b0 = bp;
+            rows(fold(K + 1, cd.nz, cd.pz), ap, bp);
+        }
+        if (pf > 0 && k + pf < w.k1)
+            pf2(zf, (long long)(k + pf) * w.nxy + (long long)w.j * f.nx + 4 * w.i4);
+        // the second coarse plane: K + 1 for odd fine planes, K - 1 for even
+        const bool odd = (k & 1) != 0;
+        const float4 acc = pcomb(a0, b0, odd ? ap : am, odd ? bp : bm);
         const long long c = (long long)k * w.nxy + (long long)w.j * f.nx + 4 * w.i4;
         if (w.valid) {
             float4 z = ld4(zf, c);
