@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="grid cells per axis")
     ap.add_argument("--sources", type=int, default=65536)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp32-coef-steps", type=int, default=3,
+                    help="steps of the same mixed step with FP32 smoothing coefficients (precond_bf16 = 0)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--one-core-n", type=int, default=128,
                     help="grid of the one-core oracle sample of the CPU baseline (0 skips it)")
@@ -409,6 +411,25 @@ def main():
     E_mx_h = E_mx.cpu().numpy()
     del E_mx
 
+    # ---- the same mixed step with the V-cycle's smoothing coefficients read
+    # as FP32 (precond_bf16 = 0), with the timed context's launch shapes
+    fp32_coef = None
+    if args.fp32_coef_steps > 0:
+        import dataclasses
+        pc = dataclasses.replace(pm, precond_bf16=0)
+        ctxc = fld.fld_create(case.grid, pc, stream)
+        fld.fld_set_tuning(ctxc, fld.fld_get_tuning(ctx))
+        Ec = E0.clone()
+        fld.fld_step(ctxc, Ec, nHI, eta)
+        msc, _, infc = time_steps(fld, torch, ctxc, Ec, nHI, eta, args.fp32_coef_steps)
+        fp32_coef = {"value": cells * args.fp32_coef_steps / (msc * 1e-3), "unit": UNIT,
+                     "ms_per_step": msc / args.fp32_coef_steps, "iters": [i["iters"] for i in infc],
+                     "outer_iters": [i["outer_iters"] for i in infc], "rel_res": [i["rel_res"] for i in infc],
+                     "what": "the same mixed step with the V-cycle's smoothing coefficients read as FP32 "
+                             "(precond_bf16 = 0), the timed context's launch shapes"}
+        ctxc.close()
+        del Ec
+
     # ---- plain FP64 multigrid on the same input
     fp64 = None
     E_64_h = None
@@ -607,6 +628,7 @@ def main():
             "rel_res": [i["rel_res"] for i in infos],
             "fp64_mg": fp64,
             "mixed_over_fp64": (value / world) / fp64["value"] if fp64 else None,
+            "mixed_fp32_coefficients": fp32_coef,
             "roofline": roofline, "step_roofline_frac": step_frac, "step_roofline_model": step_model,
             "kernel_breakdown_one_step": breakdown,
             "oracle_err": oracle_err,
