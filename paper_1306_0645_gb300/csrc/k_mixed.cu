@@ -22,6 +22,12 @@
 // accuracy where neighbouring values nearly cancel: the residual's error is
 // of order 2^-47 (|b| + m |x| + sum_f w_f |x - x_nbr|), and the refinement
 // converges as an FP64 one would.
+//
+// On levels whose x extent is a multiple of 4 the right-hand side, the
+// refinement residual and the update run four cells per thread (walk4.cuh),
+// with the same operations per cell as the one-cell kernels; the right-hand
+// side also writes the bfloat16 copies of the V-cycle's smoothing
+// coefficients where the context keeps them.
 #include "limiter.cuh"
 #include "walk4.cuh"
 #include <cuda_bf16.h>
