@@ -7,7 +7,10 @@
 // adjacent lanes with warp shuffles, and reads the y-neighbour rows (which
 // the neighbouring threads of the block stream) through L1.  These are the
 // same operations as the scalar kernels of k_mg.cu / k_cg.cu, restricted to
-// levels whose x extent is a multiple of 4.
+// levels whose x extent is a multiple of 4.  The V-cycle's sweeps (zero-guess
+// smoothing, colour sweeps, zero-guess residual) read their coefficients from
+// FP32 or from bfloat16 storage (the template parameter T), the CG's
+// matrix-vector product always from the FP32 operator.
 #include "walk4.cuh"
 #include <cuda_bf16.h>
 
